@@ -1,0 +1,208 @@
+"""ctypes front-end of the plain FP64 CPU oracle (``rpa_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it.  The GPU library never imports, links
+or calls anything here, and nothing here imports the GPU library.
+
+Each function restates one step of the paper's method (arXiv 2505.06021):
+
+* :func:`chi0`      - fit-basis response chi0_PQ(q, i omega), Sec. 2.2
+* :func:`vhalf`     - V(q)^(1/2) by Hermitian Jacobi, Sec. 2.1 / Algorithm 1
+* :func:`sandwich`  - Pi = V^(1/2) chi0 V^(1/2), Sec. 2.1 / Algorithm 1
+* :func:`logdet`    - ln det(1 - Pi) (Cholesky) and Tr Pi, Algorithm 1
+* :func:`logabsdet_lu` - cross-check of ln|det| by pivoted LU
+* :func:`energy_sum`   - E_c = (1/2pi) sum_w zeta_w sum_q w_q eps_qw, Sec. 2.6
+* :func:`energy`    - the whole job, composed from the above
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Dict, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rpa_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, IEEE semantics, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-D_GNU_SOURCE", _SRC, "-o", _LIB + ".tmp",
+               "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        i, d = ctypes.c_int, ctypes.c_double
+        lib.oracle_chi0.argtypes = [i, i, i, i, i, ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.POINTER(_dp), d,
+                                    d, _dp, i]
+        lib.oracle_jacobi_eigh.argtypes = [i, i, _dp, _dp, _dp, i, d]
+        lib.oracle_vhalf.argtypes = [i, i, _dp, _dp]
+        lib.oracle_sandwich.argtypes = [i, i, _dp, _dp, _dp, i]
+        lib.oracle_logdet_cholesky.argtypes = [i, i, _dp, _dp, _dp]
+        lib.oracle_logabsdet_lu.argtypes = [i, i, _dp, _dp]
+        lib.oracle_energy_sum.argtypes = [i, i, _dp, _dp, _dp, _dp]
+        lib.oracle_max_threads.argtypes = []
+        for f in (lib.oracle_chi0, lib.oracle_jacobi_eigh, lib.oracle_vhalf, lib.oracle_sandwich,
+                  lib.oracle_logdet_cholesky, lib.oracle_logabsdet_lu, lib.oracle_energy_sum, lib.oracle_max_threads):
+            f.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a: np.ndarray, is_complex: bool) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128 if is_complex else np.float64)
+    return a
+
+
+def chi0(C_blocks: Sequence[np.ndarray], eps_occ: Sequence[np.ndarray], eps_virt: Sequence[np.ndarray], zeta_k: float,
+         omega: float, n_threads: Optional[int] = None) -> np.ndarray:
+    """chi0_PQ at one q and one frequency from the n_k blocks C_j = C(q, k_j)
+    ([n_aux, n_occ*n_virt]), eps_occ[j] at k_j and eps_virt[j] at k_j + q."""
+    is_c = bool(np.iscomplexobj(C_blocks[0]))
+    Cs = [_f64(c, is_c) for c in C_blocks]
+    eo = [np.ascontiguousarray(e, np.float64) for e in eps_occ]
+    ev = [np.ascontiguousarray(e, np.float64) for e in eps_virt]
+    n_aux, n_ov = Cs[0].shape
+    n_occ, n_virt = eo[0].shape[0], ev[0].shape[0]
+    if n_occ * n_virt != n_ov:
+        raise ValueError("C width must be n_occ * n_virt")
+    out = np.zeros((n_aux, n_aux), np.complex128 if is_c else np.float64)
+    cp = (_dp * len(Cs))(*[_ptr(c.view(np.float64)) for c in Cs])
+    op = (_dp * len(eo))(*[_ptr(e) for e in eo])
+    vp = (_dp * len(ev))(*[_ptr(e) for e in ev])
+    rc = _load().oracle_chi0(int(is_c), n_aux, n_occ, n_virt, len(Cs), cp, op, vp, float(zeta_k), float(omega),
+                             _ptr(out.view(np.float64)), int(n_threads or max_threads()))
+    if rc != 0:
+        raise OracleError("oracle_chi0 rc=%d" % rc)
+    return out
+
+
+def jacobi_eigh(A: np.ndarray, max_sweeps: int = 100, tol: float = 1e-14) -> Tuple[np.ndarray, np.ndarray, int]:
+    is_c = bool(np.iscomplexobj(A))
+    A = _f64(A, is_c)
+    n = A.shape[0]
+    lam = np.zeros(n)
+    U = np.zeros_like(A)
+    rc = _load().oracle_jacobi_eigh(int(is_c), n, _ptr(A.view(np.float64)), _ptr(lam), _ptr(U.view(np.float64)),
+                                    max_sweeps, tol)
+    if rc < 0:
+        raise OracleError("jacobi rc=%d" % rc)
+    return lam, U, rc
+
+
+def vhalf(V: np.ndarray) -> np.ndarray:
+    is_c = bool(np.iscomplexobj(V))
+    V = _f64(V, is_c)
+    out = np.zeros_like(V)
+    rc = _load().oracle_vhalf(int(is_c), V.shape[0], _ptr(V.view(np.float64)), _ptr(out.view(np.float64)))
+    if rc != 0:
+        raise OracleError("oracle_vhalf rc=%d" % rc)
+    return out
+
+
+def sandwich(Vh: np.ndarray, chi: np.ndarray, n_threads: Optional[int] = None) -> np.ndarray:
+    is_c = bool(np.iscomplexobj(Vh) or np.iscomplexobj(chi))
+    Vh, chi = _f64(Vh, is_c), _f64(chi, is_c)
+    out = np.zeros_like(chi)
+    rc = _load().oracle_sandwich(int(is_c), chi.shape[0], _ptr(Vh.view(np.float64)), _ptr(chi.view(np.float64)),
+                                 _ptr(out.view(np.float64)), int(n_threads or max_threads()))
+    if rc != 0:
+        raise OracleError("oracle_sandwich rc=%d" % rc)
+    return out
+
+
+def logdet(Pi: np.ndarray) -> Tuple[float, float]:
+    """(ln det(1 - Pi), Tr Pi) by unblocked Cholesky of 1 - Pi."""
+    is_c = bool(np.iscomplexobj(Pi))
+    Pi = _f64(Pi, is_c)
+    ld, tr = ctypes.c_double(), ctypes.c_double()
+    rc = _load().oracle_logdet_cholesky(int(is_c), Pi.shape[0], _ptr(Pi.view(np.float64)), ctypes.byref(ld),
+                                        ctypes.byref(tr))
+    if rc != 0:
+        raise OracleError("oracle_logdet_cholesky rc=%d (not positive definite)" % rc)
+    return float(ld.value), float(tr.value)
+
+
+def logabsdet_lu(M: np.ndarray) -> float:
+    is_c = bool(np.iscomplexobj(M))
+    M = _f64(M, is_c)
+    out = ctypes.c_double()
+    rc = _load().oracle_logabsdet_lu(int(is_c), M.shape[0], _ptr(M.view(np.float64)), ctypes.byref(out))
+    if rc != 0:
+        raise OracleError("oracle_logabsdet_lu rc=%d" % rc)
+    return float(out.value)
+
+
+def energy_sum(w_q: np.ndarray, zeta_w: np.ndarray, eps_qw: np.ndarray) -> float:
+    w_q = np.ascontiguousarray(w_q, np.float64)
+    zeta_w = np.ascontiguousarray(zeta_w, np.float64)
+    eps_qw = np.ascontiguousarray(eps_qw, np.float64)
+    out = ctypes.c_double()
+    rc = _load().oracle_energy_sum(eps_qw.shape[0], eps_qw.shape[1], _ptr(w_q), _ptr(zeta_w), _ptr(eps_qw),
+                                   ctypes.byref(out))
+    if rc != 0:
+        raise OracleError("oracle_energy_sum rc=%d" % rc)
+    return float(out.value)
+
+
+def term(problem, q: int, w: int, Vh: Optional[np.ndarray] = None, n_threads: Optional[int] = None,
+         C_blocks=None) -> Dict[str, float]:
+    """One integrand term eps_{q,w} = ln det(1 - Pi) + Tr Pi of a synthetic
+    problem (``paper_2505_06021_gb300.synth.Problem``)."""
+    if C_blocks is None:
+        C_blocks = [problem.C(q, j) for j in range(problem.n_k)]
+    eo = [problem.eps_pair(q, j)[0] for j in range(problem.n_k)]
+    ev = [problem.eps_pair(q, j)[1] for j in range(problem.n_k)]
+    if Vh is None:
+        Vh = vhalf(problem.V(q))
+    chi = chi0(C_blocks, eo, ev, problem.grid.zeta_k, float(problem.omega[w]), n_threads)
+    Pi = sandwich(Vh, chi, n_threads)
+    ld, tr = logdet(Pi)
+    return {"lndet": ld, "trPi": tr, "eps": ld + tr}
+
+
+def energy(problem, n_threads: Optional[int] = None, qs: Optional[Sequence[int]] = None,
+           ws: Optional[Sequence[int]] = None) -> Dict[str, object]:
+    """Whole job (or a (q, w) subset): per-term table and E_c (E_c only when
+    the full table is computed)."""
+    qs = list(range(problem.n_q)) if qs is None else list(qs)
+    ws = list(range(problem.n_w)) if ws is None else list(ws)
+    lndet = np.full((problem.n_q, problem.n_w), np.nan)
+    trpi = np.full((problem.n_q, problem.n_w), np.nan)
+    for q in qs:
+        Vh = vhalf(problem.V(q))
+        C_blocks = [problem.C(q, j) for j in range(problem.n_k)]
+        for w in ws:
+            t = term(problem, q, w, Vh=Vh, n_threads=n_threads, C_blocks=C_blocks)
+            lndet[q, w], trpi[q, w] = t["lndet"], t["trPi"]
+    eps = lndet + trpi
+    Ec = None
+    if len(qs) == problem.n_q and len(ws) == problem.n_w:
+        Ec = energy_sum(problem.grid.w_q, problem.zeta_w, eps)
+    return {"lndet": lndet, "trPi": trpi, "eps": eps, "Ec": Ec}
