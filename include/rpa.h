@@ -1,0 +1,177 @@
+/*
+ * librpa — GB300 (sm_103a) library for the hot path of the periodic RPA
+ * correlation energy with density fitting and dual k-grids
+ * (Spadetto, Philipsen, Foerster, Visscher, arXiv 2505.06021).
+ *
+ * For every q of the job's q-grid and every imaginary frequency omega the
+ * library
+ *   (A3) builds chi0_PQ(q, i omega) = zeta_k sum_k sum_{i in occ(k),
+ *        a in virt(k+q)} conj(C_{P,ia}) C_{Q,ia} * (-4 Delta_ia /
+ *        (Delta_ia^2 + omega^2)),  Delta_ia = eps_a(k+q) - eps_i(k)
+ *        (Sec. 2.2, the fit-basis polarizability P^(0)_{gamma gamma'}; the
+ *        resonant and complex-conjugate terms combined, occupations 2/0);
+ *   (A4/A5) forms the symmetrised response Pi = V^(1/2) chi0 V^(1/2)
+ *        (Sec. 2.1 working equation; Algorithm 1, "Z = V^0.5 P V^0.5");
+ *   (A6) evaluates eps_{q,omega} = ln det(1 - Pi) + Tr Pi by an FP64
+ *        Cholesky factorisation of 1 - Pi (Algorithm 1, the RPA integrand;
+ *        sign as in eq. 1 of Sec. 2.1);
+ *   (A7) reduces E_c = (1/2pi) sum_omega zeta_omega sum_q w_q eps_{q,omega}
+ *        (Sec. 2.6, the (q, omega) double sum).
+ *
+ * Conventions
+ * -----------
+ * - Complex data is interleaved complex128 ((re, im) doubles); real data
+ *   (Gamma-only jobs, is_complex = 0) is float64.  All matrices are
+ *   row-major.  C(q, k_j) is n_aux x (n_occ*n_virt) with the pair index
+ *   t = i*n_virt + a contiguous.  V(q) is n_aux x n_aux Hermitian positive
+ *   definite (both triangles are read by the sandwich; only the lower one by
+ *   the factorisation).
+ * - Ownership: input buffers are borrowed; the caller keeps them alive and
+ *   unmodified until the synchronous call returns, or, for rpa_submit, until
+ *   rpa_poll / rpa_wait has reported completion.  Outputs go to caller
+ *   buffers.  Device workspace belongs to the context.
+ * - Errors: no exception crosses this boundary.  Every entry point returns an
+ *   rpa_status; rpa_last_error() gives the message of the last failure on a
+ *   context.  A non-positive pivot found on the device is reported as
+ *   RPA_E_NOTPD (with q and omega in the message); kernels never trap.
+ * - Streams: a `void *stream` argument is a cudaStream_t (0 = legacy default
+ *   stream), e.g. torch.cuda.current_stream().cuda_stream.
+ * - Determinism: in RPA_FP64 mode the same job gives bit-identical results
+ *   whatever else runs on the device; all reductions have a fixed order.
+ */
+#ifndef RPA_H
+#define RPA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rpa_ctx rpa_ctx;
+typedef int rpa_status;
+
+#define RPA_OK 0
+#define RPA_E_INVAL 1    /* malformed job or argument */
+#define RPA_E_NOMEM 2    /* device memory or admission cap exhausted */
+#define RPA_E_CUDA 3     /* a CUDA runtime call failed */
+#define RPA_E_NOTPD 4    /* V(q) or 1 - Pi(q, omega) not positive definite */
+#define RPA_E_TIMEOUT 5  /* a bounded wait ran out */
+#define RPA_E_BUSY 6     /* request queue full */
+#define RPA_E_NOTREADY 7 /* submitted job not finished yet */
+
+/* Arithmetic of the chi0 contraction.  The sandwich, the factorisation and
+ * all sums are FP64 in every mode. */
+#define RPA_PREC_FP64 0  /* chi0 in FP64 (DFMA) */
+#define RPA_PREC_MIXED 1 /* chi0 on tcgen05 tensor cores from BF16 slices of
+                            the FP64 operands, FP32 accumulation in exact
+                            chunks, FP64 result (split-precision, Ozaki-style) */
+
+/* Where a job's C, V and band-energy buffers live. */
+#define RPA_MEM_DEVICE 0
+#define RPA_MEM_HOST 1 /* host memory (pinned for speed): the library stages it
+                          to device workspace per q, copies inside the call */
+
+typedef struct {
+  int device;           /* CUDA device ordinal */
+  size_t hbm_cap_bytes; /* cap on workspace + admitted serving jobs; 0 = 120 GB */
+  int n_slices;         /* BF16 slices per operand in RPA_PREC_MIXED (2..6; 0 = 4) */
+  double timeout_s;     /* limit of every bounded wait (0 = 60 s) */
+  int max_inflight;     /* serving: jobs admitted at once (0 = 64) */
+} rpa_config;
+
+typedef struct {
+  int is_complex;                 /* 1: complex128 data; 0: real float64 (Gamma only) */
+  int n_aux, n_occ, n_virt;       /* N, occupied and virtual bands per k */
+  int n_q;                        /* q-points of the (dual) q-grid */
+  int n_k;                        /* k-pairs per q (|K_reg|) */
+  int n_w;                        /* imaginary frequencies */
+  int n_kpts;                     /* rows of eps_occ / eps_virt (|K_G|) */
+  const int *pair_k;              /* host [n_q*n_k]: row of eps_occ for k_j */
+  const int *pair_kq;             /* host [n_q*n_k]: row of eps_virt for k_j+q */
+  const double *w_q;              /* host [n_q]: q weights */
+  double zeta_k;                  /* k weight (1/|K_reg|) */
+  const double *omega;            /* host [n_w]: frequencies */
+  const double *zeta_w;           /* host [n_w]: frequency weights */
+  const double *eps_occ;          /* [n_kpts*n_occ], device or host (mem) */
+  const double *eps_virt;         /* [n_kpts*n_virt], device or host (mem) */
+  const void *const *C;           /* host array [n_q*n_k] of pointers to C(q,k_j) */
+  const void *const *V;           /* host array [n_q] of pointers to V(q) */
+  int prec;                       /* RPA_PREC_* */
+  int mem;                        /* RPA_MEM_* */
+} rpa_job;
+
+/* Create a context on cfg->device (NULL cfg = defaults).  Allocates nothing
+ * large; workspace grows on first use.  RPA_E_CUDA if the device is absent. */
+rpa_status rpa_create(const rpa_config *cfg, rpa_ctx **out);
+
+/* Wait for outstanding work, free all workspace and the context. */
+rpa_status rpa_destroy(rpa_ctx *ctx);
+
+/* Message of the last failure on ctx ("" if none).  Valid until the next call
+ * on ctx.  With ctx == NULL: the last failure of rpa_create on this thread. */
+const char *rpa_last_error(const rpa_ctx *ctx);
+
+/* Host-only check of a job description (no device access; usable without a
+ * GPU).  Writes a message into msg (if msg_len > 0) on failure. */
+rpa_status rpa_job_validate(const rpa_job *job, char *msg, size_t msg_len);
+
+/* Host-only: device bytes the job occupies while it runs (its inputs when
+ * mem == RPA_MEM_DEVICE plus the workspace of one q-batch) - the admission
+ * footprint used by rpa_submit. */
+rpa_status rpa_job_footprint(const rpa_job *job, size_t *bytes);
+
+/* Step A3: chi0(q, i omega_w) for every w, written to the device buffer
+ * chi_out [n_w][n_aux][n_aux] (full Hermitian matrices; complex128 or
+ * float64).  Asynchronous on `stream`; job->mem must be RPA_MEM_DEVICE. */
+rpa_status rpa_chi0(rpa_ctx *ctx, const rpa_job *job, int q, void *chi_out, void *stream);
+
+/* Steps A4-A6 for one q: from chi (device [n_w][n_aux][n_aux], as written by
+ * rpa_chi0) computes out[2*w] = ln det(1 - Pi) and out[2*w+1] = Tr Pi,
+ * Pi = V(q)^(1/2) chi V(q)^(1/2), into the HOST array out [n_w*2].
+ * Synchronises `stream`.  RPA_E_NOTPD if V(q) or 1 - Pi is not positive
+ * definite.  job->mem must be RPA_MEM_DEVICE. */
+rpa_status rpa_logdet(rpa_ctx *ctx, const rpa_job *job, int q, const void *chi, double *out, void *stream);
+
+/* The whole hot path A3-A7 for one job, synchronously on the context's own
+ * stream: *Ec receives E_c; eps_qw (host [n_q*n_w] or NULL) the integrand
+ * table eps_{q,w} = ln det + Tr; parts (host [n_q*n_w*2] or NULL) the pairs
+ * (ln det(1 - Pi), Tr Pi).  Inputs on the device or, with mem ==
+ * RPA_MEM_HOST, on the host (staged per q, copies overlapped with compute). */
+rpa_status rpa_energy(rpa_ctx *ctx, const rpa_job *job, double *Ec, double *eps_qw, double *parts);
+
+/* Many independent jobs (uneven sizes) in one call: all (job, q) work is
+ * packed into persistent launches recorded once into a CUDA graph per batch
+ * shape; Ec_out (host [n_jobs]) receives each job's E_c.  Jobs must have
+ * mem == RPA_MEM_DEVICE. */
+rpa_status rpa_energy_batch(rpa_ctx *ctx, const rpa_job *jobs, int n_jobs, double *Ec_out);
+
+/* Serving: enqueue a job (deep-copies the host descriptors; device buffers
+ * stay borrowed).  The job is admitted once its footprint fits under the
+ * context's cap next to the jobs already running; admitted jobs share the
+ * device (continuous batching).  RPA_E_BUSY if the queue is full,
+ * RPA_E_NOMEM if the job alone exceeds the cap. */
+rpa_status rpa_submit(rpa_ctx *ctx, const rpa_job *job, uint64_t *ticket);
+
+/* RPA_E_NOTREADY until the ticket's job is done; then its status, with *Ec
+ * and (optionally, host [n_q*n_w]) eps_qw filled.  A finished ticket can be
+ * polled once; afterwards it is unknown (RPA_E_INVAL). */
+rpa_status rpa_poll(rpa_ctx *ctx, uint64_t ticket, double *Ec, double *eps_qw);
+
+/* rpa_poll with a bounded wait of at most timeout_s seconds
+ * (RPA_E_TIMEOUT when it runs out). */
+rpa_status rpa_wait(rpa_ctx *ctx, uint64_t ticket, double timeout_s, double *Ec, double *eps_qw);
+
+/* Serving statistics since creation: jobs done, mean/p50/p99 latency from
+ * submit to completion and p50/p99 queue wait, in seconds. */
+rpa_status rpa_serving_stats(rpa_ctx *ctx, uint64_t *jobs_done, double *lat_mean, double *lat_p50,
+                             double *lat_p99, double *wait_p50, double *wait_p99);
+
+/* Number of kernels this context has launched so far (all entry points). */
+uint64_t rpa_kernel_launches(const rpa_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPA_H */

@@ -1,0 +1,293 @@
+"""Python binding of librpa (GB300 / sm_103a): argument marshalling only.
+
+Every step of the RPA hot path runs in the library's CUDA kernels; this
+module builds the ``rpa_job`` descriptors of ``include/rpa.h`` from device
+(or pinned host) tensors and calls the C ABI through ctypes.  PyTorch is used
+for device memory and streams.  If the compiled library is missing, importing
+the binding's entry points raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "librpa.so")
+
+RPA_OK, RPA_E_INVAL, RPA_E_NOMEM, RPA_E_CUDA, RPA_E_NOTPD, RPA_E_TIMEOUT, RPA_E_BUSY, RPA_E_NOTREADY = range(8)
+PREC_FP64, PREC_MIXED = 0, 1
+MEM_DEVICE, MEM_HOST = 0, 1
+
+STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "NOMEM", 3: "CUDA", 4: "NOTPD", 5: "TIMEOUT", 6: "BUSY", 7: "NOTREADY"}
+
+# Entry points declared in include/rpa.h
+EXPORTS = ("rpa_create", "rpa_destroy", "rpa_last_error", "rpa_job_validate", "rpa_job_footprint", "rpa_chi0",
+           "rpa_logdet", "rpa_energy", "rpa_energy_batch", "rpa_submit", "rpa_poll", "rpa_wait",
+           "rpa_serving_stats", "rpa_kernel_launches")
+
+
+class RpaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(status, "?"), status, msg))
+        self.status = status
+
+
+class rpa_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_cap_bytes", ctypes.c_size_t), ("n_slices", ctypes.c_int),
+                ("timeout_s", ctypes.c_double), ("max_inflight", ctypes.c_int)]
+
+
+class rpa_job(ctypes.Structure):
+    _fields_ = [("is_complex", ctypes.c_int), ("n_aux", ctypes.c_int), ("n_occ", ctypes.c_int),
+                ("n_virt", ctypes.c_int), ("n_q", ctypes.c_int), ("n_k", ctypes.c_int), ("n_w", ctypes.c_int),
+                ("n_kpts", ctypes.c_int), ("pair_k", ctypes.POINTER(ctypes.c_int)),
+                ("pair_kq", ctypes.POINTER(ctypes.c_int)), ("w_q", ctypes.POINTER(ctypes.c_double)),
+                ("zeta_k", ctypes.c_double), ("omega", ctypes.POINTER(ctypes.c_double)),
+                ("zeta_w", ctypes.POINTER(ctypes.c_double)), ("eps_occ", ctypes.c_void_p),
+                ("eps_virt", ctypes.c_void_p), ("C", ctypes.POINTER(ctypes.c_void_p)),
+                ("V", ctypes.POINTER(ctypes.c_void_p)), ("prec", ctypes.c_int), ("mem", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load librpa.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("librpa.so not built at %s: run `python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    lib = ctypes.CDLL(path)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    J = ctypes.POINTER(rpa_job)
+    u64 = ctypes.c_uint64
+    sig = {
+        "rpa_create": (I, [ctypes.POINTER(rpa_config), ctypes.POINTER(P)]),
+        "rpa_destroy": (I, [P]),
+        "rpa_last_error": (ctypes.c_char_p, [P]),
+        "rpa_job_validate": (I, [J, ctypes.c_char_p, S]),
+        "rpa_job_footprint": (I, [J, ctypes.POINTER(S)]),
+        "rpa_chi0": (I, [P, J, I, P, P]),
+        "rpa_logdet": (I, [P, J, I, P, ctypes.POINTER(D), P]),
+        "rpa_energy": (I, [P, J, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "rpa_energy_batch": (I, [P, J, I, ctypes.POINTER(D)]),
+        "rpa_submit": (I, [P, J, ctypes.POINTER(u64)]),
+        "rpa_poll": (I, [P, u64, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "rpa_wait": (I, [P, u64, D, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "rpa_serving_stats": (I, [P, ctypes.POINTER(u64)] + [ctypes.POINTER(D)] * 5),
+        "rpa_kernel_launches": (u64, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Job:
+    """An ``rpa_job`` plus the host arrays and tensors it points to (kept
+    alive with the descriptor).
+
+    ``C`` is a list (length n_q*n_k, q-major) of tensors [n_aux, n_occ*n_virt]
+    and ``V`` a list of n_q tensors [n_aux, n_aux], complex128 or float64, all
+    on the device (mem=MEM_DEVICE) or all in host memory (mem=MEM_HOST,
+    pinned for speed).  ``eps_occ`` [n_kpts, n_occ], ``eps_virt`` [n_kpts,
+    n_virt] float64 tensors in the same memory."""
+
+    def __init__(self, *, is_complex: bool, n_aux: int, n_occ: int, n_virt: int, pair_k, pair_kq, w_q, zeta_k: float,
+                 omega, zeta_w, eps_occ, eps_virt, C: Sequence, V: Sequence, prec: int = PREC_FP64,
+                 mem: int = MEM_DEVICE):
+        self.pair_k = np.array(pair_k, np.int32).reshape(-1)
+        self.pair_kq = np.array(pair_kq, np.int32).reshape(-1)
+        self.w_q = np.array(w_q, np.float64).reshape(-1)
+        self.omega = np.array(omega, np.float64).reshape(-1)
+        self.zeta_w = np.array(zeta_w, np.float64).reshape(-1)
+        n_q = int(self.w_q.shape[0])
+        n_k = int(self.pair_k.shape[0] // n_q)
+        self.C_t, self.V_t = list(C), list(V)
+        self.eps_occ_t, self.eps_virt_t = eps_occ, eps_virt
+        self._Cp = (ctypes.c_void_p * len(self.C_t))(*[int(c.data_ptr()) for c in self.C_t])
+        self._Vp = (ctypes.c_void_p * len(self.V_t))(*[int(v.data_ptr()) for v in self.V_t])
+        s = rpa_job()
+        s.is_complex, s.n_aux, s.n_occ, s.n_virt = int(is_complex), n_aux, n_occ, n_virt
+        s.n_q, s.n_k, s.n_w, s.n_kpts = n_q, n_k, int(self.omega.shape[0]), int(eps_occ.shape[0])
+        s.pair_k = self.pair_k.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        s.pair_kq = self.pair_kq.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        s.w_q, s.zeta_k = _dptr(self.w_q), float(zeta_k)
+        s.omega, s.zeta_w = _dptr(self.omega), _dptr(self.zeta_w)
+        s.eps_occ, s.eps_virt = int(eps_occ.data_ptr()), int(eps_virt.data_ptr())
+        s.C = ctypes.cast(self._Cp, ctypes.POINTER(ctypes.c_void_p))
+        s.V = ctypes.cast(self._Vp, ctypes.POINTER(ctypes.c_void_p))
+        s.prec, s.mem = int(prec), int(mem)
+        self.s = s
+
+    @property
+    def n_q(self):
+        return self.s.n_q
+
+    @property
+    def n_w(self):
+        return self.s.n_w
+
+    def with_prec(self, prec: int) -> "Job":
+        j = Job.__new__(Job)
+        j.__dict__.update(self.__dict__)
+        s = rpa_job.from_buffer_copy(self.s)
+        s.prec = int(prec)
+        j.s = s
+        return j
+
+    def validate(self) -> Tuple[int, str]:
+        buf = ctypes.create_string_buffer(512)
+        st = load_library().rpa_job_validate(ctypes.byref(self.s), buf, 512)
+        return st, buf.value.decode()
+
+    def footprint(self) -> int:
+        out = ctypes.c_size_t()
+        st = load_library().rpa_job_footprint(ctypes.byref(self.s), ctypes.byref(out))
+        if st:
+            raise RpaError(st, self.validate()[1])
+        return int(out.value)
+
+
+def job_from_problem(problem, tensors: Dict[str, object], prec: int = PREC_FP64, mem: int = MEM_DEVICE) -> Job:
+    g = problem.grid
+    return Job(is_complex=problem.is_complex, n_aux=problem.n_aux, n_occ=problem.n_occ, n_virt=problem.n_virt,
+               pair_k=g.pair_k, pair_kq=g.pair_kq, w_q=g.w_q, zeta_k=g.zeta_k, omega=problem.omega,
+               zeta_w=problem.zeta_w, eps_occ=tensors["eps_occ"], eps_virt=tensors["eps_virt"], C=tensors["C"],
+               V=tensors["V"], prec=prec, mem=mem)
+
+
+def upload_problem(problem, device="cuda", qs: Optional[Sequence[int]] = None, pin: bool = False):
+    """Materialise a synthetic problem's inputs as torch tensors on `device`
+    (or pinned host memory with device='cpu', pin=True)."""
+    import torch
+
+    dt = torch.complex128 if problem.is_complex else torch.float64
+    qs = list(range(problem.n_q)) if qs is None else list(qs)
+
+    def put(a):
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        if device == "cpu":
+            return t.pin_memory() if pin else t
+        return t.to(device)
+
+    C = [put(problem.C(q, j)) for q in qs for j in range(problem.n_k)]
+    V = [put(problem.V(q)) for q in qs]
+    eo = put(problem.eps_occ.astype(np.float64))
+    ev = put(problem.eps_virt.astype(np.float64))
+    assert all(c.dtype == dt for c in C)
+    return {"C": C, "V": V, "eps_occ": eo, "eps_virt": ev}
+
+
+class Context:
+    """An ``rpa_ctx`` on one device."""
+
+    def __init__(self, device: int = 0, hbm_cap_bytes: int = 0, n_slices: int = 0, timeout_s: float = 0.0,
+                 max_inflight: int = 0):
+        self.lib = load_library()
+        cfg = rpa_config(device, hbm_cap_bytes, n_slices, timeout_s, max_inflight)
+        h = ctypes.c_void_p()
+        st = self.lib.rpa_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st:
+            raise RpaError(st, self.lib.rpa_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rpa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st):
+        if st:
+            raise RpaError(st, self.lib.rpa_last_error(self.h).decode())
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.rpa_kernel_launches(self.h))
+
+    def chi0(self, job: Job, q: int, out=None, stream=None):
+        import torch
+
+        n = job.s.n_aux
+        if out is None:
+            dt = torch.complex128 if job.s.is_complex else torch.float64
+            out = torch.empty((job.s.n_w, n, n), dtype=dt, device="cuda")
+        st_ptr = (stream or torch.cuda.current_stream()).cuda_stream
+        self._check(self.lib.rpa_chi0(self.h, ctypes.byref(job.s), int(q), ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(st_ptr)))
+        return out
+
+    def logdet(self, job: Job, q: int, chi, stream=None) -> np.ndarray:
+        import torch
+
+        out = np.zeros(2 * job.s.n_w)
+        st_ptr = (stream or torch.cuda.current_stream()).cuda_stream
+        self._check(self.lib.rpa_logdet(self.h, ctypes.byref(job.s), int(q), ctypes.c_void_p(chi.data_ptr()),
+                                        _dptr(out), ctypes.c_void_p(st_ptr)))
+        return out.reshape(job.s.n_w, 2)
+
+    def energy(self, job: Job) -> Dict[str, object]:
+        nqw = job.s.n_q * job.s.n_w
+        Ec = ctypes.c_double()
+        eps = np.zeros(nqw)
+        parts = np.zeros(2 * nqw)
+        self._check(self.lib.rpa_energy(self.h, ctypes.byref(job.s), ctypes.byref(Ec), _dptr(eps), _dptr(parts)))
+        parts = parts.reshape(job.s.n_q, job.s.n_w, 2)
+        return {"Ec": Ec.value, "eps": eps.reshape(job.s.n_q, job.s.n_w), "lndet": parts[..., 0],
+                "trPi": parts[..., 1]}
+
+    def energy_batch(self, jobs: Sequence[Job]) -> np.ndarray:
+        arr = (rpa_job * len(jobs))(*[j.s for j in jobs])
+        out = np.zeros(len(jobs))
+        self._check(self.lib.rpa_energy_batch(self.h, arr, len(jobs), _dptr(out)))
+        return out
+
+    def submit(self, job: Job) -> int:
+        t = ctypes.c_uint64()
+        self._check(self.lib.rpa_submit(self.h, ctypes.byref(job.s), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int, job: Optional[Job] = None):
+        Ec = ctypes.c_double()
+        eps = np.zeros(job.s.n_q * job.s.n_w) if job is not None else None
+        st = self.lib.rpa_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(Ec),
+                               _dptr(eps) if eps is not None else None)
+        if st == RPA_E_NOTREADY:
+            return None
+        self._check(st)
+        return Ec.value, eps
+
+    def wait(self, ticket: int, timeout_s: float = 60.0, job: Optional[Job] = None):
+        Ec = ctypes.c_double()
+        eps = np.zeros(job.s.n_q * job.s.n_w) if job is not None else None
+        self._check(self.lib.rpa_wait(self.h, ctypes.c_uint64(ticket), float(timeout_s), ctypes.byref(Ec),
+                                      _dptr(eps) if eps is not None else None))
+        return Ec.value, eps
+
+    def serving_stats(self) -> Dict[str, float]:
+        n = ctypes.c_uint64()
+        v = [ctypes.c_double() for _ in range(5)]
+        self._check(self.lib.rpa_serving_stats(self.h, ctypes.byref(n), *[ctypes.byref(x) for x in v]))
+        return {"jobs_done": int(n.value), "lat_mean_s": v[0].value, "lat_p50_s": v[1].value,
+                "lat_p99_s": v[2].value, "wait_p50_s": v[3].value, "wait_p99_s": v[4].value}

@@ -1,0 +1,640 @@
+// C-ABI of librpa: context, job validation, workspace, and the orchestration
+// of the RPA hot path (chi0 -> sandwich -> Cholesky log-det -> quadrature) on
+// one GB300.  Declarations and argument contracts: include/rpa.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "rpa_internal.h"
+#include "rpa_runtime.h"
+
+using namespace rpa;
+
+static thread_local std::string g_create_error;
+
+namespace rpa {
+
+void ctx_set_error(rpa_ctx* ctx, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  std::lock_guard<std::mutex> g(ctx->err_mu);
+  ctx->last_error = buf;
+}
+
+#define CK(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) {                                                                          \
+      ctx_set_error(ctx, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return RPA_E_CUDA;                                                                              \
+    }                                                                                                 \
+  } while (0)
+
+// ------------------------------------------------------------------ Exec --
+
+bool Exec::init() {
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return false;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return false;
+  for (int i = 0; i < 2; ++i) {
+    if (cudaEventCreateWithFlags(&ready[i], cudaEventDisableTiming) != cudaSuccess) return false;
+    if (cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming) != cudaSuccess) return false;
+  }
+  if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) return false;
+  return hres.reserve(4096);
+}
+
+void Exec::destroy() {
+  if (s) cudaStreamSynchronize(s);
+  if (cs) cudaStreamSynchronize(cs);
+  if (ws) cudaFree(ws);
+  ws = nullptr;
+  ws_bytes = 0;
+  if (s) cudaStreamDestroy(s);
+  if (cs) cudaStreamDestroy(cs);
+  for (int i = 0; i < 2; ++i) {
+    if (ready[i]) cudaEventDestroy(ready[i]);
+    if (freed[i]) cudaEventDestroy(freed[i]);
+  }
+  if (done) cudaEventDestroy(done);
+  s = cs = nullptr;
+  done = nullptr;
+  hstage.release();
+  hres.release();
+}
+
+bool Exec::ensure_ws(size_t bytes) {
+  if (ws_bytes >= bytes) return true;
+  if (ws) {
+    cudaStreamSynchronize(s);
+    cudaStreamSynchronize(cs);
+    cudaFree(ws);
+    ws = nullptr;
+    ws_bytes = 0;
+  }
+  const size_t want = std::max(bytes, (size_t)64 << 20);
+  if (cudaMalloc(&ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    ws = nullptr;
+    return false;
+  }
+  ws_bytes = want;
+  return true;
+}
+
+rpa_status wait_event(rpa_ctx* ctx, cudaEvent_t ev, double timeout_s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int spins = 0;
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return RPA_OK;
+    if (e != cudaErrorNotReady) {
+      ctx_set_error(ctx, "device error: %s", cudaGetErrorString(e));
+      return RPA_E_CUDA;
+    }
+    const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (dt > timeout_s) {
+      ctx_set_error(ctx, "wait ran out after %.1f s", dt);
+      return RPA_E_TIMEOUT;
+    }
+    if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(spins > 1000 ? 200 : 20));
+  }
+}
+
+// ------------------------------------------------------------ validation --
+
+static int set_msg(char* msg, size_t len, const char* fmt, ...) {
+  if (msg && len > 0) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, len, fmt, ap);
+    va_end(ap);
+  }
+  return RPA_E_INVAL;
+}
+
+rpa_status validate_job(const rpa_job* j, char* msg, size_t len) {
+  if (!j) return set_msg(msg, len, "job is NULL");
+  if (j->is_complex != 0 && j->is_complex != 1) return set_msg(msg, len, "is_complex must be 0 or 1");
+  if (j->n_aux <= 0 || j->n_occ <= 0 || j->n_virt <= 0)
+    return set_msg(msg, len, "n_aux, n_occ, n_virt must be positive (got %d, %d, %d)", j->n_aux, j->n_occ,
+                   j->n_virt);
+  if (j->n_q <= 0 || j->n_k <= 0 || j->n_w <= 0 || j->n_kpts <= 0)
+    return set_msg(msg, len, "n_q, n_k, n_w, n_kpts must be positive");
+  if ((long long)j->n_occ * j->n_virt > (1LL << 28)) return set_msg(msg, len, "n_occ*n_virt too large");
+  if (j->n_aux > 32768) return set_msg(msg, len, "n_aux > 32768 not supported");
+  if ((long long)j->n_q * j->n_k > (1LL << 24)) return set_msg(msg, len, "n_q*n_k too large");
+  if (!j->is_complex && (j->n_q != 1 || j->n_k != 1))
+    return set_msg(msg, len, "real (is_complex=0) jobs are Gamma-only: n_q = n_k = 1");
+  if (!j->pair_k || !j->pair_kq || !j->w_q || !j->omega || !j->zeta_w || !j->eps_occ || !j->eps_virt || !j->C ||
+      !j->V)
+    return set_msg(msg, len, "a required pointer is NULL");
+  if (j->prec != RPA_PREC_FP64 && j->prec != RPA_PREC_MIXED) return set_msg(msg, len, "unknown prec %d", j->prec);
+  if (j->mem != RPA_MEM_DEVICE && j->mem != RPA_MEM_HOST) return set_msg(msg, len, "unknown mem %d", j->mem);
+  if (!(j->zeta_k > 0.0) || !isfinite(j->zeta_k)) return set_msg(msg, len, "zeta_k must be positive");
+  for (long i = 0; i < (long)j->n_q * j->n_k; ++i) {
+    if (j->pair_k[i] < 0 || j->pair_k[i] >= j->n_kpts || j->pair_kq[i] < 0 || j->pair_kq[i] >= j->n_kpts)
+      return set_msg(msg, len, "pair index %ld out of range [0, %d)", i, j->n_kpts);
+    if (!j->C[i]) return set_msg(msg, len, "C[%ld] is NULL", i);
+  }
+  for (int q = 0; q < j->n_q; ++q) {
+    if (!j->V[q]) return set_msg(msg, len, "V[%d] is NULL", q);
+    if (!isfinite(j->w_q[q])) return set_msg(msg, len, "w_q[%d] not finite", q);
+  }
+  for (int w = 0; w < j->n_w; ++w)
+    if (!isfinite(j->omega[w]) || !isfinite(j->zeta_w[w]) || j->omega[w] < 0.0)
+      return set_msg(msg, len, "omega/zeta_w[%d] invalid", w);
+  return RPA_OK;
+}
+
+// -------------------------------------------------------------- layout ----
+// Workspace of one lane for a job processed in q-batches of qb q-points.
+
+struct Layout {
+  size_t meta, dtab, chi, T, L, stageC, stageV, eps, mixed, total;
+  int qb;
+};
+
+static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static Layout plan_layout(const rpa_job* j, int qb, int n_slices) {
+  Layout L{};
+  const size_t es = j->is_complex ? 16 : 8;
+  const size_t NN = (size_t)j->n_aux * j->n_aux;
+  const size_t nov = (size_t)j->n_occ * j->n_virt;
+  const size_t npk = (size_t)j->n_q * j->n_k;
+  const size_t nqw = (size_t)j->n_q * j->n_w;
+  L.qb = qb;
+  L.meta = al(sizeof(void*) * npk + sizeof(int) * 2 * npk + 64) +
+           al(sizeof(double) * (2 * j->n_w + j->n_q + 3 * nqw + 8) + 64);
+  L.dtab = al(sizeof(double) * qb * j->n_k * j->n_w * nov);
+  L.chi = al(es * NN * qb * j->n_w);
+  L.T = L.chi;
+  L.L = al(es * NN * qb);
+  if (j->mem == RPA_MEM_HOST) {
+    L.stageC = al(es * j->n_aux * nov * qb * j->n_k);
+    L.stageV = al(es * NN * qb);
+    L.eps = al(sizeof(double) * (size_t)j->n_kpts * (j->n_occ + j->n_virt));
+  }
+  if (j->prec == RPA_PREC_MIXED) {
+    BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, (int)nov, j->n_k, j->n_w, 1};
+    L.mixed = al(mixed_workspace_bytes(g, n_slices));
+  }
+  L.total = L.meta + L.dtab + L.chi + L.T + L.L + 2 * (L.stageC + L.stageV) + L.eps + L.mixed;
+  return L;
+}
+
+static int choose_qb(const rpa_job* j, int n_slices, size_t cap) {
+  int qb = j->n_q;
+  while (qb > 1 && plan_layout(j, qb, n_slices).total > cap) qb = (qb + 1) / 2;
+  return qb;
+}
+
+size_t job_footprint(const rpa_job* j, int n_slices, size_t ws_cap) {
+  Layout L = plan_layout(j, choose_qb(j, n_slices, ws_cap), n_slices);
+  size_t in = 0;
+  if (j->mem == RPA_MEM_DEVICE) {
+    const size_t es = j->is_complex ? 16 : 8;
+    in = es * (size_t)j->n_aux * j->n_occ * j->n_virt * j->n_q * j->n_k + es * (size_t)j->n_aux * j->n_aux * j->n_q;
+  }
+  return in + L.total;
+}
+
+// Device pointers into a lane's workspace.
+struct Bufs {
+  const void** Cptrs;  // [n_q*n_k]
+  int* kidx;           // [n_q*n_k]
+  int* kqidx;          // [n_q*n_k]
+  double* omega;       // [n_w]
+  double* zeta_w;      // [n_w]
+  double* w_q;         // [n_q]
+  double* Ec;          // [1]
+  double* eps;         // [n_q*n_w]
+  double* parts;       // [n_q*n_w*2]
+  int* status;
+  double* dtab;
+  double* chi;
+  double* T;
+  double* L;
+  char* stageC[2];
+  char* stageV[2];
+  double* eps_occ;
+  double* eps_virt;
+  void* mixed;
+  size_t mixed_bytes;
+};
+
+static Bufs carve(void* ws, const rpa_job* j, const Layout& L) {
+  Bufs b{};
+  const size_t npk = (size_t)j->n_q * j->n_k;
+  const size_t nqw = (size_t)j->n_q * j->n_w;
+  char* p = (char*)ws;
+  char* m = p;
+  b.Cptrs = (const void**)m;
+  m += sizeof(void*) * npk;
+  b.kidx = (int*)m;
+  m += sizeof(int) * npk;
+  b.kqidx = (int*)m;
+  m = p + al(sizeof(void*) * npk + sizeof(int) * 2 * npk + 64);
+  // doubles block, in the same order as the pinned upload/download images
+  double* d = (double*)m;
+  b.omega = d;
+  d += j->n_w;
+  b.zeta_w = d;
+  d += j->n_w;
+  b.w_q = d;
+  d += j->n_q;
+  b.Ec = d;
+  d += 1;
+  b.eps = d;
+  d += nqw;
+  b.parts = d;
+  d += 2 * nqw;
+  b.status = (int*)d;
+  p += L.meta;
+  b.dtab = (double*)p;
+  p += L.dtab;
+  b.chi = (double*)p;
+  p += L.chi;
+  b.T = (double*)p;
+  p += L.T;
+  b.L = (double*)p;
+  p += L.L;
+  for (int i = 0; i < 2; ++i) {
+    b.stageC[i] = p;
+    p += L.stageC;
+    b.stageV[i] = p;
+    p += L.stageV;
+  }
+  b.eps_occ = (double*)p;
+  b.eps_virt = (double*)(p + sizeof(double) * (size_t)j->n_kpts * j->n_occ);
+  p += L.eps;
+  b.mixed = p;
+  b.mixed_bytes = L.mixed;
+  return b;
+}
+
+// Uploads the job's small tables in one pinned copy: C pointers (device or
+// staged), eps row indices, frequencies and weights; zeroes the status word.
+static rpa_status upload_tables(rpa_ctx* ctx, Exec& ex, const rpa_job* j, const Bufs& b, const void* const* Cdev) {
+  const size_t npk = (size_t)j->n_q * j->n_k;
+  const size_t tbytes = sizeof(void*) * npk + sizeof(int) * 2 * npk;
+  const size_t dbytes = sizeof(double) * (2 * j->n_w + j->n_q);
+  if (!ex.hstage.reserve(tbytes + dbytes + 64)) {
+    ctx_set_error(ctx, "cannot allocate pinned host staging");
+    return RPA_E_NOMEM;
+  }
+  char* h = (char*)ex.hstage.ptr;
+  memcpy(h, Cdev, sizeof(void*) * npk);
+  memcpy(h + sizeof(void*) * npk, j->pair_k, sizeof(int) * npk);
+  memcpy(h + sizeof(void*) * npk + sizeof(int) * npk, j->pair_kq, sizeof(int) * npk);
+  double* hd = (double*)(h + ((tbytes + 63) & ~(size_t)63));
+  memcpy(hd, j->omega, sizeof(double) * j->n_w);
+  memcpy(hd + j->n_w, j->zeta_w, sizeof(double) * j->n_w);
+  memcpy(hd + 2 * j->n_w, j->w_q, sizeof(double) * j->n_q);
+  CK(cudaMemcpyAsync((void*)b.Cptrs, h, tbytes, cudaMemcpyHostToDevice, ex.s));
+  CK(cudaMemcpyAsync(b.omega, hd, dbytes, cudaMemcpyHostToDevice, ex.s));
+  CK(cudaMemsetAsync(b.status, 0, sizeof(int), ex.s));
+  return RPA_OK;
+}
+
+// Hot path for q in [q0, q0+nq).  Device tables are indexed by q*n_k + j;
+// V of the batch at Vdev[0..nq).  chi_user: write chi0 there and stop.
+static rpa_status run_qbatch(rpa_ctx* ctx, const rpa_job* j, const Bufs& b, int q0, int nq,
+                             const void* const* Vdev, const double* eps_occ, const double* eps_virt, cudaStream_t s,
+                             double* chi_user, int n_slices) {
+  const int nk = j->n_k;
+  const size_t es = j->is_complex ? 16 : 8;
+  const size_t NN = (size_t)j->n_aux * j->n_aux;
+  BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, j->n_occ * j->n_virt, nk, j->n_w, nq};
+  CK(launch_dtab(g, eps_occ, eps_virt, b.kidx + (size_t)q0 * nk, b.kqidx + (size_t)q0 * nk, b.omega, j->zeta_k,
+                 b.dtab, s));
+  ctx->launches++;
+  double* chi = chi_user ? chi_user : b.chi;
+  if (j->prec == RPA_PREC_MIXED) {
+    for (int qi = 0; qi < nq; ++qi) {
+      BatchGeom g1 = g;
+      g1.n_qb = 1;
+      uint64_t nl = 0;
+      CK(launch_chi0_mixed(g1, n_slices, (const double* const*)(b.Cptrs + (size_t)(q0 + qi) * nk),
+                           b.dtab + (size_t)qi * nk * j->n_w * g.n_ov, chi + (size_t)qi * j->n_w * NN * (es / 8),
+                           b.mixed, b.mixed_bytes, &nl, s));
+      ctx->launches += nl;
+    }
+  } else {
+    CK(launch_chi0_fp64(g, (const double* const*)(b.Cptrs + (size_t)q0 * nk), b.dtab, chi, s));
+    ctx->launches++;
+  }
+  if (chi_user) return RPA_OK;
+  // V(q) -> L, the lower Cholesky factor (V = L L^H), one matrix per q
+  for (int qi = 0; qi < nq; ++qi)
+    CK(cudaMemcpyAsync(b.L + qi * NN * (es / 8), Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
+  CK(launch_cholesky(j->is_complex, j->n_aux, nq, b.L, (long)(NN * (es / 8)), 1, nullptr, b.status, (1 << 29) + q0,
+                     s));
+  ctx->launches++;
+  // Y = -(L^H chi L) (lower triangle), overwriting chi's storage
+  CK(launch_sandwich(j->is_complex, j->n_aux, nq * j->n_w, j->n_w, chi, b.L, b.T, b.chi, s));
+  ctx->launches += 2;
+  // 1 - Pi' = 1 + Y: Cholesky, ln det, Tr
+  CK(launch_cholesky(j->is_complex, j->n_aux, nq * j->n_w, b.chi, (long)(NN * (es / 8)), 0,
+                     b.parts + (size_t)2 * q0 * j->n_w, b.status, q0 * j->n_w, s));
+  ctx->launches++;
+  return RPA_OK;
+}
+
+static rpa_status decode_status(rpa_ctx* ctx, int st, int n_w) {
+  if (st == 0) return RPA_OK;
+  const int code = st - 1;
+  if (code >= (1 << 29))
+    ctx_set_error(ctx, "V(q=%d) is not positive definite", code - (1 << 29));
+  else
+    ctx_set_error(ctx, "1 - Pi(q=%d, w=%d) is not positive definite", code / n_w, code % n_w);
+  return RPA_E_NOTPD;
+}
+
+rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_cap) {
+  char msg[512];
+  if (validate_job(job, msg, sizeof msg)) {
+    ctx_set_error(ctx, "%s", msg);
+    return RPA_E_INVAL;
+  }
+  if (job->prec == RPA_PREC_MIXED && !mixed_supported()) {
+    ctx_set_error(ctx, "mixed-precision chi0 not available in this build");
+    return RPA_E_INVAL;
+  }
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ex.s;
+  const int qb = choose_qb(job, ctx->n_slices, ws_cap);
+  Layout L = plan_layout(job, qb, ctx->n_slices);
+  if (!ex.ensure_ws(L.total)) {
+    ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", L.total);
+    return RPA_E_NOMEM;
+  }
+  Bufs b = carve(ex.ws, job, L);
+  const size_t es = job->is_complex ? 16 : 8;
+  const size_t NN = (size_t)job->n_aux * job->n_aux;
+  const size_t nov = (size_t)job->n_occ * job->n_virt;
+  const size_t cblk = es * job->n_aux * nov;
+  const size_t nqw = (size_t)job->n_q * job->n_w;
+  const bool host = job->mem == RPA_MEM_HOST;
+  const int nbatch = (job->n_q + qb - 1) / qb;
+
+  std::vector<const void*> cp((size_t)job->n_q * job->n_k), vp(job->n_q);
+  for (int q = 0; q < job->n_q; ++q) {
+    const int bi = q / qb, slot = bi % 2, qi = q - bi * qb;
+    for (int jj = 0; jj < job->n_k; ++jj) {
+      const size_t i = (size_t)q * job->n_k + jj;
+      cp[i] = host ? (const void*)(b.stageC[slot] + ((size_t)qi * job->n_k + jj) * cblk) : job->C[i];
+    }
+    vp[q] = host ? (const void*)(b.stageV[slot] + (size_t)qi * es * NN) : job->V[q];
+  }
+  if (rpa_status st0 = upload_tables(ctx, ex, job, b, cp.data())) return st0;
+
+  const double* eo = job->eps_occ;
+  const double* ev = job->eps_virt;
+  // host staging: the copy stream fills stage[bi % 2] while the compute
+  // stream works on the other slot
+  auto issue_copy = [&](int bi) -> rpa_status {
+    const int q0 = bi * qb, nq = std::min(qb, job->n_q - q0), slot = bi % 2;
+    CK(cudaStreamWaitEvent(ex.cs, ex.freed[slot], 0));
+    for (int i = 0; i < nq * job->n_k; ++i)
+      CK(cudaMemcpyAsync(b.stageC[slot] + i * cblk, job->C[(size_t)q0 * job->n_k + i], cblk, cudaMemcpyHostToDevice,
+                         ex.cs));
+    for (int i = 0; i < nq; ++i)
+      CK(cudaMemcpyAsync(b.stageV[slot] + i * es * NN, job->V[q0 + i], es * NN, cudaMemcpyHostToDevice, ex.cs));
+    CK(cudaEventRecord(ex.ready[slot], ex.cs));
+    return RPA_OK;
+  };
+  if (host) {
+    CK(cudaMemcpyAsync(b.eps_occ, job->eps_occ, sizeof(double) * job->n_kpts * job->n_occ, cudaMemcpyHostToDevice,
+                       s));
+    CK(cudaMemcpyAsync(b.eps_virt, job->eps_virt, sizeof(double) * job->n_kpts * job->n_virt,
+                       cudaMemcpyHostToDevice, s));
+    eo = b.eps_occ;
+    ev = b.eps_virt;
+    for (int i = 0; i < 2; ++i) CK(cudaEventRecord(ex.freed[i], s));
+    for (int bi = 0; bi < std::min(2, nbatch); ++bi)
+      if (rpa_status st = issue_copy(bi)) return st;
+  }
+  for (int bi = 0; bi < nbatch; ++bi) {
+    const int q0 = bi * qb, nq = std::min(qb, job->n_q - q0), slot = bi % 2;
+    if (host) CK(cudaStreamWaitEvent(s, ex.ready[slot], 0));
+    if (rpa_status st = run_qbatch(ctx, job, b, q0, nq, vp.data() + q0, eo, ev, s, nullptr, ctx->n_slices)) return st;
+    if (host) {
+      CK(cudaEventRecord(ex.freed[slot], s));
+      if (bi + 2 < nbatch)
+        if (rpa_status st2 = issue_copy(bi + 2)) return st2;
+    }
+  }
+  CK(launch_energy_reduce(job->n_q, job->n_w, b.parts, b.w_q, b.zeta_w, b.eps, b.Ec, s));
+  ctx->launches++;
+  if (!ex.hres.reserve(64 + sizeof(double) * (3 * nqw + 1))) {
+    ctx_set_error(ctx, "cannot allocate pinned result buffer");
+    return RPA_E_NOMEM;
+  }
+  CK(cudaMemcpyAsync(ex.results(), b.Ec, sizeof(double) * (3 * nqw + 1), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&ex.status_word(), b.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ex.done, s));
+  return RPA_OK;
+}
+
+rpa_status energy_finish(rpa_ctx* ctx, Exec& ex, const rpa_job* job, double* Ec, double* eps_qw, double* parts) {
+  const size_t nqw = (size_t)job->n_q * job->n_w;
+  if (rpa_status st = decode_status(ctx, ex.status_word(), job->n_w)) return st;
+  const double* r = ex.results();
+  if (Ec) *Ec = r[0];
+  if (eps_qw) memcpy(eps_qw, r + 1, sizeof(double) * nqw);
+  if (parts) memcpy(parts, r + 1 + nqw, sizeof(double) * 2 * nqw);
+  return RPA_OK;
+}
+
+static size_t sync_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap, (size_t)24 << 30); }
+
+}  // namespace rpa
+
+// ============================================================== C ABI =====
+
+extern "C" {
+
+rpa_status rpa_create(const rpa_config* cfg, rpa_ctx** out) {
+  if (!out) return RPA_E_INVAL;
+  *out = nullptr;
+  rpa_config c{};
+  if (cfg) c = *cfg;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    g_create_error = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    return RPA_E_CUDA;
+  }
+  if (c.device < 0 || c.device >= n) {
+    g_create_error = "device ordinal out of range";
+    return RPA_E_INVAL;
+  }
+  if (c.n_slices == 0) c.n_slices = 4;
+  if (c.n_slices < 2 || c.n_slices > 6) {
+    g_create_error = "n_slices must be in [2, 6]";
+    return RPA_E_INVAL;
+  }
+  rpa_ctx* ctx = new rpa_ctx();
+  ctx->device = c.device;
+  ctx->n_slices = c.n_slices;
+  ctx->cap = c.hbm_cap_bytes ? c.hbm_cap_bytes : (size_t)120 << 30;
+  ctx->timeout_s = c.timeout_s > 0 ? c.timeout_s : 60.0;
+  ctx->max_inflight = c.max_inflight > 0 ? c.max_inflight : 64;
+  if (cudaSetDevice(c.device) != cudaSuccess || !ctx->ex.init()) {
+    g_create_error = std::string("stream/event creation failed: ") + cudaGetErrorString(cudaGetLastError());
+    ctx->ex.destroy();
+    delete ctx;
+    return RPA_E_CUDA;
+  }
+  *out = ctx;
+  return RPA_OK;
+}
+
+rpa_status rpa_destroy(rpa_ctx* ctx) {
+  if (!ctx) return RPA_E_INVAL;
+  rpa::serving_shutdown(ctx);
+  cudaSetDevice(ctx->device);
+  rpa::batch_release(ctx);
+  ctx->ex.destroy();
+  delete ctx;
+  return RPA_OK;
+}
+
+const char* rpa_last_error(const rpa_ctx* ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->last_error.c_str();
+}
+
+rpa_status rpa_job_validate(const rpa_job* job, char* msg, size_t msg_len) {
+  if (msg && msg_len) msg[0] = 0;
+  return validate_job(job, msg, msg_len);
+}
+
+rpa_status rpa_job_footprint(const rpa_job* job, size_t* bytes) {
+  if (!bytes) return RPA_E_INVAL;
+  if (rpa_status st = validate_job(job, nullptr, 0)) return st;
+  *bytes = job_footprint(job, 4, (size_t)24 << 30);
+  return RPA_OK;
+}
+
+uint64_t rpa_kernel_launches(const rpa_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+rpa_status rpa_chi0(rpa_ctx* ctx, const rpa_job* job, int q, void* chi_out, void* stream) {
+  if (!ctx) return RPA_E_INVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  char msg[512];
+  if (validate_job(job, msg, sizeof msg)) {
+    ctx_set_error(ctx, "%s", msg);
+    return RPA_E_INVAL;
+  }
+  if (q < 0 || q >= job->n_q || !chi_out) {
+    ctx_set_error(ctx, "rpa_chi0: q out of range or chi_out NULL");
+    return RPA_E_INVAL;
+  }
+  if (job->mem != RPA_MEM_DEVICE) {
+    ctx_set_error(ctx, "rpa_chi0 needs device-resident inputs (mem = RPA_MEM_DEVICE)");
+    return RPA_E_INVAL;
+  }
+  if (job->prec == RPA_PREC_MIXED && !mixed_supported()) {
+    ctx_set_error(ctx, "mixed-precision chi0 not available in this build");
+    return RPA_E_INVAL;
+  }
+  CK(cudaSetDevice(ctx->device));
+  Exec& ex = ctx->ex;
+  cudaStream_t s = (cudaStream_t)stream;
+  Layout L = plan_layout(job, 1, ctx->n_slices);
+  if (!ex.ensure_ws(L.total)) {
+    ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", L.total);
+    return RPA_E_NOMEM;
+  }
+  Bufs b = carve(ex.ws, job, L);
+  // the lane's uploads run on ex.s; order the caller's stream after them
+  if (rpa_status st0 = upload_tables(ctx, ex, job, b, job->C)) return st0;
+  CK(cudaEventRecord(ex.done, ex.s));
+  CK(cudaStreamWaitEvent(s, ex.done, 0));
+  if (rpa_status st = run_qbatch(ctx, job, b, q, 1, job->V + q, job->eps_occ, job->eps_virt, s, (double*)chi_out,
+                                 ctx->n_slices))
+    return st;
+  // the d table in the workspace is reused by the next call on this context
+  CK(cudaEventRecord(ex.done, s));
+  return wait_event(ctx, ex.done, ctx->timeout_s);
+}
+
+rpa_status rpa_logdet(rpa_ctx* ctx, const rpa_job* job, int q, const void* chi, double* out, void* stream) {
+  if (!ctx) return RPA_E_INVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  char msg[512];
+  if (validate_job(job, msg, sizeof msg)) {
+    ctx_set_error(ctx, "%s", msg);
+    return RPA_E_INVAL;
+  }
+  if (q < 0 || q >= job->n_q || !chi || !out || job->mem != RPA_MEM_DEVICE) {
+    ctx_set_error(ctx, "rpa_logdet: bad q, NULL pointer or host-resident job");
+    return RPA_E_INVAL;
+  }
+  CK(cudaSetDevice(ctx->device));
+  Exec& ex = ctx->ex;
+  cudaStream_t s = (cudaStream_t)stream;
+  rpa_job j1 = *job;
+  j1.prec = RPA_PREC_FP64;
+  Layout L = plan_layout(&j1, 1, ctx->n_slices);
+  if (!ex.ensure_ws(L.total)) {
+    ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", L.total);
+    return RPA_E_NOMEM;
+  }
+  Bufs b = carve(ex.ws, &j1, L);
+  const size_t es = job->is_complex ? 16 : 8;
+  const size_t NN = (size_t)job->n_aux * job->n_aux;
+  CK(cudaMemsetAsync(b.status, 0, sizeof(int), s));
+  CK(cudaMemcpyAsync(b.L, job->V[q], es * NN, cudaMemcpyDeviceToDevice, s));
+  CK(launch_cholesky(job->is_complex, job->n_aux, 1, b.L, (long)(NN * (es / 8)), 1, nullptr, b.status,
+                     (1 << 29) + q, s));
+  CK(launch_sandwich(job->is_complex, job->n_aux, job->n_w, job->n_w, (const double*)chi, b.L, b.T, b.chi, s));
+  CK(launch_cholesky(job->is_complex, job->n_aux, job->n_w, b.chi, (long)(NN * (es / 8)), 0, b.parts, b.status, 0,
+                     s));
+  ctx->launches += 4;
+  if (!ex.hres.reserve(64 + sizeof(double) * 2 * job->n_w)) return RPA_E_NOMEM;
+  CK(cudaMemcpyAsync(ex.results(), b.parts, sizeof(double) * 2 * job->n_w, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&ex.status_word(), b.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ex.done, s));
+  if (rpa_status st = wait_event(ctx, ex.done, ctx->timeout_s)) return st;
+  const int sw = ex.status_word();
+  if (sw) {
+    const int code = sw - 1;
+    if (code >= (1 << 29))
+      ctx_set_error(ctx, "V(q=%d) is not positive definite", q);
+    else
+      ctx_set_error(ctx, "1 - Pi(q=%d, w=%d) is not positive definite", q, code);
+    return RPA_E_NOTPD;
+  }
+  memcpy(out, ex.results(), sizeof(double) * 2 * job->n_w);
+  return RPA_OK;
+}
+
+rpa_status rpa_energy(rpa_ctx* ctx, const rpa_job* job, double* Ec, double* eps_qw, double* parts) {
+  if (!ctx || !Ec) return RPA_E_INVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (rpa_status st = rpa::energy_enqueue(ctx, ctx->ex, job, rpa::sync_ws_cap(ctx))) return st;
+  // bounded wait: scaled with the job's chi0 work at a conservative 0.2 TFLOP/s
+  const double work = 8.0 * job->n_aux * (double)job->n_aux * job->n_occ * job->n_virt * job->n_q * job->n_k *
+                      job->n_w / (job->is_complex ? 1.0 : 4.0);
+  const double limit = ctx->timeout_s + work / 0.2e12;
+  if (rpa_status st = rpa::wait_event(ctx, ctx->ex.done, limit)) return st;
+  return rpa::energy_finish(ctx, ctx->ex, job, Ec, eps_qw, parts);
+}
+
+}  // extern "C"

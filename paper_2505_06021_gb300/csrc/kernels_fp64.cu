@@ -1,0 +1,615 @@
+// FP64 kernels of the RPA hot path on GB300 (sm_103a).
+//
+// GB300 executes FP64 at about 1/58 of its FP32 rate (1.2 TFLOP/s measured
+// for DFMA and DGEMM), so every kernel here is bound by the FP64 pipe and is
+// organised to issue as few FP64 instructions per useful result as possible:
+//   * chi0: the product conj(C_P,t) C_Q,t is formed once per t and reused for
+//     a group of G frequencies (2 DFMA per frequency instead of 4), and only
+//     the lower triangle of tiles is computed (chi0 is Hermitian);
+//   * the sandwich uses the Cholesky factor L of V (triangular operands, lower
+//     output only) instead of the dense V^(1/2);
+//   * the factorisation of 1 - Pi keeps the diagonal in "pivot minus one"
+//     form so that ln det = sum log1p(u) keeps its digits as Pi -> 0.
+// All reductions run in a fixed order, so results are bit-reproducible.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rpa_internal.h"
+
+namespace rpa {
+namespace {
+
+// ---------------------------------------------------------------- helpers --
+
+template <bool C>
+struct Elem;
+template <>
+struct Elem<true> {
+  double re, im;
+};
+template <>
+struct Elem<false> {
+  double re;
+};
+
+template <bool C>
+__device__ __forceinline__ Elem<C> ld_elem(const double* p, long i) {
+  Elem<C> e;
+  if constexpr (C) {
+    double2 v = *reinterpret_cast<const double2*>(p + 2 * i);
+    e.re = v.x;
+    e.im = v.y;
+  } else {
+    e.re = p[i];
+  }
+  return e;
+}
+template <bool C>
+__device__ __forceinline__ Elem<C> zero_elem() {
+  Elem<C> e;
+  e.re = 0.0;
+  if constexpr (C) e.im = 0.0;
+  return e;
+}
+template <bool C>
+__device__ __forceinline__ void st_elem(double* p, long i, Elem<C> e) {
+  if constexpr (C) {
+    *reinterpret_cast<double2*>(p + 2 * i) = make_double2(e.re, e.im);
+  } else {
+    p[i] = e.re;
+  }
+}
+template <bool C>
+__device__ __forceinline__ Elem<C> conj_e(Elem<C> a) {
+  if constexpr (C) a.im = -a.im;
+  return a;
+}
+// acc += a * b
+template <bool C>
+__device__ __forceinline__ void mac(Elem<C>& acc, Elem<C> a, Elem<C> b) {
+  if constexpr (C) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+  } else {
+    acc.re = fma(a.re, b.re, acc.re);
+  }
+}
+
+// Lower-triangular tile index -> (I, J), J <= I.
+__device__ __forceinline__ void tri_index(int t, int& I, int& J) {
+  int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  while (i * (i + 1) / 2 > t) --i;
+  I = i;
+  J = t - i * (i + 1) / 2;
+}
+
+// ------------------------------------------------------------ d table -----
+
+__global__ void dtab_kernel(BatchGeom g, const double* __restrict__ eps_occ, const double* __restrict__ eps_virt,
+                            const int* __restrict__ kidx, const int* __restrict__ kqidx,
+                            const double* __restrict__ omega, double zeta_k, double* __restrict__ dtab) {
+  const long total = (long)g.n_qb * g.n_k * g.n_w * g.n_ov;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    long r = idx;
+    const int t = (int)(r % g.n_ov);
+    r /= g.n_ov;
+    const int w = (int)(r % g.n_w);
+    r /= g.n_w;
+    const int pair = (int)r;  // qb * n_k + j
+    const int i = t / g.n_virt, a = t - i * g.n_virt;
+    const double delta = eps_virt[(long)kqidx[pair] * g.n_virt + a] - eps_occ[(long)kidx[pair] * g.n_occ + i];
+    const double om = omega[w];
+    dtab[idx] = zeta_k * (-4.0 * delta / (delta * delta + om * om));
+  }
+}
+
+// --------------------------------------------------------------- chi0 -----
+// Grid: one CTA per (q in batch, lower tile pair (I, J), frequency group).
+// Tile 32 x 32 outputs, 256 threads, each thread a 2 x 2 block of outputs
+// (rows ty, ty+16; columns tx, tx+16) for G frequencies.
+
+constexpr int CT = 32;  // output tile edge
+constexpr int TK = 16;  // t-chunk
+
+template <bool C, int G>
+__global__ void __launch_bounds__(256, 1)
+    chi0_fp64_kernel(BatchGeom g, const double* const* __restrict__ Cptrs, const double* __restrict__ dtab,
+                     double* __restrict__ chi, int n_tiles, int n_wg) {
+  __shared__ Elem<C> As[TK][CT];
+  __shared__ Elem<C> Bs[TK][CT];
+  __shared__ double Ds[G][TK];
+
+  int bid = blockIdx.x;
+  const int wg = bid % n_wg;
+  bid /= n_wg;
+  const int tile = bid % n_tiles;
+  const int qb = bid / n_tiles;
+  int I, J;
+  tri_index(tile, I, J);
+  const int w0 = wg * G;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int N = g.n_aux, n_ov = g.n_ov;
+
+  Elem<C> acc[G][4];
+#pragma unroll
+  for (int k = 0; k < G; ++k)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc[k][m] = zero_elem<C>();
+
+  for (int j = 0; j < g.n_k; ++j) {
+    const double* Cj = Cptrs[qb * g.n_k + j];
+    const double* dj = dtab + ((long)(qb * g.n_k + j) * g.n_w) * n_ov;
+    for (int t0 = 0; t0 < n_ov; t0 += TK) {
+      for (int idx = tid; idx < CT * TK; idx += 256) {
+        const int r = idx / TK, tt = idx % TK, t = t0 + tt;
+        const int P = I * CT + r, Q = J * CT + r;
+        As[tt][r] = (P < N && t < n_ov) ? ld_elem<C>(Cj, (long)P * n_ov + t) : zero_elem<C>();
+        Bs[tt][r] = (Q < N && t < n_ov) ? ld_elem<C>(Cj, (long)Q * n_ov + t) : zero_elem<C>();
+      }
+      for (int idx = tid; idx < G * TK; idx += 256) {
+        const int k = idx / TK, tt = idx % TK, t = t0 + tt, w = w0 + k;
+        Ds[k][tt] = (t < n_ov && w < g.n_w) ? dj[(long)w * n_ov + t] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int tt = 0; tt < TK; ++tt) {
+        const Elem<C> a0 = As[tt][ty], a1 = As[tt][ty + 16];
+        const Elem<C> b0 = Bs[tt][tx], b1 = Bs[tt][tx + 16];
+        // p = conj(a) * b
+        Elem<C> p[4];
+        const Elem<C> aa[2] = {a0, a1}, bb[2] = {b0, b1};
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            if constexpr (C) {
+              p[2 * u + v].re = fma(aa[u].re, bb[v].re, aa[u].im * bb[v].im);
+              p[2 * u + v].im = fma(aa[u].re, bb[v].im, -aa[u].im * bb[v].re);
+            } else {
+              p[2 * u + v].re = aa[u].re * bb[v].re;
+            }
+          }
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+          const double d = Ds[k][tt];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            acc[k][m].re = fma(d, p[m].re, acc[k][m].re);
+            if constexpr (C) acc[k][m].im = fma(d, p[m].im, acc[k][m].im);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // write the lower triangle and its Hermitian mirror
+  const long NN = (long)N * N;
+#pragma unroll
+  for (int k = 0; k < G; ++k) {
+    const int w = w0 + k;
+    if (w >= g.n_w) break;
+    double* out = chi + ((long)qb * g.n_w + w) * NN * (C ? 2 : 1);
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const int P = I * CT + ty + 16 * u, Q = J * CT + tx + 16 * v;
+        if (P >= N || Q >= N || Q > P) continue;
+        Elem<C> e = acc[k][2 * u + v];
+        if (P == Q) {
+          if constexpr (C) e.im = 0.0;
+          st_elem<C>(out, (long)P * N + Q, e);
+        } else {
+          st_elem<C>(out, (long)P * N + Q, e);
+          st_elem<C>(out, (long)Q * N + P, conj_e<C>(e));
+        }
+      }
+  }
+}
+
+template <bool C, int G>
+cudaError_t chi0_launch_g(const BatchGeom& g, const double* const* Cptrs, const double* dtab, double* chi,
+                          cudaStream_t s) {
+  const int nt = (g.n_aux + CT - 1) / CT;
+  const int n_tiles = nt * (nt + 1) / 2;
+  const int n_wg = (g.n_w + G - 1) / G;
+  const long blocks = (long)n_tiles * n_wg * g.n_qb;
+  if (blocks > 0x7fffffffL) return cudaErrorInvalidConfiguration;
+  chi0_fp64_kernel<C, G><<<(unsigned)blocks, 256, 0, s>>>(g, Cptrs, dtab, chi, n_tiles, n_wg);
+  return cudaGetLastError();
+}
+
+// Frequency group size: minimises FP64 instructions per (P, Q, t),
+// 4 * ceil(n_w / G) (products, complex) + 2 * G * ceil(n_w / G) (weights).
+int pick_group(int n_w) {
+  const int cand[4] = {4, 5, 8, 10};
+  int best = 8;
+  long best_cost = -1;
+  for (int c : cand) {
+    const long ng = (n_w + c - 1) / c;
+    const long cost = 4 * ng + 2 * (long)c * ng;
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = c;
+    }
+  }
+  return best;
+}
+
+template <bool C>
+cudaError_t chi0_dispatch(const BatchGeom& g, const double* const* Cptrs, const double* dtab, double* chi,
+                          cudaStream_t s) {
+  switch (pick_group(g.n_w)) {
+    case 4:
+      return chi0_launch_g<C, 4>(g, Cptrs, dtab, chi, s);
+    case 5:
+      return chi0_launch_g<C, 5>(g, Cptrs, dtab, chi, s);
+    case 10:
+      return chi0_launch_g<C, 10>(g, Cptrs, dtab, chi, s);
+    default:
+      return chi0_launch_g<C, 8>(g, Cptrs, dtab, chi, s);
+  }
+}
+
+// ----------------------------------------------------------- sandwich -----
+// MODE 0: T = X L      (L lower triangular; K-range of output column tile J
+//                       starts at J*64)
+// MODE 1: Y = -L^H T   (lower output tiles only; K-range of row tile I starts
+//                       at I*64)
+// 64 x 64 output tile, 256 threads, 4 x 4 outputs per thread.
+
+constexpr int GT = 64;
+constexpr int GK = 16;
+
+template <bool C, int MODE>
+__global__ void __launch_bounds__(256)
+    sandwich_kernel(int N, int n_w, const double* __restrict__ Xb, const double* __restrict__ Lb,
+                    double* __restrict__ Ob, int n_tiles_row, int tiles_per_mat) {
+  __shared__ Elem<C> As[GK][GT];
+  __shared__ Elem<C> Bs[GK][GT];
+  const int b = blockIdx.x / tiles_per_mat;
+  const int tile = blockIdx.x % tiles_per_mat;
+  int I, J;
+  if (MODE == 0) {
+    I = tile / n_tiles_row;
+    J = tile % n_tiles_row;
+  } else {
+    tri_index(tile, I, J);
+  }
+  const long NN = (long)N * N;
+  const int cs = C ? 2 : 1;
+  const double* X = Xb + (long)b * NN * cs;
+  const double* L = Lb + (long)(b / n_w) * NN * cs;
+  double* O = Ob + (long)b * NN * cs;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+
+  Elem<C> acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = zero_elem<C>();
+
+  const int k_begin = (MODE == 0 ? J : I) * GT;
+  for (int k0 = k_begin; k0 < N; k0 += GK) {
+    for (int idx = tid; idx < GK * GT; idx += 256) {
+      if (MODE == 0) {
+        // A = X[P][R] (row-major, R contiguous): idx -> (p, kk) with kk fastest
+        const int p = idx / GK, kk = idx % GK, P = I * GT + p, R = k0 + kk;
+        As[kk][p] = (P < N && R < N) ? ld_elem<C>(X, (long)P * N + R) : zero_elem<C>();
+        // B = L[R][Q], zero above the diagonal (R < Q)
+        const int q = idx % GT, kb = idx / GT, Q = J * GT + q, R2 = k0 + kb;
+        Bs[kb][q] = (Q < N && R2 < N && R2 >= Q) ? ld_elem<C>(L, (long)R2 * N + Q) : zero_elem<C>();
+      } else {
+        // A[P][R] = conj(L[R][P]), zero for R < P; read L rows R, P contiguous
+        const int p = idx % GT, kk = idx / GT, P = I * GT + p, R = k0 + kk;
+        As[kk][p] = (P < N && R < N && R >= P) ? conj_e<C>(ld_elem<C>(L, (long)R * N + P)) : zero_elem<C>();
+        const int q = idx % GT, Q = J * GT + q;
+        Bs[kk][q] = (Q < N && R < N) ? ld_elem<C>(X, (long)R * N + Q) : zero_elem<C>();
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      Elem<C> a[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) bv[v] = Bs[kk][tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) mac<C>(acc[u][v], a[u], bv[v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int P = I * GT + ty + 16 * u, Q = J * GT + tx + 16 * v;
+      if (P >= N || Q >= N) continue;
+      Elem<C> e = acc[u][v];
+      if (MODE == 1) {
+        e.re = -e.re;
+        if constexpr (C) e.im = -e.im;
+      }
+      st_elem<C>(O, (long)P * N + Q, e);
+    }
+}
+
+// ----------------------------------------------------------- Cholesky -----
+// One CTA (256 threads) per matrix, right-looking blocked with 32-wide panels.
+// mode 0: A holds Y = -Pi; the factorised matrix is 1 + Y, whose diagonal is
+//         kept as u = pivot - 1; ln det = sum_j log1p(u_j); Tr Pi = -sum Y_jj.
+// mode 1: A holds V; factor in place, strict upper triangle zeroed.
+
+constexpr int CB = 32;
+
+template <bool C>
+__global__ void __launch_bounds__(256)
+    cholesky_kernel(int N, double* __restrict__ mats, long bstride, int mode, double* __restrict__ out,
+                    int* __restrict__ status, int status_base) {
+  __shared__ Elem<C> D[CB][CB + 1];
+  __shared__ Elem<C> S2[CB][CB + 1];
+  Elem<C>(*S1)[CB + 1] = D;  // the diagonal block is free again during the trailing update
+  __shared__ double red[256];
+  __shared__ int bad;
+  __shared__ double logacc;
+  const int b = blockIdx.x;
+  double* A = mats + (long)b * bstride;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // trace of Pi (mode 0), fixed-order reduction
+  if (mode == 0) {
+    double s = 0.0;
+    for (int j = tid; j < N; j += 256) s += ld_elem<C>(A, (long)j * N + j).re;
+    red[tid] = s;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+      if (tid < off) red[tid] += red[tid + off];
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    bad = 0;
+    logacc = 0.0;
+  }
+  __syncthreads();
+
+  for (int kb = 0; kb < N; kb += CB) {
+    const int nb = min(CB, N - kb);
+    // (i) diagonal block
+    for (int idx = tid; idx < CB * CB; idx += 256) {
+      const int r = idx / CB, c = idx % CB;
+      D[r][c] = (r < nb && c <= r) ? ld_elem<C>(A, (long)(kb + r) * N + kb + c) : zero_elem<C>();
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double lacc = 0.0;
+      int lbad = 0;
+      for (int c = 0; c < nb; ++c) {
+        double l = 0.0;
+        if (lane == c) {
+          const double u = D[c][c].re;
+          const double piv = (mode == 0) ? 1.0 + u : u;
+          if (!(piv > 0.0)) {
+            lbad = 1;
+          } else {
+            l = sqrt(piv);
+            lacc += (mode == 0) ? log1p(u) : 0.0;
+            Elem<C> e = zero_elem<C>();
+            e.re = l;
+            D[c][c] = e;
+          }
+        }
+        const int anybad = __any_sync(0xffffffffu, lbad);
+        if (anybad) {
+          lbad = 1;
+          break;
+        }
+        l = __shfl_sync(0xffffffffu, l, c);
+        __syncwarp();
+        if (lane > c && lane < nb) {
+          Elem<C> e = D[lane][c];
+          e.re /= l;
+          if constexpr (C) e.im /= l;
+          D[lane][c] = e;
+        }
+        __syncwarp();
+        if (lane > c && lane < nb) {
+          const Elem<C> lr = D[lane][c];
+          for (int cc = c + 1; cc <= lane; ++cc) {
+            const Elem<C> lc = conj_e<C>(D[cc][c]);
+            Elem<C> e = D[lane][cc];
+            Elem<C> prod = zero_elem<C>();
+            mac<C>(prod, lr, lc);
+            e.re -= prod.re;
+            if constexpr (C) e.im -= prod.im;
+            D[lane][cc] = e;
+          }
+        }
+        __syncwarp();
+      }
+      // lane-wise partial log sums, combined in lane order (fixed)
+      for (int l2 = 0; l2 < 32; ++l2) {
+        const double v = __shfl_sync(0xffffffffu, lacc, l2);
+        if (lane == 0) logacc += v;
+      }
+      if (lbad && lane == 0) bad = 1;
+    }
+    __syncthreads();
+    if (bad) {
+      if (tid == 0 && status) atomicCAS(status, 0, 1 + status_base + b);
+      if (out && tid == 0) {
+        out[2 * b] = nan("");
+        out[2 * b + 1] = nan("");
+      }
+      return;
+    }
+    // write the factored diagonal block back (lower part)
+    for (int idx = tid; idx < CB * CB; idx += 256) {
+      const int r = idx / CB, c = idx % CB;
+      if (r < nb && c <= r) st_elem<C>(A, (long)(kb + r) * N + kb + c, D[r][c]);
+    }
+    // (ii) panel: rows i >= kb + nb solve X L_kk^H = A_panel
+    for (int i = kb + nb + tid; i < N; i += 256) {
+      Elem<C> x[CB];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        if (c < nb) {
+          Elem<C> v = ld_elem<C>(A, (long)i * N + kb + c);
+#pragma unroll
+          for (int c2 = 0; c2 < CB; ++c2) {
+            if (c2 < c) {
+              Elem<C> prod = zero_elem<C>();
+              mac<C>(prod, x[c2], conj_e<C>(D[c][c2]));
+              v.re -= prod.re;
+              if constexpr (C) v.im -= prod.im;
+            }
+          }
+          const double dd = D[c][c].re;
+          v.re /= dd;
+          if constexpr (C) v.im /= dd;
+          x[c] = v;
+          st_elem<C>(A, (long)i * N + kb + c, v);
+        }
+      }
+    }
+    __syncthreads();
+    // (iii) trailing update of the lower part of A[kb+nb:, kb+nb:]
+    const int m0 = kb + nb;
+    const int m = N - m0;
+    if (m > 0) {
+      const int nt = (m + CB - 1) / CB;
+      const int ntiles = nt * (nt + 1) / 2;
+      const int tx = tid & 15, ty = tid >> 4;
+      for (int tt = 0; tt < ntiles; ++tt) {
+        int TI, TJ;
+        tri_index(tt, TI, TJ);
+        for (int idx = tid; idx < CB * CB; idx += 256) {
+          const int r = idx / CB, c = idx % CB;
+          const int ri = m0 + TI * CB + r, rj = m0 + TJ * CB + r;
+          S1[c][r] = (ri < N && c < nb) ? ld_elem<C>(A, (long)ri * N + kb + c) : zero_elem<C>();
+          S2[c][r] = (rj < N && c < nb) ? conj_e<C>(ld_elem<C>(A, (long)rj * N + kb + c)) : zero_elem<C>();
+        }
+        __syncthreads();
+        Elem<C> acc[2][2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) acc[u][v] = zero_elem<C>();
+        for (int c = 0; c < nb; ++c) {
+          const Elem<C> a0 = S1[c][ty], a1 = S1[c][ty + 16];
+          const Elem<C> b0 = S2[c][tx], b1 = S2[c][tx + 16];
+          mac<C>(acc[0][0], a0, b0);
+          mac<C>(acc[0][1], a0, b1);
+          mac<C>(acc[1][0], a1, b0);
+          mac<C>(acc[1][1], a1, b1);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            const int r = m0 + TI * CB + ty + 16 * u, c = m0 + TJ * CB + tx + 16 * v;
+            if (r < N && c <= r) {
+              Elem<C> e = ld_elem<C>(A, (long)r * N + c);
+              e.re -= acc[u][v].re;
+              if constexpr (C) e.im -= acc[u][v].im;
+              st_elem<C>(A, (long)r * N + c, e);
+            }
+          }
+        __syncthreads();
+      }
+    }
+  }
+  if (mode == 1) {
+    for (long idx = tid; idx < (long)N * N; idx += 256) {
+      const int r = (int)(idx / N), c = (int)(idx % N);
+      if (c > r) st_elem<C>(A, idx, zero_elem<C>());
+    }
+  }
+  if (tid == 0 && out) {
+    out[2 * b] = logacc;
+    out[2 * b + 1] = (mode == 0) ? -red[0] : 0.0;
+  }
+}
+
+// ------------------------------------------------------------- energy -----
+
+__global__ void energy_kernel(int n_q, int n_w, const double* __restrict__ parts, const double* __restrict__ w_q,
+                              const double* __restrict__ zeta_w, double* __restrict__ eps, double* __restrict__ Ec) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // Neumaier-compensated sums in a fixed order: q inside, frequency outside.
+  double E = 0.0, Ec_c = 0.0;
+  for (int w = 0; w < n_w; ++w) {
+    double e = 0.0, c = 0.0;
+    for (int q = 0; q < n_q; ++q) {
+      const double v = parts[2 * ((long)q * n_w + w)] + parts[2 * ((long)q * n_w + w) + 1];
+      eps[(long)q * n_w + w] = v;
+      const double x = w_q[q] * v;
+      const double t = e + x;
+      c += (fabs(e) >= fabs(x)) ? (e - t) + x : (x - t) + e;
+      e = t;
+    }
+    const double x = zeta_w[w] * (e + c);
+    const double t = E + x;
+    Ec_c += (fabs(E) >= fabs(x)) ? (E - t) + x : (x - t) + E;
+    E = t;
+  }
+  *Ec = (E + Ec_c) / (2.0 * M_PI);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers ----
+
+cudaError_t launch_dtab(const BatchGeom& g, const double* eps_occ, const double* eps_virt, const int* kidx,
+                        const int* kqidx, const double* omega, double zeta_k, double* dtab, cudaStream_t s) {
+  const long total = (long)g.n_qb * g.n_k * g.n_w * g.n_ov;
+  if (total == 0) return cudaSuccess;
+  const long blocks = std::min<long>((total + 255) / 256, 152L * 16);
+  dtab_kernel<<<(unsigned)blocks, 256, 0, s>>>(g, eps_occ, eps_virt, kidx, kqidx, omega, zeta_k, dtab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chi0_fp64(const BatchGeom& g, const double* const* Cptrs, const double* dtab, double* chi,
+                             cudaStream_t s) {
+  return g.cplx ? chi0_dispatch<true>(g, Cptrs, dtab, chi, s) : chi0_dispatch<false>(g, Cptrs, dtab, chi, s);
+}
+
+cudaError_t launch_sandwich(int cplx, int N, int n_batch, int n_w, const double* chi, const double* L, double* T,
+                            double* Y, cudaStream_t s) {
+  if (n_batch == 0) return cudaSuccess;
+  const int nt = (N + GT - 1) / GT;
+  const int full = nt * nt, tri = nt * (nt + 1) / 2;
+  if (cplx) {
+    sandwich_kernel<true, 0><<<n_batch * full, 256, 0, s>>>(N, n_w, chi, L, T, nt, full);
+    sandwich_kernel<true, 1><<<n_batch * tri, 256, 0, s>>>(N, n_w, T, L, Y, nt, tri);
+  } else {
+    sandwich_kernel<false, 0><<<n_batch * full, 256, 0, s>>>(N, n_w, chi, L, T, nt, full);
+    sandwich_kernel<false, 1><<<n_batch * tri, 256, 0, s>>>(N, n_w, T, L, Y, nt, tri);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cholesky(int cplx, int N, int n_mat, double* mats, long bstride, int mode, double* out,
+                            int* status, int status_base, cudaStream_t s) {
+  if (n_mat == 0) return cudaSuccess;
+  if (cplx)
+    cholesky_kernel<true><<<n_mat, 256, 0, s>>>(N, mats, bstride, mode, out, status, status_base);
+  else
+    cholesky_kernel<false><<<n_mat, 256, 0, s>>>(N, mats, bstride, mode, out, status, status_base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_reduce(int n_q, int n_w, const double* parts, const double* w_q, const double* zeta_w,
+                                 double* eps, double* Ec, cudaStream_t s) {
+  energy_kernel<<<1, 32, 0, s>>>(n_q, n_w, parts, w_q, zeta_w, eps, Ec);
+  return cudaGetLastError();
+}
+
+}  // namespace rpa

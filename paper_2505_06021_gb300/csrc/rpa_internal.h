@@ -1,0 +1,70 @@
+// Internal declarations shared by the librpa translation units (not part of
+// the public C ABI in include/rpa.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/rpa.h"
+
+namespace rpa {
+
+// Geometry of one q-batch handed to the kernels.  All pointers are device
+// memory.  Matrices are row-major, complex data interleaved (re, im).
+struct BatchGeom {
+  int cplx;      // 1 complex128, 0 float64
+  int n_aux;     // N
+  int n_occ, n_virt, n_ov;
+  int n_k;       // k-pairs per q
+  int n_w;       // frequencies
+  int n_qb;      // q-points in this batch
+};
+
+// ---- FP64 kernels (kernels_fp64.cu) --------------------------------------
+
+// d[qb][j][w][t] = zeta_k * (-4 Delta / (Delta^2 + omega_w^2)),
+// Delta = eps_virt[kq(qb,j)][a] - eps_occ[k(qb,j)][i], t = i*n_virt + a.
+cudaError_t launch_dtab(const BatchGeom& g, const double* eps_occ, const double* eps_virt, const int* kidx,
+                        const int* kqidx, const double* omega, double zeta_k, double* dtab, cudaStream_t s);
+
+// chi[qb][w] (N x N, full Hermitian) = sum_j sum_t conj(C[qb*n_k+j][P,t]) C[..][Q,t] d[qb][j][w][t].
+cudaError_t launch_chi0_fp64(const BatchGeom& g, const double* const* Cptrs, const double* dtab, double* chi,
+                             cudaStream_t s);
+
+// In-place Cholesky of n_mat matrices (stride bstride doubles).
+//   mode 0: input Y = -Pi (lower triangle), factorises 1 + Y = 1 - Pi and writes
+//           out[2*b] = ln det(1 - Pi) = sum log1p(pivot - 1), out[2*b+1] = Tr Pi.
+//   mode 1: input V (lower triangle), writes the factor L (upper part zeroed);
+//           out may be null.
+// A non-positive pivot sets *status (if still 0) to 1 + status_base + b and
+// the matrix is abandoned.
+cudaError_t launch_cholesky(int cplx, int N, int n_mat, double* mats, long bstride, int mode, double* out,
+                            int* status, int status_base, cudaStream_t s);
+
+// T[b] = chi[b] * L[b / n_w]   (L lower triangular, N x N).
+// Y[b] = -(L[b / n_w]^H T[b]), lower triangle only.
+cudaError_t launch_sandwich(int cplx, int N, int n_batch, int n_w, const double* chi, const double* L, double* T,
+                            double* Y, cudaStream_t s);
+
+// E_c and the eps table from parts[q][w][2] = (ln det, Tr Pi):
+// eps[q][w] = ln det + Tr, e_w = sum_q w_q eps[q][w], E = (1/2pi) sum_w zeta_w e_w.
+cudaError_t launch_energy_reduce(int n_q, int n_w, const double* parts, const double* w_q, const double* zeta_w,
+                                 double* eps, double* Ec, cudaStream_t s);
+
+// ---- mixed-precision kernels (kernels_mixed.cu) ----------------------------
+
+struct MixedPlan {
+  int n_slices;       // BF16 digit slices per operand
+  int k_pad;          // padded real contraction length per q (multiple of the chunk)
+  int n_pad;          // padded row count (2 * N rounded up to 128)
+  size_t slice_bytes; // bytes of one operand slice plane set for one (q, w)
+};
+
+// Returns bytes of mixed-path workspace needed for one q and one frequency.
+size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices);
+cudaError_t launch_chi0_mixed(const BatchGeom& g, int n_slices, const double* const* Cptrs, const double* dtab,
+                              double* chi, void* work, size_t work_bytes, uint64_t* n_launch, cudaStream_t s);
+bool mixed_supported();
+
+}  // namespace rpa

@@ -1,0 +1,93 @@
+// Host runtime state of an rpa_ctx: executors (stream + workspace + pinned
+// staging), the batched-launch cache and the serving scheduler.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/rpa.h"
+
+namespace rpa {
+
+// Growable pinned host buffer.
+struct HostStage {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  bool reserve(size_t n) {
+    if (n <= bytes) return true;
+    release();
+    size_t want = n < 4096 ? 4096 : n;
+    if (cudaHostAlloc(&ptr, want, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      ptr = nullptr;
+      return false;
+    }
+    bytes = want;
+    return true;
+  }
+  void release() {
+    if (ptr) cudaFreeHost(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+};
+
+// One independent execution lane: its own streams, events, device workspace
+// and pinned host buffers.  A synchronous entry point uses the context's
+// default lane; the serving scheduler runs each admitted job on a lane of its
+// own so that jobs overlap on the device.
+struct Exec {
+  cudaStream_t s = nullptr;   // compute
+  cudaStream_t cs = nullptr;  // host -> device staging copies
+  cudaEvent_t ready[2] = {nullptr, nullptr};
+  cudaEvent_t freed[2] = {nullptr, nullptr};
+  cudaEvent_t done = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  HostStage hstage;  // uploads (tables)
+  HostStage hres;    // downloads: [int status | pad | Ec | eps[nqw] | parts[2 nqw]]
+  bool init();
+  void destroy();
+  bool ensure_ws(size_t bytes);
+  int& status_word() { return *reinterpret_cast<int*>(hres.ptr); }
+  double* results() { return reinterpret_cast<double*>(reinterpret_cast<char*>(hres.ptr) + 64); }
+};
+
+struct ServeState;  // serving.cu
+struct BatchCache;  // batch.cu
+
+}  // namespace rpa
+
+struct rpa_ctx {
+  int device = 0;
+  int n_slices = 4;
+  size_t cap = 0;
+  double timeout_s = 60.0;
+  int max_inflight = 64;
+  rpa::Exec ex;  // default lane for the synchronous entry points
+  std::atomic<uint64_t> launches{0};
+  std::mutex mu;  // serialises the synchronous entry points on this context
+  std::mutex err_mu;
+  std::string last_error;
+  rpa::ServeState* serve = nullptr;
+  rpa::BatchCache* batch = nullptr;
+};
+
+namespace rpa {
+void ctx_set_error(rpa_ctx* ctx, const char* fmt, ...);
+rpa_status validate_job(const rpa_job* j, char* msg, size_t len);
+size_t job_footprint(const rpa_job* j, int n_slices, size_t ws_cap);
+// Enqueues the whole hot path of `job` on lane `ex` (no host wait) and records
+// ex.done after the results were copied into ex.hres.
+rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_cap);
+// After ex.done has completed: decodes the device status and copies results.
+rpa_status energy_finish(rpa_ctx* ctx, Exec& ex, const rpa_job* job, double* Ec, double* eps_qw, double* parts);
+// Bounded wait for an event (RPA_E_TIMEOUT after timeout_s).
+rpa_status wait_event(rpa_ctx* ctx, cudaEvent_t ev, double timeout_s);
+void serving_shutdown(rpa_ctx* ctx);
+void batch_release(rpa_ctx* ctx);
+}  // namespace rpa

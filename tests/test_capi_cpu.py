@@ -1,0 +1,107 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds for
+sm_103a, loads, exports every entry point include/rpa.h declares, validates
+job descriptors, computes admission footprints, and fails cleanly (no crash)
+when no device is present."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2505_06021_gb300 as rpa
+from paper_2505_06021_gb300 import build as rbuild
+from paper_2505_06021_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    rbuild.build()
+    return rpa.load_library()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "rpa.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rpa_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(rpa.EXPORTS)
+
+
+class FakeTensor:
+    """Stands in for a device tensor: only its address is passed on."""
+
+    def __init__(self, addr, shape=(1,)):
+        self.addr, self.shape = addr, shape
+
+    def data_ptr(self):
+        return self.addr
+
+
+def _fake_job(p, **over):
+    t = {"C": [FakeTensor(0x10000 + 0x100 * i) for i in range(p.n_q * p.n_k)],
+         "V": [FakeTensor(0x90000 + 0x100 * i) for i in range(p.n_q)],
+         "eps_occ": FakeTensor(0x1000, p.eps_occ.shape), "eps_virt": FakeTensor(0x2000, p.eps_virt.shape)}
+    t.update(over)
+    return rpa.job_from_problem(p, t)
+
+
+def test_validate_accepts_good_jobs(lib):
+    for p in (synth.config0(), synth.config1(n_aux=32, n_occ=2, n_virt=5), synth.config2(n_aux=16, n_occ=2,
+                                                                                          n_virt=3)):
+        st, msg = _fake_job(p).validate()
+        assert st == rpa.RPA_OK, msg
+
+
+def test_validate_rejects_bad_jobs(lib):
+    p = synth.config1(n_aux=32, n_occ=2, n_virt=5)
+    j = _fake_job(p)
+    j.s.n_aux = 0
+    assert j.validate()[0] == rpa.RPA_E_INVAL
+    j = _fake_job(p)
+    j.pair_kq[3] = 10 ** 6
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "out of range" in msg
+    j = _fake_job(p)
+    j._Cp[5] = None
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "C[5]" in msg
+    j = _fake_job(p)
+    j.s.prec = 9
+    assert j.validate()[0] == rpa.RPA_E_INVAL
+    j = _fake_job(p)
+    j.omega[2] = float("nan")
+    assert j.validate()[0] == rpa.RPA_E_INVAL
+    # real data is Gamma-only
+    j = _fake_job(p)
+    j.s.is_complex = 0
+    assert j.validate()[0] == rpa.RPA_E_INVAL
+
+
+def test_footprint_grows_with_size(lib):
+    a = _fake_job(synth.config1(n_aux=64, n_occ=2, n_virt=5)).footprint()
+    b = _fake_job(synth.config1(n_aux=128, n_occ=2, n_virt=5)).footprint()
+    assert 0 < a < b
+    c1 = _fake_job(synth.config1()).footprint()
+    # device-resident C of the 2-D periodic workload alone is 15.0 GB
+    assert c1 > 15.0e9
+
+
+def test_create_without_device_fails_cleanly(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    cfg = rpa.rpa_config(0, 0, 0, 0.0, 0)
+    st = lib.rpa_create(ctypes.byref(cfg), ctypes.byref(h))
+    assert st == rpa.RPA_E_CUDA
+    assert b"device" in lib.rpa_last_error(None)
