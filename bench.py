@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the RPA hot path on GB300.
+
+A step is one whole RPA correlation-energy job of the 2-D periodic workload
+(complex128, 4x4x1 k- and q-grids = 16 q x 16 k, N_aux = 512, N_occ = 32,
+N_virt = 224, 20 imaginary frequencies): chi0 for every (q, omega), the
+sandwich, the Cholesky log-det and the quadrature, through the C ABI
+(rpa_energy) with inputs resident in HBM.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|mixed]
+    python bench.py --impl reference ...   # the CPU oracle as reference arm
+
+Under torchrun (N > 1) every rank runs its own job on its own GPU (weak
+scaling, no collective on the data path); rank 0 prints.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "χ0 TFLOP/s & E_c jobs/s, mixed vs FP64 at |ΔE_c|≤1µHa; p50/p99 job latency"
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.259
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--n-q", type=int, default=0, help="profiling only: restrict the job to its first n q-points")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+def workload(n_q=0):
+    from paper_2505_06021_gb300 import synth
+
+    p = synth.config1()
+    if n_q:
+        g = p.grid
+        g.pair_k, g.pair_kq, g.w_q = g.pair_k[:n_q], g.pair_kq[:n_q], g.w_q[:n_q]
+        g.qpts = g.qpts[:n_q]
+    return p
+
+
+def config_of(p, prec, n_q_override):
+    return {
+        "workload": "periodic2d-c128: 2-D periodic, complex128, 4x4x1 k and q grids (16 q x 16 k pairs), "
+                    "N_aux=%d, N_occ=%d, N_virt=%d, %d imaginary frequencies" % (p.n_aux, p.n_occ, p.n_virt, p.n_w)
+                    + ("" if not n_q_override else " [first %d q only: profiling case]" % n_q_override),
+        "n_q": p.n_q, "n_k": p.n_k, "n_aux": p.n_aux, "n_occ": p.n_occ, "n_virt": p.n_virt, "n_w": p.n_w,
+        "chi0_prec": prec,
+        "l2": "inputs larger than L2 (C alone is %.1f GB per job vs 129 MB L2)" % (p.c_bytes() / 1e9),
+        "parallelism": "one job per GPU (weak scaling)",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(pw) if pw else None}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(p, q=0, w=0):
+    """Times the oracle as it stands on the host cores on one (q, omega) term
+    plus the V(q)^(1/2) it needs; returns seconds for each and the threads."""
+    import oracle
+
+    nthr = oracle.max_threads()
+    V = p.V(q)
+    t0 = time.perf_counter()
+    Vh = oracle.vhalf(V)
+    t1 = time.perf_counter()
+    C = [p.C(q, j) for j in range(p.n_k)]
+    t2 = time.perf_counter()
+    oracle.term(p, q, w, Vh=Vh, C_blocks=C)
+    t3 = time.perf_counter()
+    return {"vhalf_s": t1 - t0, "term_s": t3 - t2, "threads": nthr}
+
+
+def oracle_jobs_per_s(p, s):
+    job_s = p.n_q * s["vhalf_s"] + p.n_q * p.n_w * s["term_s"]
+    return 1.0 / job_s, job_s
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch of `kernel_key` from the committed ncu summary,
+    valid only while the kernel source is unchanged (hash recorded)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_2505_06021_gb300", "csrc")
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") != kernel_key:
+            continue
+        h = hashlib.sha256(open(os.path.join(src, f["source"]), "rb").read()).hexdigest()[:16]
+        if h != f.get("sha"):
+            return None
+        return float(f["bytes_per_launch_full"])
+    return None
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = workload()
+    import oracle
+
+    oracle.build()
+    from paper_2505_06021_gb300 import synth
+
+    # warm-up steps touch the same code paths on the small Gamma-only case
+    for i in range(args.warmup):
+        cpu_oracle_sample(synth.config0(), q=0, w=i % 16)
+    times = [cpu_oracle_sample(p, q=(5 * i) % p.n_q, w=(7 * i) % p.n_w) for i in range(args.steps)]
+    vh = statistics.median(t["vhalf_s"] for t in times)
+    tm = statistics.median(t["term_s"] for t in times)
+    val, job_s = oracle_jobs_per_s(p, {"vhalf_s": vh, "term_s": tm})
+    sample = ("per step one (q, omega) term of the job (chi0 + V^1/2 sandwich + Cholesky log-det) plus the "
+              "V(q)^1/2 Jacobi it needs; job time extrapolated as n_q*T_vhalf + n_q*n_w*T_term")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "jobs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * (vh + tm),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded, shapes of the paper's periodic workloads)",
+            "config": config_of(p, "fp64", 0),
+            "cpu_baseline": {"value": val, "unit": "jobs/s", "cores": times[0]["threads"], "kind": "oracle",
+                             "sample": sample, "extrapolated_job_s": job_s, "vhalf_s": vh, "term_s": tm},
+            "e2e": {"value": val, "unit": "jobs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    import paper_2505_06021_gb300 as rpa
+
+    prec = args.prec
+    if prec == "auto":
+        prec = "mixed" if rpa_mixed_available() else "fp64"
+    pc = rpa.PREC_MIXED if prec == "mixed" else rpa.PREC_FP64
+    p = workload(args.n_q)
+    t_gen = time.perf_counter()
+    tens = rpa.upload_problem(p, "cuda:%d" % local)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    job = rpa.job_from_problem(p, tens, prec=pc)
+    ctx = rpa.Context(local)
+    for _ in range(args.warmup):
+        ctx.energy(job)
+    ext = torch.cuda.ExternalStream(ctx.stream_handle)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.profile(True)
+    n0 = ctx.launches
+    e0.record(ext)
+    res = None
+    for _ in range(args.steps):
+        res = ctx.energy(job)
+    e1.record(ext)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.launches - n0
+    ms = e0.elapsed_time(e1)
+    ms_max = allreduce_max(ms, world)
+    jobs_per_s = world * args.steps / (ms_max / 1e3)
+    chi0_flops_job = p.chi0_flops()
+
+    # dominant kernel: chi0 (one launch per q-batch in the FP64 path)
+    chi_ms, chi_n = prof["chi0"]
+    chi_launch_ms = chi_ms / max(chi_n, 1)
+    flops_per_launch = chi0_flops_job * args.steps / max(chi_n, 1)
+    achieved = flops_per_launch / (chi_launch_ms / 1e3) / 1e12
+    if prec == "fp64":
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_for("chi0_fp64"),
+                "kernel": "chi0_fp64_kernel", "peak_source": "derived FP64 DFMA peak: 152 SMs x 2 DFMA/clk x "
+                "2 flop x 2.07 GHz (microbenchmark measured 1.205 TFLOP/s)",
+                "note": "achieved counts the algorithmic Hermitian lower-triangle flops 4N(N+1)N_ov per (q,k,w); "
+                        "the kernel forms conj(C_P)C_Q once per t and reuses it over a group of frequencies, so "
+                        "it executes fewer FP64 instructions than the algorithmic count"}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        tensor_flops = rpa_mixed_tensor_flops(p, ctx)
+        ach_t = tensor_flops * args.steps / max(chi_n, 1) / (chi_launch_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach_t, "peak": peak, "unit": "TFLOP/s", "frac": ach_t / peak,
+                "traffic": traffic_for("chi0_mixed"), "kernel": "chi0 tcgen05 sliced",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                "algorithmic_fp64_equiv_tflops": achieved}
+    kernel_ms = {k: {"ms": v[0] / args.steps, "launches": v[1] // max(args.steps, 1)} for k, v in prof.items()
+                 if v[1]}
+    line = {"metric": METRIC, "value": jobs_per_s, "unit": "jobs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "bf16-slices->f64",
+            "data": "synthetic (seeded, shapes of the paper's periodic workloads; no public data)",
+            "config": config_of(p, prec, args.n_q),
+            "chi0_tflops": chi0_flops_job * world * args.steps / (ms_max / 1e3) / 1e12,
+            "chi0_tflops_kernel": achieved, "Ec": res["Ec"], "gpu_launches": launches,
+            "kernel_ms_per_step": kernel_ms, "roofline": roof, "clocks": clk, "input_gen_s": t_gen}
+
+    # end to end through the public API with HOST buffers (pinned), copies inside
+    if not args.no_e2e and not args.n_q:
+        del job
+        for t in tens["C"]:
+            t.data = torch.empty(0, device=t.device)
+        tens = None
+        torch.cuda.empty_cache()
+        th = rpa.upload_problem(p, "cpu", pin=True)
+        jh = rpa.job_from_problem(p, th, prec=pc, mem=rpa.MEM_HOST)
+        ctx.energy(jh)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            rh = ctx.energy(jh)
+        torch.cuda.synchronize()
+        te = allreduce_max(time.perf_counter() - t0, world)
+        h2d = sum(t.numel() * t.element_size() for t in th["C"] + th["V"]) + 8 * (th["eps_occ"].numel() +
+                                                                                    th["eps_virt"].numel())
+        nqw = p.n_q * p.n_w
+        line["e2e"] = {"value": world * args.e2e_steps / te, "unit": "jobs/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": 8 * (1 + 3 * nqw) + 4, "steps": args.e2e_steps,
+                       "Ec_matches_device": bool(rh["Ec"] == res["Ec"])}
+        del th, jh
+    else:
+        line["e2e"] = None
+
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        s = cpu_oracle_sample(p)
+        v, job_s = oracle_jobs_per_s(p, s)
+        line["cpu_baseline"] = {"value": v, "unit": "jobs/s", "cores": s["threads"], "kind": "oracle",
+                                "sample": "one (q=0, w=0) term (chi0 + V^1/2 sandwich + Cholesky log-det, OpenMP "
+                                          "over rows) plus one V(q)^1/2 Jacobi; job time extrapolated as "
+                                          "n_q*T_vhalf + n_q*n_w*T_term", "extrapolated_job_s": job_s,
+                                "vhalf_s": s["vhalf_s"], "term_s": s["term_s"]}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def rpa_mixed_available():
+    try:
+        import paper_2505_06021_gb300 as rpa
+
+        return bool(getattr(rpa, "mixed_available", lambda: False)())
+    except Exception:
+        return False
+
+
+def rpa_mixed_tensor_flops(p, ctx):
+    import paper_2505_06021_gb300 as rpa
+
+    return rpa.mixed_tensor_flops(p, ctx)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

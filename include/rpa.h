@@ -171,6 +171,26 @@ rpa_status rpa_serving_stats(rpa_ctx *ctx, uint64_t *jobs_done, double *lat_mean
 /* Number of kernels this context has launched so far (all entry points). */
 uint64_t rpa_kernel_launches(const rpa_ctx *ctx);
 
+/* The context's own compute stream (a cudaStream_t) used by rpa_energy and
+ * rpa_energy_batch; callers may record CUDA events on it. */
+void *rpa_stream(rpa_ctx *ctx);
+
+/* Per-kernel device timing (tracing).  rpa_profile(ctx, 1) resets and turns on
+ * CUDA-event timing around every kernel the synchronous entry points launch
+ * (events recorded on the launching stream); rpa_profile(ctx, 0) turns it off.
+ * rpa_profile_read fills ms[RPA_K_COUNT] (summed device milliseconds) and
+ * launches[RPA_K_COUNT] (kernel launches) per kernel class. */
+#define RPA_K_DTAB 0     /* frequency-weight table */
+#define RPA_K_CHI0 1     /* chi0 contraction (FP64 or tensor-core) */
+#define RPA_K_VFACTOR 2  /* Cholesky factor of V(q) */
+#define RPA_K_SANDWICH 3 /* Pi = L^H chi0 L (two passes) */
+#define RPA_K_LOGDET 4   /* Cholesky of 1 - Pi, ln det, Tr */
+#define RPA_K_REDUCE 5   /* quadrature */
+#define RPA_K_SLICE 6    /* operand slicing of the split-precision path */
+#define RPA_K_COUNT 8
+rpa_status rpa_profile(rpa_ctx *ctx, int enable);
+rpa_status rpa_profile_read(rpa_ctx *ctx, double *ms, uint64_t *launches);
+
 #ifdef __cplusplus
 }
 #endif

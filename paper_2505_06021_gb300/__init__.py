@@ -26,7 +26,10 @@ STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "NOMEM", 3: "CUDA", 4: "NOTPD", 5: "TIME
 # Entry points declared in include/rpa.h
 EXPORTS = ("rpa_create", "rpa_destroy", "rpa_last_error", "rpa_job_validate", "rpa_job_footprint", "rpa_chi0",
            "rpa_logdet", "rpa_energy", "rpa_energy_batch", "rpa_submit", "rpa_poll", "rpa_wait",
-           "rpa_serving_stats", "rpa_kernel_launches")
+           "rpa_serving_stats", "rpa_kernel_launches", "rpa_stream", "rpa_profile", "rpa_profile_read")
+
+# kernel classes of rpa_profile_read
+KERNEL_CLASSES = ("dtab", "chi0", "vfactor", "sandwich", "logdet", "reduce", "slice", "spare")
 
 
 class RpaError(RuntimeError):
@@ -80,6 +83,9 @@ def load_library(path: str = LIB_PATH):
         "rpa_wait": (I, [P, u64, D, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "rpa_serving_stats": (I, [P, ctypes.POINTER(u64)] + [ctypes.POINTER(D)] * 5),
         "rpa_kernel_launches": (u64, [P]),
+        "rpa_stream": (P, [P]),
+        "rpa_profile": (I, [P, I]),
+        "rpa_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(u64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -166,25 +172,47 @@ def job_from_problem(problem, tensors: Dict[str, object], prec: int = PREC_FP64,
                V=tensors["V"], prec=prec, mem=mem)
 
 
-def upload_problem(problem, device="cuda", qs: Optional[Sequence[int]] = None, pin: bool = False):
+def upload_problem(problem, device="cuda", qs: Optional[Sequence[int]] = None, pin: bool = False,
+                   threads: int = 0):
     """Materialise a synthetic problem's inputs as torch tensors on `device`
-    (or pinned host memory with device='cpu', pin=True)."""
+    (a CUDA device, or host memory with device='cpu'; pinned with pin=True).
+    Blocks are generated by a thread pool (each block has its own seeded
+    stream, so the result does not depend on the thread count)."""
+    import concurrent.futures as cf
+
     import torch
 
     dt = torch.complex128 if problem.is_complex else torch.float64
+    npdt = np.complex128 if problem.is_complex else np.float64
     qs = list(range(problem.n_q)) if qs is None else list(qs)
+    on_host = str(device) == "cpu"
+    dev = None if on_host else torch.device(device)
+    if dev is not None and dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
 
     def put(a):
         t = torch.from_numpy(np.ascontiguousarray(a))
-        if device == "cpu":
+        if on_host:
             return t.pin_memory() if pin else t
-        return t.to(device)
+        return t.to(dev)
 
-    C = [put(problem.C(q, j)) for q in qs for j in range(problem.n_k)]
-    V = [put(problem.V(q)) for q in qs]
+    def make_c(qj):
+        q, j = qj
+        if on_host:
+            t = torch.empty((problem.n_aux, problem.n_ov), dtype=dt, pin_memory=pin)
+            problem.C(q, j, out=t.numpy())
+            return t
+        h = np.empty((problem.n_aux, problem.n_ov), npdt)
+        problem.C(q, j, out=h)
+        return torch.from_numpy(h).to(dev)
+
+    blocks = [(q, j) for q in qs for j in range(problem.n_k)]
+    nthr = threads or min(16, os.cpu_count() or 4)
+    with cf.ThreadPoolExecutor(nthr) as ex:
+        C = list(ex.map(make_c, blocks))
+        V = list(ex.map(lambda q: put(problem.V(q)), qs))
     eo = put(problem.eps_occ.astype(np.float64))
     ev = put(problem.eps_virt.astype(np.float64))
-    assert all(c.dtype == dt for c in C)
     return {"C": C, "V": V, "eps_occ": eo, "eps_virt": ev}
 
 
@@ -225,6 +253,20 @@ class Context:
     @property
     def launches(self) -> int:
         return int(self.lib.rpa_kernel_launches(self.h))
+
+    @property
+    def stream_handle(self) -> int:
+        """cudaStream_t of the context's compute stream (rpa_energy runs there)."""
+        return int(self.lib.rpa_stream(self.h) or 0)
+
+    def profile(self, enable: bool = True):
+        self._check(self.lib.rpa_profile(self.h, int(enable)))
+
+    def profile_read(self) -> Dict[str, Tuple[float, int]]:
+        ms = (ctypes.c_double * 8)()
+        n = (ctypes.c_uint64 * 8)()
+        self._check(self.lib.rpa_profile_read(self.h, ms, n))
+        return {k: (ms[i], int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
     def chi0(self, job: Job, q: int, out=None, stream=None):
         import torch

@@ -68,6 +68,13 @@ void Exec::destroy() {
     if (freed[i]) cudaEventDestroy(freed[i]);
   }
   if (done) cudaEventDestroy(done);
+  for (Mark& m : marks) {
+    if (m.a) ev_pool.push_back(m.a);
+    if (m.b) ev_pool.push_back(m.b);
+  }
+  marks.clear();
+  for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  ev_pool.clear();
   s = cs = nullptr;
   done = nullptr;
   hstage.release();
@@ -110,6 +117,50 @@ rpa_status wait_event(rpa_ctx* ctx, cudaEvent_t ev, double timeout_s) {
     }
     if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(spins > 1000 ? 200 : 20));
   }
+}
+
+// ------------------------------------------------------------- tracing ----
+
+cudaEvent_t Exec::take_event() {
+  if (!ev_pool.empty()) {
+    cudaEvent_t e = ev_pool.back();
+    ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void prof_begin(rpa_ctx* ctx, Exec* ex, cudaStream_t s) {
+  if (!ctx->prof || !ex) return;
+  Exec::Mark m{-1, 0, ex->take_event(), nullptr};
+  if (m.a) cudaEventRecord(m.a, s);
+  ex->marks.push_back(m);
+}
+
+void prof_end(rpa_ctx* ctx, Exec* ex, cudaStream_t s, int cls, int n_kernels) {
+  if (!ctx->prof || !ex || ex->marks.empty()) return;
+  Exec::Mark& m = ex->marks.back();
+  m.cls = cls;
+  m.n = n_kernels;
+  m.b = ex->take_event();
+  if (m.b) cudaEventRecord(m.b, s);
+}
+
+void prof_collect(rpa_ctx* ctx, Exec* ex) {
+  if (!ex) return;
+  for (Exec::Mark& m : ex->marks) {
+    float ms = 0.f;
+    if (m.a && m.b && m.cls >= 0 && cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+      ctx->prof_ms[m.cls] += ms;
+      ctx->prof_n[m.cls] += m.n;
+    }
+    cudaGetLastError();
+    if (m.a) ex->ev_pool.push_back(m.a);
+    if (m.b) ex->ev_pool.push_back(m.b);
+  }
+  ex->marks.clear();
 }
 
 // ------------------------------------------------------------ validation --
@@ -311,15 +362,17 @@ static rpa_status upload_tables(rpa_ctx* ctx, Exec& ex, const rpa_job* j, const 
 
 // Hot path for q in [q0, q0+nq).  Device tables are indexed by q*n_k + j;
 // V of the batch at Vdev[0..nq).  chi_user: write chi0 there and stop.
-static rpa_status run_qbatch(rpa_ctx* ctx, const rpa_job* j, const Bufs& b, int q0, int nq,
+static rpa_status run_qbatch(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
                              const void* const* Vdev, const double* eps_occ, const double* eps_virt, cudaStream_t s,
                              double* chi_user, int n_slices) {
   const int nk = j->n_k;
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
   BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, j->n_occ * j->n_virt, nk, j->n_w, nq};
+  prof_begin(ctx, pex, s);
   CK(launch_dtab(g, eps_occ, eps_virt, b.kidx + (size_t)q0 * nk, b.kqidx + (size_t)q0 * nk, b.omega, j->zeta_k,
                  b.dtab, s));
+  prof_end(ctx, pex, s, RPA_K_DTAB, 1);
   ctx->launches++;
   double* chi = chi_user ? chi_user : b.chi;
   if (j->prec == RPA_PREC_MIXED) {
@@ -327,28 +380,38 @@ static rpa_status run_qbatch(rpa_ctx* ctx, const rpa_job* j, const Bufs& b, int 
       BatchGeom g1 = g;
       g1.n_qb = 1;
       uint64_t nl = 0;
+      prof_begin(ctx, pex, s);
       CK(launch_chi0_mixed(g1, n_slices, (const double* const*)(b.Cptrs + (size_t)(q0 + qi) * nk),
                            b.dtab + (size_t)qi * nk * j->n_w * g.n_ov, chi + (size_t)qi * j->n_w * NN * (es / 8),
-                           b.mixed, b.mixed_bytes, &nl, s));
+                           b.mixed, b.mixed_bytes, b.status, &nl, s));
+      prof_end(ctx, pex, s, RPA_K_CHI0, (int)nl);
       ctx->launches += nl;
     }
   } else {
+    prof_begin(ctx, pex, s);
     CK(launch_chi0_fp64(g, (const double* const*)(b.Cptrs + (size_t)q0 * nk), b.dtab, chi, s));
+    prof_end(ctx, pex, s, RPA_K_CHI0, 1);
     ctx->launches++;
   }
   if (chi_user) return RPA_OK;
   // V(q) -> L, the lower Cholesky factor (V = L L^H), one matrix per q
   for (int qi = 0; qi < nq; ++qi)
     CK(cudaMemcpyAsync(b.L + qi * NN * (es / 8), Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
+  prof_begin(ctx, pex, s);
   CK(launch_cholesky(j->is_complex, j->n_aux, nq, b.L, (long)(NN * (es / 8)), 1, nullptr, b.status, (1 << 29) + q0,
                      s));
+  prof_end(ctx, pex, s, RPA_K_VFACTOR, 1);
   ctx->launches++;
   // Y = -(L^H chi L) (lower triangle), overwriting chi's storage
+  prof_begin(ctx, pex, s);
   CK(launch_sandwich(j->is_complex, j->n_aux, nq * j->n_w, j->n_w, chi, b.L, b.T, b.chi, s));
+  prof_end(ctx, pex, s, RPA_K_SANDWICH, 2);
   ctx->launches += 2;
   // 1 - Pi' = 1 + Y: Cholesky, ln det, Tr
+  prof_begin(ctx, pex, s);
   CK(launch_cholesky(j->is_complex, j->n_aux, nq * j->n_w, b.chi, (long)(NN * (es / 8)), 0,
                      b.parts + (size_t)2 * q0 * j->n_w, b.status, q0 * j->n_w, s));
+  prof_end(ctx, pex, s, RPA_K_LOGDET, 1);
   ctx->launches++;
   return RPA_OK;
 }
@@ -356,6 +419,10 @@ static rpa_status run_qbatch(rpa_ctx* ctx, const rpa_job* j, const Bufs& b, int 
 static rpa_status decode_status(rpa_ctx* ctx, int st, int n_w) {
   if (st == 0) return RPA_OK;
   const int code = st - 1;
+  if (code >= (1 << 30)) {
+    ctx_set_error(ctx, "tensor-core chi0 kernel gave up waiting (code %d)", code - (1 << 30));
+    return RPA_E_TIMEOUT;
+  }
   if (code >= (1 << 29))
     ctx_set_error(ctx, "V(q=%d) is not positive definite", code - (1 << 29));
   else
@@ -430,14 +497,17 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
   for (int bi = 0; bi < nbatch; ++bi) {
     const int q0 = bi * qb, nq = std::min(qb, job->n_q - q0), slot = bi % 2;
     if (host) CK(cudaStreamWaitEvent(s, ex.ready[slot], 0));
-    if (rpa_status st = run_qbatch(ctx, job, b, q0, nq, vp.data() + q0, eo, ev, s, nullptr, ctx->n_slices)) return st;
+    if (rpa_status st = run_qbatch(ctx, &ex, job, b, q0, nq, vp.data() + q0, eo, ev, s, nullptr, ctx->n_slices))
+      return st;
     if (host) {
       CK(cudaEventRecord(ex.freed[slot], s));
       if (bi + 2 < nbatch)
         if (rpa_status st2 = issue_copy(bi + 2)) return st2;
     }
   }
+  prof_begin(ctx, &ex, s);
   CK(launch_energy_reduce(job->n_q, job->n_w, b.parts, b.w_q, b.zeta_w, b.eps, b.Ec, s));
+  prof_end(ctx, &ex, s, RPA_K_REDUCE, 1);
   ctx->launches++;
   if (!ex.hres.reserve(64 + sizeof(double) * (3 * nqw + 1))) {
     ctx_set_error(ctx, "cannot allocate pinned result buffer");
@@ -451,6 +521,7 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
 
 rpa_status energy_finish(rpa_ctx* ctx, Exec& ex, const rpa_job* job, double* Ec, double* eps_qw, double* parts) {
   const size_t nqw = (size_t)job->n_q * job->n_w;
+  prof_collect(ctx, &ex);
   if (rpa_status st = decode_status(ctx, ex.status_word(), job->n_w)) return st;
   const double* r = ex.results();
   if (Ec) *Ec = r[0];
@@ -533,6 +604,29 @@ rpa_status rpa_job_footprint(const rpa_job* job, size_t* bytes) {
 
 uint64_t rpa_kernel_launches(const rpa_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
 
+void* rpa_stream(rpa_ctx* ctx) { return ctx ? (void*)ctx->ex.s : nullptr; }
+
+rpa_status rpa_profile(rpa_ctx* ctx, int enable) {
+  if (!ctx) return RPA_E_INVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->prof = enable != 0;
+  for (int i = 0; i < RPA_K_COUNT; ++i) {
+    ctx->prof_ms[i] = 0.0;
+    ctx->prof_n[i] = 0;
+  }
+  return RPA_OK;
+}
+
+rpa_status rpa_profile_read(rpa_ctx* ctx, double* ms, uint64_t* launches) {
+  if (!ctx) return RPA_E_INVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  for (int i = 0; i < RPA_K_COUNT; ++i) {
+    if (ms) ms[i] = ctx->prof_ms[i];
+    if (launches) launches[i] = ctx->prof_n[i];
+  }
+  return RPA_OK;
+}
+
 rpa_status rpa_chi0(rpa_ctx* ctx, const rpa_job* job, int q, void* chi_out, void* stream) {
   if (!ctx) return RPA_E_INVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -566,12 +660,14 @@ rpa_status rpa_chi0(rpa_ctx* ctx, const rpa_job* job, int q, void* chi_out, void
   if (rpa_status st0 = upload_tables(ctx, ex, job, b, job->C)) return st0;
   CK(cudaEventRecord(ex.done, ex.s));
   CK(cudaStreamWaitEvent(s, ex.done, 0));
-  if (rpa_status st = run_qbatch(ctx, job, b, q, 1, job->V + q, job->eps_occ, job->eps_virt, s, (double*)chi_out,
-                                 ctx->n_slices))
+  if (rpa_status st = run_qbatch(ctx, &ex, job, b, q, 1, job->V + q, job->eps_occ, job->eps_virt, s,
+                                 (double*)chi_out, ctx->n_slices))
     return st;
   // the d table in the workspace is reused by the next call on this context
   CK(cudaEventRecord(ex.done, s));
-  return wait_event(ctx, ex.done, ctx->timeout_s);
+  rpa_status wst = wait_event(ctx, ex.done, ctx->timeout_s + 600.0);
+  prof_collect(ctx, &ex);
+  return wst;
 }
 
 rpa_status rpa_logdet(rpa_ctx* ctx, const rpa_job* job, int q, const void* chi, double* out, void* stream) {
@@ -601,17 +697,24 @@ rpa_status rpa_logdet(rpa_ctx* ctx, const rpa_job* job, int q, const void* chi, 
   const size_t NN = (size_t)job->n_aux * job->n_aux;
   CK(cudaMemsetAsync(b.status, 0, sizeof(int), s));
   CK(cudaMemcpyAsync(b.L, job->V[q], es * NN, cudaMemcpyDeviceToDevice, s));
+  prof_begin(ctx, &ex, s);
   CK(launch_cholesky(job->is_complex, job->n_aux, 1, b.L, (long)(NN * (es / 8)), 1, nullptr, b.status,
                      (1 << 29) + q, s));
+  prof_end(ctx, &ex, s, RPA_K_VFACTOR, 1);
+  prof_begin(ctx, &ex, s);
   CK(launch_sandwich(job->is_complex, job->n_aux, job->n_w, job->n_w, (const double*)chi, b.L, b.T, b.chi, s));
+  prof_end(ctx, &ex, s, RPA_K_SANDWICH, 2);
+  prof_begin(ctx, &ex, s);
   CK(launch_cholesky(job->is_complex, job->n_aux, job->n_w, b.chi, (long)(NN * (es / 8)), 0, b.parts, b.status, 0,
                      s));
+  prof_end(ctx, &ex, s, RPA_K_LOGDET, 1);
   ctx->launches += 4;
   if (!ex.hres.reserve(64 + sizeof(double) * 2 * job->n_w)) return RPA_E_NOMEM;
   CK(cudaMemcpyAsync(ex.results(), b.parts, sizeof(double) * 2 * job->n_w, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&ex.status_word(), b.status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaEventRecord(ex.done, s));
-  if (rpa_status st = wait_event(ctx, ex.done, ctx->timeout_s)) return st;
+  if (rpa_status st = wait_event(ctx, ex.done, ctx->timeout_s + 600.0)) return st;
+  prof_collect(ctx, &ex);
   const int sw = ex.status_word();
   if (sw) {
     const int code = sw - 1;

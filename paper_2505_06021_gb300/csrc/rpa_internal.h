@@ -54,17 +54,13 @@ cudaError_t launch_energy_reduce(int n_q, int n_w, const double* parts, const do
 
 // ---- mixed-precision kernels (kernels_mixed.cu) ----------------------------
 
-struct MixedPlan {
-  int n_slices;       // BF16 digit slices per operand
-  int k_pad;          // padded real contraction length per q (multiple of the chunk)
-  int n_pad;          // padded row count (2 * N rounded up to 128)
-  size_t slice_bytes; // bytes of one operand slice plane set for one (q, w)
-};
-
 // Returns bytes of mixed-path workspace needed for one q and one frequency.
 size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices);
+// chi0 of one q for all frequencies on the tensor cores (split precision);
+// `dtab` is the FP64 weight table of this q; a device time-out sets *status.
 cudaError_t launch_chi0_mixed(const BatchGeom& g, int n_slices, const double* const* Cptrs, const double* dtab,
-                              double* chi, void* work, size_t work_bytes, uint64_t* n_launch, cudaStream_t s);
+                              double* chi, void* work, size_t work_bytes, int* status, uint64_t* n_launch,
+                              cudaStream_t s);
 bool mixed_supported();
 
 }  // namespace rpa

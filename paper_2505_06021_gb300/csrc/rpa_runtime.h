@@ -48,6 +48,14 @@ struct Exec {
   cudaEvent_t done = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // per-kernel timing: (class, start, end) recorded on the launching stream
+  struct Mark {
+    int cls, n;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> ev_pool;
+  cudaEvent_t take_event();
   HostStage hstage;  // uploads (tables)
   HostStage hres;    // downloads: [int status | pad | Ec | eps[nqw] | parts[2 nqw]]
   bool init();
@@ -75,6 +83,9 @@ struct rpa_ctx {
   std::string last_error;
   rpa::ServeState* serve = nullptr;
   rpa::BatchCache* batch = nullptr;
+  bool prof = false;
+  double prof_ms[RPA_K_COUNT] = {0};
+  uint64_t prof_n[RPA_K_COUNT] = {0};
 };
 
 namespace rpa {
@@ -88,6 +99,12 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
 rpa_status energy_finish(rpa_ctx* ctx, Exec& ex, const rpa_job* job, double* Ec, double* eps_qw, double* parts);
 // Bounded wait for an event (RPA_E_TIMEOUT after timeout_s).
 rpa_status wait_event(rpa_ctx* ctx, cudaEvent_t ev, double timeout_s);
+// Timing marks around kernel launches (no-ops when profiling is off or ex is
+// null); prof_collect adds the elapsed times of completed marks to the
+// context's totals and recycles the events.
+void prof_begin(rpa_ctx* ctx, Exec* ex, cudaStream_t s);
+void prof_end(rpa_ctx* ctx, Exec* ex, cudaStream_t s, int cls, int n_kernels);
+void prof_collect(rpa_ctx* ctx, Exec* ex);
 void serving_shutdown(rpa_ctx* ctx);
 void batch_release(rpa_ctx* ctx);
 }  // namespace rpa

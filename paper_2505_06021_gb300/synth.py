@@ -229,21 +229,18 @@ class Problem:
     def dtype(self):
         return np.complex128 if self.is_complex else np.float64
 
-    def C(self, q: int, j: int) -> np.ndarray:
+    def C(self, q: int, j: int, out: Optional[np.ndarray] = None) -> np.ndarray:
         """Fit coefficients C_{P,ia}(q, k_j): [n_aux, n_occ*n_virt], row-major
-        with the pair index t = i*n_virt + a contiguous."""
+        with the pair index t = i*n_virt + a contiguous.  `out` (optional, C
+        contiguous, right shape and dtype) receives the block in place."""
         rng = _rng(self.seed, "C", q, j)
         shape = (self.n_aux, self.n_ov)
-        if self.is_complex:
-            s = math.sqrt(0.5 / self.n_ov)
-            out = np.empty(shape, np.complex128)
-            v = out.view(np.float64)
-            rng.standard_normal(out=v, dtype=np.float64)
-            v *= s
-            return out
-        out = np.empty(shape, np.float64)
-        rng.standard_normal(out=out, dtype=np.float64)
-        out *= 1.0 / math.sqrt(self.n_ov)
+        if out is None:
+            out = np.empty(shape, self.dtype)
+        assert out.shape == shape and out.dtype == self.dtype and out.flags.c_contiguous
+        v = out.view(np.float64)
+        rng.standard_normal(out=v, dtype=np.float64)
+        v *= math.sqrt(0.5 / self.n_ov) if self.is_complex else 1.0 / math.sqrt(self.n_ov)
         return out
 
     def V_eig(self, q: int) -> Tuple[np.ndarray, np.ndarray]:
