@@ -178,8 +178,9 @@ __device__ __forceinline__ int fixed_point(double c, double w, int e) {
   const unsigned long long mc = (((cb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) + (1ull << 22)) >> 23;  // <= 2^30
   const unsigned long long mw = (((wb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) + (1ull << 22)) >> 23;
   const unsigned long long p = mc * mw;  // <= 2^60
-  const int sh = e + 2073 - Ec - Ew;
+  const int sh = e + 2073 - Ec - Ew;  // >= 30 by the choice of e
   if (sh >= 62) return 0;
+  if (sh < 30) return 0;  // unreachable when e bounds the row
   const int F = (int)((p + (1ull << (sh - 1))) >> sh);
   return (cb >> 63) ? -F : F;
 }
@@ -624,7 +625,7 @@ MixedLayout mixed_layout(const BatchGeom& g, int s, int sms) {
 
 bool mixed_supported() { return get_encode() != nullptr; }
 
-size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices) { return mixed_layout(g, n_slices, 160).total; }
+size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices) { return mixed_layout(g, n_slices, num_sms()).total; }
 
 cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cptrs, const double* dtab,
                               double* chi, void* work, size_t work_bytes, int* status, uint64_t* n_launch,
