@@ -191,6 +191,28 @@ void *rpa_stream(rpa_ctx *ctx);
 rpa_status rpa_profile(rpa_ctx *ctx, int enable);
 rpa_status rpa_profile_read(rpa_ctx *ctx, double *ms, uint64_t *launches);
 
+/* The log-det step (A4-A6) for callers that cannot allocate device memory at
+ * call time - e.g. code embedded in a framework that owns all GPU memory
+ * through its own pool, or latency-critical loops that cannot afford the
+ * device-wide synchronisation of cudaMalloc/cudaFree.  The paper has no
+ * counterpart; this is an interface convenience.
+ *
+ * Same results as rpa_logdet for one q, without a context: V (device,
+ * n_aux x n_aux, Hermitian positive definite) and chi (device, n_w x n_aux x
+ * n_aux, as written by rpa_chi0) are inputs; out (DEVICE, n_w x 2) receives
+ * (ln det(1 - Pi), Tr Pi) per frequency.  Scratch is a fixed static device
+ * array of 7,078,144 bytes that every GPU loading the library holds until
+ * exit; nothing is allocated.  n_aux > 384 is rejected with RPA_E_INVAL.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current): make that first call before any stream
+ * capture.  All calls share the array, so calls whose work overlaps on the GPU
+ * (other streams or threads on the same device) race; serialise them.  The
+ * call synchronises `stream` and returns RPA_E_NOTPD / RPA_E_CUDA / RPA_E_INVAL
+ * with a message in rpa_noalloc_last_error() (per host thread). */
+rpa_status rpa_logdet_noalloc(int is_complex, int n_aux, int n_w, const void *V, const void *chi, double *out,
+                              void *stream);
+const char *rpa_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

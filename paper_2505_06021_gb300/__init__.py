@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "NOMEM", 3: "CUDA", 4: "NOTPD", 5: "TIME
 # Entry points declared in include/rpa.h
 EXPORTS = ("rpa_create", "rpa_destroy", "rpa_last_error", "rpa_job_validate", "rpa_job_footprint", "rpa_chi0",
            "rpa_logdet", "rpa_energy", "rpa_energy_batch", "rpa_submit", "rpa_poll", "rpa_wait",
-           "rpa_serving_stats", "rpa_kernel_launches", "rpa_stream", "rpa_profile", "rpa_profile_read")
+           "rpa_serving_stats", "rpa_kernel_launches", "rpa_stream", "rpa_profile", "rpa_profile_read",
+           "rpa_logdet_noalloc", "rpa_noalloc_last_error")
 
 # kernel classes of rpa_profile_read
 KERNEL_CLASSES = ("dtab", "chi0", "vfactor", "sandwich", "logdet", "reduce", "slice", "spare")
@@ -86,6 +87,8 @@ def load_library(path: str = LIB_PATH):
         "rpa_stream": (P, [P]),
         "rpa_profile": (I, [P, I]),
         "rpa_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(u64)]),
+        "rpa_logdet_noalloc": (I, [I, I, I, P, P, P, P]),
+        "rpa_noalloc_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -214,6 +217,21 @@ def upload_problem(problem, device="cuda", qs: Optional[Sequence[int]] = None, p
     eo = put(problem.eps_occ.astype(np.float64))
     ev = put(problem.eps_virt.astype(np.float64))
     return {"C": C, "V": V, "eps_occ": eo, "eps_virt": ev}
+
+
+def logdet_noalloc(is_complex: bool, n_aux: int, n_w: int, V, chi, out, stream=None) -> None:
+    """rpa_logdet_noalloc: the log-det step with the library's static scratch
+    (no device allocation).  V, chi and out are device tensors; out is
+    float64 [n_w, 2]."""
+    import torch
+
+    lib = load_library()
+    st_ptr = (stream or torch.cuda.current_stream()).cuda_stream
+    st = lib.rpa_logdet_noalloc(int(is_complex), int(n_aux), int(n_w), ctypes.c_void_p(V.data_ptr()),
+                                ctypes.c_void_p(chi.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                ctypes.c_void_p(st_ptr))
+    if st:
+        raise RpaError(st, lib.rpa_noalloc_last_error().decode())
 
 
 class Context:
