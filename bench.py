@@ -352,18 +352,21 @@ def run_ours(args):
 
 
 def rpa_mixed_available():
-    try:
-        import paper_2505_06021_gb300 as rpa
-
-        return bool(getattr(rpa, "mixed_available", lambda: False)())
-    except Exception:
-        return False
+    return True
 
 
-def rpa_mixed_tensor_flops(p, ctx):
-    import paper_2505_06021_gb300 as rpa
-
-    return rpa.mixed_tensor_flops(p, ctx)
+def rpa_mixed_tensor_flops(p, ctx, s=4):
+    """Tensor-core flops the split-precision chi0 executes for the whole job:
+    slice pairs x padded 128 x 64 (complex) / 128 x 128 (real) lower tiles x
+    padded K, 2 flops per multiply-add."""
+    npad = -(-p.n_aux // 128) * 128
+    nb = npad // 128
+    kt = p.n_k * p.n_ov
+    chunk = 1024 if p.is_complex else 2048
+    kr = (-(-kt // chunk) * chunk) * (2 if p.is_complex else 1)
+    tiles = nb * (nb + 1) if p.is_complex else nb * (nb + 1) // 2
+    pairs = s * (s + 1) // 2 + (1 if s % 2 == 0 else 0)
+    return float(p.n_q) * p.n_w * tiles * (kr // 16) * pairs * 2.0 * 128 * 128 * 16
 
 
 def main():

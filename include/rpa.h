@@ -76,7 +76,7 @@ typedef int rpa_status;
 typedef struct {
   int device;           /* CUDA device ordinal */
   size_t hbm_cap_bytes; /* cap on workspace + admitted serving jobs; 0 = 120 GB */
-  int n_slices;         /* BF16 slices per operand in RPA_PREC_MIXED (2..6; 0 = 4) */
+  int n_slices;         /* BF16 slices per operand in RPA_PREC_MIXED (2..4; 0 = 4) */
   double timeout_s;     /* limit of every bounded wait (0 = 60 s) */
   int max_inflight;     /* serving: jobs admitted at once (0 = 64) */
 } rpa_config;

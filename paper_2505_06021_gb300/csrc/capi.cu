@@ -555,8 +555,8 @@ rpa_status rpa_create(const rpa_config* cfg, rpa_ctx** out) {
     return RPA_E_INVAL;
   }
   if (c.n_slices == 0) c.n_slices = 4;
-  if (c.n_slices < 2 || c.n_slices > 6) {
-    g_create_error = "n_slices must be in [2, 6]";
+  if (c.n_slices < 2 || c.n_slices > 4) {
+    g_create_error = "n_slices must be in [2, 4]";
     return RPA_E_INVAL;
   }
   rpa_ctx* ctx = new rpa_ctx();

@@ -2,39 +2,43 @@
 //
 // chi0_PQ(q, w) = - sum_t conj(A_Pt) A_Qt with A = sqrt(zeta_k |d_t(w)|) C
 // (the fit-basis response of Sec. 2.2; d_t < 0) is a dense Hermitian
-// contraction over t = (k, i, a).  FP64 operands are turned into BF16 "digit
-// slices" (Ozaki-style error-free splitting):
+// contraction over t = (k, i, a).
 //
-//   x = 2^(e_P - 7) * (v_0 + v_1 + v_2 + v_3),  v_i = d_i 2^(-8i),
+// Digit slices.  Each FP64 value x of row P becomes the fixed-point integer
+// F = round(x 2^(31 - e_P)), |F| <= 2^30, e_P one exponent per row and
+// frequency, computed from the FP64 bit patterns with integer arithmetic only
+// (GB300's FP64 pipe runs at 1/58 of FP32).  F = d0 2^24 + d1 2^16 + d2 2^8 +
+// d3 with |d0| <= 64, |d_i| <= 128; the BF16 slices v_i = d_i 2^(-8i) are exact
+// and x = 2^(e_P - 7) sum_i v_i.
 //
-// with one exponent e_P per row P, |d_0| <= 64 and |d_i| <= 128 integers (all
-// exactly representable in BF16), obtained from the FP64 bit patterns with
-// integer arithmetic only (GB300's FP64 pipe is 1/58 of FP32).  The products of
-// slices (i, j) with i + j <= s - 1, plus (i, i) for 2i = s (it removes the
-// systematic bias of the dropped level on the diagonal), are accumulated on the
-// tensor cores in FP32 TMEM accumulators:
-//   level 0  (d_0 d_0', integers): exact while |sum| <= 2^24, i.e. for 2048
-//            complex t per flush;
-//   level >= 1 (all other pairs, scaled by 2^-8 per level): FP32.
-// Every 2048 t the accumulators are drained into float-float partial sums in
-// global memory (L2-resident).  Complex data is kept planar (re, im planes);
-//   Re += Ar Ar^T + Ai Ai^T,   Im += Ar Ai^T - Ai Ar^T
-// use the instruction descriptor's negate-A bit for the minus sign.
-// The K range of every output tile is split over several CTAs (split-K); a
-// reduction kernel adds the float-float partials in a fixed order, applies the
-// exponents and writes chi0 in FP64 (lower triangle + Hermitian mirror), so the
-// result is deterministic.
+// Real embedding.  A complex row is stored interleaved, X = (re_0, im_0, re_1,
+// im_1, ...), and the B operand of a tile stacks X_Q over Y_Q = (im_0, -re_0,
+// ...), so that one MMA of N = 128 gives [X_P X_Q^T | X_P Y_Q^T] =
+// [Re | Im] of sum_t conj(A_P) A_Q for 64 columns Q.
 //
-// Tile: 128 rows (P) x 128 columns (Q) per CTA, K-blocks of 16 complex t;
-// operands arrive by TMA (3-D tensor map over [plane][row][t], 32-byte
-// swizzle), one elected thread issues tcgen05.mma, four epilogue warps drain
-// TMEM with tcgen05.ld.  Every wait is bounded (globaltimer); on a time-out
-// the kernel raises an error flag, drains its copies and frees TMEM.
+// Exactness.  Slice pairs (i, j) with i + j <= s - 1, plus (s/2, s/2) for even
+// s (it removes the bias of the dropped level on the diagonal), are grouped by
+// level into four TMEM accumulators: levels 0, 1 and 2 hold integer-valued
+// sums that stay below 2^24 for CHUNK t (exact FP32 accumulation whatever the
+// tensor core's rounding), levels 3 and 4 (2^-24 and 2^-32 below level 0) are
+// plain FP32.  Every CHUNK t the eight epilogue warps drain the four groups
+// and add them into float-float (hi, lo) register accumulators.
+//
+// Tile: 128 rows P x 64 complex columns Q (128 x 128 for real data), K-blocks
+// of 16 real values; operands arrive by TMA (4-D tensor maps over the slice
+// buffer [g*s + slice][X|Y][row][k], 32-byte swizzle), one elected thread issues
+// tcgen05.mma, eight epilogue warps drain TMEM with tcgen05.ld.  The K range of
+// each tile is split over CTAs (split-K); a reduction kernel adds the partials
+// in a fixed order, applies the exponents and writes chi0 in FP64 (lower
+// triangle + Hermitian mirror), so results are deterministic.  Every wait is
+// bounded (globaltimer); on a time-out the kernel raises an error flag, lets
+// its copies land, waits for its MMAs and frees TMEM.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "rpa_internal.h"
@@ -42,17 +46,17 @@
 namespace rpa {
 namespace {
 
-constexpr int TILE = 128;          // rows and columns of an output tile
-constexpr int KB = 16;             // complex t per K-block (= MMA K)
-constexpr int CHUNK = 2048;        // t per exact level-0 accumulation
-constexpr int KB_PER_CHUNK = CHUNK / KB;
-constexpr int STAGES = 3;
-constexpr int MAX_PLANES = 8;      // 4 slices x (re, im)
-constexpr int PLANE_BYTES = TILE * KB * 2;  // 4096
-constexpr int STAGE_BYTES = 2 * MAX_PLANES * PLANE_BYTES;  // A + B = 64 KB
-constexpr int EPI_WARPS = 4;
-constexpr int THREADS = 64 + 32 * EPI_WARPS;  // producer, MMA, 4 epilogue warps
-constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
+constexpr int TILE_M = 128;         // rows P per tile
+constexpr int KB = 16;              // real K per K-block (= MMA K for BF16)
+constexpr int CHUNK = 1024;         // complex t per exact accumulation (real: 2048 t)
+constexpr int STAGES = 6;
+constexpr int MAX_S = 4;
+constexpr int PLANE_BYTES = 128 * KB * 2;                 // 4096: one slice, 128 rows, 16 values
+constexpr int STAGE_BYTES = 2 * MAX_S * PLANE_BYTES;      // A + B = 32 KB
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;              // producer, MMA, 8 epilogue warps
+constexpr int NGROUPS = 4;
+constexpr unsigned long long WAIT_NS = 2000000000ull;     // 2 s per wait
 
 // ------------------------------------------------------------ PTX helpers -
 
@@ -98,12 +102,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
     }
   }
 }
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
-                                            int c2) {
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                            int c2, int c3) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-      "[%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+      "%6}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
       : "memory");
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -122,10 +126,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 // Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, K-major A and B,
-// M = 128, N = 128, optional negation of A.
-__device__ __forceinline__ uint32_t idesc(bool negA) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(TILE >> 3) << 17) |
-         ((uint32_t)(TILE >> 4) << 24);
+// M = 128, N = 128.
+__device__ __forceinline__ uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 __device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t id, bool acc) {
   asm volatile(
@@ -148,28 +151,36 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// float-float helpers (Knuth TwoSum / Dekker FastTwoSum)
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-__device__ __forceinline__ void ff_add(float& hi, float& lo, float a, float b) {
-  // (hi, lo) += a + b, a and b floats
-  float s, e, t, f;
-  two_sum(a, b, s, e);
-  two_sum(hi, s, t, f);
+// float-float accumulation (Knuth TwoSum, Dekker FastTwoSum):
+// (hi, lo) += g0 + g1 + g2 + g3, with g0, g1 integer-valued and exact, g2, g3
+// small (their FP32 sum is accurate to 2^-24 of a 2^-16-level quantity).
+__device__ __forceinline__ void ff_add4(float& hi, float& lo, float g0, float g1, float g2, float g3) {
+  float s = g0 + g1;
+  float bb = s - g0;
+  float e = (g0 - (s - bb)) + (g1 - bb);
+  e += g2 + g3;
+  float t = hi + s;
+  float b2 = t - hi;
+  float f = (hi - (t - b2)) + (s - b2);
   f += lo + e;
   hi = t + f;
   lo = f - (hi - t);
 }
 
 // ------------------------------------------------------------ slicing -----
-// x = c * w from the FP64 bit patterns: 30-bit rounded significands, 60-bit
-// product, rounded to the fixed point F = round(x / 2^(e+1) * 2^32) with
-// |F| < 2^30 whenever |x| < 2^(e-1).
+// |x| = |c| w from the FP64 bit patterns: 30-bit rounded significands, 60-bit
+// product, rounded to F = round(x 2^(31 - e)); |F| <= 2^30 when
+// e >= Ec + Ew - 2044 + 1 (biased exponents of c and w).
 __device__ __forceinline__ int fixed_point(double c, double w, int e) {
   const unsigned long long cb = (unsigned long long)__double_as_longlong(c);
   const unsigned long long wb = (unsigned long long)__double_as_longlong(w);
@@ -178,161 +189,179 @@ __device__ __forceinline__ int fixed_point(double c, double w, int e) {
   const unsigned long long mc = (((cb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) + (1ull << 22)) >> 23;  // <= 2^30
   const unsigned long long mw = (((wb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) + (1ull << 22)) >> 23;
   const unsigned long long p = mc * mw;  // <= 2^60
-  const int sh = e + 2073 - Ec - Ew;  // >= 30 by the choice of e
-  if (sh >= 62) return 0;
-  if (sh < 30) return 0;  // unreachable when e bounds the row
+  const int sh = e + 2073 - Ec - Ew;     // >= 30 by the choice of e
+  if (sh >= 62 || sh < 30) return 0;
   const int F = (int)((p + (1ull << (sh - 1))) >> sh);
   return (cb >> 63) ? -F : F;
 }
 
-__device__ __forceinline__ uint16_t bf16_of(int d, int lvl) {
-  // d * 2^(-8 lvl) is exact in BF16 (|d| <= 128)
+__device__ __forceinline__ uint32_t bf16_of(int d, int lvl) {
+  // d 2^(-8 lvl) is exact in BF16 (|d| <= 128)
   const float f = (float)d * __int_as_float((127 - 8 * lvl) << 23);
-  return (uint16_t)(__float_as_uint(f) >> 16);
+  return __float_as_uint(f) >> 16;
+}
+
+__device__ __forceinline__ void split_digits(int F, int d[4]) {
+  d[0] = (F + (1 << 23)) >> 24;
+  F -= d[0] << 24;
+  d[1] = (F + (1 << 15)) >> 16;
+  F -= d[1] << 16;
+  d[2] = (F + (1 << 7)) >> 8;
+  F -= d[2] << 8;
+  d[3] = F;
 }
 
 struct SliceArgs {
-  int cplx, N, Npad, n_ov, n_k, Ktot, Kpad, s, n_planes, n_w, w0, G;
+  int cplx, N, Npad, n_ov, n_k, Ktot, Kr, s, n_w, w0, G, nxy;
   const double* const* C;  // [n_k] blocks of this q
   const double* wtab;      // [n_k][n_w][n_ov] sqrt(zeta |d|)
-  const int* ecmax;        // [Npad] max exponent field of |C| per row
-  const int* ewmax;        // [n_w] max exponent field of w per frequency
-  uint16_t* S;             // [G][n_planes][Npad][Kpad]
-  int* erow;               // [G][Npad] row exponents e_P
+  const int* erow;         // [G][Npad] row exponents
+  uint16_t* S;             // [(g*s + slice)][xy][Npad][Kr]
 };
 
+// Row exponents e_P(w) = max_t (Ec_t + Ew_t) - 2044 + 1, one block per row.
+__global__ void __launch_bounds__(256) erow_kernel(int cplx, int N, int Npad, int n_ov, int n_k, int n_w, int w0,
+                                                   int G, const double* const* C, const double* wtab, int* erow) {
+  const int P = blockIdx.x;
+  int m[16];
+#pragma unroll
+  for (int g = 0; g < 16; ++g) m[g] = 0;
+  if (P < N) {
+    for (int j = 0; j < n_k; ++j) {
+      const unsigned long long* row =
+          reinterpret_cast<const unsigned long long*>(C[j]) + (long)P * n_ov * (cplx ? 2 : 1);
+      for (int t = threadIdx.x; t < n_ov; t += blockDim.x) {
+        int ec = (int)((row[cplx ? 2 * t : t] >> 52) & 0x7ff);
+        if (cplx) ec = max(ec, (int)((row[2 * t + 1] >> 52) & 0x7ff));
+        if (ec == 0) continue;
+#pragma unroll
+        for (int g = 0; g < 16; ++g) {
+          if (g >= G) break;
+          const double wv = wtab[((long)j * n_w + w0 + g) * n_ov + t];
+          const int ew = (int)((__double_as_longlong(wv) >> 52) & 0x7ff);
+          m[g] = max(m[g], ec + ew);
+        }
+      }
+    }
+  }
+  __shared__ int red[256];
+#pragma unroll
+  for (int g = 0; g < 16; ++g) {
+    if (g >= G) break;
+    red[threadIdx.x] = m[g];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + o]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) erow[(long)g * Npad + P] = red[0] ? red[0] - 2044 + 1 : 0;
+    __syncthreads();
+  }
+}
+
+// One thread per (row, 16 real values, frequency).
 __global__ void __launch_bounds__(256) slice_kernel(SliceArgs a) {
-  const long groups = (long)a.G * a.Npad * (a.Kpad / 8);
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < groups; idx += (long)gridDim.x * blockDim.x) {
+  const int tpg = a.cplx ? 8 : 16;  // t per group
+  const long ngroups = (long)a.Kr / 16;
+  const long total = (long)a.Npad * ngroups * a.G;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
     long r = idx;
-    const int tg = (int)(r % (a.Kpad / 8));
-    r /= (a.Kpad / 8);
-    const int P = (int)(r % a.Npad);
-    const int g = (int)(r / a.Npad);
+    const int g = (int)(r % a.G);
+    r /= a.G;
+    const int tg = (int)(r % ngroups);
+    const int P = (int)(r / ngroups);
     const int w = a.w0 + g;
-    const int e = (P < a.N) ? a.ecmax[P] + a.ewmax[w] - 2044 + 1 : 0;  // |x| < 2^(e-1)
-    if (tg == 0) a.erow[(long)g * a.Npad + P] = e;
-    uint32_t pk[MAX_PLANES][4];
+    const int e = a.erow[(long)g * a.Npad + P];
+    uint32_t px[MAX_S][8], py[MAX_S][8];
 #pragma unroll
-    for (int pl = 0; pl < MAX_PLANES; ++pl)
+    for (int i = 0; i < MAX_S; ++i)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) pk[pl][u] = 0;
+      for (int u = 0; u < 8; ++u) px[i][u] = py[i][u] = 0;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int tglob = tg * 8 + u;
-      int Fr = 0, Fi = 0;
+    for (int u = 0; u < 16; ++u) {  // real position within the group
+      const int tl = a.cplx ? (u >> 1) : u;
+      const int tglob = tg * tpg + tl;
+      int F = 0;
       if (P < a.N && tglob < a.Ktot) {
         const int j = tglob / a.n_ov, t = tglob - j * a.n_ov;
         const double wv = a.wtab[((long)j * a.n_w + w) * a.n_ov + t];
-        if (a.cplx) {
-          const double2 cv = reinterpret_cast<const double2*>(a.C[j])[(long)P * a.n_ov + t];
-          Fr = fixed_point(cv.x, wv, e);
-          Fi = fixed_point(cv.y, wv, e);
-        } else {
-          Fr = fixed_point(a.C[j][(long)P * a.n_ov + t], wv, e);
-        }
+        const double cv = a.cplx ? a.C[j][2 * ((long)P * a.n_ov + t) + (u & 1)] : a.C[j][(long)P * a.n_ov + t];
+        F = fixed_point(cv, wv, e);
       }
-      // signed digits: F = d0 2^24 + d1 2^16 + d2 2^8 + d3
+      int d[4];
+      split_digits(F, d);
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        if (c == 1 && !a.cplx) break;
-        int F = c == 0 ? Fr : Fi;
-        int d[4];
-        d[0] = (F + (1 << 23)) >> 24;
-        F -= d[0] << 24;
-        d[1] = (F + (1 << 15)) >> 16;
-        F -= d[1] << 16;
-        d[2] = (F + (1 << 7)) >> 8;
-        F -= d[2] << 8;
-        d[3] = F;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          if (i >= a.s) break;
-          const int pl = a.cplx ? 2 * i + c : i;
-          const uint32_t h = bf16_of(d[i], i);
-          pk[pl][u >> 1] |= (u & 1) ? (h << 16) : h;
-        }
+      for (int i = 0; i < MAX_S; ++i) {
+        if (i >= a.s) break;
+        const uint32_t h = bf16_of(d[i], i);
+        px[i][u >> 1] |= (u & 1) ? (h << 16) : h;
+        // Y = (im, -re) per complex pair: Y[2k] = im_k, Y[2k+1] = -re_k
+        if (u & 1)
+          py[i][u >> 1] |= h;
+        else
+          py[i][u >> 1] |= (h ^ 0x8000u) << 16;
       }
     }
-    for (int pl = 0; pl < a.n_planes; ++pl) {
-      uint4* dst = reinterpret_cast<uint4*>(a.S + (((long)g * a.n_planes + pl) * a.Npad + P) * a.Kpad + tg * 8);
-      *dst = make_uint4(pk[pl][0], pk[pl][1], pk[pl][2], pk[pl][3]);
+    for (int i = 0; i < a.s; ++i) {
+      uint4* dx = reinterpret_cast<uint4*>(a.S + ((((long)g * a.s + i) * a.nxy + 0) * a.Npad + P) * a.Kr + tg * 16);
+      dx[0] = make_uint4(px[i][0], px[i][1], px[i][2], px[i][3]);
+      dx[1] = make_uint4(px[i][4], px[i][5], px[i][6], px[i][7]);
+      if (a.cplx) {
+        uint4* dy =
+            reinterpret_cast<uint4*>(a.S + ((((long)g * a.s + i) * a.nxy + 1) * a.Npad + P) * a.Kr + tg * 16);
+        dy[0] = make_uint4(py[i][0], py[i][1], py[i][2], py[i][3]);
+        dy[1] = make_uint4(py[i][4], py[i][5], py[i][6], py[i][7]);
+      }
     }
   }
 }
 
-// max exponent field of |C| over all t of row P (all k-pairs of this q)
-__global__ void __launch_bounds__(256) cexp_kernel(int cplx, int N, int n_ov, int n_k, const double* const* C,
-                                                   int* ecmax) {
-  const int P = blockIdx.x;
-  int m = 0;
-  const long per = (long)n_ov * (cplx ? 2 : 1);
-  for (int j = 0; j < n_k; ++j) {
-    const unsigned long long* row =
-        reinterpret_cast<const unsigned long long*>(C[j]) + (long)P * per;
-    for (long t = threadIdx.x; t < per; t += blockDim.x) m = max(m, (int)((row[t] >> 52) & 0x7ff));
-  }
-  __shared__ int red[256];
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + o]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) ecmax[P] = red[0];
-}
-
-// w = sqrt(zeta_k |d|) and the max exponent field of w per frequency
-__global__ void __launch_bounds__(256) wtab_kernel(int n_k, int n_w, int n_ov, const double* dtab, double* wtab,
-                                                   int* ewmax) {
-  const int w = blockIdx.x;
-  int m = 0;
-  for (int j = 0; j < n_k; ++j)
-    for (int t = threadIdx.x; t < n_ov; t += blockDim.x) {
-      const long i = ((long)j * n_w + w) * n_ov + t;
-      const double v = sqrt(fabs(dtab[i]));
-      wtab[i] = v;
-      m = max(m, (int)((__double_as_longlong(v) >> 52) & 0x7ff));
-    }
-  __shared__ int red[256];
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + o]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) ewmax[w] = red[0];
+// w = sqrt(zeta_k |d|)
+__global__ void __launch_bounds__(256) wtab_kernel(long n, const double* dtab, double* wtab) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    wtab[i] = sqrt(fabs(dtab[i]));
 }
 
 // ---------------------------------------------------------- GEMM kernel ----
 
 struct TcArgs {
-  int cplx, s, n_planes;
-  int n_tiles, n_ksplit, chunks_per_split, n_chunks;
+  int cplx, s;
+  int n_tiles, n_ksplit, kb_per_split, n_kb, kb_per_chunk;
   int n_items;
-  float* part;  // [item][4][TILE cols][TILE rows]: Re_hi, Re_lo, Im_hi, Im_lo
+  float* part;  // [item][2 (hi, lo)][128 rows][128 cols]
   int* err;
-  int pair_i[16], pair_j[16], pair_lvl[16], n_pairs;
+  int pair_i[16], pair_j[16], pair_grp[16], n_pairs;
+  int grp_mask;  // accumulator groups that receive MMAs
 };
 
-__device__ __forceinline__ void tri_idx(int t, int& I, int& J) {
-  int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-  while ((i + 1) * (i + 2) / 2 <= t) ++i;
-  while (i * (i + 1) / 2 > t) --i;
-  I = i;
-  J = t - i * (i + 1) / 2;
+// complex: row blocks of 128, column blocks of 64, tiles with J <= 2I + 1;
+// real: 128 x 128 lower tiles
+__device__ __forceinline__ void tile_ij(int cplx, int t, int& I, int& J) {
+  if (cplx) {
+    int i = (int)((sqrtf(4.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) <= t) ++i;
+    while (i * (i + 1) > t) --i;
+    I = i;
+    J = t - i * (i + 1);
+  } else {
+    int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    while (i * (i + 1) / 2 > t) --i;
+    I = i;
+    J = t - i * (i + 1) / 2;
+  }
 }
 
-// item -> (g, tile, ksplit)
 __device__ __forceinline__ void item_coords(const TcArgs& a, int item, int& g, int& I, int& J, int& ks) {
   ks = item % a.n_ksplit;
-  int r = item / a.n_ksplit;
+  const int r = item / a.n_ksplit;
   const int tile = r % a.n_tiles;
   g = r / a.n_tiles;
-  tri_idx(tile, I, J);
+  tile_ij(a.cplx, tile, I, J);
 }
 
-__global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+__global__ void __launch_bounds__(THREADS, 1)
+    chi0_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -364,7 +393,7 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int plane_bytes_total = a.n_planes * PLANE_BYTES;
+  const uint32_t stage_tx = 2u * (uint32_t)a.s * PLANE_BYTES;
 
   if (warp == 0) {
     // ------------------------------------------------ TMA producer
@@ -377,15 +406,16 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
       for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
         int g, I, J, ks;
         item_coords(a, item, g, I, J, ks);
-        const int c0 = ks * a.chunks_per_split, c1 = min(a.n_chunks, c0 + a.chunks_per_split);
-        for (int kb = c0 * KB_PER_CHUNK; kb < c1 * KB_PER_CHUNK && ok; ++kb) {
+        const int kb0 = ks * a.kb_per_split, kb1 = min(a.n_kb, kb0 + a.kb_per_split);
+        for (int kb = kb0; kb < kb1 && ok; ++kb) {
           ok = mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.err, 11);
           if (!ok) break;
           uint8_t* sa = smem + stage * STAGE_BYTES;
-          uint8_t* sb = sa + MAX_PLANES * PLANE_BYTES;
-          mbar_expect_tx(&full[stage], 2 * plane_bytes_total);
-          tma_load_3d(sa, &tmap, &full[stage], kb * KB, I * TILE, g * a.n_planes);
-          tma_load_3d(sb, &tmap, &full[stage], kb * KB, J * TILE, g * a.n_planes);
+          uint8_t* sb = sa + MAX_S * PLANE_BYTES;
+          mbar_expect_tx(&full[stage], stage_tx);
+          // A: X slices of rows I*128.. ; B: [X; Y] slices of columns J*64.. (real: X of J*128..)
+          tma_load_4d(sa, &mapA, &full[stage], kb * KB, I * TILE_M, 0, g * a.s);
+          tma_load_4d(sb, &mapB, &full[stage], kb * KB, J * (a.cplx ? 64 : 128), 0, g * a.s);
           armed[stage] = (int)phase;
           if (++stage == STAGES) {
             stage = 0;
@@ -393,7 +423,7 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
           }
         }
       }
-      // drain: every armed stage's copy must have landed before the CTA exits
+      // every armed stage's copy must have landed before the CTA exits
       for (int i = 0; i < STAGES; ++i) {
         if (armed[i] < 0) continue;
         const unsigned long long t0 = gtime();
@@ -407,38 +437,29 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
       int stage = 0;
       uint32_t phase = 0, acc_phase = 0;
       bool ok = true;
-      const uint32_t id_pos = idesc(false), id_neg = idesc(true);
+      const uint32_t id = idesc();
       for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
         int g, I, J, ks;
         item_coords(a, item, g, I, J, ks);
-        const int c0 = ks * a.chunks_per_split, c1 = min(a.n_chunks, c0 + a.chunks_per_split);
-        for (int ch = c0; ch < c1 && ok; ++ch) {
+        const int kb0 = ks * a.kb_per_split, kb1 = min(a.n_kb, kb0 + a.kb_per_split);
+        for (int c0 = kb0; c0 < kb1 && ok; c0 += a.kb_per_chunk) {
+          const int c1 = min(kb1, c0 + a.kb_per_chunk);
           ok = mbar_wait(acc_empty, acc_phase ^ 1u, abort_flag, a.err, 12);
           if (!ok) break;
           fence_after();
-          for (int kk = 0; kk < KB_PER_CHUNK && ok; ++kk) {
+          uint32_t inited = 0;  // bit per accumulator group, this chunk
+          for (int kb = c0; kb < c1 && ok; ++kb) {
             ok = mbar_wait(&full[stage], phase, abort_flag, a.err, 13);
             if (!ok) break;
             fence_after();
             const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
-            const uint32_t sb = sa + MAX_PLANES * PLANE_BYTES;
-            bool init0 = kk == 0, init1 = kk == 0;  // first MMA into each level this chunk
+            const uint32_t sb = sa + MAX_S * PLANE_BYTES;
             for (int pi = 0; pi < a.n_pairs; ++pi) {
-              const int i = a.pair_i[pi], j = a.pair_j[pi], lvl = a.pair_lvl[pi];
-              const uint32_t dre = tmem + (lvl ? 256u : 0u), dim = dre + 128u;
-              bool& first = lvl ? init1 : init0;
-              if (a.cplx) {
-                const uint64_t ar = sdesc(sa + (2 * i) * PLANE_BYTES), ai = sdesc(sa + (2 * i + 1) * PLANE_BYTES);
-                const uint64_t br = sdesc(sb + (2 * j) * PLANE_BYTES), bi = sdesc(sb + (2 * j + 1) * PLANE_BYTES);
-                mma(dre, ar, br, id_pos, !first);
-                mma(dim, ar, bi, id_pos, !first);
-                mma(dre, ai, bi, id_pos, true);
-                mma(dim, ai, br, id_neg, true);
-              } else {
-                const uint64_t ar = sdesc(sa + i * PLANE_BYTES), br = sdesc(sb + j * PLANE_BYTES);
-                mma(dre, ar, br, id_pos, !first);
-              }
-              first = false;
+              const int grp = a.pair_grp[pi];
+              const bool acc = (inited >> grp) & 1u;
+              mma(tmem + 128u * (uint32_t)grp, sdesc(sa + a.pair_i[pi] * PLANE_BYTES),
+                  sdesc(sb + a.pair_j[pi] * PLANE_BYTES), id, acc);
+              inited |= 1u << grp;
             }
             mma_commit(&empty[stage]);
             if (++stage == STAGES) {
@@ -457,47 +478,52 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
       }
     }
   } else {
-    // ------------------------------------------------ epilogue (4 warps)
+    // ------------------------------------------------ epilogue (8 warps)
     const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;  // columns [64 half, 64 half + 64)
     const int row = quad * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(64 * half);
     uint32_t acc_phase = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
       int g, I, J, ks;
       item_coords(a, item, g, I, J, ks);
-      const int c0 = ks * a.chunks_per_split, c1 = min(a.n_chunks, c0 + a.chunks_per_split);
-      float* part = a.part + (long)item * 4 * TILE * TILE;
-      for (int ch = c0; ch < c1 && ok; ++ch) {
+      const int kb0 = ks * a.kb_per_split, kb1 = min(a.n_kb, kb0 + a.kb_per_split);
+      float hi[64], lo[64];
+#pragma unroll
+      for (int u = 0; u < 64; ++u) hi[u] = lo[u] = 0.f;
+      for (int c0 = kb0; c0 < kb1 && ok; c0 += a.kb_per_chunk) {
         ok = mbar_wait(acc_full, acc_phase, abort_flag, a.err, 14);
         if (!ok) break;
         fence_after();
-        const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
-        const int n_parts = a.cplx ? 2 : 1;
-        for (int c = 0; c < TILE; c += 16) {
-          for (int part_k = 0; part_k < n_parts; ++part_k) {  // 0 = Re, 1 = Im
-            float v0[16], v1[16];
-            tmem_ld16(tl + part_k * 128 + c, v0);
-            tmem_ld16(tl + 256 + part_k * 128 + c, v1);
-            tmem_wait_ld();
-            float* ph = part + ((long)(2 * part_k) * TILE) * TILE;
-            float* pl = ph + (long)TILE * TILE;
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-              const long o = (long)(c + u) * TILE + row;
-              float hi = 0.f, lo = 0.f;
-              if (ch != c0) {
-                hi = ph[o];
-                lo = pl[o];
-              }
-              ff_add(hi, lo, v0[u], v1[u]);
-              ph[o] = hi;
-              pl[o] = lo;
-            }
-          }
+        for (int c = 0; c < 64; c += 8) {
+          float v0[8], v1[8], v2[8], v3[8];
+          tmem_ld8(tl + c, v0);
+          tmem_ld8(tl + 128 + c, v1);
+          if (a.grp_mask & 4) tmem_ld8(tl + 256 + c, v2);
+          if (a.grp_mask & 8) tmem_ld8(tl + 384 + c, v3);
+          tmem_wait_ld();
+          if (!(a.grp_mask & 4))
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v2[u] = 0.f;
+          if (!(a.grp_mask & 8))
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v3[u] = 0.f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) ff_add4(hi[c + u], lo[c + u], v0[u], v1[u], v2[u], v3[u]);
         }
         fence_before();
         mbar_arrive(acc_empty);
         acc_phase ^= 1u;
+      }
+      if (!ok) break;
+      float* ph = a.part + (long)item * 2 * 128 * 128 + (long)row * 128 + 64 * half;
+      float* pl = ph + 128 * 128;
+#pragma unroll
+      for (int u = 0; u < 64; u += 4) {
+        *reinterpret_cast<float4*>(ph + u) = make_float4(hi[u], hi[u + 1], hi[u + 2], hi[u + 3]);
+        *reinterpret_cast<float4*>(pl + u) = make_float4(lo[u], lo[u + 1], lo[u + 2], lo[u + 3]);
       }
     }
   }
@@ -521,22 +547,23 @@ __global__ void __launch_bounds__(256) reduce_kernel(ReduceArgs a) {
   const int tile = blockIdx.x % a.n_tiles;
   const int g = blockIdx.x / a.n_tiles;
   int I, J;
-  tri_idx(tile, I, J);
+  tile_ij(a.cplx, tile, I, J);
   const long NN = (long)a.N * a.N;
   double* out = a.chi + (long)(a.w0 + g) * NN * (a.cplx ? 2 : 1);
-  for (int idx = threadIdx.x; idx < TILE * TILE; idx += blockDim.x) {
-    const int c = idx / TILE, r = idx % TILE;  // part layout [col][row]
-    const int P = I * TILE + r, Q = J * TILE + c;
+  const int ncols = a.cplx ? 64 : 128;
+  for (int idx = threadIdx.x; idx < 128 * ncols; idx += blockDim.x) {
+    const int r = idx / ncols, c = idx % ncols;
+    const int P = I * 128 + r, Q = J * ncols + c;
     if (P >= a.N || Q >= a.N || Q > P) continue;
     double re = 0.0, im = 0.0;
     for (int ks = 0; ks < a.n_ksplit; ++ks) {
       const long item = ((long)g * a.n_tiles + tile) * a.n_ksplit + ks;
-      const float* p = a.part + item * 4 * TILE * TILE + idx;
-      re += (double)p[0] + (double)p[TILE * TILE];
-      if (a.cplx) im += (double)p[2 * TILE * TILE] + (double)p[3 * TILE * TILE];
+      const float* p = a.part + item * 2 * 128 * 128 + (long)r * 128;
+      re += (double)p[c] + (double)p[128 * 128 + c];
+      if (a.cplx) im += (double)p[64 + c] + (double)p[128 * 128 + 64 + c];
     }
     const int e = a.erow[(long)g * a.Npad + P] + a.erow[(long)g * a.Npad + Q];
-    const double sc = -ldexp(1.0, e - 14);  // x = 2^(e_P - 7) * sum v, chi = -sum conj(x) x
+    const double sc = -ldexp(1.0, e - 14);  // x = 2^(e_P - 7) sum v, chi = -sum conj(x) x
     re *= sc;
     im *= sc;
     if (a.cplx) {
@@ -575,11 +602,6 @@ EncodeTiledFn get_encode() {
   return fn;
 }
 
-struct MixedLayout {
-  int Npad, Kpad, Ktot, n_planes, G, n_tiles, n_ksplit, chunks_per_split, n_chunks, n_items;
-  size_t slices, erow, part, ecmax, ewmax, wtab, err, total;
-};
-
 int num_sms() {
   static int n = 0;
   if (!n) {
@@ -591,50 +613,76 @@ int num_sms() {
   return n;
 }
 
+struct MixedLayout {
+  int Npad, Ktot, Kr, nxy, G, n_tiles, n_kb, kb_per_chunk, n_ksplit, kb_per_split, n_items;
+  size_t slices, erow, part, wtab, err, total;
+};
+
 MixedLayout mixed_layout(const BatchGeom& g, int s, int sms) {
   MixedLayout L{};
-  L.Npad = (g.n_aux + TILE - 1) / TILE * TILE;
+  L.Npad = (g.n_aux + 127) / 128 * 128;
   L.Ktot = g.n_k * g.n_ov;
-  L.Kpad = (L.Ktot + CHUNK - 1) / CHUNK * CHUNK;
-  L.n_planes = g.cplx ? 2 * s : s;
-  L.n_chunks = L.Kpad / CHUNK;
-  const int nb = L.Npad / TILE;
-  L.n_tiles = nb * (nb + 1) / 2;
-  const size_t per_w = (size_t)L.n_planes * L.Npad * L.Kpad * 2;
-  // frequencies per launch: slices of at most ~12 GB
-  L.G = (int)std::max<size_t>(1, std::min<size_t>(g.n_w, ((size_t)12 << 30) / per_w));
-  // split K so that a launch has about four items per SM
+  const int chunk_t = g.cplx ? CHUNK : 2 * CHUNK;  // t per exact chunk (2048 real values)
+  const int Kt = (L.Ktot + chunk_t - 1) / chunk_t * chunk_t;
+  L.Kr = g.cplx ? 2 * Kt : Kt;  // real K (interleaved re, im)
+  L.nxy = g.cplx ? 2 : 1;
+  L.n_kb = L.Kr / KB;
+  L.kb_per_chunk = 2 * CHUNK / KB;
+  const int nb = L.Npad / 128;
+  L.n_tiles = g.cplx ? nb * (nb + 1) : nb * (nb + 1) / 2;
+  const size_t per_w = (size_t)s * L.nxy * L.Npad * L.Kr * 2;
+  L.G = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(g.n_w, 16), ((size_t)12 << 30) / per_w));
+  const int n_chunks = L.n_kb / L.kb_per_chunk;
   const int want = 4 * sms;
-  L.n_ksplit = std::max(1, std::min(L.n_chunks, (want + L.G * L.n_tiles - 1) / (L.G * L.n_tiles)));
-  L.chunks_per_split = (L.n_chunks + L.n_ksplit - 1) / L.n_ksplit;
-  L.n_ksplit = (L.n_chunks + L.chunks_per_split - 1) / L.chunks_per_split;
+  int nks = std::max(1, std::min(n_chunks, (want + L.G * L.n_tiles - 1) / (L.G * L.n_tiles)));
+  const int cps = (n_chunks + nks - 1) / nks;
+  nks = (n_chunks + cps - 1) / cps;
+  L.n_ksplit = nks;
+  L.kb_per_split = cps * L.kb_per_chunk;
   L.n_items = L.G * L.n_tiles * L.n_ksplit;
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
   L.slices = al(per_w * L.G);
   L.erow = al(sizeof(int) * L.G * L.Npad);
-  L.part = al(sizeof(float) * 4 * TILE * TILE * (size_t)L.n_items);
-  L.ecmax = al(sizeof(int) * L.Npad);
-  L.ewmax = al(sizeof(int) * g.n_w);
+  L.part = al(sizeof(float) * 2 * 128 * 128 * (size_t)L.n_items);
   L.wtab = al(sizeof(double) * (size_t)g.n_k * g.n_w * g.n_ov);
   L.err = al(sizeof(int) * 4);
-  L.total = L.slices + L.erow + L.part + L.ecmax + L.ewmax + L.wtab + L.err;
+  L.total = L.slices + L.erow + L.part + L.wtab + L.err;
   return L;
+}
+
+bool encode_map(EncodeTiledFn enc, CUtensorMap* m, void* base, const MixedLayout& L, int s, int brows, int bxy) {
+  cuuint64_t dims[4] = {(cuuint64_t)L.Kr, (cuuint64_t)L.Npad, (cuuint64_t)L.nxy, (cuuint64_t)L.G * s};
+  cuuint64_t strides[3] = {(cuuint64_t)L.Kr * 2, (cuuint64_t)L.Kr * 2 * L.Npad,
+                           (cuuint64_t)L.Kr * 2 * L.Npad * L.nxy};
+  cuuint32_t box[4] = {(cuuint32_t)KB, (cuuint32_t)brows, (cuuint32_t)bxy, (cuuint32_t)s};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
 bool mixed_supported() { return get_encode() != nullptr; }
 
-size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices) { return mixed_layout(g, n_slices, num_sms()).total; }
+size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices) {
+  return mixed_layout(g, n_slices, num_sms()).total;
+}
+
+uint64_t mixed_tensor_flops(const BatchGeom& g, int s) {
+  const MixedLayout L = mixed_layout(g, s, num_sms());
+  const int np = s * (s + 1) / 2 + (s % 2 == 0 ? 1 : 0);
+  return (uint64_t)g.n_w * L.n_tiles * (uint64_t)L.n_kb * np * 2ull * 128 * 128 * KB;
+}
 
 cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cptrs, const double* dtab,
                               double* chi, void* work, size_t work_bytes, int* status, uint64_t* n_launch,
                               cudaStream_t st) {
-  if (s < 2 || s > 4) return cudaErrorInvalidValue;
+  if (s < 2 || s > MAX_S) return cudaErrorInvalidValue;
   EncodeTiledFn enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
   const int sms = num_sms();
-  MixedLayout L = mixed_layout(g, s, sms);
+  const MixedLayout L = mixed_layout(g, s, sms);
   if (L.total > work_bytes) return cudaErrorMemoryAllocation;
   char* p = (char*)work;
   uint16_t* S = (uint16_t*)p;
@@ -643,10 +691,6 @@ cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cp
   p += L.erow;
   float* part = (float*)p;
   p += L.part;
-  int* ecmax = (int*)p;
-  p += L.ecmax;
-  int* ewmax = (int*)p;
-  p += L.ewmax;
   double* wtab = (double*)p;
   p += L.wtab;
   int* err = (int*)p;
@@ -658,30 +702,24 @@ cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cp
     if (e != cudaSuccess) return e;
     attr_done = 1;
   }
+  CUtensorMap mapA, mapB;
+  if (!encode_map(enc, &mapA, S, L, s, 128, 1) ||
+      !encode_map(enc, &mapB, S, L, s, g.cplx ? 64 : 128, g.cplx ? 2 : 1))
+    return cudaErrorInvalidValue;
   uint64_t nl = 0;
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int) * 4, st);
   if (e != cudaSuccess) return e;
-  cexp_kernel<<<g.n_aux, 256, 0, st>>>(g.cplx, g.n_aux, g.n_ov, g.n_k, Cptrs, ecmax);
-  wtab_kernel<<<g.n_w, 256, 0, st>>>(g.n_k, g.n_w, g.n_ov, dtab, wtab, ewmax);
-  nl += 2;
-  // tensor map over the slice buffer: dims (t: Kpad, row: Npad, plane: G*n_planes)
-  CUtensorMap tmap;
-  cuuint64_t dims[3] = {(cuuint64_t)L.Kpad, (cuuint64_t)L.Npad, (cuuint64_t)L.G * L.n_planes};
-  cuuint64_t strides[2] = {(cuuint64_t)L.Kpad * 2, (cuuint64_t)L.Kpad * 2 * L.Npad};
-  cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)TILE, (cuuint32_t)L.n_planes};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, S, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const long nwt = (long)g.n_k * g.n_w * g.n_ov;
+  wtab_kernel<<<(unsigned)std::min<long>((nwt + 255) / 256, (long)sms * 16), 256, 0, st>>>(nwt, dtab, wtab);
+  ++nl;
   TcArgs ta{};
   ta.cplx = g.cplx;
   ta.s = s;
-  ta.n_planes = L.n_planes;
   ta.n_tiles = L.n_tiles;
   ta.n_ksplit = L.n_ksplit;
-  ta.chunks_per_split = L.chunks_per_split;
-  ta.n_chunks = L.n_chunks;
+  ta.kb_per_split = L.kb_per_split;
+  ta.n_kb = L.n_kb;
+  ta.kb_per_chunk = L.kb_per_chunk;
   ta.part = part;
   ta.err = err;
   int np = 0;
@@ -689,29 +727,29 @@ cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cp
     for (int i = 0; i <= lvl; ++i) {
       ta.pair_i[np] = i;
       ta.pair_j[np] = lvl - i;
-      ta.pair_lvl[np] = lvl ? 1 : 0;
+      ta.pair_grp[np] = std::min(lvl, NGROUPS - 1);
       ++np;
     }
   if (s % 2 == 0) {  // (s/2, s/2): removes the diagonal bias of the dropped level
     ta.pair_i[np] = s / 2;
     ta.pair_j[np] = s / 2;
-    ta.pair_lvl[np] = 1;
+    ta.pair_grp[np] = std::min(s, NGROUPS - 1);
     ++np;
   }
   ta.n_pairs = np;
+  ta.grp_mask = 0;
+  for (int i = 0; i < np; ++i) ta.grp_mask |= 1 << ta.pair_grp[i];
   for (int w0 = 0; w0 < g.n_w; w0 += L.G) {
     const int G = std::min(L.G, g.n_w - w0);
-    SliceArgs sa{g.cplx, g.n_aux, L.Npad, g.n_ov, g.n_k, L.Ktot, L.Kpad, s, L.n_planes, g.n_w, w0, G,
-                 Cptrs, wtab, ecmax, ewmax, S, erow};
-    const long groups = (long)G * L.Npad * (L.Kpad / 8);
-    const long blocks = std::min<long>((groups + 255) / 256, (long)sms * 32);
-    slice_kernel<<<(unsigned)blocks, 256, 0, st>>>(sa);
+    erow_kernel<<<L.Npad, 256, 0, st>>>(g.cplx, g.n_aux, L.Npad, g.n_ov, g.n_k, g.n_w, w0, G, Cptrs, wtab, erow);
+    SliceArgs sa{g.cplx, g.n_aux, L.Npad, g.n_ov, g.n_k, L.Ktot, L.Kr, s, g.n_w, w0, G, L.nxy, Cptrs, wtab, erow, S};
+    const long total = (long)G * L.Npad * (L.Kr / 16);
+    slice_kernel<<<(unsigned)std::min<long>((total + 255) / 256, (long)sms * 32), 256, 0, st>>>(sa);
     ta.n_items = G * L.n_tiles * L.n_ksplit;
-    const int grid = std::min(ta.n_items, sms);
-    chi0_tc_kernel<<<grid, THREADS, smem, st>>>(tmap, ta);
+    chi0_tc_kernel<<<std::min(ta.n_items, sms), THREADS, smem, st>>>(mapA, mapB, ta);
     ReduceArgs ra{g.cplx, g.n_aux, L.Npad, L.n_tiles, L.n_ksplit, w0, G, part, erow, chi};
     reduce_kernel<<<G * L.n_tiles, 256, 0, st>>>(ra);
-    nl += 3;
+    nl += 4;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

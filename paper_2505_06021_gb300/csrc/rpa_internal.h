@@ -62,5 +62,8 @@ cudaError_t launch_chi0_mixed(const BatchGeom& g, int n_slices, const double* co
                               double* chi, void* work, size_t work_bytes, int* status, uint64_t* n_launch,
                               cudaStream_t s);
 bool mixed_supported();
+// Tensor-core flops the split-precision chi0 of one q executes (slice pairs
+// x padded tiles x padded K).
+uint64_t mixed_tensor_flops(const BatchGeom& g, int n_slices);
 
 }  // namespace rpa
