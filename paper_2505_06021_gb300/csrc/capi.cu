@@ -192,6 +192,8 @@ rpa_status validate_job(const rpa_job* j, char* msg, size_t len) {
       !j->V)
     return set_msg(msg, len, "a required pointer is NULL");
   if (j->prec != RPA_PREC_FP64 && j->prec != RPA_PREC_MIXED) return set_msg(msg, len, "unknown prec %d", j->prec);
+  if (j->prec == RPA_PREC_MIXED && j->n_w > 32)
+    return set_msg(msg, len, "the split-precision path takes at most 32 frequencies (got %d)", j->n_w);
   if (j->mem != RPA_MEM_DEVICE && j->mem != RPA_MEM_HOST) return set_msg(msg, len, "unknown mem %d", j->mem);
   if (!(j->zeta_k > 0.0) || !isfinite(j->zeta_k)) return set_msg(msg, len, "zeta_k must be positive");
   for (long i = 0; i < (long)j->n_q * j->n_k; ++i) {

@@ -1,8 +1,10 @@
 // Split-precision chi0 on the tcgen05 tensor cores of GB300 (sm_103a).
 //
-// chi0_PQ(q, w) = - sum_t conj(A_Pt) A_Qt with A = sqrt(zeta_k |d_t(w)|) C
-// (the fit-basis response of Sec. 2.2; d_t < 0) is a dense Hermitian
-// contraction over t = (k, i, a).
+// chi0_PQ(q, w) = - sum_t conj(A_Pt) C_Qt with A = zeta_k |d_t(w)| C (the
+// fit-basis response of Sec. 2.2; d_t < 0) is a dense Hermitian contraction
+// over t = (k, i, a).  The frequency weight sits on the A side only, so the B
+// operand (slices of C itself) is built once per q and reused by every
+// frequency; only A is re-sliced per frequency.
 //
 // Digit slices.  Each FP64 value x of row P becomes the fixed-point integer
 // F = round(x 2^(31 - e_P)), |F| <= 2^30, e_P one exponent per row and
@@ -13,11 +15,11 @@
 //
 // Real embedding.  A complex row is stored interleaved, X = (re_0, im_0, re_1,
 // im_1, ...), and the B operand of a tile stacks X_Q over Y_Q = (im_0, -re_0,
-// ...), so that one MMA of N = 128 gives [X_P X_Q^T | X_P Y_Q^T] =
-// [Re | Im] of sum_t conj(A_P) A_Q for 64 columns Q.
+// ...) of C, so that one MMA of N = 128 gives [X_P X_Q^T | X_P Y_Q^T] =
+// [Re | Im] of sum_t conj(A_P) C_Q for 64 columns Q.
 //
 // Exactness.  Slice pairs (i, j) with i + j <= s - 1, plus (s/2, s/2) for even
-// s (it removes the bias of the dropped level on the diagonal), are grouped by
+// s (the largest dropped level), are grouped by
 // level into four TMEM accumulators: levels 0, 1 and 2 hold integer-valued
 // sums that stay below 2^24 for CHUNK t (exact FP32 accumulation whatever the
 // tensor core's rounding), levels 3 and 4 (2^-24 and 2^-32 below level 0) are
@@ -26,7 +28,8 @@
 //
 // Tile: 128 rows P x 64 complex columns Q (128 x 128 for real data), K-blocks
 // of 16 real values; operands arrive by TMA (4-D tensor maps over the slice
-// buffer [g*s + slice][X|Y][row][k], 32-byte swizzle), one elected thread issues
+// buffers [g*s + slice][X][row][k] of A and [slice][X|Y][row][k] of C, 32-byte
+// swizzle), one elected thread issues
 // tcgen05.mma, eight epilogue warps drain TMEM with tcgen05.ld.  The K range of
 // each tile is split over CTAs (split-K); a reduction kernel adds the partials
 // in a fixed order, applies the exponents and writes chi0 in FP64 (lower
@@ -178,154 +181,254 @@ __device__ __forceinline__ void ff_add4(float& hi, float& lo, float g0, float g1
 }
 
 // ------------------------------------------------------------ slicing -----
-// |x| = |c| w from the FP64 bit patterns: 30-bit rounded significands, 60-bit
-// product, rounded to F = round(x 2^(31 - e)); |F| <= 2^30 when
-// e >= Ec + Ew - 2044 + 1 (biased exponents of c and w).
-__device__ __forceinline__ int fixed_point(double c, double w, int e) {
-  const unsigned long long cb = (unsigned long long)__double_as_longlong(c);
-  const unsigned long long wb = (unsigned long long)__double_as_longlong(w);
-  const int Ec = (int)((cb >> 52) & 0x7ff), Ew = (int)((wb >> 52) & 0x7ff);
-  if (Ec == 0 || Ew == 0) return 0;
-  const unsigned long long mc = (((cb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) + (1ull << 22)) >> 23;  // <= 2^30
-  const unsigned long long mw = (((wb & 0xFFFFFFFFFFFFFull) | (1ull << 52)) + (1ull << 22)) >> 23;
-  const unsigned long long p = mc * mw;  // <= 2^60
-  const int sh = e + 2073 - Ec - Ew;     // >= 30 by the choice of e
-  if (sh >= 62 || sh < 30) return 0;
-  const int F = (int)((p + (1ull << (sh - 1))) >> sh);
-  return (cb >> 63) ? -F : F;
-}
+// Fixed-point inputs, built once per q (C) and once per frequency table (w):
+//   c_fix = round(c 2^(30 - eC_P)), |c| < 2^eC_P for the whole row P, |c_fix| <= 2^30;
+//   w = w_m 2^(ew - 31) with w_m in [2^30, 2^31), one 31-bit mantissa per (k, t, w).
+// A digit set is produced from an integer F (|F| <= 2^30):
+//   F + 0x808080 = (d0 2^24) + (d1+128) 2^16 + (d2+128) 2^8 + (d3+128),
+// each biased byte b is turned into the BF16 of (b - 128) 2^(-8i) by the
+// exact float trick (2^23 + b) 2^(-8i) - (2^23 + 128) 2^(-8i) (one FFMA, no I2F).
 
-__device__ __forceinline__ uint32_t bf16_of(int d, int lvl) {
-  // d 2^(-8 lvl) is exact in BF16 (|d| <= 128)
-  const float f = (float)d * __int_as_float((127 - 8 * lvl) << 23);
+__device__ __forceinline__ uint32_t bf16_digit(uint32_t byte, int lvl) {
+  const float scale = __int_as_float((127 - 8 * lvl) << 23);
+  const float f = fmaf(__uint_as_float(0x4B000000u | byte), scale, -8388736.0f * scale);
   return __float_as_uint(f) >> 16;
 }
 
-__device__ __forceinline__ void split_digits(int F, int d[4]) {
-  d[0] = (F + (1 << 23)) >> 24;
-  F -= d[0] << 24;
-  d[1] = (F + (1 << 15)) >> 16;
-  F -= d[1] << 16;
-  d[2] = (F + (1 << 7)) >> 8;
-  F -= d[2] << 8;
-  d[3] = F;
+// Biased digit bytes of F: b[0] = d0 + 128, b[i] = d_i + 128.
+__device__ __forceinline__ void digit_bytes(int F, uint32_t b[4]) {
+  const uint32_t G = (uint32_t)(F + 0x808080);
+  b[0] = ((G ^ 0x80000000u) >> 24);
+  b[1] = (G >> 16) & 0xFFu;
+  b[2] = (G >> 8) & 0xFFu;
+  b[3] = G & 0xFFu;
+}
+
+// c_fix of one q: [Npad][Kr] int32, zero outside the data; eC per row.
+__global__ void __launch_bounds__(256) cfix_kernel(int cplx, int N, int Npad, int n_ov, int n_k, int Ktot, int Kr,
+                                                   const double* const* C, const int* eC, int* cfix) {
+  const long total = (long)Npad * Kr;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int P = (int)(idx / Kr), k = (int)(idx % Kr);
+    const int tglob = cplx ? (k >> 1) : k;
+    int v = 0;
+    if (P < N && tglob < Ktot) {
+      const int j = tglob / n_ov, t = tglob - j * n_ov;
+      const double c = cplx ? C[j][2 * ((long)P * n_ov + t) + (k & 1)] : C[j][(long)P * n_ov + t];
+      const unsigned long long cb = (unsigned long long)__double_as_longlong(c);
+      const int Ec = (int)((cb >> 52) & 0x7ff);
+      if (Ec != 0) {
+        // c = mant 2^(Ec - 1075); c_fix = c 2^(30 - eC) = mant >> (1045 - Ec + eC)
+        const int sh = 1045 - Ec + eC[P];
+        const unsigned long long mant = (cb & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        if (sh < 64) {
+          const int m = (int)((mant + (1ull << (sh - 1))) >> sh);
+          v = (cb >> 63) ? -m : m;
+        }
+      }
+    }
+    cfix[idx] = v;
+  }
 }
 
 struct SliceArgs {
-  int cplx, N, Npad, n_ov, n_k, Ktot, Kr, s, n_w, w0, G, nxy;
-  const double* const* C;  // [n_k] blocks of this q
-  const double* wtab;      // [n_k][n_w][n_ov] sqrt(zeta |d|)
-  const int* erow;         // [G][Npad] row exponents
-  uint16_t* S;             // [(g*s + slice)][xy][Npad][Kr]
+  int cplx, Npad, n_ov, Ktot, Kr, s, n_w, w0, G, nxy;
+  const int* cfix;       // [Npad][Kr]
+  const int* eC;         // [Npad] exponent of c_fix
+  const uint32_t* wm;    // [n_k][n_w][n_ov] weight mantissas, or null for weight 1
+  const int16_t* ew;     // [n_k][n_w][n_ov] weight exponents
+  const int* eA;         // [n_w][Npad] row exponents of A
+  uint16_t* S;           // [(g*s + slice)][xy][Npad][Kr]
 };
 
-// Row exponents e_P(w) = max_t (Ec_t + Ew_t) - 2044 + 1, one block per row.
-__global__ void __launch_bounds__(256) erow_kernel(int cplx, int N, int Npad, int n_ov, int n_k, int n_w, int w0,
-                                                   int G, const double* const* C, const double* wtab, int* erow) {
-  const int P = blockIdx.x;
-  int m[16];
+// One thread per (row, 16 real values); it loops over the G frequencies of the
+// launch (the 16 fixed-point values of C are loaded once).  With wm == null
+// the digits of C itself are written (X and, for complex data, Y = (im, -re)).
+__device__ __forceinline__ void store_planes(const SliceArgs& a, int g, int P, int tg, const uint32_t (&px)[MAX_S][8],
+                                             const uint32_t (&py)[MAX_S][8]) {
 #pragma unroll
-  for (int g = 0; g < 16; ++g) m[g] = 0;
+  for (int i = 0; i < MAX_S; ++i) {
+    if (i >= a.s) break;
+    uint4* dx = reinterpret_cast<uint4*>(a.S + ((((long)g * a.s + i) * a.nxy + 0) * a.Npad + P) * a.Kr + tg * 16);
+    dx[0] = make_uint4(px[i][0], px[i][1], px[i][2], px[i][3]);
+    dx[1] = make_uint4(px[i][4], px[i][5], px[i][6], px[i][7]);
+    if (a.nxy == 2) {
+      uint4* dy = reinterpret_cast<uint4*>(a.S + ((((long)g * a.s + i) * a.nxy + 1) * a.Npad + P) * a.Kr + tg * 16);
+      dy[0] = make_uint4(py[i][0], py[i][1], py[i][2], py[i][3]);
+      dy[1] = make_uint4(py[i][4], py[i][5], py[i][6], py[i][7]);
+    }
+  }
+}
+
+__device__ __forceinline__ void digits_to_planes(int F, int u, int s, bool with_y, uint32_t (&px)[MAX_S][8],
+                                                 uint32_t (&py)[MAX_S][8]) {
+  uint32_t b[4];
+  digit_bytes(F, b);
+#pragma unroll
+  for (int i = 0; i < MAX_S; ++i) {
+    if (i >= s) break;
+    const uint32_t h = bf16_digit(b[i], i);
+    px[i][u >> 1] |= (u & 1) ? (h << 16) : h;
+    if (with_y) {  // Y[2k] = im_k, Y[2k+1] = -re_k
+      if (u & 1)
+        py[i][u >> 1] |= h;
+      else
+        py[i][u >> 1] |= (h ^ 0x8000u) << 16;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) slice_kernel(SliceArgs a) {
+  const long ngroups = (long)a.Kr / 16;
+  const long total = (long)a.Npad * ngroups;
+  const bool with_y = a.nxy == 2;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int tg = (int)(idx % ngroups);
+    const int P = (int)(idx / ngroups);
+    const int4* src = reinterpret_cast<const int4*>(a.cfix + (long)P * a.Kr + tg * 16);
+    int cv[16];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int4 x = src[v];
+      cv[4 * v] = x.x;
+      cv[4 * v + 1] = x.y;
+      cv[4 * v + 2] = x.z;
+      cv[4 * v + 3] = x.w;
+    }
+    uint32_t px[MAX_S][8], py[MAX_S][8];
+    if (!a.wm) {
+#pragma unroll
+      for (int i = 0; i < MAX_S; ++i)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) px[i][u] = py[i][u] = 0;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) digits_to_planes(cv[u], u, a.s, with_y, px, py);
+      store_planes(a, 0, P, tg, px, py);
+      continue;
+    }
+    // weights of the t's of this group: complex 8 t (2 real values each), real 16 t
+    const int tpg = a.cplx ? 8 : 16;
+    const int t0 = tg * tpg;
+    for (int g = 0; g < a.G; ++g) {
+      const int w = a.w0 + g;
+      const int shbase = 30 + a.eA[(long)w * a.Npad + P] - a.eC[P];
+#pragma unroll
+      for (int i = 0; i < MAX_S; ++i)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) px[i][u] = py[i][u] = 0;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int tl = a.cplx ? (u >> 1) : u;
+        const int tglob = t0 + tl;
+        int F = 0;
+        if (cv[u] != 0 && tglob < a.Ktot) {
+          const int j = tglob / a.n_ov, t = tglob - j * a.n_ov;
+          const long wi = ((long)j * a.n_w + w) * a.n_ov + t;
+          const long long p = (long long)cv[u] * (long long)__ldg(a.wm + wi);
+          const int sh = shbase - (int)__ldg(a.ew + wi);
+          F = (sh > 0) ? (int)((p + (1ll << (sh - 1))) >> sh) : (int)(p << (-sh));
+        }
+        digits_to_planes(F, u, a.s, false, px, py);
+      }
+      store_planes(a, g, P, tg, px, py);
+    }
+  }
+}
+
+// Row exponents.  eA[w][P] = max_t (Ec_t + Ew_t) - 2044 + 1 (biased fields),
+// so |c w| < 2^(eA - 1) on row P; eC[P] = max_t Ec_t - 1022, so |c| < 2^eC.
+// One block per row; the weight exponents come from the 16-bit table ew.
+constexpr int MAX_W = 32;
+__global__ void __launch_bounds__(256) erow_kernel(int cplx, int N, int Npad, int n_ov, int n_k, int n_w,
+                                                   const double* const* C, const int16_t* ew, int* eA, int* eC) {
+  const int P = blockIdx.x;
+  int m[MAX_W];
+  int mc = 0;
+#pragma unroll
+  for (int g = 0; g < MAX_W; ++g) m[g] = 0;
   if (P < N) {
+    const int n8 = (n_ov + 7) / 8;
     for (int j = 0; j < n_k; ++j) {
       const unsigned long long* row =
           reinterpret_cast<const unsigned long long*>(C[j]) + (long)P * n_ov * (cplx ? 2 : 1);
-      for (int t = threadIdx.x; t < n_ov; t += blockDim.x) {
-        int ec = (int)((row[cplx ? 2 * t : t] >> 52) & 0x7ff);
-        if (cplx) ec = max(ec, (int)((row[2 * t + 1] >> 52) & 0x7ff));
-        if (ec == 0) continue;
+      for (int t8 = threadIdx.x; t8 < n8; t8 += blockDim.x) {
+        int ec[8];
+        int emax = 0;
 #pragma unroll
-        for (int g = 0; g < 16; ++g) {
-          if (g >= G) break;
-          const double wv = wtab[((long)j * n_w + w0 + g) * n_ov + t];
-          const int ew = (int)((__double_as_longlong(wv) >> 52) & 0x7ff);
-          m[g] = max(m[g], ec + ew);
+        for (int u = 0; u < 8; ++u) {
+          const int t = t8 * 8 + u;
+          ec[u] = -100000;
+          if (t < n_ov) {
+            int e = (int)((row[cplx ? 2 * t : t] >> 52) & 0x7ff);
+            if (cplx) e = max(e, (int)((row[2 * t + 1] >> 52) & 0x7ff));
+            if (e != 0) ec[u] = e;
+            emax = max(emax, e);
+          }
+        }
+        mc = max(mc, emax);
+        if (emax == 0) continue;
+        const int16_t* e0 = ew + (long)j * n_w * n_ov + t8 * 8;
+        const bool vec = (n_ov % 8 == 0);
+#pragma unroll
+        for (int g = 0; g < MAX_W; ++g) {
+          if (g >= n_w) break;
+          int16_t ev[8];
+          if (vec) {
+            const uint4 v = *reinterpret_cast<const uint4*>(e0 + (long)g * n_ov);
+            memcpy(ev, &v, 16);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) ev[u] = (t8 * 8 + u < n_ov) ? e0[(long)g * n_ov + u] : (int16_t)0;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) m[g] = max(m[g], ec[u] + (int)ev[u] + 1022);
         }
       }
     }
   }
   __shared__ int red[256];
 #pragma unroll
-  for (int g = 0; g < 16; ++g) {
-    if (g >= G) break;
+  for (int g = 0; g < MAX_W; ++g) {
+    if (g >= n_w) break;
     red[threadIdx.x] = m[g];
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
       if (threadIdx.x < o) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + o]);
       __syncthreads();
     }
-    if (threadIdx.x == 0) erow[(long)g * Npad + P] = red[0] ? red[0] - 2044 + 1 : 0;
+    if (threadIdx.x == 0) eA[(long)g * Npad + P] = red[0] > 0 ? red[0] - 2044 + 1 : -2000;
     __syncthreads();
   }
-}
-
-// One thread per (row, 16 real values, frequency).
-__global__ void __launch_bounds__(256) slice_kernel(SliceArgs a) {
-  const int tpg = a.cplx ? 8 : 16;  // t per group
-  const long ngroups = (long)a.Kr / 16;
-  const long total = (long)a.Npad * ngroups * a.G;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    long r = idx;
-    const int g = (int)(r % a.G);
-    r /= a.G;
-    const int tg = (int)(r % ngroups);
-    const int P = (int)(r / ngroups);
-    const int w = a.w0 + g;
-    const int e = a.erow[(long)g * a.Npad + P];
-    uint32_t px[MAX_S][8], py[MAX_S][8];
-#pragma unroll
-    for (int i = 0; i < MAX_S; ++i)
-#pragma unroll
-      for (int u = 0; u < 8; ++u) px[i][u] = py[i][u] = 0;
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {  // real position within the group
-      const int tl = a.cplx ? (u >> 1) : u;
-      const int tglob = tg * tpg + tl;
-      int F = 0;
-      if (P < a.N && tglob < a.Ktot) {
-        const int j = tglob / a.n_ov, t = tglob - j * a.n_ov;
-        const double wv = a.wtab[((long)j * a.n_w + w) * a.n_ov + t];
-        const double cv = a.cplx ? a.C[j][2 * ((long)P * a.n_ov + t) + (u & 1)] : a.C[j][(long)P * a.n_ov + t];
-        F = fixed_point(cv, wv, e);
-      }
-      int d[4];
-      split_digits(F, d);
-#pragma unroll
-      for (int i = 0; i < MAX_S; ++i) {
-        if (i >= a.s) break;
-        const uint32_t h = bf16_of(d[i], i);
-        px[i][u >> 1] |= (u & 1) ? (h << 16) : h;
-        // Y = (im, -re) per complex pair: Y[2k] = im_k, Y[2k+1] = -re_k
-        if (u & 1)
-          py[i][u >> 1] |= h;
-        else
-          py[i][u >> 1] |= (h ^ 0x8000u) << 16;
-      }
-    }
-    for (int i = 0; i < a.s; ++i) {
-      uint4* dx = reinterpret_cast<uint4*>(a.S + ((((long)g * a.s + i) * a.nxy + 0) * a.Npad + P) * a.Kr + tg * 16);
-      dx[0] = make_uint4(px[i][0], px[i][1], px[i][2], px[i][3]);
-      dx[1] = make_uint4(px[i][4], px[i][5], px[i][6], px[i][7]);
-      if (a.cplx) {
-        uint4* dy =
-            reinterpret_cast<uint4*>(a.S + ((((long)g * a.s + i) * a.nxy + 1) * a.Npad + P) * a.Kr + tg * 16);
-        dy[0] = make_uint4(py[i][0], py[i][1], py[i][2], py[i][3]);
-        dy[1] = make_uint4(py[i][4], py[i][5], py[i][6], py[i][7]);
-      }
-    }
+  red[threadIdx.x] = mc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
   }
+  if (threadIdx.x == 0) eC[P] = red[0] ? red[0] - 1022 : -2000;
 }
 
-// w = sqrt(zeta_k |d|)
-__global__ void __launch_bounds__(256) wtab_kernel(long n, const double* dtab, double* wtab) {
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    wtab[i] = sqrt(fabs(dtab[i]));
+// w = zeta_k |d| as a 31-bit mantissa and exponent: w = wm 2^(ew - 31),
+// wm in [2^30, 2^31)
+__global__ void __launch_bounds__(256) wtab_kernel(long n, const double* dtab, uint32_t* wm, int16_t* ew) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(dtab[i]));
+    const int E = (int)((b >> 52) & 0x7ff);
+    unsigned long long m = (((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) + (1ull << 21)) >> 22;  // [2^30, 2^31]
+    int e = E - 1022;
+    if (m >> 31) {
+      m >>= 1;
+      ++e;
+    }
+    wm[i] = E ? (uint32_t)m : 0u;
+    ew[i] = (int16_t)(E ? e : -2000);
+  }
 }
 
 // ---------------------------------------------------------- GEMM kernel ----
 
 struct TcArgs {
-  int cplx, s;
+  int cplx, s, G;
   int n_tiles, n_ksplit, kb_per_split, n_kb, kb_per_chunk;
   int n_items;
   float* part;  // [item][2 (hi, lo)][128 rows][128 cols]
@@ -352,11 +455,14 @@ __device__ __forceinline__ void tile_ij(int cplx, int t, int& I, int& J) {
   }
 }
 
+// item = (ks * G + g) * n_tiles + tile: CTAs that run at the same time work on
+// the same K range, so the frequency-independent B operand (slices of C) and
+// the A rows of each frequency are read from HBM about once and shared in L2.
 __device__ __forceinline__ void item_coords(const TcArgs& a, int item, int& g, int& I, int& J, int& ks) {
-  ks = item % a.n_ksplit;
-  const int r = item / a.n_ksplit;
-  const int tile = r % a.n_tiles;
-  g = r / a.n_tiles;
+  const int tile = item % a.n_tiles;
+  const int r = item / a.n_tiles;
+  g = r % a.G;
+  ks = r / a.G;
   tile_ij(a.cplx, tile, I, J);
 }
 
@@ -415,7 +521,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           mbar_expect_tx(&full[stage], stage_tx);
           // A: X slices of rows I*128.. ; B: [X; Y] slices of columns J*64.. (real: X of J*128..)
           tma_load_4d(sa, &mapA, &full[stage], kb * KB, I * TILE_M, 0, g * a.s);
-          tma_load_4d(sb, &mapB, &full[stage], kb * KB, J * (a.cplx ? 64 : 128), 0, g * a.s);
+          tma_load_4d(sb, &mapB, &full[stage], kb * KB, J * (a.cplx ? 64 : 128), 0, 0);
           armed[stage] = (int)phase;
           if (++stage == STAGES) {
             stage = 0;
@@ -539,8 +645,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 struct ReduceArgs {
   int cplx, N, Npad, n_tiles, n_ksplit, w0, G;
   const float* part;
-  const int* erow;  // [G][Npad]
-  double* chi;      // [n_w][N][N] of this q
+  const int* erow;   // [n_w][Npad] exponents of the weighted rows (A)
+  const int* erowC;  // [Npad] exponents eC of C (B digits use e = eC + 1)
+  double* chi;       // [n_w][N][N] of this q
 };
 
 __global__ void __launch_bounds__(256) reduce_kernel(ReduceArgs a) {
@@ -557,13 +664,13 @@ __global__ void __launch_bounds__(256) reduce_kernel(ReduceArgs a) {
     if (P >= a.N || Q >= a.N || Q > P) continue;
     double re = 0.0, im = 0.0;
     for (int ks = 0; ks < a.n_ksplit; ++ks) {
-      const long item = ((long)g * a.n_tiles + tile) * a.n_ksplit + ks;
+      const long item = ((long)ks * a.G + g) * a.n_tiles + tile;
       const float* p = a.part + item * 2 * 128 * 128 + (long)r * 128;
       re += (double)p[c] + (double)p[128 * 128 + c];
       if (a.cplx) im += (double)p[64 + c] + (double)p[128 * 128 + 64 + c];
     }
-    const int e = a.erow[(long)g * a.Npad + P] + a.erow[(long)g * a.Npad + Q];
-    const double sc = -ldexp(1.0, e - 14);  // x = 2^(e_P - 7) sum v, chi = -sum conj(x) x
+    const int e = a.erow[(long)(a.w0 + g) * a.Npad + P] + a.erowC[Q] + 1;  // B side: e = eC + 1
+    const double sc = -ldexp(1.0, e - 14);  // x = 2^(e - 7) sum v, chi = -sum conj(a) c
     re *= sc;
     im *= sc;
     if (a.cplx) {
@@ -615,7 +722,7 @@ int num_sms() {
 
 struct MixedLayout {
   int Npad, Ktot, Kr, nxy, G, n_tiles, n_kb, kb_per_chunk, n_ksplit, kb_per_split, n_items;
-  size_t slices, erow, part, wtab, err, total;
+  size_t slices, slicesC, erow, erowC, part, wm, ew, cfix, err, total;
 };
 
 MixedLayout mixed_layout(const BatchGeom& g, int s, int sms) {
@@ -630,7 +737,7 @@ MixedLayout mixed_layout(const BatchGeom& g, int s, int sms) {
   L.kb_per_chunk = 2 * CHUNK / KB;
   const int nb = L.Npad / 128;
   L.n_tiles = g.cplx ? nb * (nb + 1) : nb * (nb + 1) / 2;
-  const size_t per_w = (size_t)s * L.nxy * L.Npad * L.Kr * 2;
+  const size_t per_w = (size_t)s * L.Npad * L.Kr * 2;  // A: X planes only
   L.G = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(g.n_w, 16), ((size_t)12 << 30) / per_w));
   const int n_chunks = L.n_kb / L.kb_per_chunk;
   const int want = 4 * sms;
@@ -642,18 +749,23 @@ MixedLayout mixed_layout(const BatchGeom& g, int s, int sms) {
   L.n_items = L.G * L.n_tiles * L.n_ksplit;
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
   L.slices = al(per_w * L.G);
-  L.erow = al(sizeof(int) * L.G * L.Npad);
+  L.slicesC = al(per_w * L.nxy);
+  L.erow = al(sizeof(int) * (size_t)g.n_w * L.Npad);
+  L.erowC = al(sizeof(int) * (size_t)L.Npad);
   L.part = al(sizeof(float) * 2 * 128 * 128 * (size_t)L.n_items);
-  L.wtab = al(sizeof(double) * (size_t)g.n_k * g.n_w * g.n_ov);
+  L.wm = al(sizeof(uint32_t) * (size_t)g.n_k * g.n_w * g.n_ov);
+  L.ew = al(sizeof(int16_t) * (size_t)g.n_k * g.n_w * g.n_ov);
+  L.cfix = al(sizeof(int) * (size_t)L.Npad * L.Kr);
   L.err = al(sizeof(int) * 4);
-  L.total = L.slices + L.erow + L.part + L.wtab + L.err;
+  L.total = L.slices + L.slicesC + L.erow + L.erowC + L.part + L.wm + L.ew + L.cfix + L.err;
   return L;
 }
 
-bool encode_map(EncodeTiledFn enc, CUtensorMap* m, void* base, const MixedLayout& L, int s, int brows, int bxy) {
-  cuuint64_t dims[4] = {(cuuint64_t)L.Kr, (cuuint64_t)L.Npad, (cuuint64_t)L.nxy, (cuuint64_t)L.G * s};
-  cuuint64_t strides[3] = {(cuuint64_t)L.Kr * 2, (cuuint64_t)L.Kr * 2 * L.Npad,
-                           (cuuint64_t)L.Kr * 2 * L.Npad * L.nxy};
+// 4-D map over [planes][nxy][Npad][Kr] BF16 with a box of {16, brows, bxy, s}
+bool encode_map(EncodeTiledFn enc, CUtensorMap* m, void* base, const MixedLayout& L, int s, int brows, int bxy,
+                int nxy, int planes) {
+  cuuint64_t dims[4] = {(cuuint64_t)L.Kr, (cuuint64_t)L.Npad, (cuuint64_t)nxy, (cuuint64_t)planes};
+  cuuint64_t strides[3] = {(cuuint64_t)L.Kr * 2, (cuuint64_t)L.Kr * 2 * L.Npad, (cuuint64_t)L.Kr * 2 * L.Npad * nxy};
   cuuint32_t box[4] = {(cuuint32_t)KB, (cuuint32_t)brows, (cuuint32_t)bxy, (cuuint32_t)s};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -678,7 +790,7 @@ uint64_t mixed_tensor_flops(const BatchGeom& g, int s) {
 cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cptrs, const double* dtab,
                               double* chi, void* work, size_t work_bytes, int* status, uint64_t* n_launch,
                               cudaStream_t st) {
-  if (s < 2 || s > MAX_S) return cudaErrorInvalidValue;
+  if (s < 2 || s > MAX_S || g.n_w > MAX_W) return cudaErrorInvalidValue;
   EncodeTiledFn enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
   const int sms = num_sms();
@@ -687,12 +799,20 @@ cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cp
   char* p = (char*)work;
   uint16_t* S = (uint16_t*)p;
   p += L.slices;
+  uint16_t* SC = (uint16_t*)p;
+  p += L.slicesC;
   int* erow = (int*)p;
   p += L.erow;
+  int* erowC = (int*)p;
+  p += L.erowC;
   float* part = (float*)p;
   p += L.part;
-  double* wtab = (double*)p;
-  p += L.wtab;
+  uint32_t* wm = (uint32_t*)p;
+  p += L.wm;
+  int16_t* ew = (int16_t*)p;
+  p += L.ew;
+  int* cfix = (int*)p;
+  p += L.cfix;
   int* err = (int*)p;
 
   static thread_local int attr_done = 0;
@@ -703,18 +823,30 @@ cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cp
     attr_done = 1;
   }
   CUtensorMap mapA, mapB;
-  if (!encode_map(enc, &mapA, S, L, s, 128, 1) ||
-      !encode_map(enc, &mapB, S, L, s, g.cplx ? 64 : 128, g.cplx ? 2 : 1))
+  if (!encode_map(enc, &mapA, S, L, s, 128, 1, 1, L.G * s) ||
+      !encode_map(enc, &mapB, SC, L, s, g.cplx ? 64 : 128, L.nxy, L.nxy, s))
     return cudaErrorInvalidValue;
   uint64_t nl = 0;
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int) * 4, st);
   if (e != cudaSuccess) return e;
   const long nwt = (long)g.n_k * g.n_w * g.n_ov;
-  wtab_kernel<<<(unsigned)std::min<long>((nwt + 255) / 256, (long)sms * 16), 256, 0, st>>>(nwt, dtab, wtab);
-  ++nl;
+  wtab_kernel<<<(unsigned)std::min<long>((nwt + 255) / 256, (long)sms * 16), 256, 0, st>>>(nwt, dtab, wm, ew);
+  erow_kernel<<<L.Npad, 256, 0, st>>>(g.cplx, g.n_aux, L.Npad, g.n_ov, g.n_k, g.n_w, Cptrs, ew, erow, erowC);
+  {
+    const long total = (long)L.Npad * L.Kr;
+    cfix_kernel<<<(unsigned)std::min<long>((total + 255) / 256, (long)sms * 32), 256, 0, st>>>(
+        g.cplx, g.n_aux, L.Npad, g.n_ov, g.n_k, L.Ktot, L.Kr, Cptrs, erowC, cfix);
+  }
+  {  // digits of C itself (B operand, X and Y), once per q
+    SliceArgs sc{g.cplx, L.Npad, g.n_ov, L.Ktot, L.Kr, s, g.n_w, 0, 1, L.nxy, cfix, erowC, nullptr, nullptr, erow, SC};
+    const long total = (long)L.Npad * (L.Kr / 16);
+    slice_kernel<<<(unsigned)std::min<long>((total + 255) / 256, (long)sms * 32), 256, 0, st>>>(sc);
+  }
+  nl += 4;
   TcArgs ta{};
   ta.cplx = g.cplx;
   ta.s = s;
+  ta.G = L.G;
   ta.n_tiles = L.n_tiles;
   ta.n_ksplit = L.n_ksplit;
   ta.kb_per_split = L.kb_per_split;
@@ -741,15 +873,15 @@ cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cp
   for (int i = 0; i < np; ++i) ta.grp_mask |= 1 << ta.pair_grp[i];
   for (int w0 = 0; w0 < g.n_w; w0 += L.G) {
     const int G = std::min(L.G, g.n_w - w0);
-    erow_kernel<<<L.Npad, 256, 0, st>>>(g.cplx, g.n_aux, L.Npad, g.n_ov, g.n_k, g.n_w, w0, G, Cptrs, wtab, erow);
-    SliceArgs sa{g.cplx, g.n_aux, L.Npad, g.n_ov, g.n_k, L.Ktot, L.Kr, s, g.n_w, w0, G, L.nxy, Cptrs, wtab, erow, S};
-    const long total = (long)G * L.Npad * (L.Kr / 16);
+    SliceArgs sa{g.cplx, L.Npad, g.n_ov, L.Ktot, L.Kr, s, g.n_w, w0, G, 1, cfix, erowC, wm, ew, erow, S};
+    const long total = (long)L.Npad * (L.Kr / 16);
     slice_kernel<<<(unsigned)std::min<long>((total + 255) / 256, (long)sms * 32), 256, 0, st>>>(sa);
     ta.n_items = G * L.n_tiles * L.n_ksplit;
+    ta.G = G;
     chi0_tc_kernel<<<std::min(ta.n_items, sms), THREADS, smem, st>>>(mapA, mapB, ta);
-    ReduceArgs ra{g.cplx, g.n_aux, L.Npad, L.n_tiles, L.n_ksplit, w0, G, part, erow, chi};
+    ReduceArgs ra{g.cplx, g.n_aux, L.Npad, L.n_tiles, L.n_ksplit, w0, G, part, erow, erowC, chi};
     reduce_kernel<<<G * L.n_tiles, 256, 0, st>>>(ra);
-    nl += 4;
+    nl += 3;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
