@@ -216,12 +216,16 @@ rpa_status validate_job(const rpa_job* j, char* msg, size_t len) {
 
 struct Layout {
   size_t meta, dtab, chi, T, L, stageC, stageV, eps, mixed, total;
+  size_t slice_cap;  // mixed path: bytes for the weighted operand's digit planes
   int qb;
 };
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static Layout plan_layout(const rpa_job* j, int qb, int n_slices) {
+// Workspace cap of the synchronous calls (the serving lanes use a smaller one).
+static size_t sync_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap, (size_t)64 << 30); }
+
+static Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap) {
   Layout L{};
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
@@ -242,7 +246,8 @@ static Layout plan_layout(const rpa_job* j, int qb, int n_slices) {
   }
   if (j->prec == RPA_PREC_MIXED) {
     BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, (int)nov, j->n_k, j->n_w, 1};
-    L.mixed = al(mixed_workspace_bytes(g, n_slices));
+    L.slice_cap = ws_cap / 2;
+    L.mixed = al(mixed_workspace_bytes(g, n_slices, L.slice_cap));
   }
   L.total = L.meta + L.dtab + L.chi + L.T + L.L + 2 * (L.stageC + L.stageV) + L.eps + L.mixed;
   return L;
@@ -250,12 +255,12 @@ static Layout plan_layout(const rpa_job* j, int qb, int n_slices) {
 
 static int choose_qb(const rpa_job* j, int n_slices, size_t cap) {
   int qb = j->n_q;
-  while (qb > 1 && plan_layout(j, qb, n_slices).total > cap) qb = (qb + 1) / 2;
+  while (qb > 1 && plan_layout(j, qb, n_slices, cap).total > cap) qb = (qb + 1) / 2;
   return qb;
 }
 
 size_t job_footprint(const rpa_job* j, int n_slices, size_t ws_cap) {
-  Layout L = plan_layout(j, choose_qb(j, n_slices, ws_cap), n_slices);
+  Layout L = plan_layout(j, choose_qb(j, n_slices, ws_cap), n_slices, ws_cap);
   size_t in = 0;
   if (j->mem == RPA_MEM_DEVICE) {
     const size_t es = j->is_complex ? 16 : 8;
@@ -286,6 +291,7 @@ struct Bufs {
   double* eps_virt;
   void* mixed;
   size_t mixed_bytes;
+  size_t slice_cap;
 };
 
 static Bufs carve(void* ws, const rpa_job* j, const Layout& L) {
@@ -335,6 +341,7 @@ static Bufs carve(void* ws, const rpa_job* j, const Layout& L) {
   p += L.eps;
   b.mixed = p;
   b.mixed_bytes = L.mixed;
+  b.slice_cap = L.slice_cap;
   return b;
 }
 
@@ -385,7 +392,7 @@ static rpa_status run_qbatch(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bu
       prof_begin(ctx, pex, s);
       CK(launch_chi0_mixed(g1, n_slices, (const double* const*)(b.Cptrs + (size_t)(q0 + qi) * nk),
                            b.dtab + (size_t)qi * nk * j->n_w * g.n_ov, chi + (size_t)qi * j->n_w * NN * (es / 8),
-                           b.mixed, b.mixed_bytes, b.status, &nl, s));
+                           b.mixed, b.mixed_bytes, b.status, &nl, s, b.slice_cap));
       prof_end(ctx, pex, s, RPA_K_CHI0, (int)nl);
       ctx->launches += nl;
     }
@@ -445,7 +452,7 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
   CK(cudaSetDevice(ctx->device));
   cudaStream_t s = ex.s;
   const int qb = choose_qb(job, ctx->n_slices, ws_cap);
-  Layout L = plan_layout(job, qb, ctx->n_slices);
+  Layout L = plan_layout(job, qb, ctx->n_slices, ws_cap);
   if (!ex.ensure_ws(L.total)) {
     ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", L.total);
     return RPA_E_NOMEM;
@@ -532,7 +539,6 @@ rpa_status energy_finish(rpa_ctx* ctx, Exec& ex, const rpa_job* job, double* Ec,
   return RPA_OK;
 }
 
-static size_t sync_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap, (size_t)24 << 30); }
 
 }  // namespace rpa
 
@@ -652,7 +658,7 @@ rpa_status rpa_chi0(rpa_ctx* ctx, const rpa_job* job, int q, void* chi_out, void
   CK(cudaSetDevice(ctx->device));
   Exec& ex = ctx->ex;
   cudaStream_t s = (cudaStream_t)stream;
-  Layout L = plan_layout(job, 1, ctx->n_slices);
+  Layout L = plan_layout(job, 1, ctx->n_slices, sync_ws_cap(ctx));
   if (!ex.ensure_ws(L.total)) {
     ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", L.total);
     return RPA_E_NOMEM;
@@ -689,7 +695,7 @@ rpa_status rpa_logdet(rpa_ctx* ctx, const rpa_job* job, int q, const void* chi, 
   cudaStream_t s = (cudaStream_t)stream;
   rpa_job j1 = *job;
   j1.prec = RPA_PREC_FP64;
-  Layout L = plan_layout(&j1, 1, ctx->n_slices);
+  Layout L = plan_layout(&j1, 1, ctx->n_slices, sync_ws_cap(ctx));
   if (!ex.ensure_ws(L.total)) {
     ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", L.total);
     return RPA_E_NOMEM;

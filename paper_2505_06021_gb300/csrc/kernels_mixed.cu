@@ -43,6 +43,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "rpa_internal.h"
 
@@ -426,16 +427,29 @@ __global__ void __launch_bounds__(256) wtab_kernel(long n, const double* dtab, u
 }
 
 // ---------------------------------------------------------- GEMM kernel ----
+// One persistent launch covers several "segments": a segment is one q of one
+// job with G frequencies, its own operand tensor maps and partial buffer.  The
+// segment table travels in the kernel parameters (tensor maps as grid
+// constants), so a launch needs no device-side table and records cleanly into
+// a CUDA graph.
 
-struct TcArgs {
-  int cplx, s, G;
-  int n_tiles, n_ksplit, kb_per_split, n_kb, kb_per_chunk;
-  int n_items;
-  float* part;  // [item][2 (hi, lo)][128 rows][128 cols]
+constexpr int MAX_SEGS = 40;
+
+struct TcSeg {
+  CUtensorMap mapA;  // A: [G*s planes][1][Npad][Kr]
+  CUtensorMap mapB;  // B: [s planes][nxy][Npad][Kr]
+  float* part;       // [item][2 (hi, lo)][128 rows][128 cols]
+  int cplx, G, n_tiles, n_ksplit, kb_per_split, n_kb, item0, pad;
+};
+
+struct TcParams {
+  int n_segs, n_items, s, kb_per_chunk;
   int* err;
   int pair_i[16], pair_j[16], pair_grp[16], n_pairs;
   int grp_mask;  // accumulator groups that receive MMAs
+  TcSeg seg[MAX_SEGS];
 };
+static_assert(sizeof(TcParams) <= 32000, "kernel parameter block too large");
 
 // complex: row blocks of 128, column blocks of 64, tiles with J <= 2I + 1;
 // real: 128 x 128 lower tiles
@@ -455,19 +469,32 @@ __device__ __forceinline__ void tile_ij(int cplx, int t, int& I, int& J) {
   }
 }
 
-// item = (ks * G + g) * n_tiles + tile: CTAs that run at the same time work on
-// the same K range, so the frequency-independent B operand (slices of C) and
-// the A rows of each frequency are read from HBM about once and shared in L2.
-__device__ __forceinline__ void item_coords(const TcArgs& a, int item, int& g, int& I, int& J, int& ks) {
-  const int tile = item % a.n_tiles;
-  const int r = item / a.n_tiles;
-  g = r % a.G;
-  ks = r / a.G;
-  tile_ij(a.cplx, tile, I, J);
+struct ItemPos {
+  int seg, local, g, I, J, ks, kb0, kb1;
+};
+
+// Within a segment: local = (ks * G + g) * n_tiles + tile.  CTAs that run at
+// the same time work on the same K range, so the frequency-independent B
+// operand (slices of C) and the A rows are read from HBM about once and shared
+// in L2.
+__device__ __forceinline__ ItemPos item_pos(const TcParams& p, int item) {
+  ItemPos r;
+  int sg = 0;
+  while (sg + 1 < p.n_segs && p.seg[sg + 1].item0 <= item) ++sg;
+  const TcSeg& S = p.seg[sg];
+  r.seg = sg;
+  r.local = item - S.item0;
+  const int tile = r.local % S.n_tiles;
+  const int q = r.local / S.n_tiles;
+  r.g = q % S.G;
+  r.ks = q / S.G;
+  tile_ij(S.cplx, tile, r.I, r.J);
+  r.kb0 = r.ks * S.kb_per_split;
+  r.kb1 = min(S.n_kb, r.kb0 + S.kb_per_split);
+  return r;
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
-    chi0_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
+__global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_constant__ TcParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -499,7 +526,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t stage_tx = 2u * (uint32_t)a.s * PLANE_BYTES;
+  const uint32_t stage_tx = 2u * (uint32_t)p.s * PLANE_BYTES;
 
   if (warp == 0) {
     // ------------------------------------------------ TMA producer
@@ -509,19 +536,18 @@ __global__ void __launch_bounds__(THREADS, 1)
       int armed[STAGES];
       for (int i = 0; i < STAGES; ++i) armed[i] = -1;
       bool ok = true;
-      for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
-        int g, I, J, ks;
-        item_coords(a, item, g, I, J, ks);
-        const int kb0 = ks * a.kb_per_split, kb1 = min(a.n_kb, kb0 + a.kb_per_split);
-        for (int kb = kb0; kb < kb1 && ok; ++kb) {
-          ok = mbar_wait(&empty[stage], phase ^ 1u, abort_flag, a.err, 11);
+      for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+        const ItemPos it = item_pos(p, item);
+        const TcSeg& S = p.seg[it.seg];
+        for (int kb = it.kb0; kb < it.kb1 && ok; ++kb) {
+          ok = mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err, 11);
           if (!ok) break;
           uint8_t* sa = smem + stage * STAGE_BYTES;
           uint8_t* sb = sa + MAX_S * PLANE_BYTES;
           mbar_expect_tx(&full[stage], stage_tx);
           // A: X slices of rows I*128.. ; B: [X; Y] slices of columns J*64.. (real: X of J*128..)
-          tma_load_4d(sa, &mapA, &full[stage], kb * KB, I * TILE_M, 0, g * a.s);
-          tma_load_4d(sb, &mapB, &full[stage], kb * KB, J * (a.cplx ? 64 : 128), 0, 0);
+          tma_load_4d(sa, &S.mapA, &full[stage], kb * KB, it.I * TILE_M, 0, it.g * p.s);
+          tma_load_4d(sb, &S.mapB, &full[stage], kb * KB, it.J * (S.cplx ? 64 : 128), 0, 0);
           armed[stage] = (int)phase;
           if (++stage == STAGES) {
             stage = 0;
@@ -544,27 +570,25 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t phase = 0, acc_phase = 0;
       bool ok = true;
       const uint32_t id = idesc();
-      for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
-        int g, I, J, ks;
-        item_coords(a, item, g, I, J, ks);
-        const int kb0 = ks * a.kb_per_split, kb1 = min(a.n_kb, kb0 + a.kb_per_split);
-        for (int c0 = kb0; c0 < kb1 && ok; c0 += a.kb_per_chunk) {
-          const int c1 = min(kb1, c0 + a.kb_per_chunk);
-          ok = mbar_wait(acc_empty, acc_phase ^ 1u, abort_flag, a.err, 12);
+      for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+        const ItemPos it = item_pos(p, item);
+        for (int c0 = it.kb0; c0 < it.kb1 && ok; c0 += p.kb_per_chunk) {
+          const int c1 = min(it.kb1, c0 + p.kb_per_chunk);
+          ok = mbar_wait(acc_empty, acc_phase ^ 1u, abort_flag, p.err, 12);
           if (!ok) break;
           fence_after();
           uint32_t inited = 0;  // bit per accumulator group, this chunk
           for (int kb = c0; kb < c1 && ok; ++kb) {
-            ok = mbar_wait(&full[stage], phase, abort_flag, a.err, 13);
+            ok = mbar_wait(&full[stage], phase, abort_flag, p.err, 13);
             if (!ok) break;
             fence_after();
             const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
             const uint32_t sb = sa + MAX_S * PLANE_BYTES;
-            for (int pi = 0; pi < a.n_pairs; ++pi) {
-              const int grp = a.pair_grp[pi];
+            for (int pi = 0; pi < p.n_pairs; ++pi) {
+              const int grp = p.pair_grp[pi];
               const bool acc = (inited >> grp) & 1u;
-              mma(tmem + 128u * (uint32_t)grp, sdesc(sa + a.pair_i[pi] * PLANE_BYTES),
-                  sdesc(sb + a.pair_j[pi] * PLANE_BYTES), id, acc);
+              mma(tmem + 128u * (uint32_t)grp, sdesc(sa + p.pair_i[pi] * PLANE_BYTES),
+                  sdesc(sb + p.pair_j[pi] * PLANE_BYTES), id, acc);
               inited |= 1u << grp;
             }
             mma_commit(&empty[stage]);
@@ -591,15 +615,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(64 * half);
     uint32_t acc_phase = 0;
     bool ok = true;
-    for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
-      int g, I, J, ks;
-      item_coords(a, item, g, I, J, ks);
-      const int kb0 = ks * a.kb_per_split, kb1 = min(a.n_kb, kb0 + a.kb_per_split);
+    for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+      const ItemPos it = item_pos(p, item);
       float hi[64], lo[64];
 #pragma unroll
       for (int u = 0; u < 64; ++u) hi[u] = lo[u] = 0.f;
-      for (int c0 = kb0; c0 < kb1 && ok; c0 += a.kb_per_chunk) {
-        ok = mbar_wait(acc_full, acc_phase, abort_flag, a.err, 14);
+      for (int c0 = it.kb0; c0 < it.kb1 && ok; c0 += p.kb_per_chunk) {
+        ok = mbar_wait(acc_full, acc_phase, abort_flag, p.err, 14);
         if (!ok) break;
         fence_after();
 #pragma unroll
@@ -607,13 +629,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           float v0[8], v1[8], v2[8], v3[8];
           tmem_ld8(tl + c, v0);
           tmem_ld8(tl + 128 + c, v1);
-          if (a.grp_mask & 4) tmem_ld8(tl + 256 + c, v2);
-          if (a.grp_mask & 8) tmem_ld8(tl + 384 + c, v3);
+          if (p.grp_mask & 4) tmem_ld8(tl + 256 + c, v2);
+          if (p.grp_mask & 8) tmem_ld8(tl + 384 + c, v3);
           tmem_wait_ld();
-          if (!(a.grp_mask & 4))
+          if (!(p.grp_mask & 4))
 #pragma unroll
             for (int u = 0; u < 8; ++u) v2[u] = 0.f;
-          if (!(a.grp_mask & 8))
+          if (!(p.grp_mask & 8))
 #pragma unroll
             for (int u = 0; u < 8; ++u) v3[u] = 0.f;
 #pragma unroll
@@ -624,7 +646,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         acc_phase ^= 1u;
       }
       if (!ok) break;
-      float* ph = a.part + (long)item * 2 * 128 * 128 + (long)row * 128 + 64 * half;
+      float* ph = p.seg[it.seg].part + (long)it.local * 2 * 128 * 128 + (long)row * 128 + 64 * half;
       float* pl = ph + 128 * 128;
 #pragma unroll
       for (int u = 0; u < 64; u += 4) {
@@ -642,17 +664,27 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // Sum of the split-K partials in a fixed order, exponents, Hermitian store.
-struct ReduceArgs {
-  int cplx, N, Npad, n_tiles, n_ksplit, w0, G;
+// Blocks: (segment, frequency, tile), enumerated through block0 offsets.
+struct RedSeg {
+  int cplx, N, Npad, n_tiles, n_ksplit, w0, G, block0;
   const float* part;
   const int* erow;   // [n_w][Npad] exponents of the weighted rows (A)
   const int* erowC;  // [Npad] exponents eC of C (B digits use e = eC + 1)
   double* chi;       // [n_w][N][N] of this q
 };
+struct RedParams {
+  int n_segs;
+  RedSeg seg[MAX_SEGS];
+};
+static_assert(sizeof(RedParams) <= 32000, "kernel parameter block too large");
 
-__global__ void __launch_bounds__(256) reduce_kernel(ReduceArgs a) {
-  const int tile = blockIdx.x % a.n_tiles;
-  const int g = blockIdx.x / a.n_tiles;
+__global__ void __launch_bounds__(256) reduce_kernel(const __grid_constant__ RedParams rp) {
+  int sg = 0;
+  while (sg + 1 < rp.n_segs && rp.seg[sg + 1].block0 <= (int)blockIdx.x) ++sg;
+  const RedSeg& a = rp.seg[sg];
+  const int b = blockIdx.x - a.block0;
+  const int tile = b % a.n_tiles;
+  const int g = b / a.n_tiles;
   int I, J;
   tile_ij(a.cplx, tile, I, J);
   const long NN = (long)a.N * a.N;
@@ -665,9 +697,9 @@ __global__ void __launch_bounds__(256) reduce_kernel(ReduceArgs a) {
     double re = 0.0, im = 0.0;
     for (int ks = 0; ks < a.n_ksplit; ++ks) {
       const long item = ((long)ks * a.G + g) * a.n_tiles + tile;
-      const float* p = a.part + item * 2 * 128 * 128 + (long)r * 128;
-      re += (double)p[c] + (double)p[128 * 128 + c];
-      if (a.cplx) im += (double)p[64 + c] + (double)p[128 * 128 + 64 + c];
+      const float* pp = a.part + item * 2 * 128 * 128 + (long)r * 128;
+      re += (double)pp[c] + (double)pp[128 * 128 + c];
+      if (a.cplx) im += (double)pp[64 + c] + (double)pp[128 * 128 + 64 + c];
     }
     const int e = a.erow[(long)(a.w0 + g) * a.Npad + P] + a.erowC[Q] + 1;  // B side: e = eC + 1
     const double sc = -ldexp(1.0, e - 14);  // x = 2^(e - 7) sum v, chi = -sum conj(a) c
@@ -720,12 +752,19 @@ int num_sms() {
   return n;
 }
 
+// Workspace of one q: slices of A for up to G frequencies, slices of C,
+// exponents, fixed-point C, weights, split-K partials.
 struct MixedLayout {
-  int Npad, Ktot, Kr, nxy, G, n_tiles, n_kb, kb_per_chunk, n_ksplit, kb_per_split, n_items;
-  size_t slices, slicesC, erow, erowC, part, wm, ew, cfix, err, total;
+  int Npad, Ktot, Kr, nxy, G, n_tiles, n_kb, n_chunks, nks_cap;
+  size_t slices, slicesC, erow, erowC, part, wm, ew, cfix, total;
 };
 
-MixedLayout mixed_layout(const BatchGeom& g, int s, int sms) {
+constexpr int KB_PER_CHUNK = 2 * CHUNK / KB;
+
+// slice_cap: bytes allowed for the A slices of one q (bounds G, the number of
+// frequencies per launch).  The partial buffer is sized for the largest split
+// count any launch of this q may use (nks_cap).
+MixedLayout mixed_layout(const BatchGeom& g, int s, int sms, size_t slice_cap) {
   MixedLayout L{};
   L.Npad = (g.n_aux + 127) / 128 * 128;
   L.Ktot = g.n_k * g.n_ov;
@@ -734,30 +773,23 @@ MixedLayout mixed_layout(const BatchGeom& g, int s, int sms) {
   L.Kr = g.cplx ? 2 * Kt : Kt;  // real K (interleaved re, im)
   L.nxy = g.cplx ? 2 : 1;
   L.n_kb = L.Kr / KB;
-  L.kb_per_chunk = 2 * CHUNK / KB;
+  L.n_chunks = L.n_kb / KB_PER_CHUNK;
   const int nb = L.Npad / 128;
   L.n_tiles = g.cplx ? nb * (nb + 1) : nb * (nb + 1) / 2;
   const size_t per_w = (size_t)s * L.Npad * L.Kr * 2;  // A: X planes only
-  L.G = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(g.n_w, 16), ((size_t)12 << 30) / per_w));
-  const int n_chunks = L.n_kb / L.kb_per_chunk;
-  const int want = 4 * sms;
-  int nks = std::max(1, std::min(n_chunks, (want + L.G * L.n_tiles - 1) / (L.G * L.n_tiles)));
-  const int cps = (n_chunks + nks - 1) / nks;
-  nks = (n_chunks + cps - 1) / cps;
-  L.n_ksplit = nks;
-  L.kb_per_split = cps * L.kb_per_chunk;
-  L.n_items = L.G * L.n_tiles * L.n_ksplit;
+  const size_t gmax = std::max<size_t>(1, slice_cap / per_w);
+  L.G = (int)std::min<size_t>((size_t)std::min(g.n_w, MAX_W), gmax);
+  L.nks_cap = std::max(1, std::min(L.n_chunks, (8 * sms + L.G * L.n_tiles - 1) / (L.G * L.n_tiles)));
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
   L.slices = al(per_w * L.G);
   L.slicesC = al(per_w * L.nxy);
   L.erow = al(sizeof(int) * (size_t)g.n_w * L.Npad);
   L.erowC = al(sizeof(int) * (size_t)L.Npad);
-  L.part = al(sizeof(float) * 2 * 128 * 128 * (size_t)L.n_items);
+  L.part = al(sizeof(float) * 2 * 128 * 128 * (size_t)L.G * L.n_tiles * L.nks_cap);
   L.wm = al(sizeof(uint32_t) * (size_t)g.n_k * g.n_w * g.n_ov);
   L.ew = al(sizeof(int16_t) * (size_t)g.n_k * g.n_w * g.n_ov);
   L.cfix = al(sizeof(int) * (size_t)L.Npad * L.Kr);
-  L.err = al(sizeof(int) * 4);
-  L.total = L.slices + L.slicesC + L.erow + L.erowC + L.part + L.wm + L.ew + L.cfix + L.err;
+  L.total = L.slices + L.slicesC + L.erow + L.erowC + L.part + L.wm + L.ew + L.cfix;
   return L;
 }
 
@@ -773,115 +805,336 @@ bool encode_map(EncodeTiledFn enc, CUtensorMap* m, void* base, const MixedLayout
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+void fill_pairs(TcParams& tp, int s) {
+  int np = 0;
+  for (int lvl = 0; lvl < s; ++lvl)
+    for (int i = 0; i <= lvl; ++i) {
+      tp.pair_i[np] = i;
+      tp.pair_j[np] = lvl - i;
+      tp.pair_grp[np] = std::min(lvl, NGROUPS - 1);
+      ++np;
+    }
+  if (s % 2 == 0) {  // (s/2, s/2): the largest term of the dropped level
+    tp.pair_i[np] = s / 2;
+    tp.pair_j[np] = s / 2;
+    tp.pair_grp[np] = std::min(s, NGROUPS - 1);
+    ++np;
+  }
+  tp.n_pairs = np;
+  tp.grp_mask = 0;
+  for (int i = 0; i < np; ++i) tp.grp_mask |= 1 << tp.pair_grp[i];
+}
+
+// ---------------------------------------------------- split-K planning ----
+// A launch's segments get their split-K depth from one common target item
+// length Lc (in exact 2048-value chunks): a segment of n chunks is cut into
+// nks = ceil(n / Lc) splits (at most nks_cap), so long and short segments give
+// items of similar length.  Items are issued to CTAs round robin, longest
+// segments first; the model cost of a plan is the largest per-CTA sum of item
+// lengths plus a fixed per-item overhead (pipeline fill, partial store).
+
+struct SegShape {
+  int n_chunks, G, T, nks_cap;
+};
+
+struct SplitPlan {
+  std::vector<int> nks;  // per segment
+  std::vector<int> order;
+  double cost;
+};
+
+SplitPlan plan_for(const std::vector<SegShape>& v, int Lc, int sms) {
+  SplitPlan p;
+  const int n = (int)v.size();
+  p.nks.resize(n);
+  std::vector<int> cps(n);
+  long items = 0;
+  for (int i = 0; i < n; ++i) {
+    int k = std::min(v[i].nks_cap, std::max(1, (v[i].n_chunks + Lc - 1) / Lc));
+    cps[i] = (v[i].n_chunks + k - 1) / k;
+    k = (v[i].n_chunks + cps[i] - 1) / cps[i];
+    p.nks[i] = k;
+    items += (long)k * v[i].G * v[i].T;
+  }
+  p.order.resize(n);
+  for (int i = 0; i < n; ++i) p.order[i] = i;
+  std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) { return cps[a] > cps[b]; });
+  const int grid = (int)std::max<long>(1, std::min<long>(items, sms));
+  std::vector<double> load(grid, 0.0);
+  long it = 0;
+  for (int oi = 0; oi < n; ++oi) {
+    const int i = p.order[oi];
+    for (int ks = 0; ks < p.nks[i]; ++ks) {
+      const int len = std::min(cps[i], v[i].n_chunks - ks * cps[i]);
+      const long cnt = (long)v[i].G * v[i].T;
+      // cnt consecutive items of equal length: whole rounds over the grid
+      // plus a remainder starting at CTA it % grid
+      const long full = cnt / grid, rem = cnt % grid;
+      const double w = len + 0.3;
+      if (full)
+        for (int b = 0; b < grid; ++b) load[b] += full * w;
+      for (long r = 0; r < rem; ++r) load[(it + r) % grid] += w;
+      it += cnt;
+    }
+  }
+  p.cost = *std::max_element(load.begin(), load.end());
+  return p;
+}
+
+// Candidate target lengths: the values of Lc at which some segment's split
+// count changes.
+std::vector<int> candidates(const std::vector<SegShape>& v) {
+  std::vector<int> c;
+  for (const SegShape& s : v)
+    for (int k = 1; k <= s.nks_cap; ++k) c.push_back((s.n_chunks + k - 1) / k);
+  std::sort(c.begin(), c.end());
+  c.erase(std::unique(c.begin(), c.end()), c.end());
+  if (c.size() > 48) {  // thin out evenly, keeping both ends
+    std::vector<int> d;
+    for (int i = 0; i < 48; ++i) d.push_back(c[(size_t)i * (c.size() - 1) / 47]);
+    d.erase(std::unique(d.begin(), d.end()), d.end());
+    c.swap(d);
+  }
+  return c;
+}
+
+uint64_t round_key(const std::vector<SegShape>& v, int s) {
+  uint64_t h = 1469598103934665603ull ^ (uint64_t)s;
+  auto mix = [&](uint64_t x) {
+    h ^= x;
+    h *= 1099511628211ull;
+  };
+  for (const SegShape& q : v) {
+    mix((uint64_t)q.n_chunks);
+    mix((uint64_t)q.G);
+    mix((uint64_t)q.T);
+    mix((uint64_t)q.nks_cap);
+  }
+  return h;
+}
+
+size_t slice_cap_of(const MixedQ& q) { return q.slice_cap ? q.slice_cap : ((size_t)12 << 30); }
+
 }  // namespace
 
 bool mixed_supported() { return get_encode() != nullptr; }
 
-size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices) {
-  return mixed_layout(g, n_slices, num_sms()).total;
+size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices, size_t slice_cap) {
+  return 1024 + mixed_layout(g, n_slices, num_sms(), slice_cap).total;
 }
 
 uint64_t mixed_tensor_flops(const BatchGeom& g, int s) {
-  const MixedLayout L = mixed_layout(g, s, num_sms());
+  const MixedLayout L = mixed_layout(g, s, num_sms(), (size_t)12 << 30);
   const int np = s * (s + 1) / 2 + (s % 2 == 0 ? 1 : 0);
   return (uint64_t)g.n_w * L.n_tiles * (uint64_t)L.n_kb * np * 2ull * 128 * 128 * KB;
 }
 
-cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cptrs, const double* dtab,
-                              double* chi, void* work, size_t work_bytes, int* status, uint64_t* n_launch,
-                              cudaStream_t st) {
-  if (s < 2 || s > MAX_S || g.n_w > MAX_W) return cudaErrorInvalidValue;
+size_t mixed_multi_workspace_bytes(const MixedQ* qs, int n, int s) {
+  size_t t = 1024;
+  for (int i = 0; i < n; ++i) t += mixed_layout(qs[i].g, s, num_sms(), slice_cap_of(qs[i])).total;
+  return t;
+}
+
+// Several q (of one job or of many) share each persistent tensor-core launch.
+// Per-q preparation runs first (weights, exponents, fixed-point C, digits of
+// C); then, in rounds, every q that still has frequencies left writes the
+// digits of its next frequency group and contributes one segment; one
+// chi0_tc_kernel covers all segments of the round and one reduce_kernel
+// finishes them.  Each q has its own workspace region.  With tune set (never
+// under stream capture), the first round of each new shape class times the
+// best few split plans and records the fastest.
+cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, size_t work_bytes, int* status,
+                                    uint64_t* n_launch, cudaStream_t st, bool tune) {
+  if (n <= 0) return cudaSuccess;
+  if (s < 2 || s > MAX_S) return cudaErrorInvalidValue;
   EncodeTiledFn enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
   const int sms = num_sms();
-  const MixedLayout L = mixed_layout(g, s, sms);
-  if (L.total > work_bytes) return cudaErrorMemoryAllocation;
-  char* p = (char*)work;
-  uint16_t* S = (uint16_t*)p;
-  p += L.slices;
-  uint16_t* SC = (uint16_t*)p;
-  p += L.slicesC;
-  int* erow = (int*)p;
-  p += L.erow;
-  int* erowC = (int*)p;
-  p += L.erowC;
-  float* part = (float*)p;
-  p += L.part;
-  uint32_t* wm = (uint32_t*)p;
-  p += L.wm;
-  int16_t* ew = (int16_t*)p;
-  p += L.ew;
-  int* cfix = (int*)p;
-  p += L.cfix;
-  int* err = (int*)p;
-
-  static thread_local int attr_done = 0;
   const size_t smem = STAGES * STAGE_BYTES + 1024 + 256;  // stages, alignment pad, barriers
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(chi0_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = 1;
+  {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [&] {
+      attr = cudaFuncSetAttribute(chi0_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr != cudaSuccess) return attr;
   }
-  CUtensorMap mapA, mapB;
-  if (!encode_map(enc, &mapA, S, L, s, 128, 1, 1, L.G * s) ||
-      !encode_map(enc, &mapB, SC, L, s, g.cplx ? 64 : 128, L.nxy, L.nxy, s))
-    return cudaErrorInvalidValue;
+  struct QState {
+    MixedLayout L;
+    uint16_t *S, *SC;
+    int *erow, *erowC, *cfix;
+    uint32_t* wm;
+    int16_t* ew;
+    float* part;
+    int w_next, rounds_left;
+  };
+  std::vector<QState> Q(n);
+  char* p = (char*)work;
+  int* err = (int*)p;
+  p += 1024;
+  size_t used = 1024;
+  for (int i = 0; i < n; ++i) {
+    const BatchGeom& g = qs[i].g;
+    if (g.n_w > MAX_W || g.n_w <= 0) return cudaErrorInvalidValue;
+    QState& q = Q[i];
+    q.L = mixed_layout(g, s, sms, slice_cap_of(qs[i]));
+    used += q.L.total;
+    if (used > work_bytes) return cudaErrorMemoryAllocation;
+    q.S = (uint16_t*)p;
+    p += q.L.slices;
+    q.SC = (uint16_t*)p;
+    p += q.L.slicesC;
+    q.erow = (int*)p;
+    p += q.L.erow;
+    q.erowC = (int*)p;
+    p += q.L.erowC;
+    q.part = (float*)p;
+    p += q.L.part;
+    q.wm = (uint32_t*)p;
+    p += q.L.wm;
+    q.ew = (int16_t*)p;
+    p += q.L.ew;
+    q.cfix = (int*)p;
+    p += q.L.cfix;
+    q.w_next = 0;
+    q.rounds_left = (g.n_w + q.L.G - 1) / q.L.G;
+  }
   uint64_t nl = 0;
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int) * 4, st);
   if (e != cudaSuccess) return e;
-  const long nwt = (long)g.n_k * g.n_w * g.n_ov;
-  wtab_kernel<<<(unsigned)std::min<long>((nwt + 255) / 256, (long)sms * 16), 256, 0, st>>>(nwt, dtab, wm, ew);
-  erow_kernel<<<L.Npad, 256, 0, st>>>(g.cplx, g.n_aux, L.Npad, g.n_ov, g.n_k, g.n_w, Cptrs, ew, erow, erowC);
-  {
-    const long total = (long)L.Npad * L.Kr;
-    cfix_kernel<<<(unsigned)std::min<long>((total + 255) / 256, (long)sms * 32), 256, 0, st>>>(
-        g.cplx, g.n_aux, L.Npad, g.n_ov, g.n_k, L.Ktot, L.Kr, Cptrs, erowC, cfix);
+  for (int i = 0; i < n; ++i) {
+    const BatchGeom& g = qs[i].g;
+    QState& q = Q[i];
+    const long nwt = (long)g.n_k * g.n_w * g.n_ov;
+    wtab_kernel<<<(unsigned)std::min<long>((nwt + 255) / 256, (long)sms * 16), 256, 0, st>>>(nwt, qs[i].dtab, q.wm,
+                                                                                               q.ew);
+    erow_kernel<<<q.L.Npad, 256, 0, st>>>(g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_k, g.n_w, qs[i].Cptrs, q.ew,
+                                           q.erow, q.erowC);
+    const long tot = (long)q.L.Npad * q.L.Kr;
+    cfix_kernel<<<(unsigned)std::min<long>((tot + 255) / 256, (long)sms * 32), 256, 0, st>>>(
+        g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_k, q.L.Ktot, q.L.Kr, qs[i].Cptrs, q.erowC, q.cfix);
+    SliceArgs sc{g.cplx, q.L.Npad, g.n_ov, q.L.Ktot, q.L.Kr, s, g.n_w, 0, 1, q.L.nxy, q.cfix, q.erowC,
+                 nullptr, nullptr, q.erow, q.SC};
+    const long tg = (long)q.L.Npad * (q.L.Kr / 16);
+    slice_kernel<<<(unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), 256, 0, st>>>(sc);
+    nl += 4;
   }
-  {  // digits of C itself (B operand, X and Y), once per q
-    SliceArgs sc{g.cplx, L.Npad, g.n_ov, L.Ktot, L.Kr, s, g.n_w, 0, 1, L.nxy, cfix, erowC, nullptr, nullptr, erow, SC};
-    const long total = (long)L.Npad * (L.Kr / 16);
-    slice_kernel<<<(unsigned)std::min<long>((total + 255) / 256, (long)sms * 32), 256, 0, st>>>(sc);
-  }
-  nl += 4;
-  TcArgs ta{};
-  ta.cplx = g.cplx;
-  ta.s = s;
-  ta.G = L.G;
-  ta.n_tiles = L.n_tiles;
-  ta.n_ksplit = L.n_ksplit;
-  ta.kb_per_split = L.kb_per_split;
-  ta.n_kb = L.n_kb;
-  ta.kb_per_chunk = L.kb_per_chunk;
-  ta.part = part;
-  ta.err = err;
-  int np = 0;
-  for (int lvl = 0; lvl < s; ++lvl)
-    for (int i = 0; i <= lvl; ++i) {
-      ta.pair_i[np] = i;
-      ta.pair_j[np] = lvl - i;
-      ta.pair_grp[np] = std::min(lvl, NGROUPS - 1);
-      ++np;
+  TcParams tp;
+  RedParams rp;
+  while (true) {
+    // this round's segments: every q with frequencies left, its next group
+    // (groups spread evenly over the q's rounds)
+    std::vector<int> who;
+    std::vector<int> w0s, Gs;
+    std::vector<SegShape> shp;
+    for (int i = 0; i < n && (int)who.size() < MAX_SEGS; ++i) {
+      QState& q = Q[i];
+      const BatchGeom& g = qs[i].g;
+      if (q.w_next >= g.n_w) continue;
+      const int left = g.n_w - q.w_next;
+      const int G = (left + q.rounds_left - 1) / q.rounds_left;
+      who.push_back(i);
+      w0s.push_back(q.w_next);
+      Gs.push_back(G);
+      shp.push_back(SegShape{q.L.n_chunks, G, q.L.n_tiles, q.L.nks_cap});
+      q.w_next += G;
+      q.rounds_left -= 1;
     }
-  if (s % 2 == 0) {  // (s/2, s/2): removes the diagonal bias of the dropped level
-    ta.pair_i[np] = s / 2;
-    ta.pair_j[np] = s / 2;
-    ta.pair_grp[np] = std::min(s, NGROUPS - 1);
-    ++np;
-  }
-  ta.n_pairs = np;
-  ta.grp_mask = 0;
-  for (int i = 0; i < np; ++i) ta.grp_mask |= 1 << ta.pair_grp[i];
-  for (int w0 = 0; w0 < g.n_w; w0 += L.G) {
-    const int G = std::min(L.G, g.n_w - w0);
-    SliceArgs sa{g.cplx, L.Npad, g.n_ov, L.Ktot, L.Kr, s, g.n_w, w0, G, 1, cfix, erowC, wm, ew, erow, S};
-    const long total = (long)L.Npad * (L.Kr / 16);
-    slice_kernel<<<(unsigned)std::min<long>((total + 255) / 256, (long)sms * 32), 256, 0, st>>>(sa);
-    ta.n_items = G * L.n_tiles * L.n_ksplit;
-    ta.G = G;
-    chi0_tc_kernel<<<std::min(ta.n_items, sms), THREADS, smem, st>>>(mapA, mapB, ta);
-    ReduceArgs ra{g.cplx, g.n_aux, L.Npad, L.n_tiles, L.n_ksplit, w0, G, part, erow, erowC, chi};
-    reduce_kernel<<<G * L.n_tiles, 256, 0, st>>>(ra);
-    nl += 3;
+    if (who.empty()) break;
+    for (size_t k = 0; k < who.size(); ++k) {
+      const int i = who[k];
+      QState& q = Q[i];
+      const BatchGeom& g = qs[i].g;
+      SliceArgs sa{g.cplx, q.L.Npad, g.n_ov, q.L.Ktot, q.L.Kr, s, g.n_w, w0s[k], Gs[k], 1, q.cfix, q.erowC,
+                   q.wm, q.ew, q.erow, q.S};
+      const long tg = (long)q.L.Npad * (q.L.Kr / 16);
+      slice_kernel<<<(unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), 256, 0, st>>>(sa);
+      ++nl;
+    }
+    // split plan: tuned value for this shape class if recorded, else the model's best
+    const uint64_t key = round_key(shp, s);
+    const std::vector<int> cand = candidates(shp);
+    std::vector<std::pair<double, int>> ranked;
+    for (int Lc : cand) ranked.push_back({plan_for(shp, Lc, sms).cost, Lc});
+    std::stable_sort(ranked.begin(), ranked.end());
+    int Lc = autotune_lookup(key);
+    const bool do_tune = tune && Lc <= 0 && ranked.size() > 1;
+    if (Lc <= 0) Lc = ranked[0].second;
+    // builds both parameter blocks for target length Lc; returns the item count
+    auto build = [&](int Lc_, int& items, int& blocks) -> bool {
+      const SplitPlan pl = plan_for(shp, Lc_, sms);
+      memset(&tp, 0, sizeof tp);
+      memset(&rp, 0, sizeof rp);
+      tp.s = s;
+      tp.kb_per_chunk = KB_PER_CHUNK;
+      tp.err = err;
+      fill_pairs(tp, s);
+      items = 0;
+      blocks = 0;
+      for (int oi = 0; oi < (int)who.size(); ++oi) {
+        const int k = pl.order[oi];
+        const int i = who[k];
+        QState& q = Q[i];
+        const BatchGeom& g = qs[i].g;
+        const int nks = pl.nks[k];
+        const int cps = (q.L.n_chunks + nks - 1) / nks;
+        TcSeg& S = tp.seg[tp.n_segs++];
+        if (!encode_map(enc, &S.mapA, q.S, q.L, s, 128, 1, 1, q.L.G * s) ||
+            !encode_map(enc, &S.mapB, q.SC, q.L, s, g.cplx ? 64 : 128, q.L.nxy, q.L.nxy, s))
+          return false;
+        S.part = q.part;
+        S.cplx = g.cplx;
+        S.G = Gs[k];
+        S.n_tiles = q.L.n_tiles;
+        S.n_ksplit = nks;
+        S.kb_per_split = cps * KB_PER_CHUNK;
+        S.n_kb = q.L.n_kb;
+        S.item0 = items;
+        items += Gs[k] * q.L.n_tiles * nks;
+        rp.seg[rp.n_segs++] = RedSeg{g.cplx, g.n_aux, q.L.Npad, q.L.n_tiles, nks, w0s[k], Gs[k], blocks,
+                                     q.part, q.erow, q.erowC, qs[i].chi};
+        blocks += Gs[k] * q.L.n_tiles;
+      }
+      tp.n_items = items;
+      rp.n_segs = tp.n_segs;
+      return true;
+    };
+    int items = 0, blocks = 0;
+    if (do_tune) {
+      cudaEvent_t e0, e1;
+      if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+      if ((e = cudaEventCreate(&e1)) != cudaSuccess) return e;
+      float best = 1e30f;
+      int bestLc = Lc;
+      const size_t ntry = std::min<size_t>(4, ranked.size());
+      for (size_t c = 0; c < ntry && e == cudaSuccess; ++c) {
+        if (!build(ranked[c].second, items, blocks)) return cudaErrorInvalidValue;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {  // first run warms L2 and the instruction cache
+          cudaEventRecord(e0, st);
+          chi0_tc_kernel<<<std::min(items, sms), THREADS, smem, st>>>(tp);
+          cudaEventRecord(e1, st);
+          nl += 1;
+          if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          ms = std::min(ms, t);
+        }
+        if (ms < best) {
+          best = ms;
+          bestLc = ranked[c].second;
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (e != cudaSuccess) return e;
+      Lc = bestLc;
+      autotune_record(key, Lc);
+    }
+    if (!build(Lc, items, blocks)) return cudaErrorInvalidValue;
+    chi0_tc_kernel<<<std::min(items, sms), THREADS, smem, st>>>(tp);
+    reduce_kernel<<<blocks, 256, 0, st>>>(rp);
+    nl += 2;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -891,6 +1144,13 @@ cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cp
   }
   if (n_launch) *n_launch = nl;
   return cudaSuccess;
+}
+
+cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cptrs, const double* dtab,
+                              double* chi, void* work, size_t work_bytes, int* status, uint64_t* n_launch,
+                              cudaStream_t st, size_t slice_cap) {
+  MixedQ q{g, Cptrs, dtab, chi, slice_cap};
+  return launch_chi0_mixed_multi(&q, 1, s, work, work_bytes, status, n_launch, st, false);
 }
 
 }  // namespace rpa

@@ -54,13 +54,32 @@ cudaError_t launch_energy_reduce(int n_q, int n_w, const double* parts, const do
 
 // ---- mixed-precision kernels (kernels_mixed.cu) ----------------------------
 
-// Returns bytes of mixed-path workspace needed for one q and one frequency.
-size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices);
+// Bytes of mixed-path workspace for one q; slice_cap bounds the BF16 digit
+// planes of the weighted operand (and so the frequencies per launch).
+size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices, size_t slice_cap);
 // chi0 of one q for all frequencies on the tensor cores (split precision);
 // `dtab` is the FP64 weight table of this q; a device time-out sets *status.
 cudaError_t launch_chi0_mixed(const BatchGeom& g, int n_slices, const double* const* Cptrs, const double* dtab,
                               double* chi, void* work, size_t work_bytes, int* status, uint64_t* n_launch,
-                              cudaStream_t s);
+                              cudaStream_t s, size_t slice_cap);
+// One q of a multi-q mixed launch.
+struct MixedQ {
+  BatchGeom g;                 // n_qb = 1
+  const double* const* Cptrs;  // device table of the q's n_k C blocks
+  const double* dtab;          // device weights of the q, [n_k][n_w][n_ov]
+  double* chi;                 // device output [n_w][N][N] (complex: interleaved)
+  size_t slice_cap;            // 0: 12 GiB
+};
+// chi0 of n q-points, sharing persistent tensor-core launches (one per round
+// of frequency groups).  tune: time the best split plans of each new shape
+// class and record the fastest (must not be set under stream capture).
+cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int n_slices, void* work, size_t work_bytes,
+                                    int* status, uint64_t* n_launch, cudaStream_t s, bool tune);
+size_t mixed_multi_workspace_bytes(const MixedQ* qs, int n, int n_slices);
+// Autotuner cache (autotune.cu): the recorded split target for a shape-class
+// key, 0 if none; autotune_record stores a measured choice.
+int autotune_lookup(uint64_t key);
+void autotune_record(uint64_t key, int value);
 bool mixed_supported();
 // Tensor-core flops the split-precision chi0 of one q executes (slice pairs
 // x padded tiles x padded K).
