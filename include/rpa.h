@@ -168,6 +168,11 @@ rpa_status rpa_wait(rpa_ctx *ctx, uint64_t ticket, double timeout_s, double *Ec,
 rpa_status rpa_serving_stats(rpa_ctx *ctx, uint64_t *jobs_done, double *lat_mean, double *lat_p50,
                              double *lat_p99, double *wait_p50, double *wait_p99);
 
+/* Serving high-water marks since creation: the most jobs running on the
+ * device at once and the largest sum of their footprints (bytes) admitted
+ * under the HBM cap.  Either pointer may be NULL. */
+rpa_status rpa_serving_peak(rpa_ctx *ctx, int *max_running, size_t *max_bytes);
+
 /* Number of kernels this context has launched so far (all entry points). */
 uint64_t rpa_kernel_launches(const rpa_ctx *ctx);
 
@@ -181,12 +186,13 @@ void *rpa_stream(rpa_ctx *ctx);
  * rpa_profile_read fills ms[RPA_K_COUNT] (summed device milliseconds) and
  * launches[RPA_K_COUNT] (kernel launches) per kernel class. */
 #define RPA_K_DTAB 0     /* frequency-weight table */
-#define RPA_K_CHI0 1     /* chi0 contraction (FP64 or tensor-core) */
+#define RPA_K_CHI0 1     /* chi0 contraction kernel (FP64 or tensor-core) */
 #define RPA_K_VFACTOR 2  /* Cholesky factor of V(q) */
 #define RPA_K_SANDWICH 3 /* Pi = L^H chi0 L (two passes) */
 #define RPA_K_LOGDET 4   /* Cholesky of 1 - Pi, ln det, Tr */
 #define RPA_K_REDUCE 5   /* quadrature */
-#define RPA_K_SLICE 6    /* operand slicing of the split-precision path */
+#define RPA_K_SLICE 6    /* operand preparation of the split-precision path */
+#define RPA_K_CHI0_RED 7 /* split-K reduction of the tensor-core chi0 */
 #define RPA_K_COUNT 8
 rpa_status rpa_profile(rpa_ctx *ctx, int enable);
 rpa_status rpa_profile_read(rpa_ctx *ctx, double *ms, uint64_t *launches);

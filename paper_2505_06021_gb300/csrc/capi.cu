@@ -212,20 +212,13 @@ rpa_status validate_job(const rpa_job* j, char* msg, size_t len) {
 }
 
 // -------------------------------------------------------------- layout ----
-// Workspace of one lane for a job processed in q-batches of qb q-points.
-
-struct Layout {
-  size_t meta, dtab, chi, T, L, stageC, stageV, eps, mixed, total;
-  size_t slice_cap;  // mixed path: bytes for the weighted operand's digit planes
-  int qb;
-};
 
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace cap of the synchronous calls (the serving lanes use a smaller one).
-static size_t sync_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap, (size_t)64 << 30); }
+size_t sync_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap, (size_t)64 << 30); }
 
-static Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap) {
+Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap) {
   Layout L{};
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
@@ -253,7 +246,7 @@ static Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap)
   return L;
 }
 
-static int choose_qb(const rpa_job* j, int n_slices, size_t cap) {
+int choose_qb(const rpa_job* j, int n_slices, size_t cap) {
   int qb = j->n_q;
   while (qb > 1 && plan_layout(j, qb, n_slices, cap).total > cap) qb = (qb + 1) / 2;
   return qb;
@@ -269,32 +262,7 @@ size_t job_footprint(const rpa_job* j, int n_slices, size_t ws_cap) {
   return in + L.total;
 }
 
-// Device pointers into a lane's workspace.
-struct Bufs {
-  const void** Cptrs;  // [n_q*n_k]
-  int* kidx;           // [n_q*n_k]
-  int* kqidx;          // [n_q*n_k]
-  double* omega;       // [n_w]
-  double* zeta_w;      // [n_w]
-  double* w_q;         // [n_q]
-  double* Ec;          // [1]
-  double* eps;         // [n_q*n_w]
-  double* parts;       // [n_q*n_w*2]
-  int* status;
-  double* dtab;
-  double* chi;
-  double* T;
-  double* L;
-  char* stageC[2];
-  char* stageV[2];
-  double* eps_occ;
-  double* eps_virt;
-  void* mixed;
-  size_t mixed_bytes;
-  size_t slice_cap;
-};
-
-static Bufs carve(void* ws, const rpa_job* j, const Layout& L) {
+Bufs carve(void* ws, const rpa_job* j, const Layout& L) {
   Bufs b{};
   const size_t npk = (size_t)j->n_q * j->n_k;
   const size_t nqw = (size_t)j->n_q * j->n_w;
@@ -345,17 +313,18 @@ static Bufs carve(void* ws, const rpa_job* j, const Layout& L) {
   return b;
 }
 
-// Uploads the job's small tables in one pinned copy: C pointers (device or
-// staged), eps row indices, frequencies and weights; zeroes the status word.
-static rpa_status upload_tables(rpa_ctx* ctx, Exec& ex, const rpa_job* j, const Bufs& b, const void* const* Cdev) {
+size_t tables_bytes(const rpa_job* j) {
   const size_t npk = (size_t)j->n_q * j->n_k;
   const size_t tbytes = sizeof(void*) * npk + sizeof(int) * 2 * npk;
-  const size_t dbytes = sizeof(double) * (2 * j->n_w + j->n_q);
-  if (!ex.hstage.reserve(tbytes + dbytes + 64)) {
-    ctx_set_error(ctx, "cannot allocate pinned host staging");
-    return RPA_E_NOMEM;
-  }
-  char* h = (char*)ex.hstage.ptr;
+  return ((tbytes + 63) & ~(size_t)63) + sizeof(double) * (2 * j->n_w + j->n_q);
+}
+
+// Writes the job's small tables into pinned host memory `h` (tables_bytes of
+// room): C pointers (device or staged), eps row indices, frequencies and
+// weights.
+void fill_tables_host(const rpa_job* j, const void* const* Cdev, char* h) {
+  const size_t npk = (size_t)j->n_q * j->n_k;
+  const size_t tbytes = sizeof(void*) * npk + sizeof(int) * 2 * npk;
   memcpy(h, Cdev, sizeof(void*) * npk);
   memcpy(h + sizeof(void*) * npk, j->pair_k, sizeof(int) * npk);
   memcpy(h + sizeof(void*) * npk + sizeof(int) * npk, j->pair_kq, sizeof(int) * npk);
@@ -363,9 +332,68 @@ static rpa_status upload_tables(rpa_ctx* ctx, Exec& ex, const rpa_job* j, const 
   memcpy(hd, j->omega, sizeof(double) * j->n_w);
   memcpy(hd + j->n_w, j->zeta_w, sizeof(double) * j->n_w);
   memcpy(hd + 2 * j->n_w, j->w_q, sizeof(double) * j->n_q);
-  CK(cudaMemcpyAsync((void*)b.Cptrs, h, tbytes, cudaMemcpyHostToDevice, ex.s));
-  CK(cudaMemcpyAsync(b.omega, hd, dbytes, cudaMemcpyHostToDevice, ex.s));
-  CK(cudaMemsetAsync(b.status, 0, sizeof(int), ex.s));
+}
+
+// Copies the tables at `h` to the device and zeroes the status word.  The
+// copies read `h` when they execute, so a captured graph picks up whatever
+// `h` holds at replay.
+rpa_status enqueue_table_copies(rpa_ctx* ctx, const rpa_job* j, const Bufs& b, const char* h, cudaStream_t s) {
+  const size_t npk = (size_t)j->n_q * j->n_k;
+  const size_t tbytes = sizeof(void*) * npk + sizeof(int) * 2 * npk;
+  const size_t dbytes = sizeof(double) * (2 * j->n_w + j->n_q);
+  CK(cudaMemcpyAsync((void*)b.Cptrs, h, tbytes, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(b.omega, h + ((tbytes + 63) & ~(size_t)63), dbytes, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(b.status, 0, sizeof(int), s));
+  return RPA_OK;
+}
+
+static rpa_status upload_tables(rpa_ctx* ctx, Exec& ex, const rpa_job* j, const Bufs& b, const void* const* Cdev) {
+  if (!ex.hstage.reserve(tables_bytes(j) + 64)) {
+    ctx_set_error(ctx, "cannot allocate pinned host staging");
+    return RPA_E_NOMEM;
+  }
+  fill_tables_host(j, Cdev, (char*)ex.hstage.ptr);
+  return enqueue_table_copies(ctx, j, b, (const char*)ex.hstage.ptr, ex.s);
+}
+
+// d_t(omega) table for q in [q0, q0+nq).
+rpa_status stage_dtab(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
+                      const double* eps_occ, const double* eps_virt, cudaStream_t s) {
+  const int nk = j->n_k;
+  BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, j->n_occ * j->n_virt, nk, j->n_w, nq};
+  prof_begin(ctx, pex, s);
+  CK(launch_dtab(g, eps_occ, eps_virt, b.kidx + (size_t)q0 * nk, b.kqidx + (size_t)q0 * nk, b.omega, j->zeta_k,
+                 b.dtab, s));
+  prof_end(ctx, pex, s, RPA_K_DTAB, 1);
+  ctx->launches++;
+  return RPA_OK;
+}
+
+// The FP64 steps after chi0 for q in [q0, q0+nq), chi0 in b.chi: factor V,
+// sandwich, Cholesky log-det.  V of the batch at Vdev[0..nq).
+rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
+                      const void* const* Vdev, cudaStream_t s) {
+  const size_t es = j->is_complex ? 16 : 8;
+  const size_t NN = (size_t)j->n_aux * j->n_aux;
+  // V(q) -> L, the lower Cholesky factor (V = L L^H), one matrix per q
+  for (int qi = 0; qi < nq; ++qi)
+    CK(cudaMemcpyAsync(b.L + qi * NN * (es / 8), Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
+  prof_begin(ctx, pex, s);
+  CK(launch_cholesky(j->is_complex, j->n_aux, nq, b.L, (long)(NN * (es / 8)), 1, nullptr, b.status, (1 << 29) + q0,
+                     s));
+  prof_end(ctx, pex, s, RPA_K_VFACTOR, 1);
+  ctx->launches++;
+  // Y = -(L^H chi L) (lower triangle), overwriting chi's storage
+  prof_begin(ctx, pex, s);
+  CK(launch_sandwich(j->is_complex, j->n_aux, nq * j->n_w, j->n_w, b.chi, b.L, b.T, b.chi, s));
+  prof_end(ctx, pex, s, RPA_K_SANDWICH, 2);
+  ctx->launches += 2;
+  // 1 - Pi' = 1 + Y: Cholesky, ln det, Tr
+  prof_begin(ctx, pex, s);
+  CK(launch_cholesky(j->is_complex, j->n_aux, nq * j->n_w, b.chi, (long)(NN * (es / 8)), 0,
+                     b.parts + (size_t)2 * q0 * j->n_w, b.status, q0 * j->n_w, s));
+  prof_end(ctx, pex, s, RPA_K_LOGDET, 1);
+  ctx->launches++;
   return RPA_OK;
 }
 
@@ -378,22 +406,29 @@ static rpa_status run_qbatch(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bu
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
   BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, j->n_occ * j->n_virt, nk, j->n_w, nq};
-  prof_begin(ctx, pex, s);
-  CK(launch_dtab(g, eps_occ, eps_virt, b.kidx + (size_t)q0 * nk, b.kqidx + (size_t)q0 * nk, b.omega, j->zeta_k,
-                 b.dtab, s));
-  prof_end(ctx, pex, s, RPA_K_DTAB, 1);
-  ctx->launches++;
+  if (rpa_status st = stage_dtab(ctx, pex, j, b, q0, nq, eps_occ, eps_virt, s)) return st;
   double* chi = chi_user ? chi_user : b.chi;
   if (j->prec == RPA_PREC_MIXED) {
+    struct HookCtx {
+      rpa_ctx* ctx;
+      Exec* ex;
+    } hc{ctx, pex};
+    LaunchHook hook{&hc,
+                    [](void* u, cudaStream_t st) {
+                      HookCtx* h = (HookCtx*)u;
+                      prof_begin(h->ctx, h->ex, st);
+                    },
+                    [](void* u, cudaStream_t st, int cls, int n) {
+                      HookCtx* h = (HookCtx*)u;
+                      prof_end(h->ctx, h->ex, st, cls, n);
+                    }};
     for (int qi = 0; qi < nq; ++qi) {
       BatchGeom g1 = g;
       g1.n_qb = 1;
       uint64_t nl = 0;
-      prof_begin(ctx, pex, s);
       CK(launch_chi0_mixed(g1, n_slices, (const double* const*)(b.Cptrs + (size_t)(q0 + qi) * nk),
                            b.dtab + (size_t)qi * nk * j->n_w * g.n_ov, chi + (size_t)qi * j->n_w * NN * (es / 8),
-                           b.mixed, b.mixed_bytes, b.status, &nl, s, b.slice_cap));
-      prof_end(ctx, pex, s, RPA_K_CHI0, (int)nl);
+                           b.mixed, b.mixed_bytes, b.status, &nl, s, b.slice_cap, pex ? &hook : nullptr));
       ctx->launches += nl;
     }
   } else {
@@ -403,29 +438,10 @@ static rpa_status run_qbatch(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bu
     ctx->launches++;
   }
   if (chi_user) return RPA_OK;
-  // V(q) -> L, the lower Cholesky factor (V = L L^H), one matrix per q
-  for (int qi = 0; qi < nq; ++qi)
-    CK(cudaMemcpyAsync(b.L + qi * NN * (es / 8), Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
-  prof_begin(ctx, pex, s);
-  CK(launch_cholesky(j->is_complex, j->n_aux, nq, b.L, (long)(NN * (es / 8)), 1, nullptr, b.status, (1 << 29) + q0,
-                     s));
-  prof_end(ctx, pex, s, RPA_K_VFACTOR, 1);
-  ctx->launches++;
-  // Y = -(L^H chi L) (lower triangle), overwriting chi's storage
-  prof_begin(ctx, pex, s);
-  CK(launch_sandwich(j->is_complex, j->n_aux, nq * j->n_w, j->n_w, chi, b.L, b.T, b.chi, s));
-  prof_end(ctx, pex, s, RPA_K_SANDWICH, 2);
-  ctx->launches += 2;
-  // 1 - Pi' = 1 + Y: Cholesky, ln det, Tr
-  prof_begin(ctx, pex, s);
-  CK(launch_cholesky(j->is_complex, j->n_aux, nq * j->n_w, b.chi, (long)(NN * (es / 8)), 0,
-                     b.parts + (size_t)2 * q0 * j->n_w, b.status, q0 * j->n_w, s));
-  prof_end(ctx, pex, s, RPA_K_LOGDET, 1);
-  ctx->launches++;
-  return RPA_OK;
+  return stage_tail(ctx, pex, j, b, q0, nq, Vdev, s);
 }
 
-static rpa_status decode_status(rpa_ctx* ctx, int st, int n_w) {
+rpa_status decode_status(rpa_ctx* ctx, int st, int n_w) {
   if (st == 0) return RPA_OK;
   const int code = st - 1;
   if (code >= (1 << 30)) {

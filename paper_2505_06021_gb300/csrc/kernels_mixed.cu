@@ -944,7 +944,13 @@ size_t mixed_multi_workspace_bytes(const MixedQ* qs, int n, int s) {
 // under stream capture), the first round of each new shape class times the
 // best few split plans and records the fastest.
 cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, size_t work_bytes, int* status,
-                                    uint64_t* n_launch, cudaStream_t st, bool tune) {
+                                    uint64_t* n_launch, cudaStream_t st, bool tune, const LaunchHook* hook) {
+  auto hb = [&]() {
+    if (hook) hook->begin(hook->user, st);
+  };
+  auto he = [&](int cls, int nk) {
+    if (hook) hook->end(hook->user, st, cls, nk);
+  };
   if (n <= 0) return cudaSuccess;
   if (s < 2 || s > MAX_S) return cudaErrorInvalidValue;
   EncodeTiledFn enc = get_encode();
@@ -1002,6 +1008,7 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
   uint64_t nl = 0;
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int) * 4, st);
   if (e != cudaSuccess) return e;
+  hb();
   for (int i = 0; i < n; ++i) {
     const BatchGeom& g = qs[i].g;
     QState& q = Q[i];
@@ -1019,6 +1026,7 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
     slice_kernel<<<(unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), 256, 0, st>>>(sc);
     nl += 4;
   }
+  he(RPA_K_SLICE, 4 * n);
   TcParams tp;
   RedParams rp;
   while (true) {
@@ -1041,6 +1049,7 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
       q.rounds_left -= 1;
     }
     if (who.empty()) break;
+    hb();
     for (size_t k = 0; k < who.size(); ++k) {
       const int i = who[k];
       QState& q = Q[i];
@@ -1051,6 +1060,7 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
       slice_kernel<<<(unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), 256, 0, st>>>(sa);
       ++nl;
     }
+    he(RPA_K_SLICE, (int)who.size());
     // split plan: tuned value for this shape class if recorded, else the model's best
     const uint64_t key = round_key(shp, s);
     const std::vector<int> cand = candidates(shp);
@@ -1132,8 +1142,12 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
       autotune_record(key, Lc);
     }
     if (!build(Lc, items, blocks)) return cudaErrorInvalidValue;
+    hb();
     chi0_tc_kernel<<<std::min(items, sms), THREADS, smem, st>>>(tp);
+    he(RPA_K_CHI0, 1);
+    hb();
     reduce_kernel<<<blocks, 256, 0, st>>>(rp);
+    he(RPA_K_CHI0_RED, 1);
     nl += 2;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1148,9 +1162,9 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
 
 cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cptrs, const double* dtab,
                               double* chi, void* work, size_t work_bytes, int* status, uint64_t* n_launch,
-                              cudaStream_t st, size_t slice_cap) {
+                              cudaStream_t st, size_t slice_cap, const LaunchHook* hook) {
   MixedQ q{g, Cptrs, dtab, chi, slice_cap};
-  return launch_chi0_mixed_multi(&q, 1, s, work, work_bytes, status, n_launch, st, false);
+  return launch_chi0_mixed_multi(&q, 1, s, work, work_bytes, status, n_launch, st, false, hook);
 }
 
 }  // namespace rpa

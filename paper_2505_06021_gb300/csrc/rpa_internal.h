@@ -52,6 +52,13 @@ cudaError_t launch_sandwich(int cplx, int N, int n_batch, int n_w, const double*
 cudaError_t launch_energy_reduce(int n_q, int n_w, const double* parts, const double* w_q, const double* zeta_w,
                                  double* eps, double* Ec, cudaStream_t s);
 
+// Optional timing hook around groups of launches (cls: an RPA_K_* class).
+struct LaunchHook {
+  void* user;
+  void (*begin)(void* user, cudaStream_t s);
+  void (*end)(void* user, cudaStream_t s, int cls, int n_kernels);
+};
+
 // ---- mixed-precision kernels (kernels_mixed.cu) ----------------------------
 
 // Bytes of mixed-path workspace for one q; slice_cap bounds the BF16 digit
@@ -61,7 +68,7 @@ size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices, size_t slice_cap)
 // `dtab` is the FP64 weight table of this q; a device time-out sets *status.
 cudaError_t launch_chi0_mixed(const BatchGeom& g, int n_slices, const double* const* Cptrs, const double* dtab,
                               double* chi, void* work, size_t work_bytes, int* status, uint64_t* n_launch,
-                              cudaStream_t s, size_t slice_cap);
+                              cudaStream_t s, size_t slice_cap, const LaunchHook* hook);
 // One q of a multi-q mixed launch.
 struct MixedQ {
   BatchGeom g;                 // n_qb = 1
@@ -74,7 +81,8 @@ struct MixedQ {
 // of frequency groups).  tune: time the best split plans of each new shape
 // class and record the fastest (must not be set under stream capture).
 cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int n_slices, void* work, size_t work_bytes,
-                                    int* status, uint64_t* n_launch, cudaStream_t s, bool tune);
+                                    int* status, uint64_t* n_launch, cudaStream_t s, bool tune,
+                                    const LaunchHook* hook = nullptr);
 size_t mixed_multi_workspace_bytes(const MixedQ* qs, int n, int n_slices);
 // Autotuner cache (autotune.cu): the recorded split target for a shape-class
 // key, 0 if none; autotune_record stores a measured choice.

@@ -89,6 +89,39 @@ struct rpa_ctx {
 };
 
 namespace rpa {
+
+// Workspace of one lane for a job processed in q-batches of qb q-points.
+struct Layout {
+  size_t meta, dtab, chi, T, L, stageC, stageV, eps, mixed, total;
+  size_t slice_cap;  // mixed path: bytes for the weighted operand's digit planes
+  int qb;
+};
+
+// Device pointers into a lane's workspace.
+struct Bufs {
+  const void** Cptrs;  // [n_q*n_k]
+  int* kidx;           // [n_q*n_k]
+  int* kqidx;          // [n_q*n_k]
+  double* omega;       // [n_w]
+  double* zeta_w;      // [n_w]
+  double* w_q;         // [n_q]
+  double* Ec;          // [1]
+  double* eps;         // [n_q*n_w]
+  double* parts;       // [n_q*n_w*2]
+  int* status;
+  double* dtab;
+  double* chi;
+  double* T;
+  double* L;
+  char* stageC[2];
+  char* stageV[2];
+  double* eps_occ;
+  double* eps_virt;
+  void* mixed;
+  size_t mixed_bytes;
+  size_t slice_cap;
+};
+
 void ctx_set_error(rpa_ctx* ctx, const char* fmt, ...);
 rpa_status validate_job(const rpa_job* j, char* msg, size_t len);
 size_t job_footprint(const rpa_job* j, int n_slices, size_t ws_cap);
@@ -105,6 +138,18 @@ rpa_status wait_event(rpa_ctx* ctx, cudaEvent_t ev, double timeout_s);
 void prof_begin(rpa_ctx* ctx, Exec* ex, cudaStream_t s);
 void prof_end(rpa_ctx* ctx, Exec* ex, cudaStream_t s, int cls, int n_kernels);
 void prof_collect(rpa_ctx* ctx, Exec* ex);
+Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap);
+int choose_qb(const rpa_job* j, int n_slices, size_t cap);
+Bufs carve(void* ws, const rpa_job* j, const Layout& L);
+size_t sync_ws_cap(rpa_ctx* ctx);
+size_t tables_bytes(const rpa_job* j);
+void fill_tables_host(const rpa_job* j, const void* const* Cdev, char* h);
+rpa_status enqueue_table_copies(rpa_ctx* ctx, const rpa_job* j, const Bufs& b, const char* h, cudaStream_t s);
+rpa_status stage_dtab(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
+                      const double* eps_occ, const double* eps_virt, cudaStream_t s);
+rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
+                      const void* const* Vdev, cudaStream_t s);
+rpa_status decode_status(rpa_ctx* ctx, int st, int n_w);
 void serving_shutdown(rpa_ctx* ctx);
 void batch_release(rpa_ctx* ctx);
 }  // namespace rpa

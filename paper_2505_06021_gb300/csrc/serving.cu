@@ -62,6 +62,8 @@ struct ServeState {
   std::vector<double> lat, wait;
   uint64_t done = 0;
   size_t max_pending = 4096;
+  int peak_running = 0;     // most jobs on the device at once
+  size_t peak_used = 0;     // largest admitted footprint sum
 };
 
 static Exec* get_lane(ServeState* S) {
@@ -106,6 +108,8 @@ static void scheduler(rpa_ctx* ctx) {
       j->state = 1;
       S->used += j->footprint;
       S->running.push_back(j);
+      S->peak_running = std::max(S->peak_running, (int)S->running.size());
+      S->peak_used = std::max(S->peak_used, S->used);
       lk.unlock();
       rpa_status st = energy_enqueue(ctx, *lane, &j->job, lane_ws_cap(ctx));
       lk.lock();
@@ -302,6 +306,20 @@ rpa_status rpa_serving_stats(rpa_ctx* ctx, uint64_t* jobs_done, double* lat_mean
   if (lat_p99) *lat_p99 = pct(S->lat, 0.99);
   if (wait_p50) *wait_p50 = pct(S->wait, 0.50);
   if (wait_p99) *wait_p99 = pct(S->wait, 0.99);
+  return RPA_OK;
+}
+
+rpa_status rpa_serving_peak(rpa_ctx* ctx, int* max_running, size_t* max_bytes) {
+  if (!ctx) return RPA_E_INVAL;
+  int r = 0;
+  size_t b = 0;
+  if (ctx->serve) {
+    std::lock_guard<std::mutex> g(ctx->serve->mu);
+    r = ctx->serve->peak_running;
+    b = ctx->serve->peak_used;
+  }
+  if (max_running) *max_running = r;
+  if (max_bytes) *max_bytes = b;
   return RPA_OK;
 }
 

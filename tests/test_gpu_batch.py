@@ -1,0 +1,85 @@
+"""GPU tests of rpa_energy_batch: many uneven jobs in shared persistent
+tensor-core launches, replayed from a captured CUDA graph.
+
+* FP64 jobs give bit-identical E_c in the batch and alone (same kernels, same
+  per-element arithmetic order).
+* Mixed jobs: the exact accumulator levels make chi0 independent of the split-K
+  plan up to the FP32 level-3 group and the float-float flush, so the batch and
+  the single-job E_c agree far inside the 1 microhartree bar; 1e-9 Ha here.
+* The graph replay gives the same numbers as the eager first call, and picks
+  up new frequency tables (same shapes and pointers) written before the replay.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_06021_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_MIX_VS_SINGLE = 1e-9  # Hartree
+TOL_EC = 1e-6  # Hartree, mixed vs oracle
+
+
+@pytest.fixture(scope="module")
+def rpa():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2505_06021_gb300 as m
+    from paper_2505_06021_gb300 import build as b
+
+    b.build()
+    return m
+
+
+def _instances():
+    return synth.config3_instances(n_inst=6, seed=77, n_w=6, aux_range=(40, 200), occ_range=(2, 8),
+                                   ratio_range=(3, 9))
+
+
+def test_batch_matches_single_jobs(rpa):
+    probs = _instances()
+    jobs = []
+    for i, p in enumerate(probs):
+        t = rpa.upload_problem(p)
+        jobs.append(rpa.job_from_problem(p, t, prec=rpa.PREC_MIXED if i % 3 != 2 else rpa.PREC_FP64))
+    with rpa.Context(0) as c:
+        single = np.array([c.energy(j)["Ec"] for j in jobs])
+        n0 = c.launches()
+        e1 = c.energy_batch(jobs)  # eager, tuned, then captured
+        e2 = c.energy_batch(jobs)  # graph replay
+        assert c.launches() > n0
+    for i, j in enumerate(jobs):
+        if j.s.prec == rpa.PREC_FP64:
+            assert e1[i] == single[i], i
+        else:
+            assert abs(e1[i] - single[i]) <= TOL_MIX_VS_SINGLE, (i, e1[i], single[i])
+    assert np.array_equal(e1, e2)
+    ref = oracle.energy(probs[0])
+    assert abs(e1[0] - ref["Ec"]) <= TOL_EC
+
+
+def test_batch_replay_reads_new_tables(rpa):
+    probs = _instances()[:3]
+    jobs = [rpa.job_from_problem(p, rpa.upload_problem(p), prec=rpa.PREC_MIXED) for p in probs]
+    with rpa.Context(0) as c:
+        c.energy_batch(jobs)
+        c.energy_batch(jobs)
+        # same shapes and device pointers, new frequency grid: a replay must see it
+        # (the descriptor points at these arrays, so an in-place update is seen)
+        for j in jobs:
+            j.omega *= 1.5
+            j.zeta_w *= 1.5
+        e = c.energy_batch(jobs)
+        single = np.array([c.energy(j)["Ec"] for j in jobs])
+    assert np.max(np.abs(e - single)) <= TOL_MIX_VS_SINGLE
+
+
+def test_batch_empty_and_invalid(rpa):
+    with rpa.Context(0) as c:
+        assert len(c.energy_batch([])) == 0
+        p = _instances()[0]
+        j = rpa.job_from_problem(p, rpa.upload_problem(p, device="cpu"), mem=rpa.MEM_HOST)
+        with pytest.raises(rpa.RpaError):
+            c.energy_batch([j])
