@@ -46,10 +46,10 @@ def test_batch_matches_single_jobs(rpa):
         jobs.append(rpa.job_from_problem(p, t, prec=rpa.PREC_MIXED if i % 3 != 2 else rpa.PREC_FP64))
     with rpa.Context(0) as c:
         single = np.array([c.energy(j)["Ec"] for j in jobs])
-        n0 = c.launches()
+        n0 = c.launches
         e1 = c.energy_batch(jobs)  # eager, tuned, then captured
         e2 = c.energy_batch(jobs)  # graph replay
-        assert c.launches() > n0
+        assert c.launches > n0
     for i, j in enumerate(jobs):
         if j.s.prec == rpa.PREC_FP64:
             assert e1[i] == single[i], i
