@@ -42,7 +42,7 @@ namespace {
 constexpr size_t kBatchSliceCap = (size_t)4 << 30;  // digit planes of one q's weighted operand
 
 struct JobPlan {
-  Layout L;        // FP64 part (whole job in one q-batch, no mixed region)
+  Layout L;        // whole job in one q-batch, without the chi0 mixed region
   size_t ws_off;   // within the group's region
   size_t tab_off;  // pinned tables
   size_t res_off;  // pinned results: [status | pad to 64 | Ec | eps | parts]
@@ -68,12 +68,6 @@ struct Plan {
     if (exec) cudaGraphExecDestroy(exec);
   }
 };
-
-rpa_job fp64_view(const rpa_job& j) {
-  rpa_job v = j;
-  v.prec = RPA_PREC_FP64;
-  return v;
-}
 
 BatchGeom geom_q(const rpa_job& j) {
   return BatchGeom{j.is_complex, j.n_aux, j.n_occ, j.n_virt, j.n_occ * j.n_virt, j.n_k, j.n_w, 1};
@@ -109,8 +103,7 @@ std::unique_ptr<Plan> make_plan(const rpa_job* jobs, int n, int n_slices, size_t
   size_t pin = 0;
   for (int i = 0; i < n; ++i) {
     JobPlan& jp = p->jobs[i];
-    const rpa_job v = fp64_view(jobs[i]);
-    jp.L = plan_layout(&v, jobs[i].n_q, n_slices, 0);
+    jp.L = plan_layout(&jobs[i], jobs[i].n_q, n_slices, 0, false);
     jp.mixed = 0;
     if (jobs[i].prec == RPA_PREC_MIXED) {
       const size_t per_q = a1k(mixed_workspace_bytes(geom_q(jobs[i]), n_slices, kBatchSliceCap));
@@ -152,15 +145,49 @@ std::unique_ptr<Plan> make_plan(const rpa_job* jobs, int n, int n_slices, size_t
 
 // The batch runs on the context's own stream (rpa_stream) with a workspace
 // and pinned buffers of its own, kept between calls for graph replay.
+// The FP64 tails of a group's jobs are independent and each is small (a few
+// matrices per kernel), so they run on side streams, forked from and joined
+// back into the context's stream (a parallel branch per side stream in the
+// captured graph).
+constexpr int kSide = 8;
+
 struct BatchCache {
   Exec mem;  // workspace only (no streams)
   HostStage pin;
   std::unique_ptr<Plan> plan;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr, join[kSide] = {};
+  bool side_ok = false;
+  bool init_side() {
+    if (side_ok) return true;
+    for (int k = 0; k < kSide; ++k) {
+      if (cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking) != cudaSuccess) return false;
+      if (cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming) != cudaSuccess) return false;
+    }
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return false;
+    side_ok = true;
+    return true;
+  }
+  void release_side() {
+    for (int k = 0; k < kSide; ++k) {
+      if (side[k]) {
+        cudaStreamSynchronize(side[k]);
+        cudaStreamDestroy(side[k]);
+      }
+      if (join[k]) cudaEventDestroy(join[k]);
+      side[k] = nullptr;
+      join[k] = nullptr;
+    }
+    if (fork) cudaEventDestroy(fork);
+    fork = nullptr;
+    side_ok = false;
+  }
 };
 
 void batch_release(rpa_ctx* ctx) {
   if (!ctx->batch) return;
   if (ctx->ex.s) cudaStreamSynchronize(ctx->ex.s);
+  ctx->batch->release_side();
   ctx->batch->plan.reset();
   ctx->batch->pin.release();
   ctx->batch->mem.destroy();
@@ -177,8 +204,8 @@ static void fill_tables(const Plan& p, const rpa_job* jobs, int n, char* pin) {
 // Enqueues the whole batch on `s` (pinned tables already filled); *n_kernels
 // gets the number of kernels enqueued.  pex (profiling lane, may be null)
 // receives per-kernel-class timing marks; never set under stream capture.
-static rpa_status enqueue_batch(rpa_ctx* ctx, const Plan& p, const rpa_job* jobs, char* ws, char* pin,
-                                cudaStream_t s, bool tune, uint64_t* n_kernels, Exec* pex) {
+static rpa_status enqueue_batch(rpa_ctx* ctx, BatchCache& bc, const Plan& p, const rpa_job* jobs, char* ws,
+                                char* pin, cudaStream_t s, bool tune, uint64_t* n_kernels, Exec* pex) {
   uint64_t nk = 0;
   struct HookCtx {
     rpa_ctx* ctx;
@@ -197,8 +224,7 @@ static rpa_status enqueue_batch(rpa_ctx* ctx, const Plan& p, const rpa_job* jobs
   std::vector<Bufs> B(jobs ? p.jobs.size() : 0);
   for (const Group& g : p.groups) {
     for (int i = g.j0; i < g.j1; ++i) {
-      const rpa_job v = fp64_view(jobs[i]);
-      B[i] = carve(ws + p.jobs[i].ws_off, &v, p.jobs[i].L);
+      B[i] = carve(ws + p.jobs[i].ws_off, &jobs[i], p.jobs[i].L);
       if (rpa_status st = enqueue_table_copies(ctx, &jobs[i], B[i], pin + p.jobs[i].tab_off, s)) return st;
       if (rpa_status st = stage_dtab(ctx, pex, &jobs[i], B[i], 0, jobs[i].n_q, jobs[i].eps_occ,
                                      jobs[i].eps_virt, s))
@@ -232,17 +258,35 @@ static rpa_status enqueue_batch(rpa_ctx* ctx, const Plan& p, const rpa_job* jobs
                                   &nl, s, tune, pex ? &hook : nullptr));
       ctx->launches += nl;
     }
-    for (int i = g.j0; i < g.j1; ++i) {
+    // fork: the jobs' tails on the side streams, largest jobs first
+    CKB(cudaEventRecord(bc.fork, s));
+    const int nside = std::min(kSide, g.j1 - g.j0);
+    for (int k = 0; k < nside; ++k) CKB(cudaStreamWaitEvent(bc.side[k], bc.fork, 0));
+    std::vector<int> order;
+    for (int i = g.j0; i < g.j1; ++i) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+      const double wa = (double)jobs[a].n_aux * jobs[a].n_aux * jobs[a].n_aux * jobs[a].n_q * jobs[a].n_w;
+      const double wc = (double)jobs[c].n_aux * jobs[c].n_aux * jobs[c].n_aux * jobs[c].n_q * jobs[c].n_w;
+      return wa > wc;
+    });
+    for (size_t oi = 0; oi < order.size(); ++oi) {
+      const int i = order[oi];
+      cudaStream_t ss = bc.side[oi % nside];
       const rpa_job& j = jobs[i];
-      if (rpa_status st = stage_tail(ctx, pex, &j, B[i], 0, j.n_q, j.V, s)) return st;
-      prof_begin(ctx, pex, s);
-      CKB(launch_energy_reduce(j.n_q, j.n_w, B[i].parts, B[i].w_q, B[i].zeta_w, B[i].eps, B[i].Ec, s));
-      prof_end(ctx, pex, s, RPA_K_REDUCE, 1);
+      if (rpa_status st = stage_tail(ctx, pex, &j, B[i], 0, j.n_q, j.V, ss)) return st;
+      prof_begin(ctx, pex, ss);
+      CKB(launch_energy_reduce(j.n_q, j.n_w, B[i].parts, B[i].w_q, B[i].zeta_w, B[i].eps, B[i].Ec, ss));
+      prof_end(ctx, pex, ss, RPA_K_REDUCE, 1);
       ctx->launches++;
       char* r = pin + p.jobs[i].res_off;
       const size_t nqw = (size_t)j.n_q * j.n_w;
-      CKB(cudaMemcpyAsync(r + 64, B[i].Ec, sizeof(double) * (3 * nqw + 1), cudaMemcpyDeviceToHost, s));
-      CKB(cudaMemcpyAsync(r, B[i].status, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CKB(cudaMemcpyAsync(r + 64, B[i].Ec, sizeof(double) * (3 * nqw + 1), cudaMemcpyDeviceToHost, ss));
+      CKB(cudaMemcpyAsync(r, B[i].status, sizeof(int), cudaMemcpyDeviceToHost, ss));
+    }
+    // join
+    for (int k = 0; k < nside; ++k) {
+      CKB(cudaEventRecord(bc.join[k], bc.side[k]));
+      CKB(cudaStreamWaitEvent(s, bc.join[k], 0));
     }
   }
   nk = ctx->launches.load() - l0;
@@ -276,6 +320,10 @@ extern "C" rpa_status rpa_energy_batch(rpa_ctx* ctx, const rpa_job* jobs, int n_
   CKB(cudaSetDevice(ctx->device));
   if (!ctx->batch) ctx->batch = new BatchCache;
   BatchCache& bc = *ctx->batch;
+  if (!bc.init_side()) {
+    ctx_set_error(ctx, "cannot create the batch side streams");
+    return RPA_E_CUDA;
+  }
   cudaStream_t s = ctx->ex.s;
   std::vector<uint64_t> sig = signature(jobs, n_jobs, ctx->n_slices);
   // with per-kernel profiling on, a known batch runs eagerly (a graph replay
@@ -306,7 +354,7 @@ extern "C" rpa_status rpa_energy_batch(rpa_ctx* ctx, const rpa_job* jobs, int n_
   } else {
     // eager run (the autotuner on for a new signature); results come from this run
     uint64_t nk = 0;
-    if (rpa_status st = enqueue_batch(ctx, p, jobs, ws, pin, s, !known, &nk, &ctx->ex)) {
+    if (rpa_status st = enqueue_batch(ctx, bc, p, jobs, ws, pin, s, !known, &nk, &ctx->ex)) {
       bc.plan.reset();
       return st;
     }
@@ -329,7 +377,7 @@ extern "C" rpa_status rpa_energy_batch(rpa_ctx* ctx, const rpa_job* jobs, int n_
     cudaGraph_t graph = nullptr;
     CKB(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     uint64_t nk = 0;
-    rpa_status st = enqueue_batch(ctx, p, jobs, ws, pin, s, false, &nk, nullptr);
+    rpa_status st = enqueue_batch(ctx, bc, p, jobs, ws, pin, s, false, &nk, nullptr);
     ctx->launches -= nk;  // captured, not launched
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
     if (st != RPA_OK) {

@@ -218,7 +218,7 @@ static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 // Workspace cap of the synchronous calls (the serving lanes use a smaller one).
 size_t sync_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap, (size_t)64 << 30); }
 
-Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap) {
+Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool mixed_ws) {
   Layout L{};
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
@@ -227,7 +227,7 @@ Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap) {
   const size_t nqw = (size_t)j->n_q * j->n_w;
   L.qb = qb;
   L.meta = al(sizeof(void*) * npk + sizeof(int) * 2 * npk + 64) +
-           al(sizeof(double) * (2 * j->n_w + j->n_q + 3 * nqw + 8) + 64);
+           al(sizeof(double) * (2 * j->n_w + 2 * j->n_q + 3 * nqw + 8) + 64);
   L.dtab = al(sizeof(double) * qb * j->n_k * j->n_w * nov);
   L.chi = al(es * NN * qb * j->n_w);
   L.T = L.chi;
@@ -238,22 +238,25 @@ Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap) {
     L.eps = al(sizeof(double) * (size_t)j->n_kpts * (j->n_occ + j->n_virt));
   }
   if (j->prec == RPA_PREC_MIXED) {
-    BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, (int)nov, j->n_k, j->n_w, 1};
-    L.slice_cap = ws_cap / 2;
-    L.mixed = al(mixed_workspace_bytes(g, n_slices, L.slice_cap));
+    L.Vc = al(es * NN * qb);  // the inverse-form tail keeps a copy of V(q)
+    if (mixed_ws) {
+      BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, (int)nov, j->n_k, j->n_w, 1};
+      L.slice_cap = ws_cap / 2;
+      L.mixed = al(mixed_workspace_bytes(g, n_slices, L.slice_cap));
+    }
   }
-  L.total = L.meta + L.dtab + L.chi + L.T + L.L + 2 * (L.stageC + L.stageV) + L.eps + L.mixed;
+  L.total = L.meta + L.dtab + L.chi + L.T + L.L + L.Vc + 2 * (L.stageC + L.stageV) + L.eps + L.mixed;
   return L;
 }
 
 int choose_qb(const rpa_job* j, int n_slices, size_t cap) {
   int qb = j->n_q;
-  while (qb > 1 && plan_layout(j, qb, n_slices, cap).total > cap) qb = (qb + 1) / 2;
+  while (qb > 1 && plan_layout(j, qb, n_slices, cap, true).total > cap) qb = (qb + 1) / 2;
   return qb;
 }
 
 size_t job_footprint(const rpa_job* j, int n_slices, size_t ws_cap) {
-  Layout L = plan_layout(j, choose_qb(j, n_slices, ws_cap), n_slices, ws_cap);
+  Layout L = plan_layout(j, choose_qb(j, n_slices, ws_cap), n_slices, ws_cap, true);
   size_t in = 0;
   if (j->mem == RPA_MEM_DEVICE) {
     const size_t es = j->is_complex ? 16 : 8;
@@ -288,6 +291,8 @@ Bufs carve(void* ws, const rpa_job* j, const Layout& L) {
   d += nqw;
   b.parts = d;
   d += 2 * nqw;
+  b.ldV = d;
+  d += j->n_q;
   b.status = (int*)d;
   p += L.meta;
   b.dtab = (double*)p;
@@ -298,6 +303,8 @@ Bufs carve(void* ws, const rpa_job* j, const Layout& L) {
   p += L.T;
   b.L = (double*)p;
   p += L.L;
+  b.Vc = L.Vc ? (double*)p : nullptr;
+  p += L.Vc;
   for (int i = 0; i < 2; ++i) {
     b.stageC[i] = p;
     p += L.stageC;
@@ -375,14 +382,31 @@ rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, 
                       const void* const* Vdev, cudaStream_t s) {
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
+  const long mstride = (long)(NN * (es / 8));
   // V(q) -> L, the lower Cholesky factor (V = L L^H), one matrix per q
-  for (int qi = 0; qi < nq; ++qi)
+  for (int qi = 0; qi < nq; ++qi) {
     CK(cudaMemcpyAsync(b.L + qi * NN * (es / 8), Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
+    if (b.Vc) CK(cudaMemcpyAsync(b.Vc + qi * NN * (es / 8), Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
+  }
   prof_begin(ctx, pex, s);
-  CK(launch_cholesky(j->is_complex, j->n_aux, nq, b.L, (long)(NN * (es / 8)), 1, nullptr, b.status, (1 << 29) + q0,
-                     s));
+  CK(launch_cholesky(j->is_complex, j->n_aux, nq, b.L, mstride, 1, b.Vc ? b.ldV + q0 : nullptr, b.status,
+                     (1 << 29) + q0, s));
   prof_end(ctx, pex, s, RPA_K_VFACTOR, 1);
   ctx->launches++;
+  if (b.Vc) {
+    // inverse form: -V^-1 per q (X = L^-1 in T's storage, then -(X^H X) over L),
+    // then one Cholesky of V^-1 - chi per (q, w); no sandwich
+    prof_begin(ctx, pex, s);
+    CK(launch_vinv(j->is_complex, j->n_aux, nq, b.L, b.T, b.L, s));
+    prof_end(ctx, pex, s, RPA_K_VFACTOR, 2);
+    ctx->launches += 2;
+    prof_begin(ctx, pex, s);
+    CK(launch_cholesky(j->is_complex, j->n_aux, nq * j->n_w, b.chi, mstride, 2, b.parts + (size_t)2 * q0 * j->n_w,
+                       b.status, q0 * j->n_w, s, b.L, b.Vc, b.ldV + q0, j->n_w));
+    prof_end(ctx, pex, s, RPA_K_LOGDET, 1);
+    ctx->launches++;
+    return RPA_OK;
+  }
   // Y = -(L^H chi L) (lower triangle), overwriting chi's storage
   prof_begin(ctx, pex, s);
   CK(launch_sandwich(j->is_complex, j->n_aux, nq * j->n_w, j->n_w, b.chi, b.L, b.T, b.chi, s));
@@ -390,8 +414,8 @@ rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, 
   ctx->launches += 2;
   // 1 - Pi' = 1 + Y: Cholesky, ln det, Tr
   prof_begin(ctx, pex, s);
-  CK(launch_cholesky(j->is_complex, j->n_aux, nq * j->n_w, b.chi, (long)(NN * (es / 8)), 0,
-                     b.parts + (size_t)2 * q0 * j->n_w, b.status, q0 * j->n_w, s));
+  CK(launch_cholesky(j->is_complex, j->n_aux, nq * j->n_w, b.chi, mstride, 0, b.parts + (size_t)2 * q0 * j->n_w,
+                     b.status, q0 * j->n_w, s));
   prof_end(ctx, pex, s, RPA_K_LOGDET, 1);
   ctx->launches++;
   return RPA_OK;
@@ -468,7 +492,7 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
   CK(cudaSetDevice(ctx->device));
   cudaStream_t s = ex.s;
   const int qb = choose_qb(job, ctx->n_slices, ws_cap);
-  Layout L = plan_layout(job, qb, ctx->n_slices, ws_cap);
+  Layout L = plan_layout(job, qb, ctx->n_slices, ws_cap, true);
   if (!ex.ensure_ws(L.total)) {
     ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", L.total);
     return RPA_E_NOMEM;
@@ -674,7 +698,7 @@ rpa_status rpa_chi0(rpa_ctx* ctx, const rpa_job* job, int q, void* chi_out, void
   CK(cudaSetDevice(ctx->device));
   Exec& ex = ctx->ex;
   cudaStream_t s = (cudaStream_t)stream;
-  Layout L = plan_layout(job, 1, ctx->n_slices, sync_ws_cap(ctx));
+  Layout L = plan_layout(job, 1, ctx->n_slices, sync_ws_cap(ctx), true);
   if (!ex.ensure_ws(L.total)) {
     ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", L.total);
     return RPA_E_NOMEM;
@@ -711,7 +735,7 @@ rpa_status rpa_logdet(rpa_ctx* ctx, const rpa_job* job, int q, const void* chi, 
   cudaStream_t s = (cudaStream_t)stream;
   rpa_job j1 = *job;
   j1.prec = RPA_PREC_FP64;
-  Layout L = plan_layout(&j1, 1, ctx->n_slices, sync_ws_cap(ctx));
+  Layout L = plan_layout(&j1, 1, ctx->n_slices, sync_ws_cap(ctx), true);
   if (!ex.ensure_ws(L.total)) {
     ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", L.total);
     return RPA_E_NOMEM;

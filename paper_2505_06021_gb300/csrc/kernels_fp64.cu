@@ -9,7 +9,11 @@
 //   * the sandwich uses the Cholesky factor L of V (triangular operands, lower
 //     output only) instead of the dense V^(1/2);
 //   * the factorisation of 1 - Pi keeps the diagonal in "pivot minus one"
-//     form so that ln det = sum log1p(u) keeps its digits as Pi -> 0.
+//     form so that ln det = sum log1p(u) keeps its digits as Pi -> 0;
+//   * the inverse form used with the split-precision chi0 needs no sandwich at
+//     all: det(1 - V^(1/2) chi V^(1/2)) = det(V^-1 - chi) det V and
+//     Tr(V^(1/2) chi V^(1/2)) = Tr(chi V), with V^-1 = X^H X, X = L^-1, formed
+//     once per q.
 // All reductions run in a fixed order, so results are bit-reproducible.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -345,14 +349,21 @@ __global__ void __launch_bounds__(256)
 // One CTA (256 threads) per matrix, right-looking blocked with 32-wide panels.
 // mode 0: A holds Y = -Pi; the factorised matrix is 1 + Y, whose diagonal is
 //         kept as u = pivot - 1; ln det = sum_j log1p(u_j); Tr Pi = -sum Y_jj.
-// mode 1: A holds V; factor in place, strict upper triangle zeroed.
+// mode 1: A holds V; factor in place, strict upper triangle zeroed; with out
+//         set, out[b] = ln det V.
+// mode 2 (inverse form): A holds chi of (q, w) = (b / n_w, b % n_w); the
+//         lower triangle becomes M = V^-1 - chi (Wn = -V^-1 of the q, lower
+//         triangle), factorised; ln det(1 - Pi) = ln det M + ln det V
+//         (ldV[q]) and Tr Pi = Tr(chi V) = sum_PQ Re(chi_PQ conj(V_PQ)) from
+//         the copy Vc of V(q).
 
 constexpr int CB = 32;
 
 template <bool C>
 __global__ void __launch_bounds__(256)
     cholesky_kernel(int N, double* __restrict__ mats, long bstride, int mode, double* __restrict__ out,
-                    int* __restrict__ status, int status_base) {
+                    int* __restrict__ status, int status_base, const double* __restrict__ Wn,
+                    const double* __restrict__ Vc, const double* __restrict__ ldV, int n_w) {
   __shared__ Elem<C> D[CB][CB + 1];
   __shared__ Elem<C> S2[CB][CB + 1];
   Elem<C>(*S1)[CB + 1] = D;  // the diagonal block is free again during the trailing update
@@ -363,10 +374,33 @@ __global__ void __launch_bounds__(256)
   double* A = mats + (long)b * bstride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  // trace of Pi (mode 0), fixed-order reduction
+  // trace of Pi (modes 0 and 2), fixed-order reduction; mode 2 also forms M
   if (mode == 0) {
     double s = 0.0;
     for (int j = tid; j < N; j += 256) s += ld_elem<C>(A, (long)j * N + j).re;
+    red[tid] = s;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+      if (tid < off) red[tid] += red[tid + off];
+      __syncthreads();
+    }
+  } else if (mode == 2) {
+    const long NN = (long)N * N;
+    const double* Wq = Wn + (long)(b / n_w) * NN * (C ? 2 : 1);
+    const double* Vq = Vc + (long)(b / n_w) * NN * (C ? 2 : 1);
+    double s = 0.0;
+    for (long idx = tid; idx < NN; idx += 256) {
+      const int r = (int)(idx / N), c = (int)(idx % N);
+      if (c > r) continue;
+      const Elem<C> x = ld_elem<C>(A, idx), v = ld_elem<C>(Vq, idx), w = ld_elem<C>(Wq, idx);
+      double t = x.re * v.re;
+      if constexpr (C) t = fma(x.im, v.im, t);
+      s += (r == c) ? t : 2.0 * t;
+      Elem<C> m;
+      m.re = -w.re - x.re;
+      if constexpr (C) m.im = -w.im - x.im;
+      st_elem<C>(A, idx, m);
+    }
     red[tid] = s;
     __syncthreads();
     for (int off = 128; off > 0; off >>= 1) {
@@ -400,7 +434,7 @@ __global__ void __launch_bounds__(256)
             lbad = 1;
           } else {
             l = sqrt(piv);
-            lacc += (mode == 0) ? log1p(u) : 0.0;
+            lacc += (mode == 0) ? log1p(u) : log(piv);
             Elem<C> e = zero_elem<C>();
             e.re = l;
             D[c][c] = e;
@@ -533,8 +567,96 @@ __global__ void __launch_bounds__(256)
     }
   }
   if (tid == 0 && out) {
-    out[2 * b] = logacc;
-    out[2 * b + 1] = (mode == 0) ? -red[0] : 0.0;
+    if (mode == 0) {
+      out[2 * b] = logacc;
+      out[2 * b + 1] = -red[0];
+    } else if (mode == 2) {
+      out[2 * b] = logacc + ldV[b / n_w];
+      out[2 * b + 1] = red[0];
+    } else {
+      out[b] = logacc;
+    }
+  }
+}
+
+// X = L^-1 for lower-triangular L (real positive diagonal), one CTA per
+// (matrix, 32-column block): block forward substitution down the rows,
+// X_r = L_rr^-1 (E_r - sum_{cb <= s < r} L_rs X_s); X is lower triangular.
+template <bool C>
+__global__ void __launch_bounds__(256) trinv_kernel(int N, const double* __restrict__ Lb, double* __restrict__ Xb) {
+  __shared__ Elem<C> Ls[CB][CB + 1];
+  __shared__ Elem<C> Xs[CB][CB + 1];
+  const int nt = (N + CB - 1) / CB;
+  const int b = blockIdx.x / nt, cb = blockIdx.x % nt;
+  const long NN = (long)N * N;
+  const double* L = Lb + (long)b * NN * (C ? 2 : 1);
+  double* X = Xb + (long)b * NN * (C ? 2 : 1);
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int c0 = cb * CB;
+  const int ncol = min(CB, N - c0);
+  for (long idx = tid; idx < (long)c0 * CB; idx += 256) {
+    const int r = (int)(idx / CB), c = (int)(idx % CB);
+    if (c < ncol) st_elem<C>(X, (long)r * N + c0 + c, zero_elem<C>());
+  }
+  for (int rb = cb; rb < nt; ++rb) {
+    const int r0 = rb * CB;
+    Elem<C> acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = zero_elem<C>();
+    for (int sb = cb; sb < rb; ++sb) {
+      const int s0 = sb * CB;
+      for (int idx = tid; idx < CB * CB; idx += 256) {
+        const int r = idx / CB, c = idx % CB;
+        Ls[r][c] = (r0 + r < N) ? ld_elem<C>(L, (long)(r0 + r) * N + s0 + c) : zero_elem<C>();
+        Xs[r][c] = (c < ncol) ? ld_elem<C>(X, (long)(s0 + r) * N + c0 + c) : zero_elem<C>();
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int k = 0; k < CB; ++k) {
+        const Elem<C> xv = Xs[k][tx];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) mac<C>(acc[u], Ls[ty + 8 * u][k], xv);
+      }
+      __syncthreads();
+    }
+    // right-hand side E_r - acc, and the diagonal block of L
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = ty + 8 * u;
+      Elem<C> e = zero_elem<C>();
+      e.re = (r0 + r == c0 + tx) ? 1.0 : 0.0;
+      e.re -= acc[u].re;
+      if constexpr (C) e.im = -acc[u].im;
+      Xs[r][tx] = e;
+    }
+    for (int idx = tid; idx < CB * CB; idx += 256) {
+      const int r = idx / CB, c = idx % CB;
+      Ls[r][c] = (r0 + r < N && r0 + c < N && c <= r) ? ld_elem<C>(L, (long)(r0 + r) * N + r0 + c) : zero_elem<C>();
+    }
+    __syncthreads();
+    if (tid < CB) {
+      const int c = tid;
+      const int nr = min(CB, N - r0);
+      for (int r = 0; r < nr; ++r) {
+        Elem<C> v = Xs[r][c];
+        for (int k = 0; k < r; ++k) {
+          Elem<C> prod = zero_elem<C>();
+          mac<C>(prod, Ls[r][k], Xs[k][c]);
+          v.re -= prod.re;
+          if constexpr (C) v.im -= prod.im;
+        }
+        const double d = Ls[r][r].re;
+        v.re /= d;
+        if constexpr (C) v.im /= d;
+        Xs[r][c] = v;
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < CB * CB; idx += 256) {
+      const int r = idx / CB, c = idx % CB;
+      if (r0 + r < N && c < ncol) st_elem<C>(X, (long)(r0 + r) * N + c0 + c, Xs[r][c]);
+    }
+    __syncthreads();
   }
 }
 
@@ -597,12 +719,29 @@ cudaError_t launch_sandwich(int cplx, int N, int n_batch, int n_w, const double*
 }
 
 cudaError_t launch_cholesky(int cplx, int N, int n_mat, double* mats, long bstride, int mode, double* out,
-                            int* status, int status_base, cudaStream_t s) {
+                            int* status, int status_base, cudaStream_t s, const double* Wn, const double* Vc,
+                            const double* ldV, int n_w) {
   if (n_mat == 0) return cudaSuccess;
+  if (mode == 2 && (!Wn || !Vc || !ldV || n_w <= 0)) return cudaErrorInvalidValue;
   if (cplx)
-    cholesky_kernel<true><<<n_mat, 256, 0, s>>>(N, mats, bstride, mode, out, status, status_base);
+    cholesky_kernel<true><<<n_mat, 256, 0, s>>>(N, mats, bstride, mode, out, status, status_base, Wn, Vc, ldV, n_w);
   else
-    cholesky_kernel<false><<<n_mat, 256, 0, s>>>(N, mats, bstride, mode, out, status, status_base);
+    cholesky_kernel<false><<<n_mat, 256, 0, s>>>(N, mats, bstride, mode, out, status, status_base, Wn, Vc, ldV,
+                                                 n_w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vinv(int cplx, int N, int n_q, const double* L, double* X, double* Wn, cudaStream_t s) {
+  if (n_q == 0) return cudaSuccess;
+  const int nb = (N + CB - 1) / CB;
+  const int nt = (N + GT - 1) / GT, tri = nt * (nt + 1) / 2;
+  if (cplx) {
+    trinv_kernel<true><<<n_q * nb, 256, 0, s>>>(N, L, X);
+    sandwich_kernel<true, 1><<<n_q * tri, 256, 0, s>>>(N, 1, X, X, Wn, nt, tri);
+  } else {
+    trinv_kernel<false><<<n_q * nb, 256, 0, s>>>(N, L, X);
+    sandwich_kernel<false, 1><<<n_q * tri, 256, 0, s>>>(N, 1, X, X, Wn, nt, tri);
+  }
   return cudaGetLastError();
 }
 

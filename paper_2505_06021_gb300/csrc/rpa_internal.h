@@ -36,11 +36,20 @@ cudaError_t launch_chi0_fp64(const BatchGeom& g, const double* const* Cptrs, con
 //   mode 0: input Y = -Pi (lower triangle), factorises 1 + Y = 1 - Pi and writes
 //           out[2*b] = ln det(1 - Pi) = sum log1p(pivot - 1), out[2*b+1] = Tr Pi.
 //   mode 1: input V (lower triangle), writes the factor L (upper part zeroed);
-//           out may be null.
+//           out[b] = ln det V unless out is null.
+//   mode 2: input chi of (q, w) = (b / n_w, b % n_w); factorises
+//           M = V^-1 - chi with Wn[q] = -V^-1 (lower triangle) and writes
+//           out[2*b] = ln det M + ldV[q] = ln det(1 - Pi), out[2*b+1] =
+//           Tr(chi V) = Tr Pi, V read from Vc[q].
 // A non-positive pivot sets *status (if still 0) to 1 + status_base + b and
 // the matrix is abandoned.
 cudaError_t launch_cholesky(int cplx, int N, int n_mat, double* mats, long bstride, int mode, double* out,
-                            int* status, int status_base, cudaStream_t s);
+                            int* status, int status_base, cudaStream_t s, const double* Wn = nullptr,
+                            const double* Vc = nullptr, const double* ldV = nullptr, int n_w = 0);
+
+// Wn[q] = -V(q)^-1 (lower triangle) from the Cholesky factors L[q]: X = L^-1
+// by block forward substitution into X[q], then -(X^H X).
+cudaError_t launch_vinv(int cplx, int N, int n_q, const double* L, double* X, double* Wn, cudaStream_t s);
 
 // T[b] = chi[b] * L[b / n_w]   (L lower triangular, N x N).
 // Y[b] = -(L[b / n_w]^H T[b]), lower triangle only.

@@ -92,7 +92,7 @@ namespace rpa {
 
 // Workspace of one lane for a job processed in q-batches of qb q-points.
 struct Layout {
-  size_t meta, dtab, chi, T, L, stageC, stageV, eps, mixed, total;
+  size_t meta, dtab, chi, T, L, Vc, stageC, stageV, eps, mixed, total;
   size_t slice_cap;  // mixed path: bytes for the weighted operand's digit planes
   int qb;
 };
@@ -108,11 +108,13 @@ struct Bufs {
   double* Ec;          // [1]
   double* eps;         // [n_q*n_w]
   double* parts;       // [n_q*n_w*2]
+  double* ldV;         // [n_q] ln det V(q) (inverse-form tail)
   int* status;
   double* dtab;
   double* chi;
   double* T;
   double* L;
+  double* Vc;  // copy of V(q) for Tr(chi V) (inverse-form tail), else null
   char* stageC[2];
   char* stageV[2];
   double* eps_occ;
@@ -138,7 +140,8 @@ rpa_status wait_event(rpa_ctx* ctx, cudaEvent_t ev, double timeout_s);
 void prof_begin(rpa_ctx* ctx, Exec* ex, cudaStream_t s);
 void prof_end(rpa_ctx* ctx, Exec* ex, cudaStream_t s, int cls, int n_kernels);
 void prof_collect(rpa_ctx* ctx, Exec* ex);
-Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap);
+// mixed_ws: include the split-precision chi0 workspace (a batch supplies its own).
+Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool mixed_ws);
 int choose_qb(const rpa_job* j, int n_slices, size_t cap);
 Bufs carve(void* ws, const rpa_job* j, const Layout& L);
 size_t sync_ws_cap(rpa_ctx* ctx);
