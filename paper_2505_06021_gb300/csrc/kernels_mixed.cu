@@ -91,13 +91,25 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait with a suspend-time hint: a waiting thread sleeps until the phase
+// completes or about `ns` nanoseconds pass, instead of spinning on the barrier
+// and stealing issue slots from the producer and MMA threads.
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t* b, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait; returns false (and raises the flags) on time-out or abort.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int code) {
+                                          int code, uint32_t sleep_ns = 0) {
   if (mbar_try(b, parity)) return true;
   const unsigned long long t0 = gtime();
   while (true) {
-    if (mbar_try(b, parity)) return true;
+    if (sleep_ns ? mbar_try_sleep(b, parity, sleep_ns) : mbar_try(b, parity)) return true;
     if (*abort_flag) return false;
     if (gtime() - t0 > WAIT_NS) {
       *abort_flag = 1;
@@ -494,7 +506,44 @@ __device__ __forceinline__ ItemPos item_pos(const TcParams& p, int item) {
   return r;
 }
 
+// Slice pairs (i, j) of S digit planes: levels i + j < S, then (S/2, S/2) for
+// even S; accumulator group = min(level, 3); `first` marks the first pair of
+// its group in a stage (it starts the group's sum at the first K-block of a
+// chunk).
+template <int S>
+struct PairTable {
+  static constexpr int N = S * (S + 1) / 2 + (S % 2 == 0 ? 1 : 0);
+  int i[16], j[16], g[16], first[16], mask;
+  constexpr PairTable() : i(), j(), g(), first(), mask(0) {
+    int n = 0;
+    for (int l = 0; l < S; ++l)
+      for (int a = 0; a <= l; ++a) {
+        i[n] = a;
+        j[n] = l - a;
+        g[n] = l < NGROUPS - 1 ? l : NGROUPS - 1;
+        ++n;
+      }
+    if (S % 2 == 0) {
+      i[n] = S / 2;
+      j[n] = S / 2;
+      g[n] = S < NGROUPS - 1 ? S : NGROUPS - 1;
+      ++n;
+    }
+    for (int k = 0; k < n; ++k) {
+      first[k] = 1;
+      for (int m = 0; m < k; ++m)
+        if (g[m] == g[k]) first[k] = 0;
+      mask |= 1 << g[k];
+    }
+  }
+};
+
+template <int S>
+__device__ constexpr PairTable<S> kPairs{};
+
+template <int S>
 __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_constant__ TcParams p) {
+  constexpr const PairTable<S>& PT = kPairs<S>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -526,7 +575,7 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t stage_tx = 2u * (uint32_t)p.s * PLANE_BYTES;
+  constexpr uint32_t stage_tx = 2u * (uint32_t)S * PLANE_BYTES;
 
   if (warp == 0) {
     // ------------------------------------------------ TMA producer
@@ -538,16 +587,16 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
       bool ok = true;
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
         const ItemPos it = item_pos(p, item);
-        const TcSeg& S = p.seg[it.seg];
+        const TcSeg& SG = p.seg[it.seg];
         for (int kb = it.kb0; kb < it.kb1 && ok; ++kb) {
-          ok = mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err, 11);
+          ok = mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.err, 11, 2000);
           if (!ok) break;
           uint8_t* sa = smem + stage * STAGE_BYTES;
           uint8_t* sb = sa + MAX_S * PLANE_BYTES;
           mbar_expect_tx(&full[stage], stage_tx);
           // A: X slices of rows I*128.. ; B: [X; Y] slices of columns J*64.. (real: X of J*128..)
-          tma_load_4d(sa, &S.mapA, &full[stage], kb * KB, it.I * TILE_M, 0, it.g * p.s);
-          tma_load_4d(sb, &S.mapB, &full[stage], kb * KB, it.J * (S.cplx ? 64 : 128), 0, 0);
+          tma_load_4d(sa, &SG.mapA, &full[stage], kb * KB, it.I * TILE_M, 0, it.g * S);
+          tma_load_4d(sb, &SG.mapB, &full[stage], kb * KB, it.J * (SG.cplx ? 64 : 128), 0, 0);
           armed[stage] = (int)phase;
           if (++stage == STAGES) {
             stage = 0;
@@ -570,6 +619,8 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
       uint32_t phase = 0, acc_phase = 0;
       bool ok = true;
       const uint32_t id = idesc();
+      // descriptors: plane 0 of stage 0, advanced by byte offsets >> 4
+      const uint64_t d0 = sdesc(smem_u32(smem));
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
         const ItemPos it = item_pos(p, item);
         for (int c0 = it.kb0; c0 < it.kb1 && ok; c0 += p.kb_per_chunk) {
@@ -577,20 +628,17 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
           ok = mbar_wait(acc_empty, acc_phase ^ 1u, abort_flag, p.err, 12);
           if (!ok) break;
           fence_after();
-          uint32_t inited = 0;  // bit per accumulator group, this chunk
           for (int kb = c0; kb < c1 && ok; ++kb) {
             ok = mbar_wait(&full[stage], phase, abort_flag, p.err, 13);
             if (!ok) break;
             fence_after();
-            const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
-            const uint32_t sb = sa + MAX_S * PLANE_BYTES;
-            for (int pi = 0; pi < p.n_pairs; ++pi) {
-              const int grp = p.pair_grp[pi];
-              const bool acc = (inited >> grp) & 1u;
-              mma(tmem + 128u * (uint32_t)grp, sdesc(sa + p.pair_i[pi] * PLANE_BYTES),
-                  sdesc(sb + p.pair_j[pi] * PLANE_BYTES), id, acc);
-              inited |= 1u << grp;
-            }
+            const uint64_t da = d0 + (uint64_t)((stage * STAGE_BYTES) >> 4);
+            const uint64_t db = da + (uint64_t)((MAX_S * PLANE_BYTES) >> 4);
+            const bool first_kb = kb == c0;
+#pragma unroll
+            for (int pi = 0; pi < PairTable<S>::N; ++pi)
+              mma(tmem + 128u * (uint32_t)PT.g[pi], da + (uint64_t)((PT.i[pi] * PLANE_BYTES) >> 4),
+                  db + (uint64_t)((PT.j[pi] * PLANE_BYTES) >> 4), id, !(first_kb && PT.first[pi]));
             mma_commit(&empty[stage]);
             if (++stage == STAGES) {
               stage = 0;
@@ -621,7 +669,7 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
 #pragma unroll
       for (int u = 0; u < 64; ++u) hi[u] = lo[u] = 0.f;
       for (int c0 = it.kb0; c0 < it.kb1 && ok; c0 += p.kb_per_chunk) {
-        ok = mbar_wait(acc_full, acc_phase, abort_flag, p.err, 14);
+        ok = mbar_wait(acc_full, acc_phase, abort_flag, p.err, 14, 20000);
         if (!ok) break;
         fence_after();
 #pragma unroll
@@ -913,6 +961,15 @@ uint64_t round_key(const std::vector<SegShape>& v, int s) {
   return h;
 }
 
+void launch_tc(int s, int grid, size_t smem, cudaStream_t st, const TcParams& tp) {
+  if (s == 2)
+    chi0_tc_kernel<2><<<grid, THREADS, smem, st>>>(tp);
+  else if (s == 3)
+    chi0_tc_kernel<3><<<grid, THREADS, smem, st>>>(tp);
+  else
+    chi0_tc_kernel<4><<<grid, THREADS, smem, st>>>(tp);
+}
+
 size_t slice_cap_of(const MixedQ& q) { return q.slice_cap ? q.slice_cap : ((size_t)12 << 30); }
 
 }  // namespace
@@ -961,7 +1018,11 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [&] {
-      attr = cudaFuncSetAttribute(chi0_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = cudaFuncSetAttribute(chi0_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (attr == cudaSuccess)
+        attr = cudaFuncSetAttribute(chi0_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (attr == cudaSuccess)
+        attr = cudaFuncSetAttribute(chi0_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
     if (attr != cudaSuccess) return attr;
   }
@@ -1122,7 +1183,7 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
         float ms = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {  // first run warms L2 and the instruction cache
           cudaEventRecord(e0, st);
-          chi0_tc_kernel<<<std::min(items, sms), THREADS, smem, st>>>(tp);
+          launch_tc(s, std::min(items, sms), smem, st, tp);
           cudaEventRecord(e1, st);
           nl += 1;
           if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
@@ -1143,7 +1204,7 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
     }
     if (!build(Lc, items, blocks)) return cudaErrorInvalidValue;
     hb();
-    chi0_tc_kernel<<<std::min(items, sms), THREADS, smem, st>>>(tp);
+    launch_tc(s, std::min(items, sms), smem, st, tp);
     he(RPA_K_CHI0, 1);
     hb();
     reduce_kernel<<<blocks, 256, 0, st>>>(rp);
