@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "rpa_internal.h"
 
@@ -25,6 +26,17 @@ namespace rpa {
 namespace {
 
 // ---------------------------------------------------------------- helpers --
+
+int num_sms_fp64() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
 
 template <bool C>
 struct Elem;
@@ -359,7 +371,106 @@ __global__ void __launch_bounds__(256)
 
 constexpr int CB = 32;
 
-template <bool C>
+// Synchronisation and shared-memory access across the CTAs that share one
+// matrix: a thread-block cluster of CL CTAs (CL = 1: a single CTA).
+template <int CL>
+struct Team {
+  __device__ static unsigned rank() {
+    if constexpr (CL == 1) {
+      return 0;
+    } else {
+      unsigned r;
+      asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+      return r;
+    }
+  }
+  __device__ static void sync() {
+    if constexpr (CL == 1) {
+      __syncthreads();
+    } else {
+      __syncthreads();
+      asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    }
+  }
+  // value of a shared variable in CTA `r` of the team
+  template <typename T>
+  __device__ static T read(T* p, unsigned r) {
+    if constexpr (CL == 1) {
+      return *p;
+    } else {
+      const uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+      uint32_t remote;
+      asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(r));
+      T v;
+      if constexpr (sizeof(T) == 8) {
+        unsigned long long x;
+        asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(x) : "r"(remote) : "memory");
+        memcpy(&v, &x, 8);
+      } else {
+        unsigned x;
+        asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(x) : "r"(remote) : "memory");
+        memcpy(&v, &x, 4);
+      }
+      return v;
+    }
+  }
+};
+
+// Matrix loads bypass L1 in the cluster variant: other CTAs of the cluster
+// write the matrix between the barriers.
+template <bool C, int CL>
+__device__ __forceinline__ Elem<C> ldm(const double* p, long i) {
+  if constexpr (CL == 1) {
+    return ld_elem<C>(p, i);
+  } else {
+    Elem<C> e;
+    if constexpr (C) {
+      const double2 v = __ldcg(reinterpret_cast<const double2*>(p + 2 * i));
+      e.re = v.x;
+      e.im = v.y;
+    } else {
+      e.re = __ldcg(p + i);
+    }
+    return e;
+  }
+}
+
+// Fixed-order sum of the per-thread values `s` over the whole team; the
+// result is valid in every thread of CTA 0 (red[0]).
+template <int CL>
+__device__ void team_sum(double s, double* red, double* part) {
+  const int tid = threadIdx.x;
+  red[tid] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (tid < off) red[tid] += red[tid + off];
+    __syncthreads();
+  }
+  if (tid == 0) *part = red[0];
+  Team<CL>::sync();
+  if (Team<CL>::rank() == 0 && tid == 0) {
+    double t = 0.0;
+    for (unsigned r = 0; r < (unsigned)CL; ++r) t += Team<CL>::read(part, r);
+    red[0] = t;
+  }
+  __syncthreads();
+}
+
+// Right-looking blocked Cholesky with 32-wide panels.  One matrix per team of
+// CL CTAs (256 threads each): CTA 0 factors the diagonal block, the panel rows
+// and the trailing tiles are dealt round robin over the team, barriers between
+// the phases.  Sums that enter the results (trace, log-det) run in a fixed
+// order, so the value does not depend on CL's scheduling.
+// mode 0: A holds Y = -Pi; the factorised matrix is 1 + Y, whose diagonal is
+//         kept as u = pivot - 1; ln det = sum_j log1p(u_j); Tr Pi = -sum Y_jj.
+// mode 1: A holds V; factor in place, strict upper triangle zeroed; with out
+//         set, out[b] = ln det V.
+// mode 2 (inverse form): A holds chi of (q, w) = (b / n_w, b % n_w); the
+//         lower triangle becomes M = V^-1 - chi (Wn = -V^-1 of the q, lower
+//         triangle), factorised; ln det(1 - Pi) = ln det M + ln det V
+//         (ldV[q]) and Tr Pi = Tr(chi V) = sum_PQ Re(chi_PQ conj(V_PQ)) from
+//         the copy Vc of V(q).
+template <bool C, int CL>
 __global__ void __launch_bounds__(256)
     cholesky_kernel(int N, double* __restrict__ mats, long bstride, int mode, double* __restrict__ out,
                     int* __restrict__ status, int status_base, const double* __restrict__ Wn,
@@ -368,31 +479,30 @@ __global__ void __launch_bounds__(256)
   __shared__ Elem<C> S2[CB][CB + 1];
   Elem<C>(*S1)[CB + 1] = D;  // the diagonal block is free again during the trailing update
   __shared__ double red[256];
+  __shared__ double part;
   __shared__ int bad;
   __shared__ double logacc;
-  const int b = blockIdx.x;
+  const int b = blockIdx.x / CL;
+  const unsigned rank = Team<CL>::rank();
   double* A = mats + (long)b * bstride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gtid = (int)rank * 256 + tid;
+  constexpr int GSTRIDE = 256 * CL;
 
-  // trace of Pi (modes 0 and 2), fixed-order reduction; mode 2 also forms M
+  // trace of Pi (modes 0 and 2); mode 2 also forms M in the lower triangle
   if (mode == 0) {
     double s = 0.0;
-    for (int j = tid; j < N; j += 256) s += ld_elem<C>(A, (long)j * N + j).re;
-    red[tid] = s;
-    __syncthreads();
-    for (int off = 128; off > 0; off >>= 1) {
-      if (tid < off) red[tid] += red[tid + off];
-      __syncthreads();
-    }
+    for (int j = gtid; j < N; j += GSTRIDE) s += ldm<C, CL>(A, (long)j * N + j).re;
+    team_sum<CL>(s, red, &part);
   } else if (mode == 2) {
     const long NN = (long)N * N;
     const double* Wq = Wn + (long)(b / n_w) * NN * (C ? 2 : 1);
     const double* Vq = Vc + (long)(b / n_w) * NN * (C ? 2 : 1);
     double s = 0.0;
-    for (long idx = tid; idx < NN; idx += 256) {
+    for (long idx = gtid; idx < NN; idx += GSTRIDE) {
       const int r = (int)(idx / N), c = (int)(idx % N);
       if (c > r) continue;
-      const Elem<C> x = ld_elem<C>(A, idx), v = ld_elem<C>(Vq, idx), w = ld_elem<C>(Wq, idx);
+      const Elem<C> x = ldm<C, CL>(A, idx), v = ld_elem<C>(Vq, idx), w = ld_elem<C>(Wq, idx);
       double t = x.re * v.re;
       if constexpr (C) t = fma(x.im, v.im, t);
       s += (r == c) ? t : 2.0 * t;
@@ -401,101 +511,104 @@ __global__ void __launch_bounds__(256)
       if constexpr (C) m.im = -w.im - x.im;
       st_elem<C>(A, idx, m);
     }
-    red[tid] = s;
-    __syncthreads();
-    for (int off = 128; off > 0; off >>= 1) {
-      if (tid < off) red[tid] += red[tid + off];
-      __syncthreads();
-    }
+    team_sum<CL>(s, red, &part);
   }
   if (tid == 0) {
     bad = 0;
     logacc = 0.0;
   }
-  __syncthreads();
+  Team<CL>::sync();
 
+  bool failed = false;
   for (int kb = 0; kb < N; kb += CB) {
     const int nb = min(CB, N - kb);
-    // (i) diagonal block
-    for (int idx = tid; idx < CB * CB; idx += 256) {
-      const int r = idx / CB, c = idx % CB;
-      D[r][c] = (r < nb && c <= r) ? ld_elem<C>(A, (long)(kb + r) * N + kb + c) : zero_elem<C>();
-    }
-    __syncthreads();
-    if (warp == 0) {
-      double lacc = 0.0;
-      int lbad = 0;
-      for (int c = 0; c < nb; ++c) {
-        double l = 0.0;
-        if (lane == c) {
-          const double u = D[c][c].re;
-          const double piv = (mode == 0) ? 1.0 + u : u;
-          if (!(piv > 0.0)) {
+    // (i) diagonal block, by CTA 0
+    if (rank == 0) {
+      for (int idx = tid; idx < CB * CB; idx += 256) {
+        const int r = idx / CB, c = idx % CB;
+        D[r][c] = (r < nb && c <= r) ? ldm<C, CL>(A, (long)(kb + r) * N + kb + c) : zero_elem<C>();
+      }
+      __syncthreads();
+      if (warp == 0) {
+        double lacc = 0.0;
+        int lbad = 0;
+        for (int c = 0; c < nb; ++c) {
+          double l = 0.0;
+          if (lane == c) {
+            const double u = D[c][c].re;
+            const double piv = (mode == 0) ? 1.0 + u : u;
+            if (!(piv > 0.0)) {
+              lbad = 1;
+            } else {
+              l = sqrt(piv);
+              lacc += (mode == 0) ? log1p(u) : log(piv);
+              Elem<C> e = zero_elem<C>();
+              e.re = l;
+              D[c][c] = e;
+            }
+          }
+          const int anybad = __any_sync(0xffffffffu, lbad);
+          if (anybad) {
             lbad = 1;
-          } else {
-            l = sqrt(piv);
-            lacc += (mode == 0) ? log1p(u) : log(piv);
-            Elem<C> e = zero_elem<C>();
-            e.re = l;
-            D[c][c] = e;
+            break;
           }
-        }
-        const int anybad = __any_sync(0xffffffffu, lbad);
-        if (anybad) {
-          lbad = 1;
-          break;
-        }
-        l = __shfl_sync(0xffffffffu, l, c);
-        __syncwarp();
-        if (lane > c && lane < nb) {
-          Elem<C> e = D[lane][c];
-          e.re /= l;
-          if constexpr (C) e.im /= l;
-          D[lane][c] = e;
-        }
-        __syncwarp();
-        if (lane > c && lane < nb) {
-          const Elem<C> lr = D[lane][c];
-          for (int cc = c + 1; cc <= lane; ++cc) {
-            const Elem<C> lc = conj_e<C>(D[cc][c]);
-            Elem<C> e = D[lane][cc];
-            Elem<C> prod = zero_elem<C>();
-            mac<C>(prod, lr, lc);
-            e.re -= prod.re;
-            if constexpr (C) e.im -= prod.im;
-            D[lane][cc] = e;
+          l = __shfl_sync(0xffffffffu, l, c);
+          __syncwarp();
+          if (lane > c && lane < nb) {
+            Elem<C> e = D[lane][c];
+            e.re /= l;
+            if constexpr (C) e.im /= l;
+            D[lane][c] = e;
           }
+          __syncwarp();
+          if (lane > c && lane < nb) {
+            const Elem<C> lr = D[lane][c];
+            for (int cc = c + 1; cc <= lane; ++cc) {
+              const Elem<C> lc = conj_e<C>(D[cc][c]);
+              Elem<C> e = D[lane][cc];
+              Elem<C> prod = zero_elem<C>();
+              mac<C>(prod, lr, lc);
+              e.re -= prod.re;
+              if constexpr (C) e.im -= prod.im;
+              D[lane][cc] = e;
+            }
+          }
+          __syncwarp();
         }
-        __syncwarp();
+        // lane-wise partial log sums, combined in lane order (fixed)
+        for (int l2 = 0; l2 < 32; ++l2) {
+          const double v = __shfl_sync(0xffffffffu, lacc, l2);
+          if (lane == 0) logacc += v;
+        }
+        if (lbad && lane == 0) bad = 1;
       }
-      // lane-wise partial log sums, combined in lane order (fixed)
-      for (int l2 = 0; l2 < 32; ++l2) {
-        const double v = __shfl_sync(0xffffffffu, lacc, l2);
-        if (lane == 0) logacc += v;
+      __syncthreads();
+      if (!bad) {
+        for (int idx = tid; idx < CB * CB; idx += 256) {
+          const int r = idx / CB, c = idx % CB;
+          if (r < nb && c <= r) st_elem<C>(A, (long)(kb + r) * N + kb + c, D[r][c]);
+        }
       }
-      if (lbad && lane == 0) bad = 1;
     }
-    __syncthreads();
-    if (bad) {
-      if (tid == 0 && status) atomicCAS(status, 0, 1 + status_base + b);
-      if (out && tid == 0) {
-        out[2 * b] = nan("");
-        out[2 * b + 1] = nan("");
-      }
-      return;
-    }
-    // write the factored diagonal block back (lower part)
-    for (int idx = tid; idx < CB * CB; idx += 256) {
-      const int r = idx / CB, c = idx % CB;
-      if (r < nb && c <= r) st_elem<C>(A, (long)(kb + r) * N + kb + c, D[r][c]);
+    Team<CL>::sync();
+    if (Team<CL>::read(&bad, 0u)) {
+      failed = true;
+      break;
     }
     // (ii) panel: rows i >= kb + nb solve X L_kk^H = A_panel
-    for (int i = kb + nb + tid; i < N; i += 256) {
+    if (rank != 0) {
+      for (int idx = tid; idx < CB * CB; idx += 256) {
+        const int r = idx / CB, c = idx % CB;
+        D[r][c] = (r < nb && c <= r) ? ldm<C, CL>(A, (long)(kb + r) * N + kb + c) : zero_elem<C>();
+      }
+      __syncthreads();
+    }
+    for (int i = kb + nb + gtid; i < N; i += GSTRIDE) {
       Elem<C> x[CB];
 #pragma unroll
       for (int c = 0; c < CB; ++c) {
         if (c < nb) {
-          Elem<C> v = ld_elem<C>(A, (long)i * N + kb + c);
+          Elem<C> v = ldm<C, CL>(A, (long)i * N + kb + c);
 #pragma unroll
           for (int c2 = 0; c2 < CB; ++c2) {
             if (c2 < c) {
@@ -513,7 +626,7 @@ __global__ void __launch_bounds__(256)
         }
       }
     }
-    __syncthreads();
+    Team<CL>::sync();
     // (iii) trailing update of the lower part of A[kb+nb:, kb+nb:]
     const int m0 = kb + nb;
     const int m = N - m0;
@@ -521,14 +634,14 @@ __global__ void __launch_bounds__(256)
       const int nt = (m + CB - 1) / CB;
       const int ntiles = nt * (nt + 1) / 2;
       const int tx = tid & 15, ty = tid >> 4;
-      for (int tt = 0; tt < ntiles; ++tt) {
+      for (int tt = (int)rank; tt < ntiles; tt += CL) {
         int TI, TJ;
         tri_index(tt, TI, TJ);
         for (int idx = tid; idx < CB * CB; idx += 256) {
           const int r = idx / CB, c = idx % CB;
           const int ri = m0 + TI * CB + r, rj = m0 + TJ * CB + r;
-          S1[c][r] = (ri < N && c < nb) ? ld_elem<C>(A, (long)ri * N + kb + c) : zero_elem<C>();
-          S2[c][r] = (rj < N && c < nb) ? conj_e<C>(ld_elem<C>(A, (long)rj * N + kb + c)) : zero_elem<C>();
+          S1[c][r] = (ri < N && c < nb) ? ldm<C, CL>(A, (long)ri * N + kb + c) : zero_elem<C>();
+          S2[c][r] = (rj < N && c < nb) ? conj_e<C>(ldm<C, CL>(A, (long)rj * N + kb + c)) : zero_elem<C>();
         }
         __syncthreads();
         Elem<C> acc[2][2];
@@ -550,7 +663,7 @@ __global__ void __launch_bounds__(256)
           for (int v = 0; v < 2; ++v) {
             const int r = m0 + TI * CB + ty + 16 * u, c = m0 + TJ * CB + tx + 16 * v;
             if (r < N && c <= r) {
-              Elem<C> e = ld_elem<C>(A, (long)r * N + c);
+              Elem<C> e = ldm<C, CL>(A, (long)r * N + c);
               e.re -= acc[u][v].re;
               if constexpr (C) e.im -= acc[u][v].im;
               st_elem<C>(A, (long)r * N + c, e);
@@ -559,24 +672,41 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
       }
     }
+    Team<CL>::sync();
   }
-  if (mode == 1) {
-    for (long idx = tid; idx < (long)N * N; idx += 256) {
-      const int r = (int)(idx / N), c = (int)(idx % N);
-      if (c > r) st_elem<C>(A, idx, zero_elem<C>());
+  if (failed) {
+    if (rank == 0 && tid == 0) {
+      if (status) atomicCAS(status, 0, 1 + status_base + b);
+      if (out) {
+        if (mode == 1) {
+          out[b] = nan("");
+        } else {
+          out[2 * b] = nan("");
+          out[2 * b + 1] = nan("");
+        }
+      }
+    }
+  } else {
+    if (mode == 1) {
+      for (long idx = gtid; idx < (long)N * N; idx += GSTRIDE) {
+        const int r = (int)(idx / N), c = (int)(idx % N);
+        if (c > r) st_elem<C>(A, idx, zero_elem<C>());
+      }
+    }
+    if (rank == 0 && tid == 0 && out) {
+      if (mode == 0) {
+        out[2 * b] = logacc;
+        out[2 * b + 1] = -red[0];
+      } else if (mode == 2) {
+        out[2 * b] = logacc + ldV[b / n_w];
+        out[2 * b + 1] = red[0];
+      } else {
+        out[b] = logacc;
+      }
     }
   }
-  if (tid == 0 && out) {
-    if (mode == 0) {
-      out[2 * b] = logacc;
-      out[2 * b + 1] = -red[0];
-    } else if (mode == 2) {
-      out[2 * b] = logacc + ldV[b / n_w];
-      out[2 * b + 1] = red[0];
-    } else {
-      out[b] = logacc;
-    }
-  }
+  // no CTA leaves while another may still read its shared memory
+  Team<CL>::sync();
 }
 
 // X = L^-1 for lower-triangular L (real positive diagonal), one CTA per
@@ -718,17 +848,48 @@ cudaError_t launch_sandwich(int cplx, int N, int n_batch, int n_w, const double*
   return cudaGetLastError();
 }
 
+// Teams of CL_BIG CTAs per matrix when the launch has too few matrices to
+// fill the GPU with one CTA each and the matrices are large enough to share.
+constexpr int CL_BIG = 8;
+
+template <bool C, int CL>
+cudaError_t launch_chol_t(int N, int n_mat, double* mats, long bstride, int mode, double* out, int* status,
+                          int status_base, cudaStream_t s, const double* Wn, const double* Vc, const double* ldV,
+                          int n_w) {
+  if constexpr (CL == 1) {
+    cholesky_kernel<C, 1><<<n_mat, 256, 0, s>>>(N, mats, bstride, mode, out, status, status_base, Wn, Vc, ldV, n_w);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_mat * CL));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cholesky_kernel<C, CL>, N, mats, bstride, mode, out, status, status_base, Wn, Vc,
+                              ldV, n_w);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cholesky(int cplx, int N, int n_mat, double* mats, long bstride, int mode, double* out,
                             int* status, int status_base, cudaStream_t s, const double* Wn, const double* Vc,
                             const double* ldV, int n_w) {
   if (n_mat == 0) return cudaSuccess;
   if (mode == 2 && (!Wn || !Vc || !ldV || n_w <= 0)) return cudaErrorInvalidValue;
+  const bool team = N >= 256 && n_mat * 2 < num_sms_fp64();
   if (cplx)
-    cholesky_kernel<true><<<n_mat, 256, 0, s>>>(N, mats, bstride, mode, out, status, status_base, Wn, Vc, ldV, n_w);
-  else
-    cholesky_kernel<false><<<n_mat, 256, 0, s>>>(N, mats, bstride, mode, out, status, status_base, Wn, Vc, ldV,
-                                                 n_w);
-  return cudaGetLastError();
+    return team ? launch_chol_t<true, CL_BIG>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV,
+                                              n_w)
+                : launch_chol_t<true, 1>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
+  return team ? launch_chol_t<false, CL_BIG>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV,
+                                             n_w)
+              : launch_chol_t<false, 1>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
 }
 
 cudaError_t launch_vinv(int cplx, int N, int n_q, const double* L, double* X, double* Wn, cudaStream_t s) {

@@ -248,8 +248,7 @@ struct SliceArgs {
   int cplx, Npad, n_ov, Ktot, Kr, s, n_w, w0, G, nxy;
   const int* cfix;       // [Npad][Kr]
   const int* eC;         // [Npad] exponent of c_fix
-  const uint32_t* wm;    // [n_k][n_w][n_ov] weight mantissas, or null for weight 1
-  const int16_t* ew;     // [n_k][n_w][n_ov] weight exponents
+  const unsigned long long* wx;  // [n_k][n_w][n_ov] weights (mantissa | exponent << 32), null: weight 1
   const int* eA;         // [n_w][Npad] row exponents of A
   uint16_t* S;           // [(g*s + slice)][xy][Npad][Kr]
 };
@@ -273,6 +272,28 @@ __device__ __forceinline__ void store_planes(const SliceArgs& a, int g, int P, i
   }
 }
 
+// X planes only (the weighted operand A has no Y part).
+__device__ __forceinline__ void store_planes_x(const SliceArgs& a, int g, int P, int tg,
+                                               const uint32_t (&px)[MAX_S][8]) {
+#pragma unroll
+  for (int i = 0; i < MAX_S; ++i) {
+    if (i >= a.s) break;
+    uint4* dx = reinterpret_cast<uint4*>(a.S + (((long)g * a.s + i) * a.Npad + P) * a.Kr + tg * 16);
+    dx[0] = make_uint4(px[i][0], px[i][1], px[i][2], px[i][3]);
+    dx[1] = make_uint4(px[i][4], px[i][5], px[i][6], px[i][7]);
+  }
+}
+__device__ __forceinline__ void digits_to_x(int F, int u, int s, uint32_t (&px)[MAX_S][8]) {
+  uint32_t b[4];
+  digit_bytes(F, b);
+#pragma unroll
+  for (int i = 0; i < MAX_S; ++i) {
+    if (i >= s) break;
+    const uint32_t h = bf16_digit(b[i], i);
+    px[i][u >> 1] |= (u & 1) ? (h << 16) : h;
+  }
+}
+
 __device__ __forceinline__ void digits_to_planes(int F, int u, int s, bool with_y, uint32_t (&px)[MAX_S][8],
                                                  uint32_t (&py)[MAX_S][8]) {
   uint32_t b[4];
@@ -291,10 +312,12 @@ __device__ __forceinline__ void digits_to_planes(int F, int u, int s, bool with_
   }
 }
 
+template <bool CPLX, bool WEIGHTED>
 __global__ void __launch_bounds__(256) slice_kernel(SliceArgs a) {
   const long ngroups = (long)a.Kr / 16;
   const long total = (long)a.Npad * ngroups;
-  const bool with_y = a.nxy == 2;
+  constexpr bool with_y = CPLX;
+  constexpr int tpg = CPLX ? 8 : 16;  // t per group of 16 real values
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
     const int tg = (int)(idx % ngroups);
     const int P = (int)(idx / ngroups);
@@ -308,8 +331,8 @@ __global__ void __launch_bounds__(256) slice_kernel(SliceArgs a) {
       cv[4 * v + 2] = x.z;
       cv[4 * v + 3] = x.w;
     }
-    uint32_t px[MAX_S][8], py[MAX_S][8];
-    if (!a.wm) {
+    if constexpr (!WEIGHTED) {
+      uint32_t px[MAX_S][8], py[MAX_S][8];
 #pragma unroll
       for (int i = 0; i < MAX_S; ++i)
 #pragma unroll
@@ -318,32 +341,41 @@ __global__ void __launch_bounds__(256) slice_kernel(SliceArgs a) {
       for (int u = 0; u < 16; ++u) digits_to_planes(cv[u], u, a.s, with_y, px, py);
       store_planes(a, 0, P, tg, px, py);
       continue;
-    }
-    // weights of the t's of this group: complex 8 t (2 real values each), real 16 t
-    const int tpg = a.cplx ? 8 : 16;
+    } else {
+    // the group's t = t0 .. t0 + tpg - 1 as (k-point j, pair tt): one division
+    // per group, then steps
     const int t0 = tg * tpg;
+    const int j0 = t0 / a.n_ov, tt0 = t0 - j0 * a.n_ov;
+    const int eC = a.eC[P];
     for (int g = 0; g < a.G; ++g) {
       const int w = a.w0 + g;
-      const int shbase = 30 + a.eA[(long)w * a.Npad + P] - a.eC[P];
+      const int shbase = 30 + a.eA[(long)w * a.Npad + P] - eC;
+      uint32_t px[MAX_S][8];
 #pragma unroll
       for (int i = 0; i < MAX_S; ++i)
 #pragma unroll
-        for (int u = 0; u < 8; ++u) px[i][u] = py[i][u] = 0;
+        for (int u = 0; u < 8; ++u) px[i][u] = 0;
+      int j = j0, tt = tt0;
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int tl = a.cplx ? (u >> 1) : u;
-        const int tglob = t0 + tl;
-        int F = 0;
-        if (cv[u] != 0 && tglob < a.Ktot) {
-          const int j = tglob / a.n_ov, t = tglob - j * a.n_ov;
-          const long wi = ((long)j * a.n_w + w) * a.n_ov + t;
-          const long long p = (long long)cv[u] * (long long)__ldg(a.wm + wi);
-          const int sh = shbase - (int)__ldg(a.ew + wi);
-          F = (sh > 0) ? (int)((p + (1ll << (sh - 1))) >> sh) : (int)(p << (-sh));
+      for (int v = 0; v < tpg; ++v) {
+        unsigned long long x = 0;
+        if (t0 + v < a.Ktot) x = __ldg(a.wx + ((long)j * a.n_w + w) * a.n_ov + tt);
+        if (++tt == a.n_ov) {
+          tt = 0;
+          ++j;
         }
-        digits_to_planes(F, u, a.s, false, px, py);
+        const long long wmv = (long long)(uint32_t)x;
+        const int sh = shbase - (int)(uint32_t)(x >> 32);
+#pragma unroll
+        for (int r = 0; r < (CPLX ? 2 : 1); ++r) {
+          const int u = CPLX ? 2 * v + r : v;
+          const long long pr = (long long)cv[u] * wmv;
+          const int F = (sh > 62) ? 0 : (sh > 0) ? (int)((pr + (1ll << (sh - 1))) >> sh) : (int)(pr << (-sh));
+          digits_to_x(F, u, a.s, px);
+        }
       }
-      store_planes(a, g, P, tg, px, py);
+      store_planes_x(a, g, P, tg, px);
+    }
     }
   }
 }
@@ -422,8 +454,8 @@ __global__ void __launch_bounds__(256) erow_kernel(int cplx, int N, int Npad, in
 }
 
 // w = zeta_k |d| as a 31-bit mantissa and exponent: w = wm 2^(ew - 31),
-// wm in [2^30, 2^31)
-__global__ void __launch_bounds__(256) wtab_kernel(long n, const double* dtab, uint32_t* wm, int16_t* ew) {
+// wm in [2^30, 2^31); wx packs wm | (uint32) ew << 32 for the slicing.
+__global__ void __launch_bounds__(256) wtab_kernel(long n, const double* dtab, unsigned long long* wx, int16_t* ew) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(dtab[i]));
     const int E = (int)((b >> 52) & 0x7ff);
@@ -433,8 +465,9 @@ __global__ void __launch_bounds__(256) wtab_kernel(long n, const double* dtab, u
       m >>= 1;
       ++e;
     }
-    wm[i] = E ? (uint32_t)m : 0u;
-    ew[i] = (int16_t)(E ? e : -2000);
+    const int ee = E ? e : -2000;
+    wx[i] = (E ? m : 0ull) | ((unsigned long long)(uint32_t)ee << 32);
+    ew[i] = (int16_t)ee;
   }
 }
 
@@ -834,7 +867,7 @@ MixedLayout mixed_layout(const BatchGeom& g, int s, int sms, size_t slice_cap) {
   L.erow = al(sizeof(int) * (size_t)g.n_w * L.Npad);
   L.erowC = al(sizeof(int) * (size_t)L.Npad);
   L.part = al(sizeof(float) * 2 * 128 * 128 * (size_t)L.G * L.n_tiles * L.nks_cap);
-  L.wm = al(sizeof(uint32_t) * (size_t)g.n_k * g.n_w * g.n_ov);
+  L.wm = al(sizeof(unsigned long long) * (size_t)g.n_k * g.n_w * g.n_ov);
   L.ew = al(sizeof(int16_t) * (size_t)g.n_k * g.n_w * g.n_ov);
   L.cfix = al(sizeof(int) * (size_t)L.Npad * L.Kr);
   L.total = L.slices + L.slicesC + L.erow + L.erowC + L.part + L.wm + L.ew + L.cfix;
@@ -961,6 +994,20 @@ uint64_t round_key(const std::vector<SegShape>& v, int s) {
   return h;
 }
 
+void launch_slice(int cplx, unsigned grid, cudaStream_t st, const SliceArgs& a) {
+  if (a.wx) {
+    if (cplx)
+      slice_kernel<true, true><<<grid, 256, 0, st>>>(a);
+    else
+      slice_kernel<false, true><<<grid, 256, 0, st>>>(a);
+  } else {
+    if (cplx)
+      slice_kernel<true, false><<<grid, 256, 0, st>>>(a);
+    else
+      slice_kernel<false, false><<<grid, 256, 0, st>>>(a);
+  }
+}
+
 void launch_tc(int s, int grid, size_t smem, cudaStream_t st, const TcParams& tp) {
   if (s == 2)
     chi0_tc_kernel<2><<<grid, THREADS, smem, st>>>(tp);
@@ -1030,7 +1077,7 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
     MixedLayout L;
     uint16_t *S, *SC;
     int *erow, *erowC, *cfix;
-    uint32_t* wm;
+    unsigned long long* wx;
     int16_t* ew;
     float* part;
     int w_next, rounds_left;
@@ -1057,7 +1104,7 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
     p += q.L.erowC;
     q.part = (float*)p;
     p += q.L.part;
-    q.wm = (uint32_t*)p;
+    q.wx = (unsigned long long*)p;
     p += q.L.wm;
     q.ew = (int16_t*)p;
     p += q.L.ew;
@@ -1074,7 +1121,7 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
     const BatchGeom& g = qs[i].g;
     QState& q = Q[i];
     const long nwt = (long)g.n_k * g.n_w * g.n_ov;
-    wtab_kernel<<<(unsigned)std::min<long>((nwt + 255) / 256, (long)sms * 16), 256, 0, st>>>(nwt, qs[i].dtab, q.wm,
+    wtab_kernel<<<(unsigned)std::min<long>((nwt + 255) / 256, (long)sms * 16), 256, 0, st>>>(nwt, qs[i].dtab, q.wx,
                                                                                                q.ew);
     erow_kernel<<<q.L.Npad, 256, 0, st>>>(g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_k, g.n_w, qs[i].Cptrs, q.ew,
                                            q.erow, q.erowC);
@@ -1082,9 +1129,9 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
     cfix_kernel<<<(unsigned)std::min<long>((tot + 255) / 256, (long)sms * 32), 256, 0, st>>>(
         g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_k, q.L.Ktot, q.L.Kr, qs[i].Cptrs, q.erowC, q.cfix);
     SliceArgs sc{g.cplx, q.L.Npad, g.n_ov, q.L.Ktot, q.L.Kr, s, g.n_w, 0, 1, q.L.nxy, q.cfix, q.erowC,
-                 nullptr, nullptr, q.erow, q.SC};
+                 nullptr, q.erow, q.SC};
     const long tg = (long)q.L.Npad * (q.L.Kr / 16);
-    slice_kernel<<<(unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), 256, 0, st>>>(sc);
+    launch_slice(g.cplx, (unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), st, sc);
     nl += 4;
   }
   he(RPA_K_SLICE, 4 * n);
@@ -1116,9 +1163,9 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
       QState& q = Q[i];
       const BatchGeom& g = qs[i].g;
       SliceArgs sa{g.cplx, q.L.Npad, g.n_ov, q.L.Ktot, q.L.Kr, s, g.n_w, w0s[k], Gs[k], 1, q.cfix, q.erowC,
-                   q.wm, q.ew, q.erow, q.S};
+                   q.wx, q.erow, q.S};
       const long tg = (long)q.L.Npad * (q.L.Kr / 16);
-      slice_kernel<<<(unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), 256, 0, st>>>(sa);
+      launch_slice(g.cplx, (unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), st, sa);
       ++nl;
     }
     he(RPA_K_SLICE, (int)who.size());

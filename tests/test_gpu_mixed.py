@@ -102,6 +102,18 @@ def test_mixed_energy_periodic(rpa, ctx):
     assert np.max(np.abs(r["eps"] - ref["eps"]) / np.abs(ref["eps"])) <= 1e-8
 
 
+def test_mixed_energy_large_aux(rpa, ctx):
+    """N_aux = 300: inverse-form tail with the cluster Cholesky (few, large
+    matrices per launch)."""
+    p = synth.make_problem("m", is_complex=True, n_aux=300, n_occ=2, n_virt=6,
+                           grid=synth.regular_kq_grid((2, 1, 1)), n_w=3, seed=45)
+    job = rpa.job_from_problem(p, rpa.upload_problem(p), prec=rpa.PREC_MIXED)
+    r = ctx.energy(job)
+    ref = oracle.energy(p)
+    assert abs(r["Ec"] - ref["Ec"]) <= TOL_EC, (r["Ec"], ref["Ec"])
+    assert np.max(np.abs(r["eps"] - ref["eps"]) / np.abs(ref["eps"])) <= 1e-8
+
+
 def test_mixed_deterministic_and_slice_count(rpa):
     p = synth.make_problem("m", is_complex=True, n_aux=96, n_occ=3, n_virt=20, grid=synth.regular_kq_grid((2, 1, 1)),
                            n_w=3, seed=44)

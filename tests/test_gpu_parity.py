@@ -177,6 +177,24 @@ def test_not_positive_definite_reported(rpa, ctx):
     assert math.isfinite(r["Ec"])
 
 
+def test_large_aux_cluster_cholesky(rpa, ctx):
+    """N_aux >= 256 with few matrices per launch: the Cholesky factorisations
+    run on thread-block clusters (8 CTAs per matrix); parity as everywhere,
+    and an indefinite V is still reported with its q."""
+    p = _small_complex(n_aux=300, n_occ=2, n_virt=6, kdims=(2, 1, 1), n_w=3)
+    t = rpa.upload_problem(p)
+    job = rpa.job_from_problem(p, t)
+    _check_energy(ctx.energy(job), oracle.energy(p))
+    Vbad = t["V"][0].clone()
+    Vbad[7, 7] = -80.0
+    t2 = dict(t)
+    t2["V"] = [Vbad, t["V"][1]]
+    with pytest.raises(rpa.RpaError) as e:
+        ctx.energy(rpa.job_from_problem(p, t2))
+    assert e.value.status == rpa.RPA_E_NOTPD and "V(q=0)" in str(e.value)
+    assert math.isfinite(ctx.energy(job)["Ec"])
+
+
 def test_kernel_launch_count(rpa, ctx):
     p = _small_complex(n_aux=40, n_occ=2, n_virt=4)
     job = rpa.job_from_problem(p, rpa.upload_problem(p))
