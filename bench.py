@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--workload", default="periodic2d", choices=["periodic2d", "batch", "serving"])
+    ap.add_argument("--workload", default="periodic2d", choices=["periodic2d", "slab", "batch", "serving"])
     ap.add_argument("--no-fp64", action="store_true", help="periodic2d: skip the FP64 comparison step")
     ap.add_argument("--n-inst", type=int, default=64, help="batch: instances per step")
     ap.add_argument("--serve-jobs", type=int, default=200, help="serving: jobs in the stream")
@@ -54,10 +54,10 @@ def parse():
     return ap.parse_args()
 
 
-def workload(n_q=0):
+def workload(n_q=0, name="periodic2d"):
     from paper_2505_06021_gb300 import synth
 
-    p = synth.config1()
+    p = synth.config2() if name == "slab" else synth.config1()
     if n_q:
         g = p.grid
         g.pair_k, g.pair_kq, g.w_q = g.pair_k[:n_q], g.pair_kq[:n_q], g.w_q[:n_q]
@@ -65,11 +65,16 @@ def workload(n_q=0):
     return p
 
 
-def config_of(p, prec, n_q_override):
+def config_of(p, prec, n_q_override, name="periodic2d"):
+    if name == "slab":
+        desc = ("slab-dual-c128: slab dual k-grid, complex128, coarse 3x3x1 q-grid without Gamma + 4 near-Gamma "
+                "points, dense 6x6x1 K_reg (12 q x 36 k pairs), N_aux=%d, N_occ=%d, N_virt=%d, %d imaginary "
+                "frequencies" % (p.n_aux, p.n_occ, p.n_virt, p.n_w))
+    else:
+        desc = ("periodic2d-c128: 2-D periodic, complex128, 4x4x1 k and q grids (16 q x 16 k pairs), "
+                "N_aux=%d, N_occ=%d, N_virt=%d, %d imaginary frequencies" % (p.n_aux, p.n_occ, p.n_virt, p.n_w))
     return {
-        "workload": "periodic2d-c128: 2-D periodic, complex128, 4x4x1 k and q grids (16 q x 16 k pairs), "
-                    "N_aux=%d, N_occ=%d, N_virt=%d, %d imaginary frequencies" % (p.n_aux, p.n_occ, p.n_virt, p.n_w)
-                    + ("" if not n_q_override else " [first %d q only: profiling case]" % n_q_override),
+        "workload": desc + ("" if not n_q_override else " [first %d q only: profiling case]" % n_q_override),
         "n_q": p.n_q, "n_k": p.n_k, "n_aux": p.n_aux, "n_occ": p.n_occ, "n_virt": p.n_virt, "n_w": p.n_w,
         "chi0_prec": prec,
         "l2": "inputs larger than L2 (C alone is %.1f GB per job vs 129 MB L2)" % (p.c_bytes() / 1e9),
@@ -249,7 +254,7 @@ def run_ours(args):
     if prec == "auto":
         prec = "mixed" if rpa_mixed_available() else "fp64"
     pc = rpa.PREC_MIXED if prec == "mixed" else rpa.PREC_FP64
-    p = workload(args.n_q)
+    p = workload(args.n_q, args.workload)
     t_gen = time.perf_counter()
     tens = rpa.upload_problem(p, "cuda:%d" % local)
     torch.cuda.synchronize()
@@ -312,7 +317,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "bf16-slices->f64",
             "data": "synthetic (seeded, shapes of the paper's periodic workloads; no public data)",
-            "config": config_of(p, prec, args.n_q),
+            "config": config_of(p, prec, args.n_q, args.workload),
             "chi0_tflops": chi0_flops_job * world * args.steps / (ms_max / 1e3) / 1e12,
             "chi0_tflops_kernel": achieved, "Ec": res["Ec"], "gpu_launches": launches,
             "kernel_ms_per_step": kernel_ms, "roofline": roof, "clocks": clk, "input_gen_s": t_gen}
@@ -704,7 +709,7 @@ def main():
     elif args.workload == "serving":
         run_serving(args)
     else:
-        run_ours(args)
+        run_ours(args)  # periodic2d (default) or slab
 
 
 if __name__ == "__main__":

@@ -27,16 +27,15 @@
 // and add them into float-float (hi, lo) register accumulators.
 //
 // Tile: 128 rows P x 64 complex columns Q (128 x 128 for real data), K-blocks
-// of 16 real values; operands arrive by TMA (4-D tensor maps over the slice
-// buffers [g*s + slice][X][row][k] of A and [slice][X|Y][row][k] of C, 32-byte
-// swizzle), one elected thread issues
+// of 16 real values; operands arrive by bulk copies of pre-blocked digit
+// planes (one contiguous 16 KB run per operand and K-block, no-swizzle
+// core-matrix layout), one elected thread issues
 // tcgen05.mma, eight epilogue warps drain TMEM with tcgen05.ld.  The K range of
 // each tile is split over CTAs (split-K); a reduction kernel adds the partials
 // in a fixed order, applies the exponents and writes chi0 in FP64 (lower
 // triangle + Hermitian mirror), so results are deterministic.  Every wait is
 // bounded (globaltimer); on a time-out the kernel raises an error flag, lets
 // its copies land, waits for its MMAs and frees TMEM.
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -50,7 +49,6 @@
 namespace rpa {
 namespace {
 
-constexpr int TILE_M = 128;         // rows P per tile
 constexpr int KB = 16;              // real K per K-block (= MMA K for BF16)
 constexpr int CHUNK = 1024;         // complex t per exact accumulation (real: 2048 t)
 constexpr int STAGES = 6;
@@ -118,27 +116,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
     }
   }
 }
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
-                                            int c2, int c3) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
-      "%6}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-      : "memory");
+// Contiguous global -> shared copy completing on an mbarrier (addresses 16-byte
+// aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor (K-major, 32-byte swizzle): start >> 4,
-// LBO = 16 B (unused for this layout), SBO = 256 B between 8-row groups,
-// descriptor version 1, swizzle mode 6 (32 B).
+// Shared-memory matrix descriptor, K-major without swizzle: start >> 4,
+// LBO = 128 B between K-adjacent core matrices, SBO = 256 B between 8-row
+// groups, descriptor version 1, swizzle mode 0.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)(16 >> 4) << 16;
+  d |= (uint64_t)(128 >> 4) << 16;
   d |= (uint64_t)(256 >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)6 << 61;
   return d;
 }
 // Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, K-major A and B,
@@ -156,16 +153,6 @@ __device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   uint32_t r[8];
@@ -250,37 +237,51 @@ struct SliceArgs {
   const int* eC;         // [Npad] exponent of c_fix
   const unsigned long long* wx;  // [n_k][n_w][n_ov] weights (mantissa | exponent << 32), null: weight 1
   const int* eA;         // [n_w][Npad] row exponents of A
-  uint16_t* S;           // [(g*s + slice)][xy][Npad][Kr]
+  uint16_t* S;           // digit planes, blocked (see store_planes)
 };
 
 // One thread per (row, 16 real values); it loops over the G frequencies of the
 // launch (the 16 fixed-point values of C are loaded once).  With wm == null
 // the digits of C itself are written (X and, for complex data, Y = (im, -re)).
-__device__ __forceinline__ void store_planes(const SliceArgs& a, int g, int P, int tg, const uint32_t (&px)[MAX_S][8],
+// Digit planes are stored in the order the tensor-core kernel consumes them,
+// so that one stage of operand data is a single contiguous 16 KB copy:
+//   weighted A: [g][I = P/128][kb][plane][m-core 16][k-core 2][8 rows][8 values]
+//   C (B side): [J][kb][plane][n-core 16][k-core 2][8 rows][8 values]
+// with J = P/64 for complex data (n-cores 0-7: X rows, 8-15: Y rows) and
+// J = P/128 for real data.  A 4 KB plane block is the no-swizzle K-major
+// core-matrix layout of a 128 x 16 BF16 operand tile (core matrix = 8 rows x
+// 16 bytes, K-adjacent cores 128 B apart, row-adjacent cores 256 B apart).
+__device__ __forceinline__ void store_core_rows(uint16_t* block, int row, const uint32_t (&v)[8]) {
+  uint4* d0 = reinterpret_cast<uint4*>(block + (((row >> 3) * 2 + 0) * 8 + (row & 7)) * 8);
+  uint4* d1 = reinterpret_cast<uint4*>(block + (((row >> 3) * 2 + 1) * 8 + (row & 7)) * 8);
+  *d0 = make_uint4(v[0], v[1], v[2], v[3]);
+  *d1 = make_uint4(v[4], v[5], v[6], v[7]);
+}
+
+__device__ __forceinline__ void store_planes(const SliceArgs& a, int P, int kb, const uint32_t (&px)[MAX_S][8],
                                              const uint32_t (&py)[MAX_S][8]) {
+  const long n_kb = a.Kr / 16;
+  const int J = a.nxy == 2 ? (P >> 6) : (P >> 7);
+  const int nrow = a.nxy == 2 ? (P & 63) : (P & 127);
 #pragma unroll
   for (int i = 0; i < MAX_S; ++i) {
     if (i >= a.s) break;
-    uint4* dx = reinterpret_cast<uint4*>(a.S + ((((long)g * a.s + i) * a.nxy + 0) * a.Npad + P) * a.Kr + tg * 16);
-    dx[0] = make_uint4(px[i][0], px[i][1], px[i][2], px[i][3]);
-    dx[1] = make_uint4(px[i][4], px[i][5], px[i][6], px[i][7]);
-    if (a.nxy == 2) {
-      uint4* dy = reinterpret_cast<uint4*>(a.S + ((((long)g * a.s + i) * a.nxy + 1) * a.Npad + P) * a.Kr + tg * 16);
-      dy[0] = make_uint4(py[i][0], py[i][1], py[i][2], py[i][3]);
-      dy[1] = make_uint4(py[i][4], py[i][5], py[i][6], py[i][7]);
-    }
+    uint16_t* blk = a.S + (((long)J * n_kb + kb) * a.s + i) * 2048;
+    store_core_rows(blk, nrow, px[i]);
+    if (a.nxy == 2) store_core_rows(blk, 64 + nrow, py[i]);
   }
 }
 
 // X planes only (the weighted operand A has no Y part).
-__device__ __forceinline__ void store_planes_x(const SliceArgs& a, int g, int P, int tg,
+__device__ __forceinline__ void store_planes_x(const SliceArgs& a, int g, int P, int kb,
                                                const uint32_t (&px)[MAX_S][8]) {
+  const long n_kb = a.Kr / 16;
+  const long nI = a.Npad / 128;
 #pragma unroll
   for (int i = 0; i < MAX_S; ++i) {
     if (i >= a.s) break;
-    uint4* dx = reinterpret_cast<uint4*>(a.S + (((long)g * a.s + i) * a.Npad + P) * a.Kr + tg * 16);
-    dx[0] = make_uint4(px[i][0], px[i][1], px[i][2], px[i][3]);
-    dx[1] = make_uint4(px[i][4], px[i][5], px[i][6], px[i][7]);
+    uint16_t* blk = a.S + ((((long)g * nI + (P >> 7)) * n_kb + kb) * a.s + i) * 2048;
+    store_core_rows(blk, P & 127, px[i]);
   }
 }
 __device__ __forceinline__ void digits_to_x(int F, int u, int s, uint32_t (&px)[MAX_S][8]) {
@@ -318,9 +319,11 @@ __global__ void __launch_bounds__(256) slice_kernel(SliceArgs a) {
   const long total = (long)a.Npad * ngroups;
   constexpr bool with_y = CPLX;
   constexpr int tpg = CPLX ? 8 : 16;  // t per group of 16 real values
+  // consecutive threads take consecutive rows of one K-block: coalesced
+  // stores into the blocked layout, shared weight loads
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int tg = (int)(idx % ngroups);
-    const int P = (int)(idx / ngroups);
+    const int P = (int)(idx % a.Npad);
+    const int tg = (int)(idx / a.Npad);
     const int4* src = reinterpret_cast<const int4*>(a.cfix + (long)P * a.Kr + tg * 16);
     int cv[16];
 #pragma unroll
@@ -339,7 +342,7 @@ __global__ void __launch_bounds__(256) slice_kernel(SliceArgs a) {
         for (int u = 0; u < 8; ++u) px[i][u] = py[i][u] = 0;
 #pragma unroll
       for (int u = 0; u < 16; ++u) digits_to_planes(cv[u], u, a.s, with_y, px, py);
-      store_planes(a, 0, P, tg, px, py);
+      store_planes(a, P, tg, px, py);
       continue;
     } else {
     // the group's t = t0 .. t0 + tpg - 1 as (k-point j, pair tt): one division
@@ -473,18 +476,19 @@ __global__ void __launch_bounds__(256) wtab_kernel(long n, const double* dtab, u
 
 // ---------------------------------------------------------- GEMM kernel ----
 // One persistent launch covers several "segments": a segment is one q of one
-// job with G frequencies, its own operand tensor maps and partial buffer.  The
-// segment table travels in the kernel parameters (tensor maps as grid
-// constants), so a launch needs no device-side table and records cleanly into
-// a CUDA graph.
+// job with G frequencies, its own operand buffers and partial buffer.  The
+// segment table travels in the kernel parameters, so a launch needs no
+// device-side table and records cleanly into a CUDA graph.  Operand data
+// arrives by plain bulk copies (cp.async.bulk): the digit planes are stored
+// pre-blocked, one contiguous 16 KB run per operand and K-block.
 
-constexpr int MAX_SEGS = 40;
+constexpr int MAX_SEGS = 96;
 
 struct TcSeg {
-  CUtensorMap mapA;  // A: [G*s planes][1][Npad][Kr]
-  CUtensorMap mapB;  // B: [s planes][nxy][Npad][Kr]
-  float* part;       // [item][2 (hi, lo)][128 rows][128 cols]
-  int cplx, G, n_tiles, n_ksplit, kb_per_split, n_kb, item0, pad;
+  const uint16_t* A;  // weighted digit planes, [g][I][kb][plane][4 KB block]
+  const uint16_t* B;  // digit planes of C, [J][kb][plane][4 KB block]
+  float* part;        // [item][2 (hi, lo)][128 rows][128 cols]
+  int cplx, G, n_tiles, n_ksplit, kb_per_split, n_kb, item0, nI;
 };
 
 struct TcParams {
@@ -628,8 +632,9 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
           uint8_t* sb = sa + MAX_S * PLANE_BYTES;
           mbar_expect_tx(&full[stage], stage_tx);
           // A: X slices of rows I*128.. ; B: [X; Y] slices of columns J*64.. (real: X of J*128..)
-          tma_load_4d(sa, &SG.mapA, &full[stage], kb * KB, it.I * TILE_M, 0, it.g * S);
-          tma_load_4d(sb, &SG.mapB, &full[stage], kb * KB, it.J * (SG.cplx ? 64 : 128), 0, 0);
+          bulk_load(sa, SG.A + (((size_t)it.g * SG.nI + it.I) * SG.n_kb + kb) * (S * 2048), S * PLANE_BYTES,
+                    &full[stage]);
+          bulk_load(sb, SG.B + ((size_t)it.J * SG.n_kb + kb) * (S * 2048), S * PLANE_BYTES, &full[stage]);
           armed[stage] = (int)phase;
           if (++stage == STAGES) {
             stage = 0;
@@ -804,24 +809,6 @@ __global__ void err_merge_kernel(const int* err, int* status) {
 
 // ------------------------------------------------------------ host side --
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn get_encode() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  });
-  return fn;
-}
-
 int num_sms() {
   static int n = 0;
   if (!n) {
@@ -872,18 +859,6 @@ MixedLayout mixed_layout(const BatchGeom& g, int s, int sms, size_t slice_cap) {
   L.cfix = al(sizeof(int) * (size_t)L.Npad * L.Kr);
   L.total = L.slices + L.slicesC + L.erow + L.erowC + L.part + L.wm + L.ew + L.cfix;
   return L;
-}
-
-// 4-D map over [planes][nxy][Npad][Kr] BF16 with a box of {16, brows, bxy, s}
-bool encode_map(EncodeTiledFn enc, CUtensorMap* m, void* base, const MixedLayout& L, int s, int brows, int bxy,
-                int nxy, int planes) {
-  cuuint64_t dims[4] = {(cuuint64_t)L.Kr, (cuuint64_t)L.Npad, (cuuint64_t)nxy, (cuuint64_t)planes};
-  cuuint64_t strides[3] = {(cuuint64_t)L.Kr * 2, (cuuint64_t)L.Kr * 2 * L.Npad, (cuuint64_t)L.Kr * 2 * L.Npad * nxy};
-  cuuint32_t box[4] = {(cuuint32_t)KB, (cuuint32_t)brows, (cuuint32_t)bxy, (cuuint32_t)s};
-  cuuint32_t estr[4] = {1, 1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 void fill_pairs(TcParams& tp, int s) {
@@ -1021,7 +996,7 @@ size_t slice_cap_of(const MixedQ& q) { return q.slice_cap ? q.slice_cap : ((size
 
 }  // namespace
 
-bool mixed_supported() { return get_encode() != nullptr; }
+bool mixed_supported() { return true; }
 
 size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices, size_t slice_cap) {
   return 1024 + mixed_layout(g, n_slices, num_sms(), slice_cap).total;
@@ -1057,8 +1032,6 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
   };
   if (n <= 0) return cudaSuccess;
   if (s < 2 || s > MAX_S) return cudaErrorInvalidValue;
-  EncodeTiledFn enc = get_encode();
-  if (!enc) return cudaErrorNotSupported;
   const int sms = num_sms();
   const size_t smem = STAGES * STAGE_BYTES + 1024 + 256;  // stages, alignment pad, barriers
   {
@@ -1197,9 +1170,9 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
         const int nks = pl.nks[k];
         const int cps = (q.L.n_chunks + nks - 1) / nks;
         TcSeg& S = tp.seg[tp.n_segs++];
-        if (!encode_map(enc, &S.mapA, q.S, q.L, s, 128, 1, 1, q.L.G * s) ||
-            !encode_map(enc, &S.mapB, q.SC, q.L, s, g.cplx ? 64 : 128, q.L.nxy, q.L.nxy, s))
-          return false;
+        S.A = q.S;
+        S.B = q.SC;
+        S.nI = q.L.Npad / 128;
         S.part = q.part;
         S.cplx = g.cplx;
         S.G = Gs[k];

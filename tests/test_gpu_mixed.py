@@ -130,3 +130,37 @@ def test_mixed_deterministic_and_slice_count(rpa):
             errs[s] = abs(a["Ec"] - ref["Ec"])
     assert errs[4] < errs[3] < errs[2]
     assert errs[4] <= TOL_EC
+
+
+@pytest.mark.slow
+def test_slab_dual_grid_full_size_subset(rpa):
+    """The slab dual-grid workload at full size (N_aux=768, 32 occ, 480 virt,
+    36 k per q, 16 freq) on two of its q-points, the first regular one and the
+    first near-Gamma one (the dual grid's displaced point, whose V has the
+    scaled leading eigenvalue): split-precision chi0 against the FP64 path per
+    (q, w) and on their weighted energy, and the FP64 path against the oracle
+    on one sampled term."""
+    from paper_2505_06021_gb300 import shard
+
+    p = synth.config2()
+    qs = [0, 8]
+    t = rpa.upload_problem(p, qs=qs)
+    g = p.grid
+    sel = [q * p.n_k + j for q in qs for j in range(p.n_k)]
+    jf = rpa.Job(is_complex=True, n_aux=p.n_aux, n_occ=p.n_occ, n_virt=p.n_virt,
+                 pair_k=g.pair_k[qs].reshape(-1), pair_kq=g.pair_kq[qs].reshape(-1), w_q=g.w_q[qs],
+                 zeta_k=g.zeta_k, omega=p.omega, zeta_w=p.zeta_w, eps_occ=t["eps_occ"], eps_virt=t["eps_virt"],
+                 C=t["C"], V=t["V"])
+    assert len(sel) == len(t["C"])
+    jm = jf.with_prec(rpa.PREC_MIXED)
+    with rpa.Context(0) as c:
+        rf = c.energy(jf)
+        rm = c.energy(jm)
+    del t
+    torch.cuda.empty_cache()
+    rel = np.abs(rm["eps"] - rf["eps"]) / np.abs(rf["eps"])
+    assert rel.max() <= 1e-8, rel.max()
+    assert abs(rm["Ec"] - rf["Ec"]) <= TOL_EC
+    ref = oracle.term(p, 8, 8)
+    assert abs(rf["eps"][1, 8] - ref["eps"]) <= 1e-10 * abs(ref["eps"])
+    assert shard.quadrature(rf["eps"], g.w_q[qs], p.zeta_w) == pytest.approx(rf["Ec"], rel=1e-12)
