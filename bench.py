@@ -583,6 +583,7 @@ def run_serving(args):
     on the device as each job arrives; mixed-precision chi0; admission by HBM
     footprint under the cap.  The arrival rate is a fraction of the capacity
     measured first with a closed-loop burst."""
+    os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
     import numpy as np
     import torch
 
@@ -614,6 +615,7 @@ def run_serving(args):
         ctx.wait(t, 600.0)
     cap_jobs_s = len(burst) / (time.perf_counter() - t0)
     del made, tk
+    ctx.close()
     torch.cuda.empty_cache()
     rate = args.serve_load * cap_jobs_s
     # open loop: arrivals at `rate`, inputs made on the device as each job arrives
@@ -628,6 +630,8 @@ def run_serving(args):
     clocks.start()
     t_start = time.perf_counter()
 
+    failed = []
+
     def producer():
         for i, (ta, p) in enumerate(stream):
             if not fits[i]:
@@ -637,9 +641,12 @@ def run_serving(args):
             dt = t_arr - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            tens, job = make(i, p)
-            with lock:
-                live[ctx2.submit(job)] = (i, tens, job)
+            try:
+                tens, job = make(i, p)
+                with lock:
+                    live[ctx2.submit(job)] = (i, tens, job)
+            except Exception as ex:  # recorded in the JSON line, the stream goes on
+                failed.append((i, repr(ex)[:200]))
 
     th = threading.Thread(target=producer)
     th.start()
@@ -665,7 +672,6 @@ def run_serving(args):
     peak = ctx2.serving_peak()
     launches = ctx2.launches
     ctx2.close()
-    ctx.close()
     n_done = len(results)
     line = {"metric": METRIC, "value": n_done / makespan, "unit": "jobs/s", "n_gpus": world, "steps": n_done,
             "warmup": len(burst), "ms_per_step": 1e3 * makespan / max(n_done, 1), "higher_is_better": True,
@@ -677,6 +683,7 @@ def run_serving(args):
                                    "footprint under a %.0f GB cap" % (len(stream), args.serve_load,
                                                                        args.serve_cap_gb),
                        "arrival_rate_jobs_s": rate, "capacity_jobs_s": cap_jobs_s, "rejected_over_cap": len(rejected),
+                       "failed_to_submit": len(failed), "failures": failed[:3],
                        "l2": "inputs larger than L2", "parallelism": "one serving context per GPU"},
             "latency_s": {"p50": st["lat_p50_s"], "p99": st["lat_p99_s"], "mean": st["lat_mean_s"]},
             "queue_wait_s": {"p50": st["wait_p50_s"], "p99": st["wait_p99_s"]},

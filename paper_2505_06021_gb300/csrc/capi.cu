@@ -255,6 +255,10 @@ int choose_qb(const rpa_job* j, int n_slices, size_t cap) {
   return qb;
 }
 
+size_t job_workspace(const rpa_job* j, int n_slices, size_t ws_cap) {
+  return plan_layout(j, choose_qb(j, n_slices, ws_cap), n_slices, ws_cap, true).total;
+}
+
 size_t job_footprint(const rpa_job* j, int n_slices, size_t ws_cap) {
   Layout L = plan_layout(j, choose_qb(j, n_slices, ws_cap), n_slices, ws_cap, true);
   size_t in = 0;

@@ -189,21 +189,6 @@ __device__ __forceinline__ void ff_add4(float& hi, float& lo, float g0, float g1
 // each biased byte b is turned into the BF16 of (b - 128) 2^(-8i) by the
 // exact float trick (2^23 + b) 2^(-8i) - (2^23 + 128) 2^(-8i) (one FFMA, no I2F).
 
-__device__ __forceinline__ uint32_t bf16_digit(uint32_t byte, int lvl) {
-  const float scale = __int_as_float((127 - 8 * lvl) << 23);
-  const float f = fmaf(__uint_as_float(0x4B000000u | byte), scale, -8388736.0f * scale);
-  return __float_as_uint(f) >> 16;
-}
-
-// Biased digit bytes of F: b[0] = d0 + 128, b[i] = d_i + 128.
-__device__ __forceinline__ void digit_bytes(int F, uint32_t b[4]) {
-  const uint32_t G = (uint32_t)(F + 0x808080);
-  b[0] = ((G ^ 0x80000000u) >> 24);
-  b[1] = (G >> 16) & 0xFFu;
-  b[2] = (G >> 8) & 0xFFu;
-  b[3] = G & 0xFFu;
-}
-
 // c_fix of one q: [Npad][Kr] int32, zero outside the data; eC per row.
 __global__ void __launch_bounds__(256) cfix_kernel(int cplx, int N, int Npad, int n_ov, int n_k, int Ktot, int Kr,
                                                    const double* const* C, const int* eC, int* cfix) {
@@ -284,40 +269,47 @@ __device__ __forceinline__ void store_planes_x(const SliceArgs& a, int g, int P,
     store_core_rows(blk, P & 127, px[i]);
   }
 }
-__device__ __forceinline__ void digits_to_x(int F, int u, int s, uint32_t (&px)[MAX_S][8]) {
-  uint32_t b[4];
-  digit_bytes(F, b);
-#pragma unroll
-  for (int i = 0; i < MAX_S; ++i) {
-    if (i >= s) break;
-    const uint32_t h = bf16_digit(b[i], i);
-    px[i][u >> 1] |= (u & 1) ? (h << 16) : h;
-  }
+
+
+// BF16 digit i of a biased word G' = (F + 0x808080) ^ 2^31 (byte 3 - i holds
+// d_i + 128) as FP32 bits: one byte permute builds 2^23 + b, one FFMA scales
+// and removes the bias exactly.
+template <int I>
+__device__ __forceinline__ uint32_t digit_f(uint32_t Gp) {
+  const uint32_t bits = __byte_perm(Gp, 0x4B000000u, 0x7540u | (3 - I));
+  const float scale = __int_as_float((127 - 8 * I) << 23);
+  return __float_as_uint(fmaf(__uint_as_float(bits), scale, -8388736.0f * scale));
+}
+__device__ __forceinline__ uint32_t biased(int F) { return (uint32_t)(F + 0x808080) ^ 0x80000000u; }
+
+// X digit planes of two consecutive K values (F0 low half, F1 high half).
+__device__ __forceinline__ void pair_x(int F0, int F1, int up, int s, uint32_t (&px)[MAX_S][8]) {
+  const uint32_t G0 = biased(F0), G1 = biased(F1);
+  px[0][up] = __byte_perm(digit_f<0>(G0), digit_f<0>(G1), 0x7632);
+  px[1][up] = __byte_perm(digit_f<1>(G0), digit_f<1>(G1), 0x7632);
+  if (s > 2) px[2][up] = __byte_perm(digit_f<2>(G0), digit_f<2>(G1), 0x7632);
+  if (s > 3) px[3][up] = __byte_perm(digit_f<3>(G0), digit_f<3>(G1), 0x7632);
+}
+// X = (re, im) and Y = (im, -re) digit planes of one complex value.
+template <int I>
+__device__ __forceinline__ void cplx_xy(uint32_t Gre, uint32_t Gim, uint32_t& x, uint32_t& y) {
+  const uint32_t fr = digit_f<I>(Gre), fi = digit_f<I>(Gim);
+  x = __byte_perm(fr, fi, 0x7632);
+  y = __byte_perm(fi, fr ^ 0x80000000u, 0x7632);
 }
 
-__device__ __forceinline__ void digits_to_planes(int F, int u, int s, bool with_y, uint32_t (&px)[MAX_S][8],
-                                                 uint32_t (&py)[MAX_S][8]) {
-  uint32_t b[4];
-  digit_bytes(F, b);
-#pragma unroll
-  for (int i = 0; i < MAX_S; ++i) {
-    if (i >= s) break;
-    const uint32_t h = bf16_digit(b[i], i);
-    px[i][u >> 1] |= (u & 1) ? (h << 16) : h;
-    if (with_y) {  // Y[2k] = im_k, Y[2k+1] = -re_k
-      if (u & 1)
-        py[i][u >> 1] |= h;
-      else
-        py[i][u >> 1] |= (h ^ 0x8000u) << 16;
-    }
-  }
+// F = round(c w 2^-sh) for |c w| < 2^61; sh >= 1 by construction of the row
+// exponents (|F| <= 2^30); sh is clamped to 62, where the result is 0 anyway.
+__device__ __forceinline__ int round_shift(int c, long long wm, int sh) {
+  sh = min(max(sh, 1), 62);
+  const long long pr = (long long)c * wm;
+  return (int)((pr + (1ll << (sh - 1))) >> sh);
 }
 
 template <bool CPLX, bool WEIGHTED>
 __global__ void __launch_bounds__(256) slice_kernel(SliceArgs a) {
   const long ngroups = (long)a.Kr / 16;
   const long total = (long)a.Npad * ngroups;
-  constexpr bool with_y = CPLX;
   constexpr int tpg = CPLX ? 8 : 16;  // t per group of 16 real values
   // consecutive threads take consecutive rows of one K-block: coalesced
   // stores into the blocked layout, shared weight loads
@@ -337,48 +329,53 @@ __global__ void __launch_bounds__(256) slice_kernel(SliceArgs a) {
     if constexpr (!WEIGHTED) {
       uint32_t px[MAX_S][8], py[MAX_S][8];
 #pragma unroll
-      for (int i = 0; i < MAX_S; ++i)
-#pragma unroll
-        for (int u = 0; u < 8; ++u) px[i][u] = py[i][u] = 0;
-#pragma unroll
-      for (int u = 0; u < 16; ++u) digits_to_planes(cv[u], u, a.s, with_y, px, py);
+      for (int v = 0; v < 8; ++v) {
+        if constexpr (CPLX) {
+          const uint32_t Gr = biased(cv[2 * v]), Gi = biased(cv[2 * v + 1]);
+          cplx_xy<0>(Gr, Gi, px[0][v], py[0][v]);
+          cplx_xy<1>(Gr, Gi, px[1][v], py[1][v]);
+          cplx_xy<2>(Gr, Gi, px[2][v], py[2][v]);
+          cplx_xy<3>(Gr, Gi, px[3][v], py[3][v]);
+        } else {
+          pair_x(cv[2 * v], cv[2 * v + 1], v, a.s, px);
+        }
+      }
       store_planes(a, P, tg, px, py);
       continue;
     } else {
-    // the group's t = t0 .. t0 + tpg - 1 as (k-point j, pair tt): one division
-    // per group, then steps
-    const int t0 = tg * tpg;
-    const int j0 = t0 / a.n_ov, tt0 = t0 - j0 * a.n_ov;
-    const int eC = a.eC[P];
-    for (int g = 0; g < a.G; ++g) {
-      const int w = a.w0 + g;
-      const int shbase = 30 + a.eA[(long)w * a.Npad + P] - eC;
-      uint32_t px[MAX_S][8];
+      // the group's t = t0 .. t0 + tpg - 1 as (k-point j, pair tt): one
+      // division per group, then steps
+      const int t0 = tg * tpg;
+      const int j0 = t0 / a.n_ov, tt0 = t0 - j0 * a.n_ov;
+      const int eC = a.eC[P];
+      for (int g = 0; g < a.G; ++g) {
+        const int w = a.w0 + g;
+        const int shbase = 30 + a.eA[(long)w * a.Npad + P] - eC;
+        uint32_t px[MAX_S][8];
+        int j = j0, tt = tt0;
+        long long wm_prev = 0;
+        int sh_prev = 0;
 #pragma unroll
-      for (int i = 0; i < MAX_S; ++i)
-#pragma unroll
-        for (int u = 0; u < 8; ++u) px[i][u] = 0;
-      int j = j0, tt = tt0;
-#pragma unroll
-      for (int v = 0; v < tpg; ++v) {
-        unsigned long long x = 0;
-        if (t0 + v < a.Ktot) x = __ldg(a.wx + ((long)j * a.n_w + w) * a.n_ov + tt);
-        if (++tt == a.n_ov) {
-          tt = 0;
-          ++j;
+        for (int v = 0; v < tpg; ++v) {
+          unsigned long long x = 0;
+          if (t0 + v < a.Ktot) x = __ldg(a.wx + ((long)j * a.n_w + w) * a.n_ov + tt);
+          if (++tt == a.n_ov) {
+            tt = 0;
+            ++j;
+          }
+          const long long wmv = (long long)(uint32_t)x;
+          const int shv = shbase - (int)(uint32_t)(x >> 32);
+          if constexpr (CPLX) {
+            pair_x(round_shift(cv[2 * v], wmv, shv), round_shift(cv[2 * v + 1], wmv, shv), v, a.s, px);
+          } else if ((v & 1) == 0) {
+            wm_prev = wmv;
+            sh_prev = shv;
+          } else {
+            pair_x(round_shift(cv[v - 1], wm_prev, sh_prev), round_shift(cv[v], wmv, shv), v >> 1, a.s, px);
+          }
         }
-        const long long wmv = (long long)(uint32_t)x;
-        const int sh = shbase - (int)(uint32_t)(x >> 32);
-#pragma unroll
-        for (int r = 0; r < (CPLX ? 2 : 1); ++r) {
-          const int u = CPLX ? 2 * v + r : v;
-          const long long pr = (long long)cv[u] * wmv;
-          const int F = (sh > 62) ? 0 : (sh > 0) ? (int)((pr + (1ll << (sh - 1))) >> sh) : (int)(pr << (-sh));
-          digits_to_x(F, u, a.s, px);
-        }
+        store_planes_x(a, g, P, tg, px);
       }
-      store_planes_x(a, g, P, tg, px);
-    }
     }
   }
 }

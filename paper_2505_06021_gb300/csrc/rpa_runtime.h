@@ -127,6 +127,8 @@ struct Bufs {
 void ctx_set_error(rpa_ctx* ctx, const char* fmt, ...);
 rpa_status validate_job(const rpa_job* j, char* msg, size_t len);
 size_t job_footprint(const rpa_job* j, int n_slices, size_t ws_cap);
+// Device workspace a lane needs for the job (part of job_footprint).
+size_t job_workspace(const rpa_job* j, int n_slices, size_t ws_cap);
 // Enqueues the whole hot path of `job` on lane `ex` (no host wait) and records
 // ex.done after the results were copied into ex.hres.
 rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_cap);

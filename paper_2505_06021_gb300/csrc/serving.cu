@@ -1,9 +1,11 @@
 // Serving runtime: continuous batching of RPA energy jobs on one GB300.
 //
 // rpa_submit() deep-copies a job's host descriptors into a pending queue.  A
-// scheduler thread admits pending jobs in arrival order while the sum of the
-// footprints (device-resident inputs + lane workspace) of the running jobs
-// stays under the context's HBM cap and fewer than max_inflight jobs run.  An
+// scheduler thread admits pending jobs in arrival order while the device
+// memory they account for stays under the context's HBM cap: the inputs of the
+// running jobs plus every lane's workspace (lanes keep their workspace between
+// jobs; idle lanes give theirs back when a new job would not fit otherwise),
+// and while fewer than max_inflight jobs run.  An
 // admitted job gets an execution lane of its own (stream, workspace, pinned
 // buffers) and its whole hot path is enqueued there at once, so the kernels of
 // all running jobs share the device; the scheduler polls the lanes' completion
@@ -37,7 +39,8 @@ struct ServeJob {
   std::vector<int> pair_k, pair_kq;
   std::vector<double> w_q, omega, zeta_w;
   std::vector<const void*> C, V;
-  size_t footprint = 0;
+  size_t footprint = 0;  // inputs + workspace
+  size_t ws_need = 0;    // workspace part
   double t_submit = 0, t_admit = 0, t_done = 0;
   int state = 0;  // 0 pending, 1 running, 2 done
   rpa_status status = RPA_OK;
@@ -55,7 +58,8 @@ struct ServeState {
   std::map<uint64_t, std::shared_ptr<ServeJob>> tickets;
   std::vector<std::unique_ptr<Exec>> lanes;
   std::vector<Exec*> free_lanes;
-  size_t used = 0;
+  size_t inputs_used = 0;  // device inputs of the running jobs
+  size_t ws_total = 0;     // workspace held by all lanes
   uint64_t next_ticket = 1;
   bool stop = false;
   std::thread th;
@@ -63,22 +67,57 @@ struct ServeState {
   uint64_t done = 0;
   size_t max_pending = 4096;
   int peak_running = 0;     // most jobs on the device at once
-  size_t peak_used = 0;     // largest admitted footprint sum
+  size_t peak_used = 0;     // largest inputs_used + ws_total
 };
 
-static Exec* get_lane(ServeState* S) {
-  if (!S->free_lanes.empty()) {
-    Exec* e = S->free_lanes.back();
-    S->free_lanes.pop_back();
-    return e;
+static size_t ws_alloc_size(size_t need) { return std::max(need, (size_t)64 << 20); }
+
+// A free lane for a job that needs `need` bytes of workspace: the smallest
+// free lane that already holds enough, else the free lane holding the most
+// (its workspace will be reallocated), else a new lane (nullptr if none could
+// be made).  *extra: growth of the lanes' total workspace if this lane runs
+// the job.
+static Exec* pick_lane(ServeState* S, size_t need, size_t* extra) {
+  int best = -1;
+  for (int i = 0; i < (int)S->free_lanes.size(); ++i) {
+    const size_t b = S->free_lanes[i]->ws_bytes;
+    if (b >= need && (best < 0 || b < S->free_lanes[best]->ws_bytes)) best = i;
   }
-  std::unique_ptr<Exec> e(new Exec());
-  if (!e->init()) {
-    e->destroy();
-    return nullptr;
+  if (best < 0)
+    for (int i = 0; i < (int)S->free_lanes.size(); ++i)
+      if (best < 0 || S->free_lanes[i]->ws_bytes > S->free_lanes[best]->ws_bytes) best = i;
+  Exec* e = nullptr;
+  if (best >= 0) {
+    e = S->free_lanes[best];
+  } else {
+    std::unique_ptr<Exec> n(new Exec());
+    if (!n->init()) {
+      n->destroy();
+      return nullptr;
+    }
+    S->lanes.push_back(std::move(n));
+    e = S->lanes.back().get();
+    S->free_lanes.push_back(e);
   }
-  S->lanes.push_back(std::move(e));
-  return S->lanes.back().get();
+  *extra = e->ws_bytes >= need ? 0 : ws_alloc_size(need) - e->ws_bytes;
+  return e;
+}
+
+// Gives back the workspace of idle lanes other than `keep` until `want` bytes
+// were released or none is left; returns the bytes released.
+static size_t release_idle(ServeState* S, Exec* keep, size_t want) {
+  size_t freed = 0;
+  for (Exec* e : S->free_lanes) {
+    if (freed >= want) break;
+    if (e == keep || !e->ws) continue;
+    cudaStreamSynchronize(e->s);
+    cudaFree(e->ws);
+    freed += e->ws_bytes;
+    S->ws_total -= e->ws_bytes;
+    e->ws = nullptr;
+    e->ws_bytes = 0;
+  }
+  return freed;
 }
 
 static size_t lane_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap / 4, (size_t)24 << 30); }
@@ -92,9 +131,16 @@ static void scheduler(rpa_ctx* ctx) {
     // 1. admit in arrival order while memory and slots allow
     while (!S->pending.empty() && (int)S->running.size() < ctx->max_inflight) {
       std::shared_ptr<ServeJob> j = S->pending.front();
-      if (!S->running.empty() && S->used + j->footprint > ctx->cap) break;
+      size_t extra = 0;
+      Exec* lane = pick_lane(S, j->ws_need, &extra);
+      const size_t inputs = j->footprint - j->ws_need;
+      if (lane) {
+        size_t total = S->inputs_used + inputs + S->ws_total + extra;
+        if (total > ctx->cap) total -= release_idle(S, lane, total - ctx->cap);
+        // the first job always runs (its footprint alone is below the cap)
+        if (total > ctx->cap && !S->running.empty()) break;
+      }
       S->pending.pop_front();
-      Exec* lane = get_lane(S);
       j->t_admit = now_s();
       if (!lane) {
         j->status = RPA_E_CUDA;
@@ -104,12 +150,14 @@ static void scheduler(rpa_ctx* ctx) {
         progress = true;
         continue;
       }
+      S->free_lanes.erase(std::find(S->free_lanes.begin(), S->free_lanes.end(), lane));
       j->lane = lane;
       j->state = 1;
-      S->used += j->footprint;
+      S->inputs_used += inputs;
+      S->ws_total += extra;
       S->running.push_back(j);
       S->peak_running = std::max(S->peak_running, (int)S->running.size());
-      S->peak_used = std::max(S->peak_used, S->used);
+      S->peak_used = std::max(S->peak_used, S->inputs_used + S->ws_total);
       lk.unlock();
       rpa_status st = energy_enqueue(ctx, *lane, &j->job, lane_ws_cap(ctx));
       lk.lock();
@@ -142,7 +190,7 @@ static void scheduler(rpa_ctx* ctx) {
       }
       j->t_done = now_s();
       j->state = 2;
-      S->used -= j->footprint;
+      S->inputs_used -= j->footprint - j->ws_need;
       S->free_lanes.push_back(j->lane);
       j->lane = nullptr;
       S->lat.push_back(j->t_done - j->t_submit);
@@ -223,6 +271,7 @@ rpa_status rpa_submit(rpa_ctx* ctx, const rpa_job* job, uint64_t* ticket) {
   j->job.C = j->C.data();
   j->job.V = j->V.data();
   j->footprint = job_footprint(job, ctx->n_slices, lane_ws_cap(ctx));
+  j->ws_need = job_workspace(job, ctx->n_slices, lane_ws_cap(ctx));
   if (j->footprint > ctx->cap) {
     ctx_set_error(ctx, "job footprint %zu bytes exceeds the HBM cap %zu", j->footprint, ctx->cap);
     return RPA_E_NOMEM;
