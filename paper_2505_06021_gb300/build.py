@@ -31,7 +31,7 @@ def sources():
 
 
 def _deps_mtime():
-    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     files.append(os.path.join(HERE, "..", "include", "rpa.h"))
     return max(os.path.getmtime(f) for f in files)
 

@@ -252,6 +252,9 @@ Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool m
 int choose_qb(const rpa_job* j, int n_slices, size_t cap) {
   int qb = j->n_q;
   while (qb > 1 && plan_layout(j, qb, n_slices, cap, true).total > cap) qb = (qb + 1) / 2;
+  // host-resident inputs: at least four q-batches, so that the copies of one
+  // batch overlap the compute of the previous one
+  if (j->mem == RPA_MEM_HOST) qb = std::min(qb, std::max(1, (j->n_q + 3) / 4));
   return qb;
 }
 
