@@ -53,6 +53,9 @@ struct Group {
   int j0, j1;        // job range
   size_t mixed_off;  // shared mixed workspace of the group's q
   size_t mixed_bytes;
+  size_t task_off;   // device ragged log-det task tables (complex, then real)
+  size_t pin_task;   // their pinned staging
+  int n_task_c, n_task_r;
   size_t bytes;
 };
 
@@ -116,11 +119,10 @@ std::unique_ptr<Plan> make_plan(const rpa_job* jobs, int n, int n_slices, size_t
     const double nq = jobs[i].n_q, nk = jobs[i].n_k, nw = jobs[i].n_w;
     p->work += 8.0 * jobs[i].n_aux * (double)jobs[i].n_aux * jobs[i].n_occ * jobs[i].n_virt * nq * nk * nw;
   }
-  p->pin_bytes = pin;
   // greedy groups in job order under the workspace budget
   int i = 0;
   while (i < n) {
-    Group g{i, i, 0, 0, 0};
+    Group g{i, i, 0, 0, 0, 0, 0, 0, 0};
     size_t fp = 0, mx = 0;
     while (g.j1 < n) {
       const JobPlan& jp = p->jobs[g.j1];
@@ -131,13 +133,20 @@ std::unique_ptr<Plan> make_plan(const rpa_job* jobs, int n, int n_slices, size_t
       mx = m2;
       ++g.j1;
     }
+    for (int k = g.j0; k < g.j1; ++k)
+      if (jobs[k].prec == RPA_PREC_MIXED) (jobs[k].is_complex ? g.n_task_c : g.n_task_r) += jobs[k].n_q * jobs[k].n_w;
+    const size_t tbytes = a1k(sizeof(CholTask) * (size_t)(g.n_task_c + g.n_task_r));
     g.mixed_off = fp;
     g.mixed_bytes = mx ? mx + 1024 : 0;
-    g.bytes = fp + g.mixed_bytes;
+    g.task_off = fp + g.mixed_bytes;
+    g.pin_task = pin;
+    pin += tbytes;
+    g.bytes = g.task_off + tbytes;
     p->ws_bytes = std::max(p->ws_bytes, g.bytes);
     p->groups.push_back(g);
     i = g.j1;
   }
+  p->pin_bytes = pin;
   return p;
 }
 
@@ -258,7 +267,10 @@ static rpa_status enqueue_batch(rpa_ctx* ctx, BatchCache& bc, const Plan& p, con
                                   &nl, s, tune, pex ? &hook : nullptr));
       ctx->launches += nl;
     }
-    // fork: the jobs' tails on the side streams, largest jobs first
+    // fork: per-job tail work on the side streams, largest jobs first.  FP64
+    // jobs run their whole tail (sandwich form) there; mixed jobs only the
+    // V-side work (V = LL^H, ln det V, -V^-1), their log-dets follow as one
+    // ragged launch over all of the group's matrices.
     CKB(cudaEventRecord(bc.fork, s));
     const int nside = std::min(kSide, g.j1 - g.j0);
     for (int k = 0; k < nside; ++k) CKB(cudaStreamWaitEvent(bc.side[k], bc.fork, 0));
@@ -269,11 +281,8 @@ static rpa_status enqueue_batch(rpa_ctx* ctx, BatchCache& bc, const Plan& p, con
       const double wc = (double)jobs[c].n_aux * jobs[c].n_aux * jobs[c].n_aux * jobs[c].n_q * jobs[c].n_w;
       return wa > wc;
     });
-    for (size_t oi = 0; oi < order.size(); ++oi) {
-      const int i = order[oi];
-      cudaStream_t ss = bc.side[oi % nside];
+    auto finish_job = [&](int i, cudaStream_t ss) -> rpa_status {
       const rpa_job& j = jobs[i];
-      if (rpa_status st = stage_tail(ctx, pex, &j, B[i], 0, j.n_q, j.V, ss)) return st;
       prof_begin(ctx, pex, ss);
       CKB(launch_energy_reduce(j.n_q, j.n_w, B[i].parts, B[i].w_q, B[i].zeta_w, B[i].eps, B[i].Ec, ss));
       prof_end(ctx, pex, ss, RPA_K_REDUCE, 1);
@@ -282,11 +291,57 @@ static rpa_status enqueue_batch(rpa_ctx* ctx, BatchCache& bc, const Plan& p, con
       const size_t nqw = (size_t)j.n_q * j.n_w;
       CKB(cudaMemcpyAsync(r + 64, B[i].Ec, sizeof(double) * (3 * nqw + 1), cudaMemcpyDeviceToHost, ss));
       CKB(cudaMemcpyAsync(r, B[i].status, sizeof(int), cudaMemcpyDeviceToHost, ss));
+      return RPA_OK;
+    };
+    for (size_t oi = 0; oi < order.size(); ++oi) {
+      const int i = order[oi];
+      cudaStream_t ss = bc.side[oi % nside];
+      const rpa_job& j = jobs[i];
+      if (j.prec == RPA_PREC_MIXED) {
+        if (rpa_status st = stage_vside(ctx, pex, &j, B[i], 0, j.n_q, j.V, ss)) return st;
+      } else {
+        if (rpa_status st = stage_tail(ctx, pex, &j, B[i], 0, j.n_q, j.V, ss)) return st;
+        if (rpa_status st = finish_job(i, ss)) return st;
+      }
     }
     // join
     for (int k = 0; k < nside; ++k) {
       CKB(cudaEventRecord(bc.join[k], bc.side[k]));
       CKB(cudaStreamWaitEvent(s, bc.join[k], 0));
+    }
+    // ragged log-det of every (job, q, w) matrix of the mixed jobs, largest
+    // matrices first (complex table, then real)
+    if (g.n_task_c + g.n_task_r > 0) {
+      std::vector<CholTask> tc, tr;
+      for (int i = g.j0; i < g.j1; ++i) {
+        const rpa_job& j = jobs[i];
+        if (j.prec != RPA_PREC_MIXED) continue;
+        const size_t es = j.is_complex ? 16 : 8;
+        const size_t NN = (size_t)j.n_aux * j.n_aux * (es / 8);
+        for (int q = 0; q < j.n_q; ++q)
+          for (int w = 0; w < j.n_w; ++w) {
+            const size_t b = (size_t)q * j.n_w + w;
+            CholTask t{B[i].chi + b * NN, B[i].parts + 2 * b, B[i].L + q * NN, B[i].Vc + q * NN, B[i].ldV + q,
+                       B[i].status, j.n_aux, 2, (int)(1 + b), 0};
+            (j.is_complex ? tc : tr).push_back(t);
+          }
+      }
+      auto by_size = [](const CholTask& a, const CholTask& c) { return a.N > c.N; };
+      std::stable_sort(tc.begin(), tc.end(), by_size);
+      std::stable_sort(tr.begin(), tr.end(), by_size);
+      CholTask* hp = reinterpret_cast<CholTask*>(pin + g.pin_task);
+      std::copy(tc.begin(), tc.end(), hp);
+      std::copy(tr.begin(), tr.end(), hp + tc.size());
+      CholTask* dp = reinterpret_cast<CholTask*>(ws + g.task_off);
+      CKB(cudaMemcpyAsync(dp, hp, sizeof(CholTask) * (tc.size() + tr.size()), cudaMemcpyHostToDevice, s));
+      prof_begin(ctx, pex, s);
+      CKB(launch_cholesky_ragged(1, dp, (int)tc.size(), s));
+      CKB(launch_cholesky_ragged(0, dp + tc.size(), (int)tr.size(), s));
+      prof_end(ctx, pex, s, RPA_K_LOGDET, (tc.empty() ? 0 : 1) + (tr.empty() ? 0 : 1));
+      ctx->launches += (tc.empty() ? 0 : 1) + (tr.empty() ? 0 : 1);
+      for (int i = g.j0; i < g.j1; ++i)
+        if (jobs[i].prec == RPA_PREC_MIXED)
+          if (rpa_status st = finish_job(i, s)) return st;
     }
   }
   nk = ctx->launches.load() - l0;

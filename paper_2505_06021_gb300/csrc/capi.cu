@@ -385,8 +385,8 @@ rpa_status stage_dtab(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, 
 
 // The FP64 steps after chi0 for q in [q0, q0+nq), chi0 in b.chi: factor V,
 // sandwich, Cholesky log-det.  V of the batch at Vdev[0..nq).
-rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
-                      const void* const* Vdev, cudaStream_t s) {
+rpa_status stage_vside(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
+                       const void* const* Vdev, cudaStream_t s) {
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
   const long mstride = (long)(NN * (es / 8));
@@ -401,12 +401,23 @@ rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, 
   prof_end(ctx, pex, s, RPA_K_VFACTOR, 1);
   ctx->launches++;
   if (b.Vc) {
-    // inverse form: -V^-1 per q (X = L^-1 in T's storage, then -(X^H X) over L),
-    // then one Cholesky of V^-1 - chi per (q, w); no sandwich
+    // inverse form: -V^-1 per q (X = L^-1 in T's storage, then -(X^H X) over L)
     prof_begin(ctx, pex, s);
     CK(launch_vinv(j->is_complex, j->n_aux, nq, b.L, b.T, b.L, s));
     prof_end(ctx, pex, s, RPA_K_VFACTOR, 2);
     ctx->launches += 2;
+  }
+  return RPA_OK;
+}
+
+rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
+                      const void* const* Vdev, cudaStream_t s) {
+  const size_t es = j->is_complex ? 16 : 8;
+  const size_t NN = (size_t)j->n_aux * j->n_aux;
+  const long mstride = (long)(NN * (es / 8));
+  if (rpa_status st = stage_vside(ctx, pex, j, b, q0, nq, Vdev, s)) return st;
+  if (b.Vc) {
+    // inverse form: one Cholesky of V^-1 - chi per (q, w); no sandwich
     prof_begin(ctx, pex, s);
     CK(launch_cholesky(j->is_complex, j->n_aux, nq * j->n_w, b.chi, mstride, 2, b.parts + (size_t)2 * q0 * j->n_w,
                        b.status, q0 * j->n_w, s, b.L, b.Vc, b.ldV + q0, j->n_w));

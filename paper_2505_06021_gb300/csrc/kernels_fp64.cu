@@ -416,23 +416,20 @@ struct Team {
   }
 };
 
-// Matrix loads bypass L1 in the cluster variant: other CTAs of the cluster
-// write the matrix between the barriers.
+// Matrix loads go to L2 (ld.global.cg): each element is read once per panel
+// step, so L1 gains nothing, and in the cluster variant other CTAs write the
+// matrix between the barriers.
 template <bool C, int CL>
 __device__ __forceinline__ Elem<C> ldm(const double* p, long i) {
-  if constexpr (CL == 1) {
-    return ld_elem<C>(p, i);
+  Elem<C> e;
+  if constexpr (C) {
+    const double2 v = __ldcg(reinterpret_cast<const double2*>(p + 2 * i));
+    e.re = v.x;
+    e.im = v.y;
   } else {
-    Elem<C> e;
-    if constexpr (C) {
-      const double2 v = __ldcg(reinterpret_cast<const double2*>(p + 2 * i));
-      e.re = v.x;
-      e.im = v.y;
-    } else {
-      e.re = __ldcg(p + i);
-    }
-    return e;
+    e.re = __ldcg(p + i);
   }
+  return e;
 }
 
 // Fixed-order sum of the per-thread values `s` over the whole team; the
@@ -470,11 +467,13 @@ __device__ void team_sum(double s, double* red, double* part) {
 //         triangle), factorised; ln det(1 - Pi) = ln det M + ln det V
 //         (ldV[q]) and Tr Pi = Tr(chi V) = sum_PQ Re(chi_PQ conj(V_PQ)) from
 //         the copy Vc of V(q).
+// One matrix A (N x N) in `mode`; out: 1 double (mode 1) or 2 (ln det, Tr);
+// on a non-positive pivot *status becomes `code` (if still 0).  Mode 2 reads
+// Wq = -V^-1 and Vq = V of the matrix's q and ldv = ln det V.
 template <bool C, int CL>
-__global__ void __launch_bounds__(256)
-    cholesky_kernel(int N, double* __restrict__ mats, long bstride, int mode, double* __restrict__ out,
-                    int* __restrict__ status, int status_base, const double* __restrict__ Wn,
-                    const double* __restrict__ Vc, const double* __restrict__ ldV, int n_w) {
+__device__ __forceinline__ void chol_one(int N, double* __restrict__ A, int mode, double* __restrict__ out,
+                                         int* __restrict__ status, int code, const double* __restrict__ Wq,
+                                         const double* __restrict__ Vq, const double* __restrict__ ldv) {
   __shared__ Elem<C> D[CB][CB + 1];
   __shared__ Elem<C> S2[CB][CB + 1];
   Elem<C>(*S1)[CB + 1] = D;  // the diagonal block is free again during the trailing update
@@ -482,9 +481,7 @@ __global__ void __launch_bounds__(256)
   __shared__ double part;
   __shared__ int bad;
   __shared__ double logacc;
-  const int b = blockIdx.x / CL;
   const unsigned rank = Team<CL>::rank();
-  double* A = mats + (long)b * bstride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gtid = (int)rank * 256 + tid;
   constexpr int GSTRIDE = 256 * CL;
@@ -496,8 +493,6 @@ __global__ void __launch_bounds__(256)
     team_sum<CL>(s, red, &part);
   } else if (mode == 2) {
     const long NN = (long)N * N;
-    const double* Wq = Wn + (long)(b / n_w) * NN * (C ? 2 : 1);
-    const double* Vq = Vc + (long)(b / n_w) * NN * (C ? 2 : 1);
     double s = 0.0;
     for (long idx = gtid; idx < NN; idx += GSTRIDE) {
       const int r = (int)(idx / N), c = (int)(idx % N);
@@ -676,14 +671,10 @@ __global__ void __launch_bounds__(256)
   }
   if (failed) {
     if (rank == 0 && tid == 0) {
-      if (status) atomicCAS(status, 0, 1 + status_base + b);
+      if (status) atomicCAS(status, 0, code);
       if (out) {
-        if (mode == 1) {
-          out[b] = nan("");
-        } else {
-          out[2 * b] = nan("");
-          out[2 * b + 1] = nan("");
-        }
+        out[0] = nan("");
+        if (mode != 1) out[1] = nan("");
       }
     }
   } else {
@@ -695,18 +686,40 @@ __global__ void __launch_bounds__(256)
     }
     if (rank == 0 && tid == 0 && out) {
       if (mode == 0) {
-        out[2 * b] = logacc;
-        out[2 * b + 1] = -red[0];
+        out[0] = logacc;
+        out[1] = -red[0];
       } else if (mode == 2) {
-        out[2 * b] = logacc + ldV[b / n_w];
-        out[2 * b + 1] = red[0];
+        out[0] = logacc + *ldv;
+        out[1] = red[0];
       } else {
-        out[b] = logacc;
+        out[0] = logacc;
       }
     }
   }
   // no CTA leaves while another may still read its shared memory
   Team<CL>::sync();
+}
+
+// Batched: matrix b of the launch (team b / CL) at mats + b * bstride.
+template <bool C, int CL>
+__global__ void __launch_bounds__(256)
+    cholesky_kernel(int N, double* __restrict__ mats, long bstride, int mode, double* __restrict__ out,
+                    int* __restrict__ status, int status_base, const double* __restrict__ Wn,
+                    const double* __restrict__ Vc, const double* __restrict__ ldV, int n_w) {
+  const int b = blockIdx.x / CL;
+  const long q = mode == 2 ? b / n_w : 0;
+  const long NN = (long)N * N * (C ? 2 : 1);
+  chol_one<C, CL>(N, mats + (long)b * bstride, mode, out ? out + (mode == 1 ? b : 2 * b) : nullptr, status,
+                  1 + status_base + b, mode == 2 ? Wn + q * NN : nullptr, mode == 2 ? Vc + q * NN : nullptr,
+                  mode == 2 ? ldV + q : nullptr);
+}
+
+// Ragged: one CTA per task, matrices of any size (tasks ordered largest
+// first by the caller, so the block scheduler packs them greedily).
+template <bool C>
+__global__ void __launch_bounds__(256) cholesky_ragged_kernel(const CholTask* __restrict__ tasks) {
+  const CholTask t = tasks[blockIdx.x];
+  chol_one<C, 1>(t.N, t.A, t.mode, t.out, t.status, t.code, t.W, t.Vc, t.ldv);
 }
 
 // X = L^-1 for lower-triangular L (real positive diagonal), one CTA per
@@ -890,6 +903,15 @@ cudaError_t launch_cholesky(int cplx, int N, int n_mat, double* mats, long bstri
   return team ? launch_chol_t<false, CL_BIG>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV,
                                              n_w)
               : launch_chol_t<false, 1>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
+}
+
+cudaError_t launch_cholesky_ragged(int cplx, const CholTask* tasks, int n_tasks, cudaStream_t s) {
+  if (n_tasks <= 0) return cudaSuccess;
+  if (cplx)
+    cholesky_ragged_kernel<true><<<n_tasks, 256, 0, s>>>(tasks);
+  else
+    cholesky_ragged_kernel<false><<<n_tasks, 256, 0, s>>>(tasks);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_vinv(int cplx, int N, int n_q, const double* L, double* X, double* Wn, cudaStream_t s) {

@@ -47,6 +47,19 @@ cudaError_t launch_cholesky(int cplx, int N, int n_mat, double* mats, long bstri
                             int* status, int status_base, cudaStream_t s, const double* Wn = nullptr,
                             const double* Vc = nullptr, const double* ldV = nullptr, int n_w = 0);
 
+// One matrix of a ragged Cholesky launch (matrices of different sizes).
+struct CholTask {
+  double* A;          // N x N, factorised in place
+  double* out;        // mode 1: 1 double, modes 0 and 2: (ln det, Tr)
+  const double* W;    // mode 2: -V^-1 of the matrix's q (lower triangle)
+  const double* Vc;   // mode 2: V of the q
+  const double* ldv;  // mode 2: ln det V of the q
+  int* status;        // set to `code` on a non-positive pivot (if still 0)
+  int N, mode, code, pad;
+};
+// Tasks in device memory, one CTA each; `cplx` selects complex128 or float64.
+cudaError_t launch_cholesky_ragged(int cplx, const CholTask* tasks, int n_tasks, cudaStream_t s);
+
 // Wn[q] = -V(q)^-1 (lower triangle) from the Cholesky factors L[q]: X = L^-1
 // by block forward substitution into X[q], then -(X^H X).
 cudaError_t launch_vinv(int cplx, int N, int n_q, const double* L, double* X, double* Wn, cudaStream_t s);

@@ -152,6 +152,10 @@ void fill_tables_host(const rpa_job* j, const void* const* Cdev, char* h);
 rpa_status enqueue_table_copies(rpa_ctx* ctx, const rpa_job* j, const Bufs& b, const char* h, cudaStream_t s);
 rpa_status stage_dtab(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
                       const double* eps_occ, const double* eps_virt, cudaStream_t s);
+// V-side work of the tail: V copies, V = LL^H (and, for the inverse form,
+// ln det V and -V^-1).
+rpa_status stage_vside(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
+                       const void* const* Vdev, cudaStream_t s);
 rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
                       const void* const* Vdev, cudaStream_t s);
 rpa_status decode_status(rpa_ctx* ctx, int st, int n_w);
