@@ -1,7 +1,7 @@
 // Batched execution of many independent, uneven jobs in one call
 // (rpa_energy_batch).
 //
-// The jobs are cut into groups whose workspace fits a budget.  Per group, on
+// The jobs are cut into groups whose workspace fits the context's HBM cap.  Per group, on
 // the context's stream:
 //   1. every job's small tables are copied in from pinned host memory and its
 //      d_t(omega) table is built for all of its q;
@@ -386,7 +386,7 @@ extern "C" rpa_status rpa_energy_batch(rpa_ctx* ctx, const rpa_job* jobs, int n_
   const bool known = bc.plan && bc.plan->exec && bc.plan->sig == sig;
   const bool replay = known && !ctx->prof;
   if (!known) {
-    bc.plan = make_plan(jobs, n_jobs, ctx->n_slices, std::min<size_t>(ctx->cap / 2, (size_t)48 << 30));
+    bc.plan = make_plan(jobs, n_jobs, ctx->n_slices, ctx->cap);
     bc.plan->sig = sig;
   }
   Plan& p = *bc.plan;
