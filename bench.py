@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--slices", type=int, default=0, help="BF16 digit slices of the mixed path (2-4; 0: library default)")
     ap.add_argument("--n-q", type=int, default=0, help="profiling only: restrict the job to its first n q-points")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -260,7 +261,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     job = rpa.job_from_problem(p, tens, prec=pc)
-    ctx = rpa.Context(local)
+    ctx = rpa.Context(local, n_slices=args.slices)
     for _ in range(args.warmup):
         ctx.energy(job)
     ext = torch.cuda.ExternalStream(ctx.stream_handle)
@@ -306,7 +307,7 @@ def run_ours(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        tensor_flops = rpa_mixed_tensor_flops(p, ctx)
+        tensor_flops = rpa_mixed_tensor_flops(p, ctx, args.slices or 4)
         ach_t = tensor_flops * args.steps / max(chi_n, 1) / (chi_launch_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": ach_t, "peak": peak, "unit": "TFLOP/s", "frac": ach_t / peak,
                 "traffic": traffic_for("chi0_mixed") if args.workload == "periodic2d" else None,
@@ -319,7 +320,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "bf16-slices->f64",
             "data": "synthetic (seeded, shapes of the paper's periodic workloads; no public data)",
-            "config": config_of(p, prec, args.n_q, args.workload),
+            "config": dict(config_of(p, prec, args.n_q, args.workload),
+                           **({"chi0_slices": args.slices or 4} if prec == "mixed" else {})),
             "chi0_tflops": chi0_flops_job * world * args.steps / (ms_max / 1e3) / 1e12,
             "chi0_tflops_kernel": achieved, "Ec": res["Ec"], "gpu_launches": launches,
             "kernel_ms_per_step": kernel_ms, "roofline": roof, "clocks": clk, "input_gen_s": t_gen}
@@ -415,7 +417,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     jobs = [rpa.job_from_problem(p, t, prec=pc) for p, t in zip(probs, tens)]
-    ctx = rpa.Context(local)
+    ctx = rpa.Context(local, n_slices=args.slices)
     t_first = time.perf_counter()
     E_first = ctx.energy_batch(jobs)  # eager + autotune + graph capture
     t_first = time.perf_counter() - t_first
@@ -451,7 +453,7 @@ def run_batch(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     if prec == "mixed":
-        tf = tensor_flops_of(probs)
+        tf = tensor_flops_of(probs, args.slices or 4)
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         ach = tf / (chi_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
@@ -469,7 +471,7 @@ def run_batch(args):
             "config": {"workload": "batch-uneven: %d independent Gamma-real / 2x2x1-complex instances, N_aux ~ "
                                    "U[128,1024], N_occ ~ U[8,64], N_virt = 4-15 x N_occ, 16 frequencies each; "
                                    "one rpa_energy_batch call per step (CUDA graph replay)" % n,
-                       "n_inst": n, "chi0_prec": prec, "c_gb": sum(p.c_bytes() for p in probs) / 1e9,
+                       "n_inst": n, "chi0_prec": prec, "chi0_slices": args.slices or 4, "c_gb": sum(p.c_bytes() for p in probs) / 1e9,
                        "l2": "inputs larger than L2", "parallelism": "one batch per GPU (weak scaling)"},
             "chi0_tflops": alg * world * args.steps / (ms / 1e3) / 1e12, "gpu_launches": launches,
             "kernel_ms_per_step": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
@@ -606,7 +608,7 @@ def run_serving(args):
         gen_stream.synchronize()
         return t, rpa.job_from_problem(p, t, prec=pc)
 
-    ctx = rpa.Context(local, hbm_cap_bytes=cap)
+    ctx = rpa.Context(local, hbm_cap_bytes=cap, n_slices=args.slices)
     fits = [footprint_of(rpa, p, pc) <= cap for _, p in stream]
     # capacity: closed-loop burst of every fourth admissible job of the stream
     # (the same size mix; also the warm-up)
@@ -624,7 +626,7 @@ def run_serving(args):
     # open loop: arrivals at `rate`, inputs made on the device as each job arrives
     import threading
 
-    ctx2 = rpa.Context(local, hbm_cap_bytes=cap)
+    ctx2 = rpa.Context(local, hbm_cap_bytes=cap, n_slices=args.slices)
     lock = threading.Lock()
     live = {}
     done_t = {}
@@ -685,6 +687,7 @@ def run_serving(args):
                                    "n ~ U{1..4}; arrival rate %.2f x measured capacity; admission by HBM "
                                    "footprint under a %.0f GB cap" % (len(stream), args.serve_load,
                                                                        args.serve_cap_gb),
+                       "chi0_slices": args.slices or 4,
                        "arrival_rate_jobs_s": rate, "capacity_jobs_s": cap_jobs_s, "rejected_over_cap": len(rejected),
                        "failed_to_submit": len(failed), "failures": failed[:3],
                        "l2": "inputs larger than L2", "parallelism": "one serving context per GPU"},
