@@ -610,16 +610,20 @@ def run_serving(args):
 
     ctx = rpa.Context(local, hbm_cap_bytes=cap, n_slices=args.slices)
     fits = [footprint_of(rpa, p, pc) <= cap for _, p in stream]
-    # capacity: closed-loop burst of every fourth admissible job of the stream
-    # (the same size mix; also the warm-up)
+    # capacity: closed loop over every fourth admissible job of the stream (the
+    # same size mix; also the warm-up), at most 8 jobs' inputs on the device
     burst = [i for i in range(len(stream)) if fits[i]][::4]
-    made = [make(i, stream[i][1]) for i in burst]
     t0 = time.perf_counter()
-    tk = [ctx.submit(j) for _, j in made]
-    for t in tk:
+    window = []
+    for i in burst:
+        tens_i, job_i = make(i, stream[i][1])
+        window.append((ctx.submit(job_i), tens_i, job_i))
+        if len(window) >= 8:
+            ctx.wait(window.pop(0)[0], 600.0)
+    for t, _, _ in window:
         ctx.wait(t, 600.0)
     cap_jobs_s = len(burst) / (time.perf_counter() - t0)
-    del made, tk
+    del window
     ctx.close()
     torch.cuda.empty_cache()
     rate = args.serve_load * cap_jobs_s

@@ -150,6 +150,13 @@ static void scheduler(rpa_ctx* ctx) {
         progress = true;
         continue;
       }
+      // memory the caller holds outside the cap (its own tensors) can leave
+      // the device short: give back idle workspace before this lane grows
+      if (extra > 0) {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && free_b < extra + ((size_t)1 << 30))
+          release_idle(S, lane, extra + ((size_t)1 << 30) - free_b);
+      }
       S->free_lanes.erase(std::find(S->free_lanes.begin(), S->free_lanes.end(), lane));
       j->lane = lane;
       j->state = 1;
