@@ -610,20 +610,24 @@ def run_serving(args):
 
     ctx = rpa.Context(local, hbm_cap_bytes=cap, n_slices=args.slices)
     fits = [footprint_of(rpa, p, pc) <= cap for _, p in stream]
-    # capacity: closed loop over every fourth admissible job of the stream (the
-    # same size mix; also the warm-up), at most 8 jobs' inputs on the device
-    burst = [i for i in range(len(stream)) if fits[i]][::4]
+    # capacity: a saturated burst of a stride sample of the stream (the same
+    # size mix), inputs made beforehand (at most ~60 GB of them), all submitted
+    # at once; first submit to last completion.  Also the warm-up.
+    adm = [i for i in range(len(stream)) if fits[i]]
+    stride = 2
+    while True:
+        burst = adm[::stride]
+        if sum(stream[i][1].c_bytes() for i in burst) <= 60e9 or stride >= len(adm):
+            break
+        stride += 1
+    made = [make(i, stream[i][1]) for i in burst]
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    window = []
-    for i in burst:
-        tens_i, job_i = make(i, stream[i][1])
-        window.append((ctx.submit(job_i), tens_i, job_i))
-        if len(window) >= 8:
-            ctx.wait(window.pop(0)[0], 600.0)
-    for t, _, _ in window:
+    tk = [ctx.submit(j) for _, j in made]
+    for t in tk:
         ctx.wait(t, 600.0)
     cap_jobs_s = len(burst) / (time.perf_counter() - t0)
-    del window
+    del made, tk
     ctx.close()
     torch.cuda.empty_cache()
     rate = args.serve_load * cap_jobs_s
@@ -692,7 +696,9 @@ def run_serving(args):
                                    "footprint under a %.0f GB cap" % (len(stream), args.serve_load,
                                                                        args.serve_cap_gb),
                        "chi0_slices": args.slices or 4,
-                       "arrival_rate_jobs_s": rate, "capacity_jobs_s": cap_jobs_s, "rejected_over_cap": len(rejected),
+                       "arrival_rate_jobs_s": rate, "capacity_jobs_s": cap_jobs_s,
+                       "capacity_sample": "every %d-th admissible job (%d jobs), inputs made beforehand, submitted at "
+                                          "once" % (stride, len(burst)), "rejected_over_cap": len(rejected),
                        "failed_to_submit": len(failed), "failures": failed[:3],
                        "l2": "inputs larger than L2", "parallelism": "one serving context per GPU"},
             "latency_s": {"p50": st["lat_p50_s"], "p99": st["lat_p99_s"], "mean": st["lat_mean_s"]},

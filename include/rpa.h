@@ -173,6 +173,14 @@ rpa_status rpa_serving_stats(rpa_ctx *ctx, uint64_t *jobs_done, double *lat_mean
  * under the HBM cap.  Either pointer may be NULL. */
 rpa_status rpa_serving_peak(rpa_ctx *ctx, int *max_running, size_t *max_bytes);
 
+/* Test hook for the failure path of the tensor-core chi0 kernel: the next
+ * split-precision launch in this process leaves the operand copies of work
+ * item `item` (and the producer's later ones) unissued, so the MMA thread's
+ * bounded wait on that K-block runs out after its 2 s limit; the kernel raises
+ * its error flag, drains, frees its tensor memory and returns, and the call
+ * reports RPA_E_TIMEOUT.  The context stays usable.  No effect unless called. */
+rpa_status rpa_test_drop_copy(rpa_ctx *ctx, int item);
+
 /* Number of kernels this context has launched so far (all entry points). */
 uint64_t rpa_kernel_launches(const rpa_ctx *ctx);
 

@@ -26,8 +26,8 @@ STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "NOMEM", 3: "CUDA", 4: "NOTPD", 5: "TIME
 # Entry points declared in include/rpa.h
 EXPORTS = ("rpa_create", "rpa_destroy", "rpa_last_error", "rpa_job_validate", "rpa_job_footprint", "rpa_chi0",
            "rpa_logdet", "rpa_energy", "rpa_energy_batch", "rpa_submit", "rpa_poll", "rpa_wait",
-           "rpa_serving_stats", "rpa_serving_peak", "rpa_kernel_launches", "rpa_stream", "rpa_profile", "rpa_profile_read",
-           "rpa_logdet_noalloc", "rpa_noalloc_last_error")
+           "rpa_serving_stats", "rpa_serving_peak", "rpa_test_drop_copy", "rpa_kernel_launches", "rpa_stream",
+           "rpa_profile", "rpa_profile_read", "rpa_logdet_noalloc", "rpa_noalloc_last_error")
 
 # kernel classes of rpa_profile_read
 KERNEL_CLASSES = ("dtab", "chi0", "vfactor", "sandwich", "logdet", "reduce", "slice", "chi0_reduce")
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "rpa_wait": (I, [P, u64, D, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "rpa_serving_stats": (I, [P, ctypes.POINTER(u64)] + [ctypes.POINTER(D)] * 5),
         "rpa_serving_peak": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_size_t)]),
+        "rpa_test_drop_copy": (I, [P, I]),
         "rpa_kernel_launches": (u64, [P]),
         "rpa_stream": (P, [P]),
         "rpa_profile": (I, [P, I]),
@@ -352,6 +353,11 @@ class Context:
         self._check(self.lib.rpa_serving_stats(self.h, ctypes.byref(n), *[ctypes.byref(x) for x in v]))
         return {"jobs_done": int(n.value), "lat_mean_s": v[0].value, "lat_p50_s": v[1].value,
                 "lat_p99_s": v[2].value, "wait_p50_s": v[3].value, "wait_p99_s": v[4].value}
+
+    def test_drop_copy(self, item: int) -> None:
+        """Test hook: the next split-precision chi0 launch leaves work item
+        `item`'s operand copies unissued; the call then reports a time-out."""
+        self._check(self.lib.rpa_test_drop_copy(self.h, int(item)))
 
     def serving_peak(self) -> Dict[str, int]:
         r = ctypes.c_int()

@@ -794,6 +794,12 @@ rpa_status rpa_logdet(rpa_ctx* ctx, const rpa_job* job, int q, const void* chi, 
   return RPA_OK;
 }
 
+rpa_status rpa_test_drop_copy(rpa_ctx* ctx, int item) {
+  if (!ctx || item < 0) return RPA_E_INVAL;
+  mixed_test_drop_arm(item);
+  return RPA_OK;
+}
+
 rpa_status rpa_energy(rpa_ctx* ctx, const rpa_job* job, double* Ec, double* eps_qw, double* parts) {
   if (!ctx || !Ec) return RPA_E_INVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);

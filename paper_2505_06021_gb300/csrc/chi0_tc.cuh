@@ -169,6 +169,8 @@ struct TcSeg {
 
 struct TcParams {
   int n_segs, n_items, s, kb_per_chunk;
+  int drop_item;  // test hook: the first K-block of this work item is never
+                  // loaded (-1: off), so one bounded wait runs out
   int* err;
   int pair_i[16], pair_j[16], pair_grp[16], n_pairs;
   int grp_mask;  // accumulator groups that receive MMAs
@@ -306,6 +308,10 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
           if (!ok) break;
           uint8_t* sa = smem + stage * STAGE_BYTES;
           uint8_t* sb = sa + MAX_S * PLANE_BYTES;
+          if (item == p.drop_item && kb == it.kb0) {  // nothing more issued: the MMA thread's wait runs out
+            ok = false;
+            break;
+          }
           mbar_expect_tx(&full[stage], stage_tx);
           // A: X slices of rows I*128.. ; B: [X; Y] slices of columns J*64.. (real: X of J*128..)
           bulk_load(sa, SG.A + (((size_t)it.g * SG.nI + it.I) * SG.n_kb + kb) * (S * 2048), S * PLANE_BYTES,

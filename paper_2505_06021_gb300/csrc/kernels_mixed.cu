@@ -35,6 +35,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -584,6 +585,12 @@ size_t slice_cap_of(const MixedQ& q) { return q.slice_cap ? q.slice_cap : ((size
 
 bool mixed_supported() { return true; }
 
+// Test hook (rpa_test_drop_copy): the next tensor-core launch in this process
+// leaves the first K-block of one work item unloaded.
+static std::atomic<int> g_drop_item{-1};
+void mixed_test_drop_arm(int item) { g_drop_item.store(item); }
+int mixed_test_drop_take() { return g_drop_item.exchange(-1); }
+
 size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices, size_t slice_cap) {
   return 1024 + mixed_layout(g, n_slices, num_sms(), slice_cap).total;
 }
@@ -744,6 +751,7 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
       memset(&rp, 0, sizeof rp);
       tp.s = s;
       tp.kb_per_chunk = KB_PER_CHUNK;
+      tp.drop_item = mixed_test_drop_take();
       tp.err = err;
       fill_pairs(tp, s);
       items = 0;

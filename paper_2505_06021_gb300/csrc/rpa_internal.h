@@ -111,6 +111,9 @@ size_t mixed_multi_workspace_bytes(const MixedQ* qs, int n, int n_slices);
 int autotune_lookup(uint64_t key);
 void autotune_record(uint64_t key, int value);
 bool mixed_supported();
+// Test hook: arm a dropped operand copy for the next tensor-core launch.
+void mixed_test_drop_arm(int item);
+int mixed_test_drop_take();
 // Tensor-core flops the split-precision chi0 of one q executes (slice pairs
 // x padded tiles x padded K).
 uint64_t mixed_tensor_flops(const BatchGeom& g, int n_slices);

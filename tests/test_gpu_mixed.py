@@ -164,3 +164,24 @@ def test_slab_dual_grid_full_size_subset(rpa):
     ref = oracle.term(p, 8, 8)
     assert abs(rf["eps"][1, 8] - ref["eps"]) <= 1e-10 * abs(ref["eps"])
     assert shard.quadrature(rf["eps"], g.w_q[qs], p.zeta_w) == pytest.approx(rf["Ec"], rel=1e-12)
+
+
+def test_tensor_core_wait_runs_out_and_context_recovers(rpa):
+    """Failure path without a GPU fault: one work item's operand copies are
+    never issued, the MMA thread's bounded wait (2 s) runs out, the kernel
+    raises its flag, drains and frees tensor memory, the call reports a
+    time-out, and the same context then computes the right energy."""
+    import time
+
+    p = synth.make_problem("m", is_complex=True, n_aux=96, n_occ=3, n_virt=10, grid=synth.regular_kq_grid((2, 1, 1)),
+                           n_w=3, seed=46)
+    job = rpa.job_from_problem(p, rpa.upload_problem(p), prec=rpa.PREC_MIXED)
+    with rpa.Context(0) as c:
+        good = c.energy(job)["Ec"]
+        c.test_drop_copy(0)
+        t0 = time.perf_counter()
+        with pytest.raises(rpa.RpaError) as e:
+            c.energy(job)
+        assert e.value.status == rpa.RPA_E_TIMEOUT
+        assert time.perf_counter() - t0 < 60.0
+        assert c.energy(job)["Ec"] == good
