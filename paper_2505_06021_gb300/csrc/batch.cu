@@ -368,7 +368,7 @@ extern "C" rpa_status rpa_energy_batch(rpa_ctx* ctx, const rpa_job* jobs, int n_
       return RPA_E_INVAL;
     }
     if (jobs[i].prec == RPA_PREC_MIXED && !mixed_supported()) {
-      ctx_set_error(ctx, "mixed-precision chi0 not available in this build");
+      ctx_set_error(ctx, "mixed-precision chi0 not supported by this library");
       return RPA_E_INVAL;
     }
   }

@@ -504,7 +504,7 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
     return RPA_E_INVAL;
   }
   if (job->prec == RPA_PREC_MIXED && !mixed_supported()) {
-    ctx_set_error(ctx, "mixed-precision chi0 not available in this build");
+    ctx_set_error(ctx, "mixed-precision chi0 not supported by this library");
     return RPA_E_INVAL;
   }
   CK(cudaSetDevice(ctx->device));
@@ -710,7 +710,7 @@ rpa_status rpa_chi0(rpa_ctx* ctx, const rpa_job* job, int q, void* chi_out, void
     return RPA_E_INVAL;
   }
   if (job->prec == RPA_PREC_MIXED && !mixed_supported()) {
-    ctx_set_error(ctx, "mixed-precision chi0 not available in this build");
+    ctx_set_error(ctx, "mixed-precision chi0 not supported by this library");
     return RPA_E_INVAL;
   }
   CK(cudaSetDevice(ctx->device));
