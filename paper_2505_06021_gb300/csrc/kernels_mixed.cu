@@ -172,7 +172,7 @@ __device__ __forceinline__ int round_shift(int c, long long wm, int sh) {
 }
 
 template <bool CPLX, bool WEIGHTED>
-__global__ void __launch_bounds__(256, 3) slice_kernel(SliceArgs a) {
+__global__ void __launch_bounds__(256, 2) slice_kernel(SliceArgs a) {
   const long ngroups = (long)a.Kr / 16;
   const long total = (long)a.Npad * ngroups;
   constexpr int tpg = CPLX ? 8 : 16;  // t per group of 16 real values
@@ -213,21 +213,39 @@ __global__ void __launch_bounds__(256, 3) slice_kernel(SliceArgs a) {
       const int t0 = tg * tpg;
       const int j0 = t0 / a.n_ov, tt0 = t0 - j0 * a.n_ov;
       const int eC = a.eC[P];
-      for (int g = 0; g < a.G; ++g) {
-        const int w = a.w0 + g;
-        const int shbase = 30 + a.eA[(long)w * a.Npad + P] - eC;
-        uint32_t px[MAX_S][8];
+      // (k-point, pair) offsets of the group's t, frequency-independent
+      long off[tpg];
+      {
         int j = j0, tt = tt0;
-        long long wm_prev = 0;
-        int sh_prev = 0;
 #pragma unroll
         for (int v = 0; v < tpg; ++v) {
-          unsigned long long x = 0;
-          if (t0 + v < a.Ktot) x = __ldg(a.wx + ((long)j * a.n_w + w) * a.n_ov + tt);
+          off[v] = (t0 + v < a.Ktot) ? ((long)j * a.n_w) * a.n_ov + tt : -1;
           if (++tt == a.n_ov) {
             tt = 0;
             ++j;
           }
+        }
+      }
+      unsigned long long xw[tpg];
+#pragma unroll
+      for (int v = 0; v < tpg; ++v) xw[v] = off[v] >= 0 ? __ldg(a.wx + off[v] + (long)a.w0 * a.n_ov) : 0ull;
+      int eAw = a.eA[(long)a.w0 * a.Npad + P];
+      for (int g = 0; g < a.G; ++g) {
+        const int w = a.w0 + g;
+        const int shbase = 30 + eAw - eC;
+        // next frequency's weights and row exponent, in flight during this one
+        unsigned long long xn[tpg];
+        const bool more = g + 1 < a.G;
+#pragma unroll
+        for (int v = 0; v < tpg; ++v)
+          xn[v] = (more && off[v] >= 0) ? __ldg(a.wx + off[v] + (long)(w + 1) * a.n_ov) : 0ull;
+        const int eAn = more ? a.eA[(long)(w + 1) * a.Npad + P] : 0;
+        uint32_t px[MAX_S][8];
+        long long wm_prev = 0;
+        int sh_prev = 0;
+#pragma unroll
+        for (int v = 0; v < tpg; ++v) {
+          const unsigned long long x = xw[v];
           const long long wmv = (long long)(uint32_t)x;
           const int shv = shbase - (int)(uint32_t)(x >> 32);
           if constexpr (CPLX) {
@@ -240,6 +258,9 @@ __global__ void __launch_bounds__(256, 3) slice_kernel(SliceArgs a) {
           }
         }
         store_planes_x(a, g, P, tg, px);
+#pragma unroll
+        for (int v = 0; v < tpg; ++v) xw[v] = xn[v];
+        eAw = eAn;
       }
     }
   }
