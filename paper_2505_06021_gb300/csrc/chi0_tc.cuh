@@ -172,8 +172,7 @@ struct TcParams {
   int drop_item;  // test hook: the first K-block of this work item is never
                   // loaded (-1: off), so one bounded wait runs out
   int* err;
-  int pair_i[16], pair_j[16], pair_grp[16], n_pairs;
-  int grp_mask;  // accumulator groups that receive MMAs
+  int grp_mask;  // accumulator groups that receive MMAs (the host's copy of PairTable<s>::mask)
   TcSeg seg[MAX_SEGS];
 };
 static_assert(sizeof(TcParams) <= 32000, "kernel parameter block too large");

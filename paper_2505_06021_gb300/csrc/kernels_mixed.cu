@@ -469,25 +469,17 @@ MixedLayout mixed_layout(const BatchGeom& g, int s, int sms, size_t slice_cap) {
   return L;
 }
 
-void fill_pairs(TcParams& tp, int s) {
-  int np = 0;
-  for (int lvl = 0; lvl < s; ++lvl)
-    for (int i = 0; i <= lvl; ++i) {
-      tp.pair_i[np] = i;
-      tp.pair_j[np] = lvl - i;
-      tp.pair_grp[np] = std::min(lvl, NGROUPS - 1);
-      ++np;
-    }
-  if (s % 2 == 0) {  // (s/2, s/2): the largest term of the dropped level
-    tp.pair_i[np] = s / 2;
-    tp.pair_j[np] = s / 2;
-    tp.pair_grp[np] = std::min(s, NGROUPS - 1);
-    ++np;
-  }
-  tp.n_pairs = np;
-  tp.grp_mask = 0;
-  for (int i = 0; i < np; ++i) tp.grp_mask |= 1 << tp.pair_grp[i];
+// Accumulator groups used by s slices: levels 0 .. s-1, plus level s for the
+// (s/2, s/2) pair of even s, capped at the last group (PairTable's rule).
+constexpr int group_mask(int s) {
+  int m = 0;
+  for (int lvl = 0; lvl < s; ++lvl) m |= 1 << (lvl < NGROUPS - 1 ? lvl : NGROUPS - 1);
+  if (s % 2 == 0) m |= 1 << (s < NGROUPS - 1 ? s : NGROUPS - 1);
+  return m;
 }
+static_assert(group_mask(2) == PairTable<2>{}.mask && group_mask(3) == PairTable<3>{}.mask &&
+                  group_mask(4) == PairTable<4>{}.mask,
+              "host and kernel pair tables disagree");
 
 // ---------------------------------------------------- split-K planning ----
 // A launch's segments get their split-K depth from one common target item
@@ -774,7 +766,7 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
       tp.kb_per_chunk = KB_PER_CHUNK;
       tp.drop_item = mixed_test_drop_take();
       tp.err = err;
-      fill_pairs(tp, s);
+      tp.grp_mask = group_mask(s);
       items = 0;
       blocks = 0;
       for (int oi = 0; oi < (int)who.size(); ++oi) {
