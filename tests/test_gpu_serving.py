@@ -80,3 +80,33 @@ def test_poll_not_ready_then_done(rpa):
         assert np.isfinite(Ec) and Ec < 0.0
         with pytest.raises(rpa.RpaError):
             c.poll(t)  # a ticket is retired once its result was read
+
+
+def test_failed_job_does_not_disturb_the_others(rpa):
+    """A job whose V(q) is indefinite fails alone (RPA_E_NOTPD with its q) while
+    the jobs around it in the stream complete with their solo results."""
+    jobs = _jobs(rpa, n=5, seed=94)
+    with rpa.Context(0) as c:
+        alone = [c.energy(j)["Ec"] for j in jobs]
+    p = synth.make_problem("bad", is_complex=True, n_aux=48, n_occ=2, n_virt=5, grid=synth.regular_kq_grid((2, 1, 1)),
+                           n_w=4, seed=95)
+    t = rpa.upload_problem(p)
+    Vbad = t["V"][1].clone()
+    Vbad[2, 2] = -40.0
+    t["V"] = [t["V"][0], Vbad]
+    bad = rpa.job_from_problem(p, t, prec=rpa.PREC_MIXED)
+    with rpa.Context(0, max_inflight=8) as c:
+        tickets = [c.submit(j) for j in jobs[:2]] + [c.submit(bad)] + [c.submit(j) for j in jobs[2:]]
+        results = []
+        for k, tk in enumerate(tickets):
+            if k == 2:
+                with pytest.raises(rpa.RpaError) as e:
+                    c.wait(tk, 300.0)
+                assert e.value.status == rpa.RPA_E_NOTPD and "V(q=1)" in str(e.value)
+            else:
+                results.append(c.wait(tk, 300.0)[0])
+    for j, a, s in zip(jobs, alone, results):
+        if j.s.prec == rpa.PREC_FP64:
+            assert s == a
+        else:
+            assert abs(s - a) <= TOL_MIX
