@@ -701,6 +701,7 @@ def run_serving(args):
             "latency_s": {"p50": st["lat_p50_s"], "p99": st["lat_p99_s"], "mean": st["lat_mean_s"]},
             "queue_wait_s": {"p50": st["wait_p50_s"], "p99": st["wait_p99_s"]},
             "peak_running_jobs": peak["max_running"], "peak_admitted_gb": peak["max_bytes"] / 1e9,
+            "largest_micro_batch": peak["max_batch"],
             "gpu_launches": launches, "clocks": clk, "roofline": None, "e2e": None}
     if rank == 0:
         print(json.dumps(line), flush=True)

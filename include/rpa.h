@@ -169,9 +169,10 @@ rpa_status rpa_serving_stats(rpa_ctx *ctx, uint64_t *jobs_done, double *lat_mean
                              double *lat_p99, double *wait_p50, double *wait_p99);
 
 /* Serving high-water marks since creation: the most jobs running on the
- * device at once and the largest sum of their footprints (bytes) admitted
- * under the HBM cap.  Either pointer may be NULL. */
-rpa_status rpa_serving_peak(rpa_ctx *ctx, int *max_running, size_t *max_bytes);
+ * device at once, the largest sum of their footprints (bytes) admitted under
+ * the HBM cap, and the most jobs admitted together as one micro-batch (their
+ * (q, omega) work shares launches).  Any pointer may be NULL. */
+rpa_status rpa_serving_peak(rpa_ctx *ctx, int *max_running, size_t *max_bytes, int *max_batch);
 
 /* Test hook for the failure path of the tensor-core chi0 kernel: the next
  * split-precision launch in this process leaves the operand copies of work

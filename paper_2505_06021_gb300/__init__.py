@@ -83,7 +83,7 @@ def load_library(path: str = LIB_PATH):
         "rpa_poll": (I, [P, u64, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "rpa_wait": (I, [P, u64, D, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "rpa_serving_stats": (I, [P, ctypes.POINTER(u64)] + [ctypes.POINTER(D)] * 5),
-        "rpa_serving_peak": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_size_t)]),
+        "rpa_serving_peak": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(I)]),
         "rpa_test_drop_copy": (I, [P, I]),
         "rpa_kernel_launches": (u64, [P]),
         "rpa_stream": (P, [P]),
@@ -362,5 +362,6 @@ class Context:
     def serving_peak(self) -> Dict[str, int]:
         r = ctypes.c_int()
         b = ctypes.c_size_t()
-        self._check(self.lib.rpa_serving_peak(self.h, ctypes.byref(r), ctypes.byref(b)))
-        return {"max_running": int(r.value), "max_bytes": int(b.value)}
+        m = ctypes.c_int()
+        self._check(self.lib.rpa_serving_peak(self.h, ctypes.byref(r), ctypes.byref(b), ctypes.byref(m)))
+        return {"max_running": int(r.value), "max_bytes": int(b.value), "max_batch": int(m.value)}

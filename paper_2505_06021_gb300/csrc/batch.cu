@@ -23,6 +23,7 @@
 #include <memory>
 #include <vector>
 
+#include "batch_internal.h"
 #include "rpa_internal.h"
 #include "rpa_runtime.h"
 
@@ -40,37 +41,6 @@ namespace rpa {
 namespace {
 
 constexpr size_t kBatchSliceCap = (size_t)4 << 30;  // digit planes of one q's weighted operand
-
-struct JobPlan {
-  Layout L;        // whole job in one q-batch, without the chi0 mixed region
-  size_t ws_off;   // within the group's region
-  size_t tab_off;  // pinned tables
-  size_t res_off;  // pinned results: [status | pad to 64 | Ec | eps | parts]
-  size_t mixed;    // mixed-path workspace of all its q
-};
-
-struct Group {
-  int j0, j1;        // job range
-  size_t mixed_off;  // shared mixed workspace of the group's q
-  size_t mixed_bytes;
-  size_t task_off;   // device ragged log-det task tables (complex, then real)
-  size_t pin_task;   // their pinned staging
-  int n_task_c, n_task_r;
-  size_t bytes;
-};
-
-struct Plan {
-  std::vector<uint64_t> sig;
-  std::vector<JobPlan> jobs;
-  std::vector<Group> groups;
-  size_t ws_bytes = 0, pin_bytes = 0;
-  cudaGraphExec_t exec = nullptr;
-  uint64_t kernels = 0;  // kernels per replay
-  double work = 0.0;     // chi0 flops, for the wait limit
-  ~Plan() {
-    if (exec) cudaGraphExecDestroy(exec);
-  }
-};
 
 BatchGeom geom_q(const rpa_job& j) {
   return BatchGeom{j.is_complex, j.n_aux, j.n_occ, j.n_virt, j.n_occ * j.n_virt, j.n_k, j.n_w, 1};
@@ -100,7 +70,9 @@ std::vector<uint64_t> signature(const rpa_job* jobs, int n, int n_slices) {
   return s;
 }
 
-std::unique_ptr<Plan> make_plan(const rpa_job* jobs, int n, int n_slices, size_t budget) {
+}  // namespace
+
+std::unique_ptr<Plan> batch_plan(const rpa_job* jobs, int n, int n_slices, size_t budget) {
   std::unique_ptr<Plan> p(new Plan);
   p->jobs.resize(n);
   size_t pin = 0;
@@ -150,53 +122,45 @@ std::unique_ptr<Plan> make_plan(const rpa_job* jobs, int n, int n_slices, size_t
   return p;
 }
 
-}  // namespace
+bool SideStreams::init() {
+  if (ok) return true;
+  for (int k = 0; k < kSide; ++k) {
+    if (cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming) != cudaSuccess) return false;
+  }
+  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return false;
+  ok = true;
+  return true;
+}
+
+void SideStreams::release() {
+  for (int k = 0; k < kSide; ++k) {
+    if (side[k]) {
+      cudaStreamSynchronize(side[k]);
+      cudaStreamDestroy(side[k]);
+    }
+    if (join[k]) cudaEventDestroy(join[k]);
+    side[k] = nullptr;
+    join[k] = nullptr;
+  }
+  if (fork) cudaEventDestroy(fork);
+  fork = nullptr;
+  ok = false;
+}
 
 // The batch runs on the context's own stream (rpa_stream) with a workspace
 // and pinned buffers of its own, kept between calls for graph replay.
-// The FP64 tails of a group's jobs are independent and each is small (a few
-// matrices per kernel), so they run on side streams, forked from and joined
-// back into the context's stream (a parallel branch per side stream in the
-// captured graph).
-constexpr int kSide = 8;
-
 struct BatchCache {
   Exec mem;  // workspace only (no streams)
   HostStage pin;
   std::unique_ptr<Plan> plan;
-  cudaStream_t side[kSide] = {};
-  cudaEvent_t fork = nullptr, join[kSide] = {};
-  bool side_ok = false;
-  bool init_side() {
-    if (side_ok) return true;
-    for (int k = 0; k < kSide; ++k) {
-      if (cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking) != cudaSuccess) return false;
-      if (cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming) != cudaSuccess) return false;
-    }
-    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return false;
-    side_ok = true;
-    return true;
-  }
-  void release_side() {
-    for (int k = 0; k < kSide; ++k) {
-      if (side[k]) {
-        cudaStreamSynchronize(side[k]);
-        cudaStreamDestroy(side[k]);
-      }
-      if (join[k]) cudaEventDestroy(join[k]);
-      side[k] = nullptr;
-      join[k] = nullptr;
-    }
-    if (fork) cudaEventDestroy(fork);
-    fork = nullptr;
-    side_ok = false;
-  }
+  SideStreams side;
 };
 
 void batch_release(rpa_ctx* ctx) {
   if (!ctx->batch) return;
   if (ctx->ex.s) cudaStreamSynchronize(ctx->ex.s);
-  ctx->batch->release_side();
+  ctx->batch->side.release();
   ctx->batch->plan.reset();
   ctx->batch->pin.release();
   ctx->batch->mem.destroy();
@@ -206,15 +170,15 @@ void batch_release(rpa_ctx* ctx) {
 
 // Fills the pinned tables of every job (read by the upload copies when they
 // execute).
-static void fill_tables(const Plan& p, const rpa_job* jobs, int n, char* pin) {
+void batch_fill_tables(const Plan& p, const rpa_job* jobs, int n, char* pin) {
   for (int i = 0; i < n; ++i) fill_tables_host(&jobs[i], jobs[i].C, pin + p.jobs[i].tab_off);
 }
 
 // Enqueues the whole batch on `s` (pinned tables already filled); *n_kernels
 // gets the number of kernels enqueued.  pex (profiling lane, may be null)
 // receives per-kernel-class timing marks; never set under stream capture.
-static rpa_status enqueue_batch(rpa_ctx* ctx, BatchCache& bc, const Plan& p, const rpa_job* jobs, char* ws,
-                                char* pin, cudaStream_t s, bool tune, uint64_t* n_kernels, Exec* pex) {
+rpa_status batch_enqueue(rpa_ctx* ctx, SideStreams& bc, const Plan& p, const rpa_job* jobs, char* ws, char* pin,
+                         cudaStream_t s, bool tune, uint64_t* n_kernels, Exec* pex) {
   uint64_t nk = 0;
   struct HookCtx {
     rpa_ctx* ctx;
@@ -272,7 +236,7 @@ static rpa_status enqueue_batch(rpa_ctx* ctx, BatchCache& bc, const Plan& p, con
     // V-side work (V = LL^H, ln det V, -V^-1), their log-dets follow as one
     // ragged launch over all of the group's matrices.
     CKB(cudaEventRecord(bc.fork, s));
-    const int nside = std::min(kSide, g.j1 - g.j0);
+    const int nside = std::min(SideStreams::kSide, g.j1 - g.j0);
     for (int k = 0; k < nside; ++k) CKB(cudaStreamWaitEvent(bc.side[k], bc.fork, 0));
     std::vector<int> order;
     for (int i = g.j0; i < g.j1; ++i) order.push_back(i);
@@ -375,7 +339,7 @@ extern "C" rpa_status rpa_energy_batch(rpa_ctx* ctx, const rpa_job* jobs, int n_
   CKB(cudaSetDevice(ctx->device));
   if (!ctx->batch) ctx->batch = new BatchCache;
   BatchCache& bc = *ctx->batch;
-  if (!bc.init_side()) {
+  if (!bc.side.init()) {
     ctx_set_error(ctx, "cannot create the batch side streams");
     return RPA_E_CUDA;
   }
@@ -386,7 +350,7 @@ extern "C" rpa_status rpa_energy_batch(rpa_ctx* ctx, const rpa_job* jobs, int n_
   const bool known = bc.plan && bc.plan->exec && bc.plan->sig == sig;
   const bool replay = known && !ctx->prof;
   if (!known) {
-    bc.plan = make_plan(jobs, n_jobs, ctx->n_slices, ctx->cap);
+    bc.plan = batch_plan(jobs, n_jobs, ctx->n_slices, ctx->cap);
     bc.plan->sig = sig;
   }
   Plan& p = *bc.plan;
@@ -402,14 +366,14 @@ extern "C" rpa_status rpa_energy_batch(rpa_ctx* ctx, const rpa_job* jobs, int n_
   }
   char* pin = (char*)bc.pin.ptr;
   char* ws = (char*)bc.mem.ws;
-  fill_tables(p, jobs, n_jobs, pin);
+  batch_fill_tables(p, jobs, n_jobs, pin);
   if (replay) {
     CKB(cudaGraphLaunch(p.exec, s));
     ctx->launches += p.kernels;
   } else {
     // eager run (the autotuner on for a new signature); results come from this run
     uint64_t nk = 0;
-    if (rpa_status st = enqueue_batch(ctx, bc, p, jobs, ws, pin, s, !known, &nk, &ctx->ex)) {
+    if (rpa_status st = batch_enqueue(ctx, bc.side, p, jobs, ws, pin, s, !known, &nk, &ctx->ex)) {
       bc.plan.reset();
       return st;
     }
@@ -432,7 +396,7 @@ extern "C" rpa_status rpa_energy_batch(rpa_ctx* ctx, const rpa_job* jobs, int n_
     cudaGraph_t graph = nullptr;
     CKB(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     uint64_t nk = 0;
-    rpa_status st = enqueue_batch(ctx, bc, p, jobs, ws, pin, s, false, &nk, nullptr);
+    rpa_status st = batch_enqueue(ctx, bc.side, p, jobs, ws, pin, s, false, &nk, nullptr);
     ctx->launches -= nk;  // captured, not launched
     cudaError_t ce = cudaStreamEndCapture(s, &graph);
     if (st != RPA_OK) {

@@ -2,18 +2,24 @@
 //
 // rpa_submit() deep-copies a job's host descriptors into a pending queue.  A
 // scheduler thread admits pending jobs in arrival order while the device
-// memory they account for stays under the context's HBM cap: the inputs of the
+// memory it accounts for stays under the context's HBM cap: the inputs of the
 // running jobs plus every lane's workspace (lanes keep their workspace between
-// jobs; idle lanes give theirs back when a new job would not fit otherwise),
-// and while fewer than max_inflight jobs run.  An
-// admitted job gets an execution lane of its own (stream, workspace, pinned
-// buffers) and its whole hot path is enqueued there at once, so the kernels of
-// all running jobs share the device; the scheduler polls the lanes' completion
-// events, publishes results and admits the next jobs as soon as memory frees
-// up.  The paper's analogue is the (q, omega) group decomposition of Sec. 2.6
-// (independent work units, one gather of the results); here the independent
-// units are whole jobs and the gather is the per-ticket result table.
+// jobs; idle lanes give theirs back when a new batch would not fit otherwise),
+// and while fewer than max_inflight jobs run.  The device-resident jobs that
+// are waiting when a lane frees up are admitted together as one micro-batch:
+// their (q, omega) work runs through the batch engine (shared persistent
+// tensor-core launches over all their (job, q) segments, per-job tail work on
+// side streams, one ragged log-det launch), so small jobs fill the GPU
+// together; micro-batches on different lanes overlap on the device.  Jobs
+// with inputs in host memory (staged copies) and jobs too large to hold every
+// q's workspace at once run alone on a lane, q-batch by q-batch.  The
+// scheduler polls the lanes' completion events, publishes results and admits
+// the next jobs as soon as memory frees up.  The paper's analogue is the
+// (q, omega) group decomposition of Sec. 2.6 (independent work units, one
+// gather of the results).
 #include <cuda_runtime.h>
+
+#include <string.h>
 
 #include <algorithm>
 #include <chrono>
@@ -25,6 +31,7 @@
 #include <thread>
 #include <vector>
 
+#include "batch_internal.h"
 #include "rpa_runtime.h"
 
 namespace rpa {
@@ -41,12 +48,31 @@ struct ServeJob {
   std::vector<const void*> C, V;
   size_t footprint = 0;  // inputs + workspace
   size_t ws_need = 0;    // workspace part
+  bool batchable = false;  // device-resident and small enough to share a micro-batch
   double t_submit = 0, t_admit = 0, t_done = 0;
   int state = 0;  // 0 pending, 1 running, 2 done
   rpa_status status = RPA_OK;
   double Ec = 0;
   std::vector<double> eps;
-  Exec* lane = nullptr;
+  std::string error;
+};
+
+// An execution lane: stream, workspace and pinned buffers (Exec) plus side
+// streams for the batch engine's tail work.
+struct ServeLane {
+  Exec ex;
+  SideStreams side;
+};
+
+// Jobs admitted together and running on one lane.
+struct ServeBatch {
+  std::vector<std::shared_ptr<ServeJob>> jobs;
+  std::vector<rpa_job> desc;    // their descriptors, in batch order
+  std::unique_ptr<Plan> plan;   // null: a single host-memory job (energy_enqueue)
+  ServeLane* lane = nullptr;
+  size_t inputs = 0;
+  bool failed = false;          // enqueue failed: every job reports `error`
+  rpa_status status = RPA_OK;
   std::string error;
 };
 
@@ -54,10 +80,11 @@ struct ServeState {
   std::mutex mu;
   std::condition_variable cv;
   std::deque<std::shared_ptr<ServeJob>> pending;
-  std::vector<std::shared_ptr<ServeJob>> running;
+  std::vector<std::unique_ptr<ServeBatch>> running;
+  int running_jobs = 0;
   std::map<uint64_t, std::shared_ptr<ServeJob>> tickets;
-  std::vector<std::unique_ptr<Exec>> lanes;
-  std::vector<Exec*> free_lanes;
+  std::vector<std::unique_ptr<ServeLane>> lanes;
+  std::vector<ServeLane*> free_lanes;
   size_t inputs_used = 0;  // device inputs of the running jobs
   size_t ws_total = 0;     // workspace held by all lanes
   uint64_t next_ticket = 1;
@@ -67,49 +94,59 @@ struct ServeState {
   uint64_t done = 0;
   size_t max_pending = 4096;
   int peak_running = 0;     // most jobs on the device at once
+  int peak_batch = 0;       // most jobs admitted as one micro-batch
   size_t peak_used = 0;     // largest inputs_used + ws_total
 };
 
 static size_t ws_alloc_size(size_t need) { return std::max(need, (size_t)64 << 20); }
 
-// A free lane for a job that needs `need` bytes of workspace: the smallest
-// free lane that already holds enough, else the free lane holding the most
-// (its workspace will be reallocated), else a new lane (nullptr if none could
-// be made).  *extra: growth of the lanes' total workspace if this lane runs
-// the job.
-static Exec* pick_lane(ServeState* S, size_t need, size_t* extra) {
+// Jobs per micro-batch (each (job, q) is a segment of the shared launches).
+constexpr int kMaxBatch = 32;
+// Micro-batches in flight at once: arrivals while all lanes are busy wait and
+// are admitted together when one frees up.
+constexpr int kMaxLanes = 4;
+
+// A free lane for `need` bytes of workspace: the smallest free lane that
+// already holds enough, else the free lane holding the most (its workspace
+// will be reallocated), else a new lane (nullptr if none could be made).
+// *extra: growth of the lanes' total workspace if this lane is used.
+static ServeLane* pick_lane(ServeState* S, size_t need, size_t* extra) {
   int best = -1;
   for (int i = 0; i < (int)S->free_lanes.size(); ++i) {
-    const size_t b = S->free_lanes[i]->ws_bytes;
-    if (b >= need && (best < 0 || b < S->free_lanes[best]->ws_bytes)) best = i;
+    const size_t b = S->free_lanes[i]->ex.ws_bytes;
+    if (b >= need && (best < 0 || b < S->free_lanes[best]->ex.ws_bytes)) best = i;
   }
   if (best < 0)
     for (int i = 0; i < (int)S->free_lanes.size(); ++i)
-      if (best < 0 || S->free_lanes[i]->ws_bytes > S->free_lanes[best]->ws_bytes) best = i;
-  Exec* e = nullptr;
+      if (best < 0 || S->free_lanes[i]->ex.ws_bytes > S->free_lanes[best]->ex.ws_bytes) best = i;
+  ServeLane* l = nullptr;
   if (best >= 0) {
-    e = S->free_lanes[best];
+    l = S->free_lanes[best];
+  } else if ((int)S->lanes.size() >= kMaxLanes) {
+    return nullptr;  // all lanes busy
   } else {
-    std::unique_ptr<Exec> n(new Exec());
-    if (!n->init()) {
-      n->destroy();
+    std::unique_ptr<ServeLane> n(new ServeLane());
+    if (!n->ex.init() || !n->side.init()) {
+      n->side.release();
+      n->ex.destroy();
       return nullptr;
     }
     S->lanes.push_back(std::move(n));
-    e = S->lanes.back().get();
-    S->free_lanes.push_back(e);
+    l = S->lanes.back().get();
+    S->free_lanes.push_back(l);
   }
-  *extra = e->ws_bytes >= need ? 0 : ws_alloc_size(need) - e->ws_bytes;
-  return e;
+  *extra = l->ex.ws_bytes >= need ? 0 : ws_alloc_size(need) - l->ex.ws_bytes;
+  return l;
 }
 
 // Gives back the workspace of idle lanes other than `keep` until `want` bytes
 // were released or none is left; returns the bytes released.
-static size_t release_idle(ServeState* S, Exec* keep, size_t want) {
+static size_t release_idle(ServeState* S, ServeLane* keep, size_t want) {
   size_t freed = 0;
-  for (Exec* e : S->free_lanes) {
+  for (ServeLane* l : S->free_lanes) {
     if (freed >= want) break;
-    if (e == keep || !e->ws) continue;
+    Exec* e = &l->ex;
+    if (l == keep || !e->ws) continue;
     cudaStreamSynchronize(e->s);
     cudaFree(e->ws);
     freed += e->ws_bytes;
@@ -122,31 +159,72 @@ static size_t release_idle(ServeState* S, Exec* keep, size_t want) {
 
 static size_t lane_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap / 4, (size_t)24 << 30); }
 
+
 static void scheduler(rpa_ctx* ctx) {
   ServeState* S = ctx->serve;
   cudaSetDevice(ctx->device);
   std::unique_lock<std::mutex> lk(S->mu);
   while (true) {
     bool progress = false;
-    // 1. admit in arrival order while memory and slots allow
-    while (!S->pending.empty() && (int)S->running.size() < ctx->max_inflight) {
-      std::shared_ptr<ServeJob> j = S->pending.front();
-      size_t extra = 0;
-      Exec* lane = pick_lane(S, j->ws_need, &extra);
-      const size_t inputs = j->footprint - j->ws_need;
-      if (lane) {
-        size_t total = S->inputs_used + inputs + S->ws_total + extra;
-        if (total > ctx->cap) total -= release_idle(S, lane, total - ctx->cap);
-        // the first job always runs (its footprint alone is below the cap)
-        if (total > ctx->cap && !S->running.empty()) break;
+    // 1. admit in arrival order while memory and slots allow: the waiting
+    //    device-resident jobs as one micro-batch per free lane
+    while (!S->pending.empty() && S->running_jobs < ctx->max_inflight) {
+      std::unique_ptr<ServeBatch> B(new ServeBatch());
+      const bool alone = !S->pending.front()->batchable;
+      size_t ws_need = 0;
+      if (alone) {
+        B->jobs.push_back(S->pending.front());
+        ws_need = B->jobs[0]->ws_need;
+        B->inputs = B->jobs[0]->footprint - B->jobs[0]->ws_need;
+        B->desc.push_back(B->jobs[0]->job);
+      } else {
+        // greedy prefix of the queue: device jobs whose inputs and workspace
+        // fit next to what runs; the plan then gives the batch's workspace
+        size_t est = 0;
+        for (const std::shared_ptr<ServeJob>& j : S->pending) {
+          if (!j->batchable || (int)B->jobs.size() >= kMaxBatch ||
+              S->running_jobs + (int)B->jobs.size() >= ctx->max_inflight)
+            break;
+          const size_t add = j->footprint;
+          if (!B->jobs.empty() && S->inputs_used + S->ws_total + est + add > ctx->cap) break;
+          B->jobs.push_back(j);
+          est += add;
+          B->inputs += j->footprint - j->ws_need;
+        }
+        for (const auto& j : B->jobs) B->desc.push_back(j->job);
+        B->plan = batch_plan(B->desc.data(), (int)B->desc.size(), ctx->n_slices, lane_ws_cap(ctx));
+        ws_need = B->plan->ws_bytes;
       }
-      S->pending.pop_front();
-      j->t_admit = now_s();
+      size_t extra = 0;
+      ServeLane* lane = pick_lane(S, ws_need, &extra);
+      if (!lane && (int)S->lanes.size() >= kMaxLanes) break;  // wait for a lane
+      if (lane) {
+        size_t total = S->inputs_used + B->inputs + S->ws_total + extra;
+        if (total > ctx->cap) total -= release_idle(S, lane, total - ctx->cap);
+        // the estimate admitted too much: shrink the batch from its end
+        while (total > ctx->cap && B->jobs.size() > 1) {
+          B->inputs -= B->jobs.back()->footprint - B->jobs.back()->ws_need;
+          B->jobs.pop_back();
+          B->desc.pop_back();
+          B->plan = batch_plan(B->desc.data(), (int)B->desc.size(), ctx->n_slices, lane_ws_cap(ctx));
+          ws_need = B->plan->ws_bytes;
+          lane = pick_lane(S, ws_need, &extra);
+          if (!lane) break;  // the lane was free a moment ago: cannot happen, but stay safe
+          total = S->inputs_used + B->inputs + S->ws_total + extra;
+        }
+        // a single job always runs when nothing else does (its footprint is below the cap)
+        if (lane && total > ctx->cap && !S->running.empty()) break;
+      }
+      const double t_admit = now_s();
+      for (size_t k = 0; k < B->jobs.size(); ++k) S->pending.pop_front();
       if (!lane) {
-        j->status = RPA_E_CUDA;
-        j->error = "cannot create an execution lane";
-        j->state = 2;
-        j->t_done = now_s();
+        for (auto& j : B->jobs) {
+          j->t_admit = t_admit;
+          j->status = RPA_E_CUDA;
+          j->error = "cannot create an execution lane";
+          j->state = 2;
+          j->t_done = now_s();
+        }
         progress = true;
         continue;
       }
@@ -158,51 +236,88 @@ static void scheduler(rpa_ctx* ctx) {
           release_idle(S, lane, extra + ((size_t)1 << 30) - free_b);
       }
       S->free_lanes.erase(std::find(S->free_lanes.begin(), S->free_lanes.end(), lane));
-      j->lane = lane;
-      j->state = 1;
-      S->inputs_used += inputs;
+      for (auto& j : B->jobs) {
+        j->t_admit = t_admit;
+        j->state = 1;
+      }
+      B->lane = lane;
+      S->inputs_used += B->inputs;
       S->ws_total += extra;
-      S->running.push_back(j);
-      S->peak_running = std::max(S->peak_running, (int)S->running.size());
+      S->running_jobs += (int)B->jobs.size();
+      S->peak_running = std::max(S->peak_running, S->running_jobs);
+      S->peak_batch = std::max(S->peak_batch, (int)B->jobs.size());
       S->peak_used = std::max(S->peak_used, S->inputs_used + S->ws_total);
+      ServeBatch* Bp = B.get();
+      S->running.push_back(std::move(B));
       lk.unlock();
-      rpa_status st = energy_enqueue(ctx, *lane, &j->job, lane_ws_cap(ctx));
+      rpa_status st = RPA_OK;
+      if (!Bp->plan) {
+        st = energy_enqueue(ctx, lane->ex, &Bp->jobs[0]->job, lane_ws_cap(ctx));
+      } else if (!lane->ex.ensure_ws(Bp->plan->ws_bytes) || !lane->ex.hstage.reserve(Bp->plan->pin_bytes + 64)) {
+        ctx_set_error(ctx, "cannot allocate the serving batch's workspace");
+        st = RPA_E_NOMEM;
+      } else {
+        char* pin = (char*)lane->ex.hstage.ptr;
+        batch_fill_tables(*Bp->plan, Bp->desc.data(), (int)Bp->desc.size(), pin);
+        uint64_t nk = 0;
+        st = batch_enqueue(ctx, lane->side, *Bp->plan, Bp->desc.data(), (char*)lane->ex.ws, pin, lane->ex.s, false,
+                           &nk, nullptr);
+        if (st == RPA_OK && cudaEventRecord(lane->ex.done, lane->ex.s) != cudaSuccess) st = RPA_E_CUDA;
+      }
       lk.lock();
       if (st != RPA_OK) {
-        j->status = st;
-        j->error = ctx->last_error;
+        Bp->failed = true;
+        Bp->status = st;
+        Bp->error = ctx->last_error;
         // let the lane drain whatever was enqueued before the failure
-        cudaEventRecord(lane->done, lane->s);
-        j->Ec = 0;
+        cudaEventRecord(lane->ex.done, lane->ex.s);
       }
       progress = true;
     }
-    // 2. collect finished jobs
+    // 2. collect finished batches
     for (size_t i = 0; i < S->running.size();) {
-      std::shared_ptr<ServeJob> j = S->running[i];
-      cudaError_t e = cudaEventQuery(j->lane->done);
+      ServeBatch* B = S->running[i].get();
+      cudaError_t e = cudaEventQuery(B->lane->ex.done);
       if (e == cudaErrorNotReady) {
         ++i;
         continue;
       }
-      if (j->status == RPA_OK) {
-        if (e != cudaSuccess) {
+      const double t_done = now_s();
+      for (size_t k = 0; k < B->jobs.size(); ++k) {
+        ServeJob* j = B->jobs[k].get();
+        if (B->failed) {
+          j->status = B->status;
+          j->error = B->error;
+        } else if (e != cudaSuccess) {
           j->status = RPA_E_CUDA;
           j->error = cudaGetErrorString(e);
-        } else {
+        } else if (!B->plan) {
           j->eps.resize((size_t)j->job.n_q * j->job.n_w);
-          j->status = energy_finish(ctx, *j->lane, &j->job, &j->Ec, j->eps.data(), nullptr);
+          j->status = energy_finish(ctx, B->lane->ex, &j->job, &j->Ec, j->eps.data(), nullptr);
           if (j->status) j->error = ctx->last_error;
+        } else {
+          const char* r = (const char*)B->lane->ex.hstage.ptr + B->plan->jobs[k].res_off;
+          int sw;
+          memcpy(&sw, r, sizeof sw);
+          j->status = decode_status(ctx, sw, j->job.n_w);
+          if (j->status) {
+            j->error = ctx->last_error;
+          } else {
+            const size_t nqw = (size_t)j->job.n_q * j->job.n_w;
+            memcpy(&j->Ec, r + 64, sizeof(double));
+            j->eps.resize(nqw);
+            memcpy(j->eps.data(), r + 64 + sizeof(double), sizeof(double) * nqw);
+          }
         }
+        j->t_done = t_done;
+        j->state = 2;
+        S->lat.push_back(j->t_done - j->t_submit);
+        S->wait.push_back(j->t_admit - j->t_submit);
+        S->done++;
       }
-      j->t_done = now_s();
-      j->state = 2;
-      S->inputs_used -= j->footprint - j->ws_need;
-      S->free_lanes.push_back(j->lane);
-      j->lane = nullptr;
-      S->lat.push_back(j->t_done - j->t_submit);
-      S->wait.push_back(j->t_admit - j->t_submit);
-      S->done++;
+      S->inputs_used -= B->inputs;
+      S->running_jobs -= (int)B->jobs.size();
+      S->free_lanes.push_back(B->lane);
       S->running.erase(S->running.begin() + i);
       progress = true;
     }
@@ -234,7 +349,10 @@ void serving_shutdown(rpa_ctx* ctx) {
     S->cv.notify_all();
   }
   if (S->th.joinable()) S->th.join();
-  for (auto& l : S->lanes) l->destroy();
+  for (auto& l : S->lanes) {
+    l->side.release();
+    l->ex.destroy();
+  }
   delete S;
   ctx->serve = nullptr;
 }
@@ -279,6 +397,18 @@ rpa_status rpa_submit(rpa_ctx* ctx, const rpa_job* job, uint64_t* ticket) {
   j->job.V = j->V.data();
   j->footprint = job_footprint(job, ctx->n_slices, lane_ws_cap(ctx));
   j->ws_need = job_workspace(job, ctx->n_slices, lane_ws_cap(ctx));
+  if (job->mem == RPA_MEM_DEVICE) {
+    // the batch engine holds every q's split-precision workspace at once:
+    // jobs whose batch workspace stays within a lane's cap share micro-batches,
+    // larger ones run alone q-batch by q-batch
+    const size_t inputs = j->footprint - j->ws_need;
+    const size_t ws_b = batch_plan(&j->job, 1, ctx->n_slices, lane_ws_cap(ctx))->ws_bytes;
+    if (ws_b <= lane_ws_cap(ctx)) {
+      j->batchable = true;
+      j->ws_need = ws_b;
+      j->footprint = inputs + ws_b;
+    }
+  }
   if (j->footprint > ctx->cap) {
     ctx_set_error(ctx, "job footprint %zu bytes exceeds the HBM cap %zu", j->footprint, ctx->cap);
     return RPA_E_NOMEM;
@@ -365,17 +495,19 @@ rpa_status rpa_serving_stats(rpa_ctx* ctx, uint64_t* jobs_done, double* lat_mean
   return RPA_OK;
 }
 
-rpa_status rpa_serving_peak(rpa_ctx* ctx, int* max_running, size_t* max_bytes) {
+rpa_status rpa_serving_peak(rpa_ctx* ctx, int* max_running, size_t* max_bytes, int* max_batch) {
   if (!ctx) return RPA_E_INVAL;
-  int r = 0;
+  int r = 0, mb = 0;
   size_t b = 0;
   if (ctx->serve) {
     std::lock_guard<std::mutex> g(ctx->serve->mu);
     r = ctx->serve->peak_running;
     b = ctx->serve->peak_used;
+    mb = ctx->serve->peak_batch;
   }
   if (max_running) *max_running = r;
   if (max_bytes) *max_bytes = b;
+  if (max_batch) *max_batch = mb;
   return RPA_OK;
 }
 

@@ -55,6 +55,7 @@ def test_served_results_equal_alone(rpa):
     assert st["jobs_done"] == len(jobs)
     assert 0.0 < st["lat_p50_s"] <= st["lat_p99_s"]
     assert peak["max_running"] >= 2  # submitted together: they overlap on the device
+    assert peak["max_batch"] >= 2  # and waiting jobs share micro-batches
 
 
 def test_admission_respects_hbm_cap(rpa):
