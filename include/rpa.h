@@ -141,17 +141,24 @@ rpa_status rpa_logdet(rpa_ctx *ctx, const rpa_job *job, int q, const void *chi, 
  * RPA_MEM_HOST, on the host (staged per q, copies overlapped with compute). */
 rpa_status rpa_energy(rpa_ctx *ctx, const rpa_job *job, double *Ec, double *eps_qw, double *parts);
 
-/* Many independent jobs (uneven sizes) in one call: all (job, q) work is
- * packed into persistent launches recorded once into a CUDA graph per batch
- * shape; Ec_out (host [n_jobs]) receives each job's E_c.  Jobs must have
- * mem == RPA_MEM_DEVICE. */
+/* Many independent jobs (uneven sizes) in one call: the split-precision
+ * chi0 of every (job, q) shares persistent tensor-core launches (a segment
+ * each), the jobs' tails run on side streams and their log-dets as one ragged
+ * launch; the whole sequence is recorded once into a CUDA graph per batch
+ * signature (shapes, precisions, device pointers) and replayed by later calls
+ * with that signature (the first call runs eagerly and tunes the split-K
+ * plans).  Ec_out (host [n_jobs]) receives each job's E_c.  Jobs must have
+ * mem == RPA_MEM_DEVICE; the batch's workspace is cut into groups under the
+ * context's HBM cap. */
 rpa_status rpa_energy_batch(rpa_ctx *ctx, const rpa_job *jobs, int n_jobs, double *Ec_out);
 
 /* Serving: enqueue a job (deep-copies the host descriptors; device buffers
  * stay borrowed).  The job is admitted once its footprint fits under the
- * context's cap next to the jobs already running; admitted jobs share the
- * device (continuous batching).  RPA_E_BUSY if the queue is full,
- * RPA_E_NOMEM if the job alone exceeds the cap. */
+ * context's cap next to the jobs already running; device-resident jobs that
+ * wait together are admitted as one micro-batch whose (q, omega) work shares
+ * the tensor-core launches, and up to four micro-batches share the device
+ * (continuous batching).  RPA_E_BUSY if the queue is full, RPA_E_NOMEM if the
+ * job alone exceeds the cap. */
 rpa_status rpa_submit(rpa_ctx *ctx, const rpa_job *job, uint64_t *ticket);
 
 /* RPA_E_NOTREADY until the ticket's job is done; then its status, with *Ec
