@@ -617,11 +617,13 @@ def run_serving(args):
     t0 = time.perf_counter()
     window = []
     for i in adm:
+        # at most 8 jobs and ~100 GB of their inputs outstanding
+        while window and (len(window) >= 8 or sum(stream[k][1].c_bytes() for k, *_ in window) +
+                          stream[i][1].c_bytes() > 100e9):
+            ctx.wait(window.pop(0)[1], 600.0)
         tens_i, job_i = make(i, stream[i][1])
-        window.append((ctx.submit(job_i), tens_i, job_i))
-        if len(window) >= 8:
-            ctx.wait(window.pop(0)[0], 600.0)
-    for t, _, _ in window:
+        window.append((i, ctx.submit(job_i), tens_i, job_i))
+    for _, t, _, _ in window:
         ctx.wait(t, 600.0)
     cap_jobs_s = len(adm) / (time.perf_counter() - t0)
     del window
@@ -651,6 +653,13 @@ def run_serving(args):
             dt = t_arr - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
+            # the harness's own memory: wait while ~130 GB of inputs are out
+            while True:
+                with lock:
+                    held = sum(stream[k][1].c_bytes() for k, _, _ in live.values())
+                if held + p.c_bytes() <= 130e9 or not live:
+                    break
+                time.sleep(0.001)
             try:
                 tens, job = make(i, p)
                 with lock:

@@ -100,6 +100,12 @@ struct ServeState {
 
 static size_t ws_alloc_size(size_t need) { return std::max(need, (size_t)64 << 20); }
 
+static size_t lanes_ws(ServeState* S) {
+  size_t t = 0;
+  for (const auto& l : S->lanes) t += l->ex.ws_bytes;
+  return t;
+}
+
 // Jobs per micro-batch (each (job, q) is a segment of the shared launches).
 constexpr int kMaxBatch = 32;
 // Micro-batches in flight at once: arrivals while all lanes are busy wait and
@@ -251,11 +257,13 @@ static void scheduler(rpa_ctx* ctx) {
       S->running.push_back(std::move(B));
       lk.unlock();
       rpa_status st = RPA_OK;
+      bool no_memory = false;
       if (!Bp->plan) {
         st = energy_enqueue(ctx, lane->ex, &Bp->jobs[0]->job, lane_ws_cap(ctx));
       } else if (!lane->ex.ensure_ws(Bp->plan->ws_bytes) || !lane->ex.hstage.reserve(Bp->plan->pin_bytes + 64)) {
         ctx_set_error(ctx, "cannot allocate the serving batch's workspace");
         st = RPA_E_NOMEM;
+        no_memory = true;
       } else {
         char* pin = (char*)lane->ex.hstage.ptr;
         batch_fill_tables(*Bp->plan, Bp->desc.data(), (int)Bp->desc.size(), pin);
@@ -265,6 +273,20 @@ static void scheduler(rpa_ctx* ctx) {
         if (st == RPA_OK && cudaEventRecord(lane->ex.done, lane->ex.s) != cudaSuccess) st = RPA_E_CUDA;
       }
       lk.lock();
+      if (no_memory) S->ws_total = lanes_ws(S);  // the lane may have given up its old workspace
+      if (no_memory && S->running.size() > 1) {
+        // the device is short (memory held outside the cap): put the jobs back
+        // at the head of the queue and admit again when a running batch ends
+        for (size_t k = Bp->jobs.size(); k-- > 0;) {
+          Bp->jobs[k]->state = 0;
+          S->pending.push_front(Bp->jobs[k]);
+        }
+        S->inputs_used -= Bp->inputs;
+        S->running_jobs -= (int)Bp->jobs.size();
+        S->free_lanes.push_back(lane);
+        S->running.pop_back();
+        break;
+      }
       if (st != RPA_OK) {
         Bp->failed = true;
         Bp->status = st;
