@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "mixed"])
     ap.add_argument("--slices", type=int, default=0, help="BF16 digit slices of the mixed path (2-4; 0: library default)")
+    ap.add_argument("--cap-gb", type=float, default=0.0,
+                    help="periodic2d/slab: the context's HBM cap (bounds the workspace; profiling small cases)")
     ap.add_argument("--n-q", type=int, default=0, help="profiling only: restrict the job to its first n q-points")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -261,7 +263,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     job = rpa.job_from_problem(p, tens, prec=pc)
-    ctx = rpa.Context(local, n_slices=args.slices)
+    ctx = rpa.Context(local, n_slices=args.slices, hbm_cap_bytes=int(args.cap_gb * 1e9))
     for _ in range(args.warmup):
         ctx.energy(job)
     ext = torch.cuda.ExternalStream(ctx.stream_handle)
