@@ -705,8 +705,8 @@ template <bool C, int CL>
 __global__ void __launch_bounds__(256)
     cholesky_kernel(int N, double* __restrict__ mats, long bstride, int mode, double* __restrict__ out,
                     int* __restrict__ status, int status_base, const double* __restrict__ Wn,
-                    const double* __restrict__ Vc, const double* __restrict__ ldV, int n_w) {
-  const int b = blockIdx.x / CL;
+                    const double* __restrict__ Vc, const double* __restrict__ ldV, int n_w, int b0) {
+  const int b = b0 + (int)(blockIdx.x / CL);
   const long q = mode == 2 ? b / n_w : 0;
   const long NN = (long)N * N * (C ? 2 : 1);
   chol_one<C, CL>(N, mats + (long)b * bstride, mode, out ? out + (mode == 1 ? b : 2 * b) : nullptr, status,
@@ -866,11 +866,12 @@ cudaError_t launch_sandwich(int cplx, int N, int n_batch, int n_w, const double*
 constexpr int CL_BIG = 8;
 
 template <bool C, int CL>
-cudaError_t launch_chol_t(int N, int n_mat, double* mats, long bstride, int mode, double* out, int* status,
+cudaError_t launch_chol_t(int N, int b0, int n_mat, double* mats, long bstride, int mode, double* out, int* status,
                           int status_base, cudaStream_t s, const double* Wn, const double* Vc, const double* ldV,
                           int n_w) {
   if constexpr (CL == 1) {
-    cholesky_kernel<C, 1><<<n_mat, 256, 0, s>>>(N, mats, bstride, mode, out, status, status_base, Wn, Vc, ldV, n_w);
+    cholesky_kernel<C, 1><<<n_mat, 256, 0, s>>>(N, mats, bstride, mode, out, status, status_base, Wn, Vc, ldV, n_w,
+                                                 b0);
   } else {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(n_mat * CL));
@@ -885,9 +886,30 @@ cudaError_t launch_chol_t(int N, int n_mat, double* mats, long bstride, int mode
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, cholesky_kernel<C, CL>, N, mats, bstride, mode, out, status, status_base, Wn, Vc,
-                              ldV, n_w);
+                              ldV, n_w, b0);
   }
   return cudaGetLastError();
+}
+
+template <bool C>
+cudaError_t launch_chol_c(int N, int n_mat, double* mats, long bstride, int mode, double* out, int* status,
+                          int status_base, cudaStream_t s, const double* Wn, const double* Vc, const double* ldV,
+                          int n_w) {
+  const int P = num_sms_fp64();
+  // few large matrices: a cluster per matrix
+  if (N >= 256 && n_mat * 2 < P)
+    return launch_chol_t<C, CL_BIG>(N, 0, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
+  // one CTA per matrix; a short last wave (fewer than P/2 matrices) goes to
+  // clusters instead, so that it does not run on a few SMs alone
+  const int r = n_mat % P;
+  if (N >= 256 && n_mat > P && r > 0 && r * 2 < P) {
+    cudaError_t e = launch_chol_t<C, 1>(N, 0, n_mat - r, mats, bstride, mode, out, status, status_base, s, Wn, Vc,
+                                        ldV, n_w);
+    if (e != cudaSuccess) return e;
+    return launch_chol_t<C, CL_BIG>(N, n_mat - r, r, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV,
+                                    n_w);
+  }
+  return launch_chol_t<C, 1>(N, 0, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
 }
 
 cudaError_t launch_cholesky(int cplx, int N, int n_mat, double* mats, long bstride, int mode, double* out,
@@ -895,14 +917,8 @@ cudaError_t launch_cholesky(int cplx, int N, int n_mat, double* mats, long bstri
                             const double* ldV, int n_w) {
   if (n_mat == 0) return cudaSuccess;
   if (mode == 2 && (!Wn || !Vc || !ldV || n_w <= 0)) return cudaErrorInvalidValue;
-  const bool team = N >= 256 && n_mat * 2 < num_sms_fp64();
-  if (cplx)
-    return team ? launch_chol_t<true, CL_BIG>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV,
-                                              n_w)
-                : launch_chol_t<true, 1>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
-  return team ? launch_chol_t<false, CL_BIG>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV,
-                                             n_w)
-              : launch_chol_t<false, 1>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
+  if (cplx) return launch_chol_c<true>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
+  return launch_chol_c<false>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
 }
 
 cudaError_t launch_cholesky_ragged(int cplx, const CholTask* tasks, int n_tasks, cudaStream_t s) {
