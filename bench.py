@@ -728,7 +728,7 @@ def rpa_mixed_tensor_flops(p, ctx, s=4):
     chunk = 1024 if p.is_complex else 2048
     kr = (-(-kt // chunk) * chunk) * (2 if p.is_complex else 1)
     tiles = nb * (nb + 1) if p.is_complex else nb * (nb + 1) // 2
-    pairs = s * (s + 1) // 2 + (1 if s % 2 == 0 else 0)
+    pairs = s * (s + 1) // 2 + (1 if s == 2 else 0)
     return float(p.n_q) * p.n_w * tiles * (kr // 16) * pairs * 2.0 * 128 * 128 * 16
 
 

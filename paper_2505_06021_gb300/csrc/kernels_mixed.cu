@@ -18,12 +18,11 @@
 // ...) of C, so that one MMA of N = 128 gives [X_P X_Q^T | X_P Y_Q^T] =
 // [Re | Im] of sum_t conj(A_P) C_Q for 64 columns Q.
 //
-// Exactness.  Slice pairs (i, j) with i + j <= s - 1, plus (s/2, s/2) for even
-// s (the largest dropped level), are grouped by
-// level into four TMEM accumulators: levels 0, 1 and 2 hold integer-valued
-// sums that stay below 2^24 for CHUNK t (exact FP32 accumulation whatever the
-// tensor core's rounding), levels 3 and 4 (2^-24 and 2^-32 below level 0) are
-// plain FP32.  Every CHUNK t the eight epilogue warps drain the four groups
+// Exactness.  Slice pairs (i, j) with i + j <= s - 1 (plus (1, 1) for s = 2)
+// are grouped by level into four TMEM accumulators: levels 0, 1 and 2 hold
+// integer-valued sums that stay below 2^24 for CHUNK t (exact FP32
+// accumulation whatever the tensor core's rounding), level 3 (2^-24 below
+// level 0) is plain FP32.  Every CHUNK t the eight epilogue warps drain the four groups
 // and add them into float-float (hi, lo) register accumulators.
 //
 // The tensor-core kernel itself is in chi0_tc.cuh.  The K range of each tile
@@ -469,12 +468,12 @@ MixedLayout mixed_layout(const BatchGeom& g, int s, int sms, size_t slice_cap) {
   return L;
 }
 
-// Accumulator groups used by s slices: levels 0 .. s-1, plus level s for the
-// (s/2, s/2) pair of even s, capped at the last group (PairTable's rule).
+// Accumulator groups used by s slices: levels 0 .. s-1, plus level 2 for the
+// (1, 1) pair of s = 2, capped at the last group (PairTable's rule).
 constexpr int group_mask(int s) {
   int m = 0;
   for (int lvl = 0; lvl < s; ++lvl) m |= 1 << (lvl < NGROUPS - 1 ? lvl : NGROUPS - 1);
-  if (s % 2 == 0) m |= 1 << (s < NGROUPS - 1 ? s : NGROUPS - 1);
+  if (s == 2) m |= 1 << 2;
   return m;
 }
 static_assert(group_mask(2) == PairTable<2>{}.mask && group_mask(3) == PairTable<3>{}.mask &&
@@ -610,7 +609,7 @@ size_t mixed_workspace_bytes(const BatchGeom& g, int n_slices, size_t slice_cap)
 
 uint64_t mixed_tensor_flops(const BatchGeom& g, int s) {
   const MixedLayout L = mixed_layout(g, s, num_sms(), (size_t)12 << 30);
-  const int np = s * (s + 1) / 2 + (s % 2 == 0 ? 1 : 0);
+  const int np = s * (s + 1) / 2 + (s == 2 ? 1 : 0);
   return (uint64_t)g.n_w * L.n_tiles * (uint64_t)L.n_kb * np * 2ull * 128 * 128 * KB;
 }
 
