@@ -6,6 +6,8 @@ or calls anything here, and nothing here imports the GPU library.
 
 Each function restates one step of the paper's method (arXiv 2505.06021):
 
+* :func:`ao2mo`     - MO-basis fit coefficients C_{gamma,ia}(q, k) from the
+                      k-dependent PADF and MO coefficients, Sec. 2.2
 * :func:`chi0`      - fit-basis response chi0_PQ(q, i omega), Sec. 2.2
 * :func:`vhalf`     - V(q)^(1/2) by Hermitian Jacobi, Sec. 2.1 / Algorithm 1
 * :func:`sandwich`  - Pi = V^(1/2) chi0 V^(1/2), Sec. 2.1 / Algorithm 1
@@ -50,13 +52,15 @@ def _load():
         lib.oracle_chi0.argtypes = [i, i, i, i, i, ctypes.POINTER(_dp), ctypes.POINTER(_dp), ctypes.POINTER(_dp), d,
                                     d, _dp, i]
         lib.oracle_jacobi_eigh.argtypes = [i, i, _dp, _dp, _dp, i, d]
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.oracle_ao2mo.argtypes = [i, i, ip, ip, i, i, i, _dp, _dp, _dp, _dp, i, ip, _dp, i]
         lib.oracle_vhalf.argtypes = [i, i, _dp, _dp]
         lib.oracle_sandwich.argtypes = [i, i, _dp, _dp, _dp, i]
         lib.oracle_logdet_cholesky.argtypes = [i, i, _dp, _dp, _dp]
         lib.oracle_logabsdet_lu.argtypes = [i, i, _dp, _dp]
         lib.oracle_energy_sum.argtypes = [i, i, _dp, _dp, _dp, _dp]
         lib.oracle_max_threads.argtypes = []
-        for f in (lib.oracle_chi0, lib.oracle_jacobi_eigh, lib.oracle_vhalf, lib.oracle_sandwich,
+        for f in (lib.oracle_chi0, lib.oracle_ao2mo, lib.oracle_jacobi_eigh, lib.oracle_vhalf, lib.oracle_sandwich,
                   lib.oracle_logdet_cholesky, lib.oracle_logabsdet_lu, lib.oracle_energy_sum, lib.oracle_max_threads):
             f.restype = ctypes.c_int
         _lib = lib
@@ -101,6 +105,48 @@ def chi0(C_blocks: Sequence[np.ndarray], eps_occ: Sequence[np.ndarray], eps_virt
     if rc != 0:
         raise OracleError("oracle_chi0 rc=%d" % rc)
     return out
+
+
+def ao2mo(is_complex: bool, n_bas_atom: Sequence[int], n_fit_atom: Sequence[int], n_occ: int, n_virt: int,
+          padf_k: np.ndarray, padf_kq: np.ndarray, mo_k: np.ndarray, mo_kq: np.ndarray,
+          entries: Optional[np.ndarray] = None, n_threads: Optional[int] = None) -> np.ndarray:
+    """MO-basis fit coefficients of one (q, k) pair from the PADF arrays at k
+    and k+q and the MO coefficients at k (occupied side) and k+q (virtual
+    side).  Returns [n_aux, n_occ*n_virt], or, with entries ([n, 2] int
+    (gamma, t) rows), the n selected values."""
+    nb = np.ascontiguousarray(n_bas_atom, np.int32)
+    nf = np.ascontiguousarray(n_fit_atom, np.int32)
+    arrs = [_f64(a, is_complex) for a in (padf_k, padf_kq, mo_k, mo_kq)]
+    n_mo = arrs[2].shape[1]
+    n_aux = int(nf.sum())
+    ip = ctypes.POINTER(ctypes.c_int)
+    if entries is None:
+        out = np.zeros((n_aux, n_occ * n_virt), np.complex128 if is_complex else np.float64)
+        ne, ep = 0, ctypes.cast(None, ip)
+    else:
+        entries = np.ascontiguousarray(entries, np.int32).reshape(-1, 2)
+        out = np.zeros(entries.shape[0], np.complex128 if is_complex else np.float64)
+        ne, ep = entries.shape[0], entries.ctypes.data_as(ip)
+    rc = _load().oracle_ao2mo(int(is_complex), len(nb), nb.ctypes.data_as(ip), nf.ctypes.data_as(ip), int(n_occ),
+                              int(n_virt), int(n_mo), *[_ptr(a.view(np.float64)) for a in arrs], ne, ep,
+                              _ptr(out.view(np.float64)), int(n_threads or max_threads()))
+    if rc != 0:
+        raise OracleError("oracle_ao2mo rc=%d" % rc)
+    return out
+
+
+def ao2mo_block(problem, q: int, j: int, entries: Optional[np.ndarray] = None,
+                n_threads: Optional[int] = None) -> np.ndarray:
+    """C(q, k_j) of an AO-form problem (``synth.AOProblem``)."""
+    k, kq = int(problem.grid.pair_k[q, j]), int(problem.grid.pair_kq[q, j])
+    return ao2mo(problem.is_complex, problem.n_bas_atom, problem.n_fit_atom, problem.n_occ, problem.n_virt,
+                 problem.padf(k), problem.padf(kq), problem.mo(k), problem.mo(kq), entries, n_threads)
+
+
+def _blocks(problem, q: int, n_threads: Optional[int] = None):
+    if hasattr(problem, "padf"):
+        return [ao2mo_block(problem, q, j, n_threads=n_threads) for j in range(problem.n_k)]
+    return [problem.C(q, j) for j in range(problem.n_k)]
 
 
 def jacobi_eigh(A: np.ndarray, max_sweeps: int = 100, tol: float = 1e-14) -> Tuple[np.ndarray, np.ndarray, int]:
@@ -176,7 +222,7 @@ def term(problem, q: int, w: int, Vh: Optional[np.ndarray] = None, n_threads: Op
     """One integrand term eps_{q,w} = ln det(1 - Pi) + Tr Pi of a synthetic
     problem (``paper_2505_06021_gb300.synth.Problem``)."""
     if C_blocks is None:
-        C_blocks = [problem.C(q, j) for j in range(problem.n_k)]
+        C_blocks = _blocks(problem, q, n_threads)
     eo = [problem.eps_pair(q, j)[0] for j in range(problem.n_k)]
     ev = [problem.eps_pair(q, j)[1] for j in range(problem.n_k)]
     if Vh is None:
@@ -197,7 +243,7 @@ def energy(problem, n_threads: Optional[int] = None, qs: Optional[Sequence[int]]
     trpi = np.full((problem.n_q, problem.n_w), np.nan)
     for q in qs:
         Vh = vhalf(problem.V(q))
-        C_blocks = [problem.C(q, j) for j in range(problem.n_k)]
+        C_blocks = _blocks(problem, q, n_threads)
         for w in ws:
             t = term(problem, q, w, Vh=Vh, n_threads=n_threads, C_blocks=C_blocks)
             lndet[q, w], trpi[q, w] = t["lndet"], t["trPi"]

@@ -106,6 +106,113 @@ int oracle_chi0(int is_complex, int n_aux, int n_occ, int n_virt, int n_k, const
   return 0;
 }
 
+/* ---------------------------------------- AO -> MO fit coefficients -- */
+/*
+ * Fit coefficients of the orbital pair psi*_i(k) psi_a(k+q) from the
+ * k-dependent pair-atomic (PADF) fit coefficients, Sec. 2.2:
+ *
+ * - PADF: a product of basis functions mu on atom A and nu on atom B is
+ *   fitted by fit functions on A and on B only;
+ * - in reciprocal space, with C_{nu mu alpha}(k) the lattice sum of the
+ *   cell-pair coefficients times e^{i k.dR} (the k-dependent coefficients),
+ *     chi*_mu(k) chi_nu(k+q) = sum_gamma B^{mu nu}_gamma f_gamma(q),
+ *     B^{mu nu}_gamma = [gamma on atom(mu)] C_{nu mu gamma}(k+q)
+ *                     + [gamma on atom(nu)] conj(C_{mu nu gamma}(k));
+ * - with the KS states psi_n(k) = sum_mu c_{mu n}(k) chi_mu(k) the pair
+ *   coefficients are
+ *     C_{gamma, ia}(q, k) = sum_{mu, nu} conj(c_{mu i}(k)) c_{nu a}(k+q)
+ *                           B^{mu nu}_gamma,
+ *   i an occupied state at k, a a virtual state at k+q (the pair convention
+ *   of oracle_chi0).
+ *
+ * Layout.  Atoms carry nb[A] basis and nf[A] fit functions, numbered atom by
+ * atom.  The PADF array of a k-point is n_bas x S, S = sum_A nb[A] nf[A]:
+ * row nu, column s(mu, alpha) = sum_{A' < A} nb[A'] nf[A']
+ * + (mu - first basis function of A) nf[A] + alpha_loc, A = atom(mu),
+ * alpha_loc the index of alpha among A's fit functions.  MO arrays are
+ * n_bas x n_mo, occupied columns 0..n_occ-1, virtual columns n_occ..
+ * n_occ+n_virt-1.  padf_k / mo_k belong to k, padf_kq / mo_kq to k+q.
+ *
+ * Output: entries (gamma, t), t = i*n_virt + a.  With entries == NULL all
+ * n_aux x n_occ*n_virt values are written row-major into out; otherwise
+ * out[e] receives the entry (entries[2e], entries[2e+1]).  Every entry is
+ * the double sum over (mu, nu) written out, B formed term by term.
+ */
+int oracle_ao2mo(int is_complex, int n_atoms, const int *nb, const int *nf, int n_occ, int n_virt, int n_mo,
+                 const double *padf_k, const double *padf_kq, const double *mo_k, const double *mo_kq,
+                 int n_entries, const int *entries, double *out, int n_threads) {
+  if (n_atoms <= 0 || n_occ <= 0 || n_virt <= 0 || n_occ + n_virt > n_mo) return 1;
+  int n_bas = 0, n_aux = 0, S = 0;
+  for (int A = 0; A < n_atoms; ++A) {
+    if (nb[A] <= 0 || nf[A] <= 0) return 1;
+    n_bas += nb[A];
+    n_aux += nf[A];
+    S += nb[A] * nf[A];
+  }
+  if (n_mo > n_bas) return 1;
+  int *atom_of_bas = (int *)malloc(sizeof(int) * n_bas);
+  int *bas_first = (int *)malloc(sizeof(int) * n_atoms);
+  int *fit_first = (int *)malloc(sizeof(int) * n_atoms);
+  int *pf_first = (int *)malloc(sizeof(int) * n_atoms);
+  if (!atom_of_bas || !bas_first || !fit_first || !pf_first) return 1;
+  for (int A = 0, b = 0, f = 0, p = 0; A < n_atoms; ++A) {
+    bas_first[A] = b;
+    fit_first[A] = f;
+    pf_first[A] = p;
+    for (int m = 0; m < nb[A]; ++m) atom_of_bas[b + m] = A;
+    b += nb[A];
+    f += nf[A];
+    p += nb[A] * nf[A];
+  }
+  const int n_ov = n_occ * n_virt;
+  const long total = entries ? (long)n_entries : (long)n_aux * n_ov;
+  if (n_threads < 1) n_threads = 1;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(n_threads)
+  for (long e = 0; e < total; ++e) {
+    const int gamma = entries ? entries[2 * e] : (int)(e / n_ov);
+    const int t = entries ? entries[2 * e + 1] : (int)(e % n_ov);
+    const int i = t / n_virt, a = n_occ + t % n_virt;
+    int G = 0;
+    while (G + 1 < n_atoms && gamma >= fit_first[G + 1]) ++G;
+    const int g_loc = gamma - fit_first[G];
+    nsum_t sr = {0, 0}, si = {0, 0};
+    for (int mu = 0; mu < n_bas; ++mu) {
+      for (int nu = 0; nu < n_bas; ++nu) {
+        double br = 0.0, bi = 0.0;
+        if (atom_of_bas[mu] == G) { /* C_{nu mu gamma}(k+q) */
+          const size_t x = (size_t)nu * S + pf_first[G] + (size_t)(mu - bas_first[G]) * nf[G] + g_loc;
+          br += re_(padf_kq, is_complex, x);
+          bi += im_(padf_kq, is_complex, x);
+        }
+        if (atom_of_bas[nu] == G) { /* conj(C_{mu nu gamma}(k)) */
+          const size_t x = (size_t)mu * S + pf_first[G] + (size_t)(nu - bas_first[G]) * nf[G] + g_loc;
+          br += re_(padf_k, is_complex, x);
+          bi -= im_(padf_k, is_complex, x);
+        }
+        if (br == 0.0 && bi == 0.0) continue;
+        const size_t xi = (size_t)mu * n_mo + i, xa = (size_t)nu * n_mo + a;
+        /* conj(c_{mu i}(k)) c_{nu a}(k+q) */
+        const double cr = re_(mo_k, is_complex, xi), ci = -im_(mo_k, is_complex, xi);
+        const double dr = re_(mo_kq, is_complex, xa), di = im_(mo_kq, is_complex, xa);
+        const double pr = cr * dr - ci * di, pi = cr * di + ci * dr;
+        nsum_add(&sr, pr * br - pi * bi);
+        if (is_complex) nsum_add(&si, pr * bi + pi * br);
+      }
+    }
+    if (is_complex) {
+      out[2 * e] = nsum_get(&sr);
+      out[2 * e + 1] = nsum_get(&si);
+    } else {
+      out[e] = nsum_get(&sr);
+    }
+  }
+  free(atom_of_bas);
+  free(bas_first);
+  free(fit_first);
+  free(pf_first);
+  return 0;
+}
+
 /* -------------------------------------------------- Hermitian Jacobi eig -- */
 /*
  * Cyclic Jacobi eigendecomposition A = U diag(lam) U^H of a Hermitian matrix

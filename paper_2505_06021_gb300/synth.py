@@ -46,7 +46,7 @@ BASE_SEED = 20250506
 # random streams
 # ----------------------------------------------------------------------------
 
-_TAGS = {"eps": 1, "C": 2, "V": 3, "batch": 4, "serve": 5}
+_TAGS = {"eps": 1, "C": 2, "V": 3, "batch": 4, "serve": 5, "padf": 6, "mo": 7}
 
 
 def _rng(seed: int, tag: str, *idx: int) -> np.random.Generator:
@@ -284,6 +284,93 @@ class Problem:
         return self.n_aux * self.n_ov * (16 if self.is_complex else 8) * self.n_q * self.n_k
 
 
+class AOProblem(Problem):
+    """An RPA job given in the atomic-orbital form of Sec. 2.2 instead of by
+    its MO-basis fit coefficients C_{P,ia}(q, k).
+
+    Atoms A = 0..n_atoms-1 carry n_bas_atom[A] primary basis functions and
+    n_fit_atom[A] fit functions, both numbered atom by atom (n_aux = sum of
+    n_fit_atom).  Per k-point kappa of K_G the job holds
+
+    * the k-dependent pair-atomic fit coefficients C_{nu mu alpha}(kappa) of
+      the PADF expansion (alpha a fit function on the atom of mu), stored as
+      ``padf(kappa)``: [n_bas, S] with S = sum_A n_bas_atom[A] n_fit_atom[A]
+      and column s = pf_off[A] + (mu - bas_off[A]) n_fit_atom[A] + alpha_loc;
+    * the MO coefficients c_{mu n}(kappa), ``mo(kappa)``: [n_bas, n_mo],
+      n_mo = n_occ + n_virt, occupied columns first.
+
+    Draws: PADF entries Gaussian (complex: variance split between the real
+    and imaginary parts) with variance n_atoms / (2 N_ov), so that for
+    orthonormal MOs the MO-basis coefficients have the variance 1/N_ov of
+    ``Problem.C``; MO coefficients are the first n_mo columns of a Haar-random
+    unitary (orthogonal when real).  The MO-basis coefficients themselves are
+    a result of the method and are not generated here.
+    """
+
+    def __init__(self, base: Problem, n_bas_atom: Sequence[int], n_fit_atom: Sequence[int]):
+        super().__init__(**{f.name: getattr(base, f.name) for f in dataclasses.fields(Problem)})
+        self.n_bas_atom = tuple(int(x) for x in n_bas_atom)
+        self.n_fit_atom = tuple(int(x) for x in n_fit_atom)
+        if len(self.n_bas_atom) != len(self.n_fit_atom) or sum(self.n_fit_atom) != self.n_aux:
+            raise ValueError("fit functions per atom must sum to n_aux")
+        if self.n_occ + self.n_virt > self.n_bas:
+            raise ValueError("n_occ + n_virt exceeds the basis size")
+
+    @property
+    def n_atoms(self) -> int:
+        return len(self.n_bas_atom)
+
+    @property
+    def n_bas(self) -> int:
+        return sum(self.n_bas_atom)
+
+    @property
+    def n_mo(self) -> int:
+        return self.n_occ + self.n_virt
+
+    @property
+    def n_pf(self) -> int:
+        return sum(b * f for b, f in zip(self.n_bas_atom, self.n_fit_atom))
+
+    @property
+    def n_kpts(self) -> int:
+        return int(self.grid.kpts.shape[0])
+
+    def C(self, q: int, j: int, out: Optional[np.ndarray] = None) -> np.ndarray:
+        raise TypeError("an AO job has no stored MO-basis fit coefficients")
+
+    def padf(self, kappa: int) -> np.ndarray:
+        rng = _rng(self.seed, "padf", kappa)
+        out = np.empty((self.n_bas, self.n_pf), self.dtype)
+        v = out.view(np.float64)
+        rng.standard_normal(out=v, dtype=np.float64)
+        var = self.n_atoms / (2.0 * self.n_ov)
+        v *= math.sqrt(0.5 * var) if self.is_complex else math.sqrt(var)
+        return out
+
+    def mo(self, kappa: int) -> np.ndarray:
+        rng = _rng(self.seed, "mo", kappa)
+        n = self.n_bas
+        if self.is_complex:
+            z = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / math.sqrt(2.0)
+        else:
+            z = rng.standard_normal((n, n))
+        Qm, R = np.linalg.qr(z)
+        d = np.diagonal(R)
+        Qm = Qm * (d / np.abs(d))[None, :]
+        return np.ascontiguousarray(Qm[:, :self.n_mo].astype(self.dtype))
+
+    def padf_bytes(self) -> int:
+        return self.n_bas * self.n_pf * (16 if self.is_complex else 8) * self.n_kpts
+
+
+def make_ao_problem(name: str, *, is_complex: bool, n_bas_atom: Sequence[int], n_fit_atom: Sequence[int],
+                    n_occ: int, n_virt: int, grid: KQGrid, n_w: int, seed: int, **kw) -> AOProblem:
+    base = make_problem(name, is_complex=is_complex, n_aux=int(sum(n_fit_atom)), n_occ=n_occ, n_virt=n_virt,
+                        grid=grid, n_w=n_w, seed=seed, **kw)
+    return AOProblem(base, n_bas_atom, n_fit_atom)
+
+
 def _bands(seed: int, grid: KQGrid, n_occ: int, n_virt: int, dispersion: float) -> Tuple[np.ndarray, np.ndarray]:
     rng = _rng(seed, "eps")
     occ_c = np.sort(rng.uniform(-1.0, -0.3, n_occ))
@@ -320,6 +407,16 @@ def config1(n_w: int = 20, seed: Optional[int] = None, n_aux: int = 512, n_occ: 
     weights), N_aux=512, N_occ=32, N_virt=224, 20 frequencies."""
     return make_problem("periodic2d-c128-N%d" % n_aux, is_complex=True, n_aux=n_aux, n_occ=n_occ, n_virt=n_virt,
                         grid=regular_kq_grid(kdims), n_w=n_w, seed=BASE_SEED + 1 if seed is None else seed)
+
+
+def config1_ao(n_w: int = 20, seed: Optional[int] = None, n_bas_atom=(128, 128), n_fit_atom=(256, 256),
+               n_occ: int = 32, n_virt: int = 224, kdims=(4, 4, 1)) -> AOProblem:
+    """The 2-D periodic workload in AO form: two atoms with 128 basis and 256
+    fit functions each (N_bas = 256 = N_occ + N_virt, N_aux = 512), PADF and
+    MO coefficients per k-point of the 4x4x1 grid, 20 frequencies."""
+    return make_ao_problem("periodic2d-ao-N%d" % sum(n_fit_atom), is_complex=True, n_bas_atom=n_bas_atom,
+                           n_fit_atom=n_fit_atom, n_occ=n_occ, n_virt=n_virt, grid=regular_kq_grid(kdims), n_w=n_w,
+                           seed=BASE_SEED + 5 if seed is None else seed)
 
 
 def config2(n_w: int = 16, seed: Optional[int] = None, n_aux: int = 768, n_occ: int = 32, n_virt: int = 480,
