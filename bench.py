@@ -12,6 +12,7 @@ timed beside it with |dE_c| between the two.  Prints one JSON line.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|mixed]
     python bench.py --workload batch     # 64 uneven instances per step (rpa_energy_batch)
     python bench.py --workload serving   # Poisson stream of jobs (rpa_submit), p50/p99 latency
+    python bench.py --workload periodic2d-ao  # the same job given as PADF + MO coefficients
     python bench.py --impl reference ... # the CPU oracle as reference arm
 
 Under torchrun (N > 1) every rank runs its own job on its own GPU (weak
@@ -48,9 +49,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--workload", default="periodic2d", choices=["periodic2d", "slab", "batch", "serving"])
+    ap.add_argument("--workload", default="periodic2d", choices=["periodic2d", "slab", "batch", "serving",
+                                                                         "periodic2d-ao"])
     ap.add_argument("--no-fp64", action="store_true", help="periodic2d: skip the FP64 comparison step")
     ap.add_argument("--n-inst", type=int, default=64, help="batch: instances per step")
+    ap.add_argument("--ao-scale", type=int, default=1,
+                    help="periodic2d-ao, profiling only: divide basis, fit, occupied and virtual counts by this")
     ap.add_argument("--serve-jobs", type=int, default=200, help="serving: jobs in the stream")
     ap.add_argument("--serve-load", type=float, default=0.8, help="serving: arrival rate / measured capacity")
     ap.add_argument("--serve-cap-gb", type=float, default=120.0, help="serving: HBM admission cap")
@@ -718,6 +722,166 @@ def run_serving(args):
         print(json.dumps(line), flush=True)
 
 
+def ao_flops(p):
+    """Algorithmic FP64 flops of the AO -> MO transform of a whole AO-form job
+    (8 per complex multiply-add, 2 per real one): the half-transforms
+    n_bas * S * n_occ per k-point used as k and n_bas * S * n_virt per k-point
+    used as k+q, then 2 * sum_A nb_A nf_A * N_ov per (q, k) pair."""
+    f = 8.0 if p.is_complex else 2.0
+    ko = len(set(p.grid.pair_k.reshape(-1).tolist()))
+    kv = len(set(p.grid.pair_kq.reshape(-1).tolist()))
+    half = f * p.n_bas * p.n_pf * (ko * p.n_occ + kv * p.n_virt)
+    asm = f * 2.0 * p.n_pf * p.n_ov * p.n_q * p.n_k
+    return half, asm
+
+
+def run_ao(args):
+    """The 2-D periodic job given in AO form (two atoms, PADF and MO
+    coefficients per k-point): the library forms each q's MO-basis fit
+    coefficients on the device just before its chi0 (rpa_energy)."""
+    import numpy as np
+    import torch
+
+    import paper_2505_06021_gb300 as rpa
+    from paper_2505_06021_gb300 import synth
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    prec = "mixed" if args.prec in ("auto", "mixed") else "fp64"
+    pc = rpa.PREC_MIXED if prec == "mixed" else rpa.PREC_FP64
+    sc = max(1, args.ao_scale)
+    p = synth.config1_ao(n_bas_atom=(128 // sc,) * 2, n_fit_atom=(256 // sc,) * 2, n_occ=32 // sc, n_virt=224 // sc)
+    if args.n_q:
+        g = p.grid
+        g.pair_k, g.pair_kq, g.w_q, g.qpts = g.pair_k[:args.n_q], g.pair_kq[:args.n_q], g.w_q[:args.n_q], \
+            g.qpts[:args.n_q]
+    t_gen = time.perf_counter()
+    tens = rpa.upload_ao_problem(p, "cuda:%d" % local)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    job = rpa.job_from_ao_problem(p, tens, prec=pc)
+    ctx = rpa.Context(local, n_slices=args.slices)
+    for _ in range(args.warmup):
+        ctx.energy(job)
+    ext = torch.cuda.ExternalStream(ctx.stream_handle)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.profile(True)
+    n0 = ctx.launches
+    e0.record(ext)
+    res = None
+    for _ in range(args.steps):
+        res = ctx.energy(job)
+    e1.record(ext)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.launches - n0
+    ms_max = allreduce_max(e0.elapsed_time(e1), world)
+    jobs_per_s = world * args.steps / (ms_max / 1e3)
+    half, asm = ao_flops(p)
+    ao_ms, ao_n = prof["ao2mo"]
+    ach = (half + asm) * args.steps / (ao_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "kernel": "ao_half_kernel + ao_assemble_kernel (AO -> MO transform, FP64)",
+            "peak_source": "derived FP64 DFMA peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+            "algorithmic_tflop_per_job": (half + asm) / 1e12, "launches_per_job": ao_n // max(args.steps, 1)}
+    kernel_ms = {k: {"ms": v[0] / args.steps, "launches": v[1] // max(args.steps, 1)} for k, v in prof.items()
+                 if v[1]}
+    line = {"metric": METRIC, "value": jobs_per_s, "unit": "jobs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "bf16-slices->f64",
+            "data": "synthetic (seeded PADF and MO coefficients with the shapes of the 2-D periodic workload)",
+            "config": {"workload": "periodic2d-ao: the 2-D periodic job (16 q x 16 k, N_aux=%d, N_occ=%d, "
+                                   "N_virt=%d, 20 frequencies) in AO form: 2 atoms x (%d basis, %d fit "
+                                   "functions), N_bas=%d, PADF %.1f GB + MO coefficients per k-point; MO-basis "
+                                   "coefficients formed per q on the device%s"
+                                   % (p.n_aux, p.n_occ, p.n_virt, p.n_bas_atom[0], p.n_fit_atom[0], p.n_bas,
+                                      p.padf_bytes() / 1e9,
+                                      "" if sc == 1 and not args.n_q else " [reduced: profiling case]"),
+                       "n_q": p.n_q, "n_k": p.n_k, "n_aux": p.n_aux, "n_occ": p.n_occ, "n_virt": p.n_virt,
+                       "n_w": p.n_w, "n_bas": p.n_bas, "n_atoms": p.n_atoms, "chi0_prec": prec,
+                       "l2": "inputs larger than L2 (PADF %.1f GB)" % (p.padf_bytes() / 1e9),
+                       "parallelism": "one job per GPU (weak scaling)"},
+            "chi0_tflops": p.chi0_flops() * world * args.steps / (ms_max / 1e3) / 1e12, "Ec": res["Ec"],
+            "gpu_launches": launches, "kernel_ms_per_step": kernel_ms, "roofline": roof, "clocks": clk,
+            "input_gen_s": t_gen}
+    if prec == "mixed" and not args.no_fp64 and not args.n_q:
+        jf = job.with_prec(rpa.PREC_FP64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rf = ctx.energy(jf)
+        tf = time.perf_counter() - t0
+        rel = np.abs(res["eps"] - rf["eps"]) / np.abs(rf["eps"])
+        line["fp64"] = {"value": 1.0 / tf, "unit": "jobs/s", "Ec": rf["Ec"],
+                        "abs_dEc_mixed_vs_fp64_Ha": abs(res["Ec"] - rf["Ec"]),
+                        "max_rel_err_per_term": float(rel.max())}
+    if not args.no_e2e and not args.n_q:
+        # host-resident AO inputs (pinned) copied to the device inside the timed region
+        hp = [t.cpu().pin_memory() for t in tens["padf"]]
+        hm = [t.cpu().pin_memory() for t in tens["mo"]]
+        hv = [t.cpu().pin_memory() for t in tens["V"]]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for d, h in zip(tens["padf"] + tens["mo"] + tens["V"], hp + hm + hv):
+                d.copy_(h, non_blocking=True)
+            torch.cuda.synchronize()
+            rh = ctx.energy(job)
+        te = allreduce_max(time.perf_counter() - t0, world)
+        h2d = sum(t.numel() * t.element_size() for t in hp + hm + hv)
+        line["e2e"] = {"value": world * args.e2e_steps / te, "unit": "jobs/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": 8 * (1 + 3 * p.n_q * p.n_w) + 4, "steps": args.e2e_steps,
+                       "Ec_matches_device": bool(rh["Ec"] == res["Ec"])}
+    else:
+        line["e2e"] = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        import oracle
+
+        rng = np.random.default_rng(3)
+        ent = np.stack([rng.integers(0, p.n_aux, 4000), rng.integers(0, p.n_ov, 4000)], axis=1)
+        t0 = time.perf_counter()
+        oracle.ao2mo_block(p, 0, 0, entries=ent)
+        t_ent = (time.perf_counter() - t0) / len(ent)
+        s = cpu_oracle_sample_ao(p)
+        job_s = p.n_q * p.n_k * p.n_aux * p.n_ov * t_ent + p.n_q * s["vhalf_s"] + p.n_q * p.n_w * s["term_s"]
+        line["cpu_baseline"] = {"value": 1.0 / job_s, "unit": "jobs/s", "cores": s["threads"], "kind": "oracle",
+                                "sample": "4000 entries of one (q, k) block of the AO -> MO transform (double "
+                                          "sum over mu, nu), one (q=0, w=0) term and one V(q)^1/2; job time "
+                                          "extrapolated", "extrapolated_job_s": job_s}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def cpu_oracle_sample_ao(p):
+    """cpu_oracle_sample for an AO-form problem: the term's coefficient blocks
+    are random stand-ins of the right shape (the term's cost does not depend
+    on their values; the transform is timed separately)."""
+    import numpy as np
+
+    import oracle
+
+    nthr = oracle.max_threads()
+    t0 = time.perf_counter()
+    Vh = oracle.vhalf(p.V(0))
+    t1 = time.perf_counter()
+    rng = np.random.default_rng(0)
+    C = [(rng.standard_normal((p.n_aux, p.n_ov)) + 1j * rng.standard_normal((p.n_aux, p.n_ov))) /
+         math.sqrt(2 * p.n_ov) for _ in range(p.n_k)]
+    t2 = time.perf_counter()
+    oracle.term(p, 0, 0, Vh=Vh, C_blocks=C)
+    t3 = time.perf_counter()
+    return {"vhalf_s": t1 - t0, "term_s": t3 - t2, "threads": nthr}
+
+
 def rpa_mixed_tensor_flops(p, ctx, s=4):
     """Tensor-core flops the split-precision chi0 executes for the whole job:
     slice pairs x padded 128 x 64 (complex) / 128 x 128 (real) lower tiles x
@@ -740,6 +904,8 @@ def main():
         run_batch(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "periodic2d-ao":
+        run_ao(args)
     else:
         run_ours(args)  # periodic2d (default) or slab
 

@@ -81,6 +81,33 @@ typedef struct {
   int max_inflight;     /* serving: jobs admitted at once (0 = 64) */
 } rpa_config;
 
+/* Atomic-orbital form of a job's fit coefficients (Sec. 2.2, PADF in
+ * reciprocal space and the transformation to KS states).  Instead of the
+ * MO-basis coefficients C(q, k_j) the job gives, per k-point kappa of K_G:
+ *   - padf[kappa]: the k-dependent pair-atomic fit coefficients
+ *     C_{nu mu alpha}(kappa), alpha a fit function on the atom of mu, as an
+ *     n_bas x S matrix, S = sum_A n_bas_atom[A] n_fit_atom[A]: row nu, column
+ *     sum_{A' < A} n_bas_atom[A'] n_fit_atom[A'] + (mu - first basis function
+ *     of A) n_fit_atom[A] + (alpha - first fit function of A), A = atom(mu);
+ *   - mo[kappa]: the KS (MO) coefficients c_{mu n}(kappa), n_bas x n_mo,
+ *     occupied states in columns 0..n_occ-1, virtual states in columns
+ *     n_occ..n_occ+n_virt-1.
+ * Basis and fit functions are numbered atom by atom.  The library forms
+ *   C_{gamma,ia}(q, k) = sum_{mu nu} conj(c_{mu i}(k)) c_{nu a}(k+q) B^{mu nu}_gamma,
+ *   B^{mu nu}_gamma = [gamma on atom(mu)] C_{nu mu gamma}(k+q)
+ *                   + [gamma on atom(nu)] conj(C_{mu nu gamma}(k)),
+ * on the fly, one q at a time (k = k_j from pair_k, k+q from pair_kq), so the
+ * MO-basis coefficients of the whole job never reside in memory at once.
+ * Device memory only; the arrays are borrowed like C. */
+typedef struct {
+  int n_atoms;
+  const int *n_bas_atom;   /* host [n_atoms]: basis functions per atom (> 0) */
+  const int *n_fit_atom;   /* host [n_atoms]: fit functions per atom (> 0), sum = n_aux */
+  int n_mo;                /* columns of every mo[kappa] (>= n_occ + n_virt, <= n_bas) */
+  const void *const *padf; /* host [n_kpts] of device pointers, n_bas x S each */
+  const void *const *mo;   /* host [n_kpts] of device pointers, n_bas x n_mo each */
+} rpa_ao;
+
 typedef struct {
   int is_complex;                 /* 1: complex128 data; 0: real float64 (Gamma only) */
   int n_aux, n_occ, n_virt;       /* N, occupied and virtual bands per k */
@@ -96,10 +123,13 @@ typedef struct {
   const double *zeta_w;           /* host [n_w]: frequency weights */
   const double *eps_occ;          /* [n_kpts*n_occ], device or host (mem) */
   const double *eps_virt;         /* [n_kpts*n_virt], device or host (mem) */
-  const void *const *C;           /* host array [n_q*n_k] of pointers to C(q,k_j) */
+  const void *const *C;           /* host array [n_q*n_k] of pointers to C(q,k_j); NULL with ao */
   const void *const *V;           /* host array [n_q] of pointers to V(q) */
   int prec;                       /* RPA_PREC_* */
   int mem;                        /* RPA_MEM_* */
+  const rpa_ao *ao;               /* NULL, or the AO form of the fit coefficients (C must then be
+                                     NULL and mem RPA_MEM_DEVICE; rpa_energy, rpa_chi0 and
+                                     rpa_ao2mo take such jobs, the batch and serving calls do not) */
 } rpa_job;
 
 /* Create a context on cfg->device (NULL cfg = defaults).  Allocates nothing
@@ -124,8 +154,18 @@ rpa_status rpa_job_footprint(const rpa_job *job, size_t *bytes);
 
 /* Step A3: chi0(q, i omega_w) for every w, written to the device buffer
  * chi_out [n_w][n_aux][n_aux] (full Hermitian matrices; complex128 or
- * float64).  Asynchronous on `stream`; job->mem must be RPA_MEM_DEVICE. */
+ * float64).  Asynchronous on `stream`; job->mem must be RPA_MEM_DEVICE.  For
+ * an AO-form job the coefficients of q are formed first, as by rpa_ao2mo. */
 rpa_status rpa_chi0(rpa_ctx *ctx, const rpa_job *job, int q, void *chi_out, void *stream);
+
+/* The AO -> MO transform of Sec. 2.2 for one q (job->ao must be set): writes
+ * C(q, k_j) for j = 0..n_k-1 into the device buffer C_out [n_k][n_aux]
+ * [n_occ*n_virt] (the layout of rpa_job.C).  FP64 throughout: each k-point's
+ * PADF array is first contracted with its MO coefficients over its row index
+ * (occupied columns for the k side, virtual ones for the k+q side), then each
+ * pair sums over the basis functions on gamma's atom.  Asynchronous on
+ * `stream`; intermediate arrays live in the context's workspace. */
+rpa_status rpa_ao2mo(rpa_ctx *ctx, const rpa_job *job, int q, void *C_out, void *stream);
 
 /* Steps A4-A6 for one q: from chi (device [n_w][n_aux][n_aux], as written by
  * rpa_chi0) computes out[2*w] = ln det(1 - Pi) and out[2*w+1] = Tr Pi,
@@ -138,7 +178,10 @@ rpa_status rpa_logdet(rpa_ctx *ctx, const rpa_job *job, int q, const void *chi, 
  * stream: *Ec receives E_c; eps_qw (host [n_q*n_w] or NULL) the integrand
  * table eps_{q,w} = ln det + Tr; parts (host [n_q*n_w*2] or NULL) the pairs
  * (ln det(1 - Pi), Tr Pi).  Inputs on the device or, with mem ==
- * RPA_MEM_HOST, on the host (staged per q, copies overlapped with compute). */
+ * RPA_MEM_HOST, on the host (staged per q, copies overlapped with compute).
+ * AO-form jobs (device memory): the half-transformed PADF arrays of every
+ * k-point are formed once, then each q's MO-basis coefficients just before
+ * its chi0. */
 rpa_status rpa_energy(rpa_ctx *ctx, const rpa_job *job, double *Ec, double *eps_qw, double *parts);
 
 /* Many independent jobs (uneven sizes) in one call: the split-precision
@@ -209,7 +252,8 @@ void *rpa_stream(rpa_ctx *ctx);
 #define RPA_K_REDUCE 5   /* quadrature */
 #define RPA_K_SLICE 6    /* operand preparation of the split-precision path */
 #define RPA_K_CHI0_RED 7 /* split-K reduction of the tensor-core chi0 */
-#define RPA_K_COUNT 8
+#define RPA_K_AO2MO 8    /* AO -> MO transform of the fit coefficients (AO-form jobs) */
+#define RPA_K_COUNT 9
 rpa_status rpa_profile(rpa_ctx *ctx, int enable);
 rpa_status rpa_profile_read(rpa_ctx *ctx, double *ms, uint64_t *launches);
 

@@ -25,12 +25,12 @@ STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "NOMEM", 3: "CUDA", 4: "NOTPD", 5: "TIME
 
 # Entry points declared in include/rpa.h
 EXPORTS = ("rpa_create", "rpa_destroy", "rpa_last_error", "rpa_job_validate", "rpa_job_footprint", "rpa_chi0",
-           "rpa_logdet", "rpa_energy", "rpa_energy_batch", "rpa_submit", "rpa_poll", "rpa_wait",
+           "rpa_ao2mo", "rpa_logdet", "rpa_energy", "rpa_energy_batch", "rpa_submit", "rpa_poll", "rpa_wait",
            "rpa_serving_stats", "rpa_serving_peak", "rpa_test_drop_copy", "rpa_kernel_launches", "rpa_stream",
            "rpa_profile", "rpa_profile_read", "rpa_logdet_noalloc", "rpa_noalloc_last_error")
 
 # kernel classes of rpa_profile_read
-KERNEL_CLASSES = ("dtab", "chi0", "vfactor", "sandwich", "logdet", "reduce", "slice", "chi0_reduce")
+KERNEL_CLASSES = ("dtab", "chi0", "vfactor", "sandwich", "logdet", "reduce", "slice", "chi0_reduce", "ao2mo")
 
 
 class RpaError(RuntimeError):
@@ -44,6 +44,12 @@ class rpa_config(ctypes.Structure):
                 ("timeout_s", ctypes.c_double), ("max_inflight", ctypes.c_int)]
 
 
+class rpa_ao(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int), ("n_bas_atom", ctypes.POINTER(ctypes.c_int)),
+                ("n_fit_atom", ctypes.POINTER(ctypes.c_int)), ("n_mo", ctypes.c_int),
+                ("padf", ctypes.POINTER(ctypes.c_void_p)), ("mo", ctypes.POINTER(ctypes.c_void_p))]
+
+
 class rpa_job(ctypes.Structure):
     _fields_ = [("is_complex", ctypes.c_int), ("n_aux", ctypes.c_int), ("n_occ", ctypes.c_int),
                 ("n_virt", ctypes.c_int), ("n_q", ctypes.c_int), ("n_k", ctypes.c_int), ("n_w", ctypes.c_int),
@@ -52,7 +58,8 @@ class rpa_job(ctypes.Structure):
                 ("zeta_k", ctypes.c_double), ("omega", ctypes.POINTER(ctypes.c_double)),
                 ("zeta_w", ctypes.POINTER(ctypes.c_double)), ("eps_occ", ctypes.c_void_p),
                 ("eps_virt", ctypes.c_void_p), ("C", ctypes.POINTER(ctypes.c_void_p)),
-                ("V", ctypes.POINTER(ctypes.c_void_p)), ("prec", ctypes.c_int), ("mem", ctypes.c_int)]
+                ("V", ctypes.POINTER(ctypes.c_void_p)), ("prec", ctypes.c_int), ("mem", ctypes.c_int),
+                ("ao", ctypes.POINTER(rpa_ao))]
 
 
 _lib = None
@@ -76,6 +83,7 @@ def load_library(path: str = LIB_PATH):
         "rpa_job_validate": (I, [J, ctypes.c_char_p, S]),
         "rpa_job_footprint": (I, [J, ctypes.POINTER(S)]),
         "rpa_chi0": (I, [P, J, I, P, P]),
+        "rpa_ao2mo": (I, [P, J, I, P, P]),
         "rpa_logdet": (I, [P, J, I, P, ctypes.POINTER(D), P]),
         "rpa_energy": (I, [P, J, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
         "rpa_energy_batch": (I, [P, J, I, ctypes.POINTER(D)]),
@@ -111,11 +119,15 @@ class Job:
     and ``V`` a list of n_q tensors [n_aux, n_aux], complex128 or float64, all
     on the device (mem=MEM_DEVICE) or all in host memory (mem=MEM_HOST,
     pinned for speed).  ``eps_occ`` [n_kpts, n_occ], ``eps_virt`` [n_kpts,
-    n_virt] float64 tensors in the same memory."""
+    n_virt] float64 tensors in the same memory.
+
+    AO form (``ao`` given, ``C`` None): ``ao`` is a dict with ``n_bas_atom``,
+    ``n_fit_atom`` (per atom), and the per-k-point device tensors ``padf``
+    [n_bas, S] and ``mo`` [n_bas, n_mo] (layouts of ``rpa_ao``)."""
 
     def __init__(self, *, is_complex: bool, n_aux: int, n_occ: int, n_virt: int, pair_k, pair_kq, w_q, zeta_k: float,
-                 omega, zeta_w, eps_occ, eps_virt, C: Sequence, V: Sequence, prec: int = PREC_FP64,
-                 mem: int = MEM_DEVICE):
+                 omega, zeta_w, eps_occ, eps_virt, C: Optional[Sequence], V: Sequence, prec: int = PREC_FP64,
+                 mem: int = MEM_DEVICE, ao: Optional[Dict[str, object]] = None):
         self.pair_k = np.array(pair_k, np.int32).reshape(-1)
         self.pair_kq = np.array(pair_kq, np.int32).reshape(-1)
         self.w_q = np.array(w_q, np.float64).reshape(-1)
@@ -123,7 +135,7 @@ class Job:
         self.zeta_w = np.array(zeta_w, np.float64).reshape(-1)
         n_q = int(self.w_q.shape[0])
         n_k = int(self.pair_k.shape[0] // n_q)
-        self.C_t, self.V_t = list(C), list(V)
+        self.C_t, self.V_t = list(C or []), list(V)
         self.eps_occ_t, self.eps_virt_t = eps_occ, eps_virt
         self._Cp = (ctypes.c_void_p * len(self.C_t))(*[int(c.data_ptr()) for c in self.C_t])
         self._Vp = (ctypes.c_void_p * len(self.V_t))(*[int(v.data_ptr()) for v in self.V_t])
@@ -135,9 +147,24 @@ class Job:
         s.w_q, s.zeta_k = _dptr(self.w_q), float(zeta_k)
         s.omega, s.zeta_w = _dptr(self.omega), _dptr(self.zeta_w)
         s.eps_occ, s.eps_virt = int(eps_occ.data_ptr()), int(eps_virt.data_ptr())
-        s.C = ctypes.cast(self._Cp, ctypes.POINTER(ctypes.c_void_p))
+        s.C = ctypes.cast(self._Cp, ctypes.POINTER(ctypes.c_void_p)) if self.C_t else None
         s.V = ctypes.cast(self._Vp, ctypes.POINTER(ctypes.c_void_p))
         s.prec, s.mem = int(prec), int(mem)
+        self.ao_t = ao
+        if ao is not None:
+            self._nb = np.array(ao["n_bas_atom"], np.int32)
+            self._nf = np.array(ao["n_fit_atom"], np.int32)
+            self._Pp = (ctypes.c_void_p * len(ao["padf"]))(*[int(t.data_ptr()) for t in ao["padf"]])
+            self._Mp = (ctypes.c_void_p * len(ao["mo"]))(*[int(t.data_ptr()) for t in ao["mo"]])
+            a = rpa_ao()
+            a.n_atoms = int(self._nb.shape[0])
+            a.n_bas_atom = self._nb.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+            a.n_fit_atom = self._nf.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+            a.n_mo = int(ao["mo"][0].shape[1])
+            a.padf = ctypes.cast(self._Pp, ctypes.POINTER(ctypes.c_void_p))
+            a.mo = ctypes.cast(self._Mp, ctypes.POINTER(ctypes.c_void_p))
+            self._ao = a
+            s.ao = ctypes.pointer(a)
         self.s = s
 
     @property
@@ -175,6 +202,41 @@ def job_from_problem(problem, tensors: Dict[str, object], prec: int = PREC_FP64,
                pair_k=g.pair_k, pair_kq=g.pair_kq, w_q=g.w_q, zeta_k=g.zeta_k, omega=problem.omega,
                zeta_w=problem.zeta_w, eps_occ=tensors["eps_occ"], eps_virt=tensors["eps_virt"], C=tensors["C"],
                V=tensors["V"], prec=prec, mem=mem)
+
+
+def job_from_ao_problem(problem, tensors: Dict[str, object], prec: int = PREC_FP64) -> Job:
+    """Job of an AO-form synthetic problem (``synth.AOProblem``) from
+    :func:`upload_ao_problem`'s tensors."""
+    g = problem.grid
+    ao = {"n_bas_atom": problem.n_bas_atom, "n_fit_atom": problem.n_fit_atom, "padf": tensors["padf"],
+          "mo": tensors["mo"]}
+    return Job(is_complex=problem.is_complex, n_aux=problem.n_aux, n_occ=problem.n_occ, n_virt=problem.n_virt,
+               pair_k=g.pair_k, pair_kq=g.pair_kq, w_q=g.w_q, zeta_k=g.zeta_k, omega=problem.omega,
+               zeta_w=problem.zeta_w, eps_occ=tensors["eps_occ"], eps_virt=tensors["eps_virt"], C=None,
+               V=tensors["V"], prec=prec, mem=MEM_DEVICE, ao=ao)
+
+
+def upload_ao_problem(problem, device="cuda", threads: int = 0):
+    """Device tensors of an AO-form problem: PADF and MO arrays per k-point,
+    V per q, band energies."""
+    import concurrent.futures as cf
+
+    import torch
+
+    dev = torch.device(device)
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+    def put(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    nthr = threads or min(16, os.cpu_count() or 4)
+    with cf.ThreadPoolExecutor(nthr) as ex:
+        padf = list(ex.map(lambda k: put(problem.padf(k)), range(problem.n_kpts)))
+        mo = list(ex.map(lambda k: put(problem.mo(k)), range(problem.n_kpts)))
+        V = list(ex.map(lambda q: put(problem.V(q)), range(problem.n_q)))
+    return {"padf": padf, "mo": mo, "V": V, "eps_occ": put(problem.eps_occ.astype(np.float64)),
+            "eps_virt": put(problem.eps_virt.astype(np.float64))}
 
 
 def upload_problem(problem, device="cuda", qs: Optional[Sequence[int]] = None, pin: bool = False,
@@ -283,8 +345,8 @@ class Context:
         self._check(self.lib.rpa_profile(self.h, int(enable)))
 
     def profile_read(self) -> Dict[str, Tuple[float, int]]:
-        ms = (ctypes.c_double * 8)()
-        n = (ctypes.c_uint64 * 8)()
+        ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+        n = (ctypes.c_uint64 * len(KERNEL_CLASSES))()
         self._check(self.lib.rpa_profile_read(self.h, ms, n))
         return {k: (ms[i], int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
@@ -298,6 +360,19 @@ class Context:
         st_ptr = (stream or torch.cuda.current_stream()).cuda_stream
         self._check(self.lib.rpa_chi0(self.h, ctypes.byref(job.s), int(q), ctypes.c_void_p(out.data_ptr()),
                                       ctypes.c_void_p(st_ptr)))
+        return out
+
+    def ao2mo(self, job: Job, q: int, out=None, stream=None):
+        """MO-basis fit coefficients of q for an AO-form job: [n_k, n_aux,
+        n_occ*n_virt] device tensor."""
+        import torch
+
+        if out is None:
+            dt = torch.complex128 if job.s.is_complex else torch.float64
+            out = torch.empty((job.s.n_k, job.s.n_aux, job.s.n_occ * job.s.n_virt), dtype=dt, device="cuda")
+        st_ptr = (stream or torch.cuda.current_stream()).cuda_stream
+        self._check(self.lib.rpa_ao2mo(self.h, ctypes.byref(job.s), int(q), ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(st_ptr)))
         return out
 
     def logdet(self, job: Job, q: int, chi, stream=None) -> np.ndarray:

@@ -1,0 +1,162 @@
+// Host side of AO-form jobs (rpa_job.ao, Sec. 2.2): validation, the layout of
+// the AO part of a lane's workspace, and the enqueue of the two transform
+// kernels of kernels_ao.cu.
+//
+// Workspace region (offsets from Bufs.ao):
+//   fit table   int4 per fit function gamma (see launch_ao_assemble)
+//   H_occ       one S x n_occ slot per k-point that appears as k (pair_k)
+//   H_virt      one S x n_virt slot per k-point that appears as k+q (pair_kq)
+//   C           n_k blocks n_aux x n_occ*n_virt: the MO-basis coefficients of
+//               the q being processed (read by the chi0 step)
+// The half-transforms depend on the k-point only, so rpa_energy forms them
+// once per job; each q then costs one assembly launch.
+#include <cuda_runtime.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ao_internal.h"
+#include "rpa_internal.h"
+#include "rpa_runtime.h"
+
+namespace rpa {
+
+namespace {
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+}  // namespace
+
+int ao_validate(const rpa_job* j, char* msg, size_t len) {
+  auto fail = [&](const char* m) {
+    if (msg && len) snprintf(msg, len, "%s", m);
+    return RPA_E_INVAL;
+  };
+  const rpa_ao* a = j->ao;
+  if (j->C) return fail("AO-form job: C must be NULL (the coefficients are formed from ao)");
+  if (j->mem != RPA_MEM_DEVICE) return fail("AO-form job: inputs must be in device memory");
+  if (a->n_atoms <= 0 || !a->n_bas_atom || !a->n_fit_atom || !a->padf || !a->mo)
+    return fail("AO-form job: n_atoms must be positive and the ao arrays non-NULL");
+  long nb = 0, nf = 0, S = 0;
+  for (int A = 0; A < a->n_atoms; ++A) {
+    if (a->n_bas_atom[A] <= 0 || a->n_fit_atom[A] <= 0)
+      return fail("AO-form job: every atom needs at least one basis and one fit function");
+    nb += a->n_bas_atom[A];
+    nf += a->n_fit_atom[A];
+    S += (long)a->n_bas_atom[A] * a->n_fit_atom[A];
+  }
+  if (nf != j->n_aux) return fail("AO-form job: fit functions per atom must sum to n_aux");
+  if (a->n_mo < j->n_occ + j->n_virt || a->n_mo > nb)
+    return fail("AO-form job: n_mo must lie in [n_occ + n_virt, n_bas]");
+  if (nb > 65536 || S > (1L << 30)) return fail("AO-form job: basis or PADF array too large");
+  for (int k = 0; k < j->n_kpts; ++k)
+    if (!a->padf[k] || !a->mo[k]) return fail("AO-form job: a padf or mo pointer is NULL");
+  return RPA_OK;
+}
+
+AoPlan ao_plan(const rpa_job* j) {
+  AoPlan p;
+  const rpa_ao* a = j->ao;
+  const size_t es = j->is_complex ? 16 : 8;
+  for (int A = 0; A < a->n_atoms; ++A) {
+    p.n_bas += a->n_bas_atom[A];
+    p.S += a->n_bas_atom[A] * a->n_fit_atom[A];
+  }
+  p.fit.resize(j->n_aux);
+  for (int A = 0, b0 = 0, f0 = 0, s0 = 0; A < a->n_atoms; ++A) {
+    const int nb = a->n_bas_atom[A], nf = a->n_fit_atom[A];
+    for (int g = 0; g < nf; ++g) p.fit[f0 + g] = make_int4(b0, nb, s0 + g, nf);
+    b0 += nb;
+    f0 += nf;
+    s0 += nb * nf;
+  }
+  p.occ_slot.assign(j->n_kpts, -1);
+  p.virt_slot.assign(j->n_kpts, -1);
+  for (long i = 0; i < (long)j->n_q * j->n_k; ++i) {
+    if (p.occ_slot[j->pair_k[i]] < 0) p.occ_slot[j->pair_k[i]] = p.n_occ_slots++;
+    if (p.virt_slot[j->pair_kq[i]] < 0) p.virt_slot[j->pair_kq[i]] = p.n_virt_slots++;
+  }
+  p.occ_bytes = al256(es * (size_t)p.S * j->n_occ);
+  p.virt_bytes = al256(es * (size_t)p.S * j->n_virt);
+  p.cblk = es * (size_t)j->n_aux * j->n_occ * j->n_virt;
+  p.off_hocc = al256(sizeof(int4) * (size_t)j->n_aux);
+  p.off_hvirt = p.off_hocc + p.occ_bytes * p.n_occ_slots;
+  p.off_c = p.off_hvirt + p.virt_bytes * p.n_virt_slots;
+  p.bytes = p.off_c + al256(p.cblk * j->n_k);
+  return p;
+}
+
+size_t ao_region_bytes(const rpa_job* j) { return j->ao ? ao_plan(j).bytes : 0; }
+
+size_t ao_input_bytes(const rpa_job* j) {
+  if (!j->ao) return 0;
+  const AoPlan p = ao_plan(j);
+  const size_t es = j->is_complex ? 16 : 8;
+  return es * (size_t)j->n_kpts * p.n_bas * ((size_t)p.S + j->ao->n_mo);
+}
+
+#define CKA(call)                                                                                    \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) {                                                                         \
+      ctx_set_error(ctx, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return RPA_E_CUDA;                                                                             \
+    }                                                                                                \
+  } while (0)
+
+rpa_status ao_enqueue_half(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const AoPlan& p, char* region, int q,
+                           cudaStream_t s) {
+  const rpa_ao* a = j->ao;
+  // the fit table (small, pageable source: consumed before the call returns)
+  CKA(cudaMemcpyAsync(region, p.fit.data(), sizeof(int4) * p.fit.size(), cudaMemcpyHostToDevice, s));
+  std::vector<char> need_o(j->n_kpts, 0), need_v(j->n_kpts, 0);
+  const int q0 = q < 0 ? 0 : q, q1 = q < 0 ? j->n_q : q + 1;
+  for (int qq = q0; qq < q1; ++qq)
+    for (int jj = 0; jj < j->n_k; ++jj) {
+      need_o[j->pair_k[(size_t)qq * j->n_k + jj]] = 1;
+      need_v[j->pair_kq[(size_t)qq * j->n_k + jj]] = 1;
+    }
+  int n = 0;
+  prof_begin(ctx, pex, s);
+  for (int k = 0; k < j->n_kpts; ++k) {
+    if (need_o[k]) {
+      CKA(launch_ao_half(j->is_complex, p.n_bas, p.S, a->n_mo, (const double*)a->padf[k], (const double*)a->mo[k], 0,
+                         j->n_occ, (double*)(region + p.off_hocc + p.occ_bytes * p.occ_slot[k]), s));
+      ++n;
+    }
+    if (need_v[k]) {
+      CKA(launch_ao_half(j->is_complex, p.n_bas, p.S, a->n_mo, (const double*)a->padf[k], (const double*)a->mo[k],
+                         j->n_occ, j->n_virt, (double*)(region + p.off_hvirt + p.virt_bytes * p.virt_slot[k]), s));
+      ++n;
+    }
+  }
+  prof_end(ctx, pex, s, RPA_K_AO2MO, n);
+  ctx->launches += n;
+  return RPA_OK;
+}
+
+rpa_status ao_enqueue_assemble(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const AoPlan& p, const char* region, int q,
+                               char* out, cudaStream_t s) {
+  const rpa_ao* a = j->ao;
+  int n = 0;
+  prof_begin(ctx, pex, s);
+  for (int j0 = 0; j0 < j->n_k; j0 += AoPairs::kMax) {
+    const int np = std::min(AoPairs::kMax, j->n_k - j0);
+    AoPairs pr{};
+    for (int t = 0; t < np; ++t) {
+      const size_t i = (size_t)q * j->n_k + j0 + t;
+      const int k = j->pair_k[i], kq = j->pair_kq[i];
+      pr.mo_k[t] = (const double*)a->mo[k];
+      pr.mo_kq[t] = (const double*)a->mo[kq];
+      pr.h_occ[t] = (const double*)(region + p.off_hocc + p.occ_bytes * p.occ_slot[k]);
+      pr.h_virt[t] = (const double*)(region + p.off_hvirt + p.virt_bytes * p.virt_slot[kq]);
+      pr.out[t] = (double*)(out + p.cblk * (size_t)(j0 + t));
+    }
+    CKA(launch_ao_assemble(j->is_complex, pr, np, (const int4*)region, j->n_aux, j->n_occ, j->n_virt, a->n_mo, s));
+    ++n;
+  }
+  prof_end(ctx, pex, s, RPA_K_AO2MO, n);
+  ctx->launches += n;
+  return RPA_OK;
+}
+
+}  // namespace rpa

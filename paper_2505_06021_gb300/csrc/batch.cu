@@ -331,6 +331,10 @@ extern "C" rpa_status rpa_energy_batch(rpa_ctx* ctx, const rpa_job* jobs, int n_
       ctx_set_error(ctx, "rpa_energy_batch: job %d is not device-resident", i);
       return RPA_E_INVAL;
     }
+    if (jobs[i].ao) {
+      ctx_set_error(ctx, "rpa_energy_batch: job %d is in AO form (run it with rpa_energy)", i);
+      return RPA_E_INVAL;
+    }
     if (jobs[i].prec == RPA_PREC_MIXED && !mixed_supported()) {
       ctx_set_error(ctx, "mixed-precision chi0 not supported by this library");
       return RPA_E_INVAL;

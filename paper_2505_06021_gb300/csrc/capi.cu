@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "rpa_internal.h"
+#include "ao_internal.h"
 #include "rpa_runtime.h"
 
 using namespace rpa;
@@ -188,8 +189,8 @@ rpa_status validate_job(const rpa_job* j, char* msg, size_t len) {
   if ((long long)j->n_q * j->n_k > (1LL << 24)) return set_msg(msg, len, "n_q*n_k too large");
   if (!j->is_complex && (j->n_q != 1 || j->n_k != 1))
     return set_msg(msg, len, "real (is_complex=0) jobs are Gamma-only: n_q = n_k = 1");
-  if (!j->pair_k || !j->pair_kq || !j->w_q || !j->omega || !j->zeta_w || !j->eps_occ || !j->eps_virt || !j->C ||
-      !j->V)
+  if (!j->pair_k || !j->pair_kq || !j->w_q || !j->omega || !j->zeta_w || !j->eps_occ || !j->eps_virt ||
+      (!j->C && !j->ao) || !j->V)
     return set_msg(msg, len, "a required pointer is NULL");
   if (j->prec != RPA_PREC_FP64 && j->prec != RPA_PREC_MIXED) return set_msg(msg, len, "unknown prec %d", j->prec);
   if (j->prec == RPA_PREC_MIXED && j->n_w > 32)
@@ -199,8 +200,10 @@ rpa_status validate_job(const rpa_job* j, char* msg, size_t len) {
   for (long i = 0; i < (long)j->n_q * j->n_k; ++i) {
     if (j->pair_k[i] < 0 || j->pair_k[i] >= j->n_kpts || j->pair_kq[i] < 0 || j->pair_kq[i] >= j->n_kpts)
       return set_msg(msg, len, "pair index %ld out of range [0, %d)", i, j->n_kpts);
-    if (!j->C[i]) return set_msg(msg, len, "C[%ld] is NULL", i);
+    if (!j->ao && !j->C[i]) return set_msg(msg, len, "C[%ld] is NULL", i);
   }
+  if (j->ao)
+    if (int st = ao_validate(j, msg, len)) return st;
   for (int q = 0; q < j->n_q; ++q) {
     if (!j->V[q]) return set_msg(msg, len, "V[%d] is NULL", q);
     if (!isfinite(j->w_q[q])) return set_msg(msg, len, "w_q[%d] not finite", q);
@@ -245,11 +248,13 @@ Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool m
       L.mixed = al(mixed_workspace_bytes(g, n_slices, L.slice_cap));
     }
   }
-  L.total = L.meta + L.dtab + L.chi + L.T + L.L + L.Vc + 2 * (L.stageC + L.stageV) + L.eps + L.mixed;
+  L.ao = al(ao_region_bytes(j));
+  L.total = L.meta + L.dtab + L.chi + L.T + L.L + L.Vc + 2 * (L.stageC + L.stageV) + L.eps + L.mixed + L.ao;
   return L;
 }
 
 int choose_qb(const rpa_job* j, int n_slices, size_t cap) {
+  if (j->ao) return 1;  // one q's MO-basis coefficients at a time
   int qb = j->n_q;
   while (qb > 1 && plan_layout(j, qb, n_slices, cap, true).total > cap) qb = (qb + 1) / 2;
   // host-resident inputs: at least four q-batches, so that the copies of one
@@ -267,7 +272,8 @@ size_t job_footprint(const rpa_job* j, int n_slices, size_t ws_cap) {
   size_t in = 0;
   if (j->mem == RPA_MEM_DEVICE) {
     const size_t es = j->is_complex ? 16 : 8;
-    in = es * (size_t)j->n_aux * j->n_occ * j->n_virt * j->n_q * j->n_k + es * (size_t)j->n_aux * j->n_aux * j->n_q;
+    in = j->ao ? ao_input_bytes(j) : es * (size_t)j->n_aux * j->n_occ * j->n_virt * j->n_q * j->n_k;
+    in += es * (size_t)j->n_aux * j->n_aux * j->n_q;
   }
   return in + L.total;
 }
@@ -324,6 +330,8 @@ Bufs carve(void* ws, const rpa_job* j, const Layout& L) {
   b.mixed = p;
   b.mixed_bytes = L.mixed;
   b.slice_cap = L.slice_cap;
+  p += L.mixed;
+  b.ao = L.ao ? p : nullptr;
   return b;
 }
 
@@ -398,8 +406,8 @@ rpa_status stage_vside(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b,
   prof_begin(ctx, pex, s);
   CK(launch_cholesky(j->is_complex, j->n_aux, nq, b.L, mstride, 1, b.Vc ? b.ldV + q0 : nullptr, b.status,
                      (1 << 29) + q0, s));
-  prof_end(ctx, pex, s, RPA_K_VFACTOR, 1);
-  ctx->launches++;
+  prof_end(ctx, pex, s, RPA_K_VFACTOR, cholesky_launches(j->n_aux, nq));
+  ctx->launches += cholesky_launches(j->n_aux, nq);
   if (b.Vc) {
     // inverse form: -V^-1 per q (X = L^-1 in T's storage, then -(X^H X) over L)
     prof_begin(ctx, pex, s);
@@ -421,8 +429,8 @@ rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, 
     prof_begin(ctx, pex, s);
     CK(launch_cholesky(j->is_complex, j->n_aux, nq * j->n_w, b.chi, mstride, 2, b.parts + (size_t)2 * q0 * j->n_w,
                        b.status, q0 * j->n_w, s, b.L, b.Vc, b.ldV + q0, j->n_w));
-    prof_end(ctx, pex, s, RPA_K_LOGDET, 1);
-    ctx->launches++;
+    prof_end(ctx, pex, s, RPA_K_LOGDET, cholesky_launches(j->n_aux, nq * j->n_w));
+    ctx->launches += cholesky_launches(j->n_aux, nq * j->n_w);
     return RPA_OK;
   }
   // Y = -(L^H chi L) (lower triangle), overwriting chi's storage
@@ -434,8 +442,8 @@ rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, 
   prof_begin(ctx, pex, s);
   CK(launch_cholesky(j->is_complex, j->n_aux, nq * j->n_w, b.chi, mstride, 0, b.parts + (size_t)2 * q0 * j->n_w,
                      b.status, q0 * j->n_w, s));
-  prof_end(ctx, pex, s, RPA_K_LOGDET, 1);
-  ctx->launches++;
+  prof_end(ctx, pex, s, RPA_K_LOGDET, cholesky_launches(j->n_aux, nq * j->n_w));
+  ctx->launches += cholesky_launches(j->n_aux, nq * j->n_w);
   return RPA_OK;
 }
 
@@ -524,16 +532,23 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
   const bool host = job->mem == RPA_MEM_HOST;
   const int nbatch = (job->n_q + qb - 1) / qb;
 
+  AoPlan aop;
+  if (job->ao) aop = ao_plan(job);
   std::vector<const void*> cp((size_t)job->n_q * job->n_k), vp(job->n_q);
   for (int q = 0; q < job->n_q; ++q) {
     const int bi = q / qb, slot = bi % 2, qi = q - bi * qb;
     for (int jj = 0; jj < job->n_k; ++jj) {
       const size_t i = (size_t)q * job->n_k + jj;
-      cp[i] = host ? (const void*)(b.stageC[slot] + ((size_t)qi * job->n_k + jj) * cblk) : job->C[i];
+      if (job->ao)  // qb == 1: every q's coefficients go to the same buffer
+        cp[i] = b.ao + aop.off_c + (size_t)jj * cblk;
+      else
+        cp[i] = host ? (const void*)(b.stageC[slot] + ((size_t)qi * job->n_k + jj) * cblk) : job->C[i];
     }
     vp[q] = host ? (const void*)(b.stageV[slot] + (size_t)qi * es * NN) : job->V[q];
   }
   if (rpa_status st0 = upload_tables(ctx, ex, job, b, cp.data())) return st0;
+  if (job->ao)
+    if (rpa_status st1 = ao_enqueue_half(ctx, &ex, job, aop, b.ao, -1, s)) return st1;
 
   const double* eo = job->eps_occ;
   const double* ev = job->eps_virt;
@@ -564,6 +579,8 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
   for (int bi = 0; bi < nbatch; ++bi) {
     const int q0 = bi * qb, nq = std::min(qb, job->n_q - q0), slot = bi % 2;
     if (host) CK(cudaStreamWaitEvent(s, ex.ready[slot], 0));
+    if (job->ao)
+      if (rpa_status st1 = ao_enqueue_assemble(ctx, &ex, job, aop, b.ao, q0, b.ao + aop.off_c, s)) return st1;
     if (rpa_status st = run_qbatch(ctx, &ex, job, b, q0, nq, vp.data() + q0, eo, ev, s, nullptr, ctx->n_slices))
       return st;
     if (host) {
@@ -722,14 +739,56 @@ rpa_status rpa_chi0(rpa_ctx* ctx, const rpa_job* job, int q, void* chi_out, void
     return RPA_E_NOMEM;
   }
   Bufs b = carve(ex.ws, job, L);
+  std::vector<const void*> cp;
+  AoPlan aop;
+  if (job->ao) {
+    aop = ao_plan(job);
+    cp.resize((size_t)job->n_q * job->n_k);
+    for (size_t i = 0; i < cp.size(); ++i) cp[i] = b.ao + aop.off_c + (i % job->n_k) * aop.cblk;
+  }
   // the lane's uploads run on ex.s; order the caller's stream after them
-  if (rpa_status st0 = upload_tables(ctx, ex, job, b, job->C)) return st0;
+  if (rpa_status st0 = upload_tables(ctx, ex, job, b, job->ao ? cp.data() : job->C)) return st0;
   CK(cudaEventRecord(ex.done, ex.s));
   CK(cudaStreamWaitEvent(s, ex.done, 0));
+  if (job->ao) {
+    if (rpa_status st1 = ao_enqueue_half(ctx, &ex, job, aop, b.ao, q, s)) return st1;
+    if (rpa_status st1 = ao_enqueue_assemble(ctx, &ex, job, aop, b.ao, q, b.ao + aop.off_c, s)) return st1;
+  }
   if (rpa_status st = run_qbatch(ctx, &ex, job, b, q, 1, job->V + q, job->eps_occ, job->eps_virt, s,
                                  (double*)chi_out, ctx->n_slices))
     return st;
   // the d table in the workspace is reused by the next call on this context
+  CK(cudaEventRecord(ex.done, s));
+  rpa_status wst = wait_event(ctx, ex.done, ctx->timeout_s + 600.0);
+  prof_collect(ctx, &ex);
+  return wst;
+}
+
+rpa_status rpa_ao2mo(rpa_ctx* ctx, const rpa_job* job, int q, void* C_out, void* stream) {
+  if (!ctx) return RPA_E_INVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  char msg[512];
+  if (validate_job(job, msg, sizeof msg)) {
+    ctx_set_error(ctx, "%s", msg);
+    return RPA_E_INVAL;
+  }
+  if (!job->ao || q < 0 || q >= job->n_q || !C_out) {
+    ctx_set_error(ctx, "rpa_ao2mo: job without ao, q out of range or C_out NULL");
+    return RPA_E_INVAL;
+  }
+  CK(cudaSetDevice(ctx->device));
+  Exec& ex = ctx->ex;
+  cudaStream_t s = (cudaStream_t)stream;
+  const AoPlan aop = ao_plan(job);
+  // only the AO region is used: fit table and half-transforms
+  if (!ex.ensure_ws(aop.off_c + 256)) {
+    ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", aop.off_c);
+    return RPA_E_NOMEM;
+  }
+  char* region = (char*)ex.ws;
+  if (rpa_status st = ao_enqueue_half(ctx, &ex, job, aop, region, q, s)) return st;
+  if (rpa_status st = ao_enqueue_assemble(ctx, &ex, job, aop, region, q, (char*)C_out, s)) return st;
+  // the workspace is reused by the next call on this context
   CK(cudaEventRecord(ex.done, s));
   rpa_status wst = wait_event(ctx, ex.done, ctx->timeout_s + 600.0);
   prof_collect(ctx, &ex);

@@ -20,6 +20,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include "fp64_elem.cuh"
 #include "rpa_internal.h"
 
 namespace rpa {
@@ -36,62 +37,6 @@ int num_sms_fp64() {
     if (n <= 0) n = 148;
   }
   return n;
-}
-
-template <bool C>
-struct Elem;
-template <>
-struct Elem<true> {
-  double re, im;
-};
-template <>
-struct Elem<false> {
-  double re;
-};
-
-template <bool C>
-__device__ __forceinline__ Elem<C> ld_elem(const double* p, long i) {
-  Elem<C> e;
-  if constexpr (C) {
-    double2 v = *reinterpret_cast<const double2*>(p + 2 * i);
-    e.re = v.x;
-    e.im = v.y;
-  } else {
-    e.re = p[i];
-  }
-  return e;
-}
-template <bool C>
-__device__ __forceinline__ Elem<C> zero_elem() {
-  Elem<C> e;
-  e.re = 0.0;
-  if constexpr (C) e.im = 0.0;
-  return e;
-}
-template <bool C>
-__device__ __forceinline__ void st_elem(double* p, long i, Elem<C> e) {
-  if constexpr (C) {
-    *reinterpret_cast<double2*>(p + 2 * i) = make_double2(e.re, e.im);
-  } else {
-    p[i] = e.re;
-  }
-}
-template <bool C>
-__device__ __forceinline__ Elem<C> conj_e(Elem<C> a) {
-  if constexpr (C) a.im = -a.im;
-  return a;
-}
-// acc += a * b
-template <bool C>
-__device__ __forceinline__ void mac(Elem<C>& acc, Elem<C> a, Elem<C> b) {
-  if constexpr (C) {
-    acc.re = fma(a.re, b.re, acc.re);
-    acc.re = fma(-a.im, b.im, acc.re);
-    acc.im = fma(a.re, b.im, acc.im);
-    acc.im = fma(a.im, b.re, acc.im);
-  } else {
-    acc.re = fma(a.re, b.re, acc.re);
-  }
 }
 
 // Lower-triangular tile index -> (I, J), J <= I.
@@ -891,18 +836,29 @@ cudaError_t launch_chol_t(int N, int b0, int n_mat, double* mats, long bstride, 
   return cudaGetLastError();
 }
 
+// The launch split of launch_chol_c: 0 = one CTA per matrix, 1 = a cluster
+// per matrix, 2 = one CTA per matrix except a short last wave on clusters.
+int chol_split(int N, int n_mat) {
+  const int P = num_sms_fp64();
+  if (N >= 256 && n_mat * 2 < P) return 1;
+  const int r = n_mat % P;
+  if (N >= 256 && n_mat > P && r > 0 && r * 2 < P) return 2;
+  return 0;
+}
+
 template <bool C>
 cudaError_t launch_chol_c(int N, int n_mat, double* mats, long bstride, int mode, double* out, int* status,
                           int status_base, cudaStream_t s, const double* Wn, const double* Vc, const double* ldV,
                           int n_w) {
   const int P = num_sms_fp64();
+  const int split = chol_split(N, n_mat);
   // few large matrices: a cluster per matrix
-  if (N >= 256 && n_mat * 2 < P)
+  if (split == 1)
     return launch_chol_t<C, CL_BIG>(N, 0, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
   // one CTA per matrix; a short last wave (fewer than P/2 matrices) goes to
   // clusters instead, so that it does not run on a few SMs alone
   const int r = n_mat % P;
-  if (N >= 256 && n_mat > P && r > 0 && r * 2 < P) {
+  if (split == 2) {
     cudaError_t e = launch_chol_t<C, 1>(N, 0, n_mat - r, mats, bstride, mode, out, status, status_base, s, Wn, Vc,
                                         ldV, n_w);
     if (e != cudaSuccess) return e;
@@ -920,6 +876,8 @@ cudaError_t launch_cholesky(int cplx, int N, int n_mat, double* mats, long bstri
   if (cplx) return launch_chol_c<true>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
   return launch_chol_c<false>(N, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
 }
+
+int cholesky_launches(int N, int n_mat) { return n_mat <= 0 ? 0 : (chol_split(N, n_mat) == 2 ? 2 : 1); }
 
 cudaError_t launch_cholesky_ragged(int cplx, const CholTask* tasks, int n_tasks, cudaStream_t s) {
   if (n_tasks <= 0) return cudaSuccess;

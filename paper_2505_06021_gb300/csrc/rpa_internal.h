@@ -47,6 +47,10 @@ cudaError_t launch_cholesky(int cplx, int N, int n_mat, double* mats, long bstri
                             int* status, int status_base, cudaStream_t s, const double* Wn = nullptr,
                             const double* Vc = nullptr, const double* ldV = nullptr, int n_w = 0);
 
+// Kernel launches launch_cholesky makes for n_mat matrices of size N (1, or 2
+// when a short last wave goes to clusters).
+int cholesky_launches(int N, int n_mat);
+
 // One matrix of a ragged Cholesky launch (matrices of different sizes).
 struct CholTask {
   double* A;          // N x N, factorised in place
@@ -63,6 +67,30 @@ cudaError_t launch_cholesky_ragged(int cplx, const CholTask* tasks, int n_tasks,
 // Wn[q] = -V(q)^-1 (lower triangle) from the Cholesky factors L[q]: X = L^-1
 // by block forward substitution into X[q], then -(X^H X).
 cudaError_t launch_vinv(int cplx, int N, int n_q, const double* L, double* X, double* Wn, cudaStream_t s);
+
+// ---- AO -> MO transform (kernels_ao.cu) -----------------------------------
+
+// H[s][n] = sum_nu P[nu][s] c[nu][n0 + n], s < S, n < ncols: the half-
+// transform of one k-point's PADF array P (n_bas x S) with the MO columns
+// [n0, n0 + ncols) of c (n_bas x n_mo).  H is S x ncols.
+cudaError_t launch_ao_half(int cplx, int n_bas, int S, int n_mo, const double* P, const double* c, int n0, int ncols,
+                           double* H, cudaStream_t s);
+
+// Per (q, k) pair of one launch: MO coefficients at k and k+q, half-
+// transforms H_occ(k) (S x n_occ) and H_virt(k+q) (S x n_virt), output
+// C(q, k) (n_aux x n_occ*n_virt).
+struct AoPairs {
+  static constexpr int kMax = 48;
+  const double* mo_k[kMax];
+  const double* mo_kq[kMax];
+  const double* h_occ[kMax];
+  const double* h_virt[kMax];
+  double* out[kMax];
+};
+// fit[gamma] = (first basis function of gamma's atom, basis functions on it,
+// PADF column of (its first basis function, gamma), fit functions on it).
+cudaError_t launch_ao_assemble(int cplx, const AoPairs& pr, int n_pairs, const int4* fit, int n_aux, int n_occ,
+                               int n_virt, int n_mo, cudaStream_t s);
 
 // T[b] = chi[b] * L[b / n_w]   (L lower triangular, N x N).
 // Y[b] = -(L[b / n_w]^H T[b]), lower triangle only.

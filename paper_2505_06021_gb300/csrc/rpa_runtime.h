@@ -92,7 +92,7 @@ namespace rpa {
 
 // Workspace of one lane for a job processed in q-batches of qb q-points.
 struct Layout {
-  size_t meta, dtab, chi, T, L, Vc, stageC, stageV, eps, mixed, total;
+  size_t meta, dtab, chi, T, L, Vc, stageC, stageV, eps, mixed, ao, total;
   size_t slice_cap;  // mixed path: bytes for the weighted operand's digit planes
   int qb;
 };
@@ -122,6 +122,7 @@ struct Bufs {
   void* mixed;
   size_t mixed_bytes;
   size_t slice_cap;
+  char* ao;  // AO-form jobs: fit table, half-transforms, one q's C (ao_internal.h)
 };
 
 void ctx_set_error(rpa_ctx* ctx, const char* fmt, ...);

@@ -400,6 +400,10 @@ rpa_status rpa_submit(rpa_ctx* ctx, const rpa_job* job, uint64_t* ticket) {
     ctx_set_error(ctx, "%s", msg);
     return RPA_E_INVAL;
   }
+  if (job->ao) {
+    ctx_set_error(ctx, "rpa_submit: AO-form jobs are run with rpa_energy");
+    return RPA_E_INVAL;
+  }
   std::shared_ptr<ServeJob> j(new ServeJob());
   const size_t npk = (size_t)job->n_q * job->n_k;
   j->pair_k.assign(job->pair_k, job->pair_k + npk);

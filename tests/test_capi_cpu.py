@@ -105,3 +105,42 @@ def test_create_without_device_fails_cleanly(lib):
     st = lib.rpa_create(ctypes.byref(cfg), ctypes.byref(h))
     assert st == rpa.RPA_E_CUDA
     assert b"device" in lib.rpa_last_error(None)
+
+
+def _fake_ao_job(p, **over):
+    t = {"padf": [FakeTensor(0x200000 + 0x100 * k) for k in range(p.n_kpts)],
+         "mo": [FakeTensor(0x300000 + 0x100 * k, (p.n_bas, p.n_mo)) for k in range(p.n_kpts)],
+         "V": [FakeTensor(0x90000 + 0x100 * i) for i in range(p.n_q)],
+         "eps_occ": FakeTensor(0x1000, p.eps_occ.shape), "eps_virt": FakeTensor(0x2000, p.eps_virt.shape)}
+    t.update(over)
+    return rpa.job_from_ao_problem(p, t)
+
+
+def test_validate_ao_jobs(lib):
+    p = synth.config1_ao(n_bas_atom=(8, 6), n_fit_atom=(10, 14), n_occ=3, n_virt=9)
+    st, msg = _fake_ao_job(p).validate()
+    assert st == rpa.RPA_OK, msg
+    j = _fake_ao_job(p)
+    j._nf[1] = 13  # fit functions no longer sum to n_aux
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "n_aux" in msg
+    j = _fake_ao_job(p)
+    j._Pp[4] = None
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "NULL" in msg
+    j = _fake_ao_job(p)
+    j._ao.n_mo = p.n_occ + p.n_virt - 1
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "n_mo" in msg
+    j = _fake_ao_job(p)
+    j.s.mem = rpa.MEM_HOST
+    assert j.validate()[0] == rpa.RPA_E_INVAL
+
+
+def test_ao_footprint_counts_padf_not_mo_basis_coefficients(lib):
+    p = synth.config1_ao()
+    fp = _fake_ao_job(p).footprint()
+    # PADF arrays of the 16 k-points 4.3 GB + half-transforms 4.3 GB + one
+    # q's MO-basis coefficients 0.94 GB; the job's 15 GB of C never resides
+    assert 9.0e9 < fp < 15.0e9
+    assert p.padf_bytes() == 16 * 256 * 65536 * 16
