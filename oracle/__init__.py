@@ -6,6 +6,7 @@ or calls anything here, and nothing here imports the GPU library.
 
 Each function restates one step of the paper's method (arXiv 2505.06021):
 
+* :func:`padf_k`    - k-dependent PADF coefficients from the cell-pair ones, Sec. 2.2
 * :func:`ao2mo`     - MO-basis fit coefficients C_{gamma,ia}(q, k) from the
                       k-dependent PADF and MO coefficients, Sec. 2.2
 * :func:`chi0`      - fit-basis response chi0_PQ(q, i omega), Sec. 2.2
@@ -54,13 +55,14 @@ def _load():
         lib.oracle_jacobi_eigh.argtypes = [i, i, _dp, _dp, _dp, i, d]
         ip = ctypes.POINTER(ctypes.c_int)
         lib.oracle_ao2mo.argtypes = [i, i, ip, ip, i, i, i, _dp, _dp, _dp, _dp, i, ip, _dp, i]
+        lib.oracle_padf_k.argtypes = [i, ip, ctypes.POINTER(_dp), ctypes.c_long, _dp, _dp, i]
         lib.oracle_vhalf.argtypes = [i, i, _dp, _dp]
         lib.oracle_sandwich.argtypes = [i, i, _dp, _dp, _dp, i]
         lib.oracle_logdet_cholesky.argtypes = [i, i, _dp, _dp, _dp]
         lib.oracle_logabsdet_lu.argtypes = [i, i, _dp, _dp]
         lib.oracle_energy_sum.argtypes = [i, i, _dp, _dp, _dp, _dp]
         lib.oracle_max_threads.argtypes = []
-        for f in (lib.oracle_chi0, lib.oracle_ao2mo, lib.oracle_jacobi_eigh, lib.oracle_vhalf, lib.oracle_sandwich,
+        for f in (lib.oracle_chi0, lib.oracle_ao2mo, lib.oracle_padf_k, lib.oracle_jacobi_eigh, lib.oracle_vhalf, lib.oracle_sandwich,
                   lib.oracle_logdet_cholesky, lib.oracle_logabsdet_lu, lib.oracle_energy_sum, lib.oracle_max_threads):
             f.restype = ctypes.c_int
         _lib = lib
@@ -135,12 +137,40 @@ def ao2mo(is_complex: bool, n_bas_atom: Sequence[int], n_fit_atom: Sequence[int]
     return out
 
 
+def padf_k(C0: Sequence[np.ndarray], R: np.ndarray, kfrac: Sequence[float],
+           n_threads: Optional[int] = None) -> np.ndarray:
+    """C(k) = sum_r C0[r] e^{2 pi i kfrac . R[r]} for real arrays C0[r] of one
+    shape and integer lattice vectors R ([n_R, 3]); complex result."""
+    arrs = [np.ascontiguousarray(a, np.float64) for a in C0]
+    Ri = np.ascontiguousarray(R, np.int32).reshape(-1, 3)
+    kf = np.ascontiguousarray(kfrac, np.float64).reshape(3)
+    out = np.zeros(arrs[0].shape, np.complex128)
+    ip = ctypes.POINTER(ctypes.c_int)
+    pp = (_dp * len(arrs))(*[_ptr(a) for a in arrs])
+    rc = _load().oracle_padf_k(len(arrs), Ri.ctypes.data_as(ip), pp, int(arrs[0].size), _ptr(kf),
+                               _ptr(out.view(np.float64)), int(n_threads or max_threads()))
+    if rc != 0:
+        raise OracleError("oracle_padf_k rc=%d" % rc)
+    return out
+
+
+def padf_of(problem, kappa: int, n_threads: Optional[int] = None) -> np.ndarray:
+    """The k-dependent PADF array of k-point kappa of an AO-form problem: given
+    directly, or (lattice form) formed from the cell-pair coefficients."""
+    if getattr(problem, "lattice", None) is None:
+        return problem.padf(kappa)
+    C = padf_k([problem.padf_R(r) for r in range(len(problem.lattice))], problem.lattice,
+               problem.grid.kpts[kappa], n_threads)
+    return C if problem.is_complex else np.ascontiguousarray(C.real)
+
+
 def ao2mo_block(problem, q: int, j: int, entries: Optional[np.ndarray] = None,
                 n_threads: Optional[int] = None) -> np.ndarray:
     """C(q, k_j) of an AO-form problem (``synth.AOProblem``)."""
     k, kq = int(problem.grid.pair_k[q, j]), int(problem.grid.pair_kq[q, j])
     return ao2mo(problem.is_complex, problem.n_bas_atom, problem.n_fit_atom, problem.n_occ, problem.n_virt,
-                 problem.padf(k), problem.padf(kq), problem.mo(k), problem.mo(kq), entries, n_threads)
+                 padf_of(problem, k, n_threads), padf_of(problem, kq, n_threads), problem.mo(k), problem.mo(kq),
+                 entries, n_threads)
 
 
 def _blocks(problem, q: int, n_threads: Optional[int] = None):

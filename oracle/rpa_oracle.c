@@ -106,6 +106,43 @@ int oracle_chi0(int is_complex, int n_aux, int n_occ, int n_virt, int n_k, const
   return 0;
 }
 
+/* ------------------------------------- k-dependent PADF coefficients -- */
+/*
+ * The k-dependent pair-atomic fit coefficients of one k-point from the
+ * cell-pair coefficients (Sec. 2.2, the lattice sum defining C(k)):
+ *   C_{nu mu alpha}(k) = sum_{dR} C^{0,dR}_{nu mu alpha} e^{i k . dR},
+ * with k . dR = 2 pi (kappa . n) for the fractional coordinates kappa of k
+ * and the integer lattice vector n of dR.  C0[r] (n_entries real values)
+ * holds the coefficients of lattice vector R[3r..3r+2]; out receives
+ * n_entries complex values (re, im).  One compensated sum per entry.
+ */
+int oracle_padf_k(int n_R, const int *R, const double *const *C0, long n_entries, const double *kfrac, double *out,
+                  int n_threads) {
+  if (n_R <= 0 || n_entries <= 0) return 1;
+  double *c = (double *)malloc(sizeof(double) * n_R), *sn = (double *)malloc(sizeof(double) * n_R);
+  if (!c || !sn) return 1;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int r = 0; r < n_R; ++r) {
+    const double x = kfrac[0] * R[3 * r] + kfrac[1] * R[3 * r + 1] + kfrac[2] * R[3 * r + 2];
+    c[r] = cos(two_pi * x);
+    sn[r] = sin(two_pi * x);
+  }
+  if (n_threads < 1) n_threads = 1;
+#pragma omp parallel for schedule(static) num_threads(n_threads)
+  for (long e = 0; e < n_entries; ++e) {
+    nsum_t sr = {0, 0}, si = {0, 0};
+    for (int r = 0; r < n_R; ++r) {
+      nsum_add(&sr, C0[r][e] * c[r]);
+      nsum_add(&si, C0[r][e] * sn[r]);
+    }
+    out[2 * e] = nsum_get(&sr);
+    out[2 * e + 1] = nsum_get(&si);
+  }
+  free(c);
+  free(sn);
+  return 0;
+}
+
 /* ---------------------------------------- AO -> MO fit coefficients -- */
 /*
  * Fit coefficients of the orbital pair psi*_i(k) psi_a(k+q) from the

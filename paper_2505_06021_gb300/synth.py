@@ -46,7 +46,7 @@ BASE_SEED = 20250506
 # random streams
 # ----------------------------------------------------------------------------
 
-_TAGS = {"eps": 1, "C": 2, "V": 3, "batch": 4, "serve": 5, "padf": 6, "mo": 7}
+_TAGS = {"eps": 1, "C": 2, "V": 3, "batch": 4, "serve": 5, "padf": 6, "mo": 7, "padfR": 8}
 
 
 def _rng(seed: int, tag: str, *idx: int) -> np.random.Generator:
@@ -305,9 +305,16 @@ class AOProblem(Problem):
     ``Problem.C``; MO coefficients are the first n_mo columns of a Haar-random
     unitary (orthogonal when real).  The MO-basis coefficients themselves are
     a result of the method and are not generated here.
+
+    Lattice form (``lattice`` given, [n_R, 3] integer vectors): the job holds
+    the real cell-pair coefficients C^{0,dR} per lattice vector instead,
+    ``padf_R(r)`` [n_bas, S] with variance shares decaying as e^{-|dR|}
+    (summing to the k-form variance), and the k-dependent arrays are the
+    method's lattice sums, not generated here.
     """
 
-    def __init__(self, base: Problem, n_bas_atom: Sequence[int], n_fit_atom: Sequence[int]):
+    def __init__(self, base: Problem, n_bas_atom: Sequence[int], n_fit_atom: Sequence[int],
+                 lattice: Optional[np.ndarray] = None):
         super().__init__(**{f.name: getattr(base, f.name) for f in dataclasses.fields(Problem)})
         self.n_bas_atom = tuple(int(x) for x in n_bas_atom)
         self.n_fit_atom = tuple(int(x) for x in n_fit_atom)
@@ -315,6 +322,7 @@ class AOProblem(Problem):
             raise ValueError("fit functions per atom must sum to n_aux")
         if self.n_occ + self.n_virt > self.n_bas:
             raise ValueError("n_occ + n_virt exceeds the basis size")
+        self.lattice = None if lattice is None else np.ascontiguousarray(lattice, np.int32).reshape(-1, 3)
 
     @property
     def n_atoms(self) -> int:
@@ -340,6 +348,8 @@ class AOProblem(Problem):
         raise TypeError("an AO job has no stored MO-basis fit coefficients")
 
     def padf(self, kappa: int) -> np.ndarray:
+        if self.lattice is not None:
+            raise TypeError("a lattice-form AO job holds cell-pair coefficients, not k-dependent ones")
         rng = _rng(self.seed, "padf", kappa)
         out = np.empty((self.n_bas, self.n_pf), self.dtype)
         v = out.view(np.float64)
@@ -360,15 +370,31 @@ class AOProblem(Problem):
         Qm = Qm * (d / np.abs(d))[None, :]
         return np.ascontiguousarray(Qm[:, :self.n_mo].astype(self.dtype))
 
+    def padf_R(self, r: int) -> np.ndarray:
+        """Real cell-pair coefficients of lattice vector lattice[r]: [n_bas, S]."""
+        rng = _rng(self.seed, "padfR", r)
+        w = np.exp(-np.linalg.norm(self.lattice.astype(np.float64), axis=1))
+        var = self.n_atoms / (2.0 * self.n_ov) * w[r] / w.sum()
+        out = rng.standard_normal((self.n_bas, self.n_pf))
+        out *= math.sqrt(var)
+        return out
+
     def padf_bytes(self) -> int:
+        if self.lattice is not None:
+            return self.n_bas * self.n_pf * 8 * len(self.lattice)
         return self.n_bas * self.n_pf * (16 if self.is_complex else 8) * self.n_kpts
 
 
+def lattice_2d(radius: int) -> np.ndarray:
+    """In-plane lattice vectors (a, b, 0) with |a|, |b| <= radius."""
+    return np.array([(a, b, 0) for a in range(-radius, radius + 1) for b in range(-radius, radius + 1)], np.int32)
+
+
 def make_ao_problem(name: str, *, is_complex: bool, n_bas_atom: Sequence[int], n_fit_atom: Sequence[int],
-                    n_occ: int, n_virt: int, grid: KQGrid, n_w: int, seed: int, **kw) -> AOProblem:
+                    n_occ: int, n_virt: int, grid: KQGrid, n_w: int, seed: int, lattice=None, **kw) -> AOProblem:
     base = make_problem(name, is_complex=is_complex, n_aux=int(sum(n_fit_atom)), n_occ=n_occ, n_virt=n_virt,
                         grid=grid, n_w=n_w, seed=seed, **kw)
-    return AOProblem(base, n_bas_atom, n_fit_atom)
+    return AOProblem(base, n_bas_atom, n_fit_atom, lattice)
 
 
 def _bands(seed: int, grid: KQGrid, n_occ: int, n_virt: int, dispersion: float) -> Tuple[np.ndarray, np.ndarray]:
@@ -410,13 +436,14 @@ def config1(n_w: int = 20, seed: Optional[int] = None, n_aux: int = 512, n_occ: 
 
 
 def config1_ao(n_w: int = 20, seed: Optional[int] = None, n_bas_atom=(128, 128), n_fit_atom=(256, 256),
-               n_occ: int = 32, n_virt: int = 224, kdims=(4, 4, 1)) -> AOProblem:
+               n_occ: int = 32, n_virt: int = 224, kdims=(4, 4, 1), lattice_radius: Optional[int] = None) -> AOProblem:
     """The 2-D periodic workload in AO form: two atoms with 128 basis and 256
     fit functions each (N_bas = 256 = N_occ + N_virt, N_aux = 512), PADF and
     MO coefficients per k-point of the 4x4x1 grid, 20 frequencies."""
     return make_ao_problem("periodic2d-ao-N%d" % sum(n_fit_atom), is_complex=True, n_bas_atom=n_bas_atom,
                            n_fit_atom=n_fit_atom, n_occ=n_occ, n_virt=n_virt, grid=regular_kq_grid(kdims), n_w=n_w,
-                           seed=BASE_SEED + 5 if seed is None else seed)
+                           seed=BASE_SEED + 5 if seed is None else seed,
+                           lattice=None if lattice_radius is None else lattice_2d(lattice_radius))
 
 
 def config2(n_w: int = 16, seed: Optional[int] = None, n_aux: int = 768, n_occ: int = 32, n_virt: int = 480,

@@ -133,3 +133,42 @@ def test_chi0_matches_ao_space_pair_response(is_complex):
         ref += p.grid.zeta_k * np.einsum("gmn,mnpr,hpr->gh", np.conj(B), R, B)
     scale = np.abs(ref).max()
     assert np.abs(chi - (ref if is_complex else ref.real)).max() <= 1e-13 * scale
+
+
+# ---- k-dependent PADF coefficients: C(k) = sum_dR C^{0,dR} e^{i k.dR} ----
+
+def test_padf_k_is_an_inverse_dft_on_the_supercell():
+    """On a regular n1 x n2 k-grid with the lattice vectors of one n1 x n2
+    supercell the lattice sum is n1 n2 times numpy's inverse 2-D DFT."""
+    n1, n2, ne = 3, 4, 7
+    rng = np.random.default_rng(21)
+    C0 = rng.standard_normal((n1, n2, ne))
+    R = np.array([(a, b, 0) for a in range(n1) for b in range(n2)])
+    ref = n1 * n2 * np.fft.ifft2(C0, axes=(0, 1))
+    for a in range(n1):
+        for b in range(n2):
+            got = oracle.padf_k([C0[x, y] for x in range(n1) for y in range(n2)], R, (a / n1, b / n2, 0.0))
+            assert np.allclose(got, ref[a, b], rtol=0, atol=1e-14)
+
+
+def test_padf_k_conjugate_at_minus_k_and_gamma_sum():
+    rng = np.random.default_rng(22)
+    R = synth.lattice_2d(2)
+    C0 = [rng.standard_normal(11) for _ in range(len(R))]
+    kf = (0.137, -0.291, 0.0)
+    a = oracle.padf_k(C0, R, kf)
+    b = oracle.padf_k(C0, R, tuple(-x for x in kf))
+    assert np.allclose(b, np.conj(a), rtol=0, atol=1e-15)
+    g = oracle.padf_k(C0, R, (0.0, 0.0, 0.0))
+    assert np.allclose(g.real, np.sum(C0, axis=0), rtol=0, atol=1e-14) and np.all(g.imag == 0.0)
+
+
+def test_padf_k_lattice_shift_is_a_phase():
+    rng = np.random.default_rng(23)
+    R = synth.lattice_2d(1)
+    C0 = [rng.standard_normal(5) for _ in range(len(R))]
+    kf = (0.25, 0.4, 0.0)
+    n0 = np.array([2, -1, 0])
+    a = oracle.padf_k(C0, R, kf)
+    b = oracle.padf_k(C0, R + n0[None, :], kf)
+    assert np.allclose(b, a * np.exp(2j * np.pi * np.dot(kf, n0)), rtol=0, atol=1e-14)
