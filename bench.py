@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--n-inst", type=int, default=64, help="batch: instances per step")
     ap.add_argument("--ao-scale", type=int, default=1,
                     help="periodic2d-ao, profiling only: divide basis, fit, occupied and virtual counts by this")
+    ap.add_argument("--ao-lattice", type=int, default=0,
+                    help="periodic2d-ao: give the PADF coefficients per lattice vector (|a|,|b| <= this) instead "
+                         "of per k-point; the library forms the lattice sums")
     ap.add_argument("--serve-jobs", type=int, default=200, help="serving: jobs in the stream")
     ap.add_argument("--serve-load", type=float, default=0.8, help="serving: arrival rate / measured capacity")
     ap.add_argument("--serve-cap-gb", type=float, default=120.0, help="serving: HBM admission cap")
@@ -726,11 +729,15 @@ def ao_flops(p):
     """Algorithmic FP64 flops of the AO -> MO transform of a whole AO-form job
     (8 per complex multiply-add, 2 per real one): the half-transforms
     n_bas * S * n_occ per k-point used as k and n_bas * S * n_virt per k-point
-    used as k+q, then 2 * sum_A nb_A nf_A * N_ov per (q, k) pair."""
+    used as k+q (plus, lattice form, the lattice sums), then
+    2 * sum_A nb_A nf_A * N_ov per (q, k) pair."""
     f = 8.0 if p.is_complex else 2.0
     ko = len(set(p.grid.pair_k.reshape(-1).tolist()))
     kv = len(set(p.grid.pair_kq.reshape(-1).tolist()))
     half = f * p.n_bas * p.n_pf * (ko * p.n_occ + kv * p.n_virt)
+    if getattr(p, "lattice", None) is not None:  # lattice sums: a real-times-phase multiply-add per vector
+        kk = len(set(p.grid.pair_k.reshape(-1).tolist()) | set(p.grid.pair_kq.reshape(-1).tolist()))
+        half += (4.0 if p.is_complex else 2.0) * len(p.lattice) * p.n_bas * p.n_pf * kk
     asm = f * 2.0 * p.n_pf * p.n_ov * p.n_q * p.n_k
     return half, asm
 
@@ -750,7 +757,8 @@ def run_ao(args):
     prec = "mixed" if args.prec in ("auto", "mixed") else "fp64"
     pc = rpa.PREC_MIXED if prec == "mixed" else rpa.PREC_FP64
     sc = max(1, args.ao_scale)
-    p = synth.config1_ao(n_bas_atom=(128 // sc,) * 2, n_fit_atom=(256 // sc,) * 2, n_occ=32 // sc, n_virt=224 // sc)
+    p = synth.config1_ao(n_bas_atom=(128 // sc,) * 2, n_fit_atom=(256 // sc,) * 2, n_occ=32 // sc, n_virt=224 // sc,
+                         lattice_radius=args.ao_lattice or None)
     if args.n_q:
         g = p.grid
         g.pair_k, g.pair_kq, g.w_q, g.qpts = g.pair_k[:args.n_q], g.pair_kq[:args.n_q], g.w_q[:args.n_q], \
@@ -801,10 +809,13 @@ def run_ao(args):
             "data": "synthetic (seeded PADF and MO coefficients with the shapes of the 2-D periodic workload)",
             "config": {"workload": "periodic2d-ao: the 2-D periodic job (16 q x 16 k, N_aux=%d, N_occ=%d, "
                                    "N_virt=%d, 20 frequencies) in AO form: 2 atoms x (%d basis, %d fit "
-                                   "functions), N_bas=%d, PADF %.1f GB + MO coefficients per k-point; MO-basis "
-                                   "coefficients formed per q on the device%s"
+                                   "functions), N_bas=%d, PADF %.1f GB %s + MO coefficients per k-point; "
+                                   "MO-basis coefficients formed per q on the device%s"
                                    % (p.n_aux, p.n_occ, p.n_virt, p.n_bas_atom[0], p.n_fit_atom[0], p.n_bas,
                                       p.padf_bytes() / 1e9,
+                                      "per k-point" if p.lattice is None else
+                                      "(real, per lattice vector of %d; k-point arrays formed as lattice sums)"
+                                      % len(p.lattice),
                                       "" if sc == 1 and not args.n_q else " [reduced: profiling case]"),
                        "n_q": p.n_q, "n_k": p.n_k, "n_aux": p.n_aux, "n_occ": p.n_occ, "n_virt": p.n_virt,
                        "n_w": p.n_w, "n_bas": p.n_bas, "n_atoms": p.n_atoms, "chi0_prec": prec,
@@ -825,13 +836,14 @@ def run_ao(args):
                         "max_rel_err_per_term": float(rel.max())}
     if not args.no_e2e and not args.n_q:
         # host-resident AO inputs (pinned) copied to the device inside the timed region
-        hp = [t.cpu().pin_memory() for t in tens["padf"]]
+        pin_src = tens["padf"] if tens["padf"] is not None else tens["padf_R"]
+        hp = [t.cpu().pin_memory() for t in pin_src]
         hm = [t.cpu().pin_memory() for t in tens["mo"]]
         hv = [t.cpu().pin_memory() for t in tens["V"]]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            for d, h in zip(tens["padf"] + tens["mo"] + tens["V"], hp + hm + hv):
+            for d, h in zip(pin_src + tens["mo"] + tens["V"], hp + hm + hv):
                 d.copy_(h, non_blocking=True)
             torch.cuda.synchronize()
             rh = ctx.energy(job)

@@ -98,14 +98,24 @@ typedef struct {
  *                   + [gamma on atom(nu)] conj(C_{mu nu gamma}(k)),
  * on the fly, one q at a time (k = k_j from pair_k, k+q from pair_kq), so the
  * MO-basis coefficients of the whole job never reside in memory at once.
+ * Lattice form (n_R > 0, padf NULL): the job gives the real cell-pair
+ * coefficients C^{0,dR} per lattice vector instead (same n_bas x S layout)
+ * and the library forms each k-point's array as the lattice sum of Sec. 2.2,
+ *   C_{nu mu alpha}(k) = sum_dR C^{0,dR}_{nu mu alpha} e^{i k . dR},
+ * k . dR = 2 pi (kfrac . n), one k-point at a time in workspace.  Real
+ * (Gamma-only) jobs need integer kfrac there.
  * Device memory only; the arrays are borrowed like C. */
 typedef struct {
   int n_atoms;
   const int *n_bas_atom;   /* host [n_atoms]: basis functions per atom (> 0) */
   const int *n_fit_atom;   /* host [n_atoms]: fit functions per atom (> 0), sum = n_aux */
   int n_mo;                /* columns of every mo[kappa] (>= n_occ + n_virt, <= n_bas) */
-  const void *const *padf; /* host [n_kpts] of device pointers, n_bas x S each */
+  const void *const *padf; /* host [n_kpts] of device pointers, n_bas x S each (NULL: lattice form) */
   const void *const *mo;   /* host [n_kpts] of device pointers, n_bas x n_mo each */
+  int n_R;                    /* lattice form: lattice vectors (1..128); 0 for the k form */
+  const int *lattice;         /* host [n_R*3]: integer lattice vectors dR */
+  const double *kfrac;        /* host [n_kpts*3]: fractional coordinates of the k-points */
+  const void *const *padf_R;  /* host [n_R] of device pointers, real float64 n_bas x S each */
 } rpa_ao;
 
 typedef struct {

@@ -47,7 +47,9 @@ class rpa_config(ctypes.Structure):
 class rpa_ao(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int), ("n_bas_atom", ctypes.POINTER(ctypes.c_int)),
                 ("n_fit_atom", ctypes.POINTER(ctypes.c_int)), ("n_mo", ctypes.c_int),
-                ("padf", ctypes.POINTER(ctypes.c_void_p)), ("mo", ctypes.POINTER(ctypes.c_void_p))]
+                ("padf", ctypes.POINTER(ctypes.c_void_p)), ("mo", ctypes.POINTER(ctypes.c_void_p)),
+                ("n_R", ctypes.c_int), ("lattice", ctypes.POINTER(ctypes.c_int)),
+                ("kfrac", ctypes.POINTER(ctypes.c_double)), ("padf_R", ctypes.POINTER(ctypes.c_void_p))]
 
 
 class rpa_job(ctypes.Structure):
@@ -123,7 +125,9 @@ class Job:
 
     AO form (``ao`` given, ``C`` None): ``ao`` is a dict with ``n_bas_atom``,
     ``n_fit_atom`` (per atom), and the per-k-point device tensors ``padf``
-    [n_bas, S] and ``mo`` [n_bas, n_mo] (layouts of ``rpa_ao``)."""
+    [n_bas, S] and ``mo`` [n_bas, n_mo] (layouts of ``rpa_ao``); lattice form:
+    ``padf`` None and ``padf_R`` (real [n_bas, S] per lattice vector),
+    ``lattice`` [n_R, 3] integers and ``kfrac`` [n_kpts, 3]."""
 
     def __init__(self, *, is_complex: bool, n_aux: int, n_occ: int, n_virt: int, pair_k, pair_kq, w_q, zeta_k: float,
                  omega, zeta_w, eps_occ, eps_virt, C: Optional[Sequence], V: Sequence, prec: int = PREC_FP64,
@@ -154,15 +158,24 @@ class Job:
         if ao is not None:
             self._nb = np.array(ao["n_bas_atom"], np.int32)
             self._nf = np.array(ao["n_fit_atom"], np.int32)
-            self._Pp = (ctypes.c_void_p * len(ao["padf"]))(*[int(t.data_ptr()) for t in ao["padf"]])
+            padf = ao.get("padf") or []
+            self._Pp = (ctypes.c_void_p * max(1, len(padf)))(*[int(t.data_ptr()) for t in padf])
             self._Mp = (ctypes.c_void_p * len(ao["mo"]))(*[int(t.data_ptr()) for t in ao["mo"]])
             a = rpa_ao()
             a.n_atoms = int(self._nb.shape[0])
             a.n_bas_atom = self._nb.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
             a.n_fit_atom = self._nf.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
             a.n_mo = int(ao["mo"][0].shape[1])
-            a.padf = ctypes.cast(self._Pp, ctypes.POINTER(ctypes.c_void_p))
+            a.padf = ctypes.cast(self._Pp, ctypes.POINTER(ctypes.c_void_p)) if padf else None
             a.mo = ctypes.cast(self._Mp, ctypes.POINTER(ctypes.c_void_p))
+            if ao.get("padf_R") is not None:
+                self._lat = np.ascontiguousarray(ao["lattice"], np.int32).reshape(-1)
+                self._kf = np.ascontiguousarray(ao["kfrac"], np.float64).reshape(-1)
+                self._Rp = (ctypes.c_void_p * len(ao["padf_R"]))(*[int(t.data_ptr()) for t in ao["padf_R"]])
+                a.n_R = len(ao["padf_R"])
+                a.lattice = self._lat.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+                a.kfrac = _dptr(self._kf)
+                a.padf_R = ctypes.cast(self._Rp, ctypes.POINTER(ctypes.c_void_p))
             self._ao = a
             s.ao = ctypes.pointer(a)
         self.s = s
@@ -208,8 +221,10 @@ def job_from_ao_problem(problem, tensors: Dict[str, object], prec: int = PREC_FP
     """Job of an AO-form synthetic problem (``synth.AOProblem``) from
     :func:`upload_ao_problem`'s tensors."""
     g = problem.grid
-    ao = {"n_bas_atom": problem.n_bas_atom, "n_fit_atom": problem.n_fit_atom, "padf": tensors["padf"],
+    ao = {"n_bas_atom": problem.n_bas_atom, "n_fit_atom": problem.n_fit_atom, "padf": tensors.get("padf"),
           "mo": tensors["mo"]}
+    if tensors.get("padf_R") is not None:
+        ao.update(padf_R=tensors["padf_R"], lattice=problem.lattice, kfrac=problem.grid.kpts)
     return Job(is_complex=problem.is_complex, n_aux=problem.n_aux, n_occ=problem.n_occ, n_virt=problem.n_virt,
                pair_k=g.pair_k, pair_kq=g.pair_kq, w_q=g.w_q, zeta_k=g.zeta_k, omega=problem.omega,
                zeta_w=problem.zeta_w, eps_occ=tensors["eps_occ"], eps_virt=tensors["eps_virt"], C=None,
@@ -217,8 +232,9 @@ def job_from_ao_problem(problem, tensors: Dict[str, object], prec: int = PREC_FP
 
 
 def upload_ao_problem(problem, device="cuda", threads: int = 0):
-    """Device tensors of an AO-form problem: PADF and MO arrays per k-point,
-    V per q, band energies."""
+    """Device tensors of an AO-form problem: PADF (or, lattice form, cell-pair
+    coefficients per lattice vector) and MO arrays per k-point, V per q, band
+    energies."""
     import concurrent.futures as cf
 
     import torch
@@ -232,10 +248,12 @@ def upload_ao_problem(problem, device="cuda", threads: int = 0):
 
     nthr = threads or min(16, os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(nthr) as ex:
-        padf = list(ex.map(lambda k: put(problem.padf(k)), range(problem.n_kpts)))
+        lat = getattr(problem, "lattice", None) is not None
+        padf = None if lat else list(ex.map(lambda k: put(problem.padf(k)), range(problem.n_kpts)))
+        padf_R = list(ex.map(lambda r: put(problem.padf_R(r)), range(len(problem.lattice)))) if lat else None
         mo = list(ex.map(lambda k: put(problem.mo(k)), range(problem.n_kpts)))
         V = list(ex.map(lambda q: put(problem.V(q)), range(problem.n_q)))
-    return {"padf": padf, "mo": mo, "V": V, "eps_occ": put(problem.eps_occ.astype(np.float64)),
+    return {"padf": padf, "padf_R": padf_R, "mo": mo, "V": V, "eps_occ": put(problem.eps_occ.astype(np.float64)),
             "eps_virt": put(problem.eps_virt.astype(np.float64))}
 
 

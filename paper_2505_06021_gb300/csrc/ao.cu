@@ -4,6 +4,7 @@
 //
 // Workspace region (offsets from Bufs.ao):
 //   fit table   int4 per fit function gamma (see launch_ao_assemble)
+//   PADF        lattice form only: one k-point's k-dependent PADF array
 //   H_occ       one S x n_occ slot per k-point that appears as k (pair_k)
 //   H_virt      one S x n_virt slot per k-point that appears as k+q (pair_kq)
 //   C           n_k blocks n_aux x n_occ*n_virt: the MO-basis coefficients of
@@ -11,6 +12,7 @@
 // The half-transforms depend on the k-point only, so rpa_energy forms them
 // once per job; each q then costs one assembly launch.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdio.h>
 
 #include <algorithm>
@@ -34,8 +36,23 @@ int ao_validate(const rpa_job* j, char* msg, size_t len) {
   const rpa_ao* a = j->ao;
   if (j->C) return fail("AO-form job: C must be NULL (the coefficients are formed from ao)");
   if (j->mem != RPA_MEM_DEVICE) return fail("AO-form job: inputs must be in device memory");
-  if (a->n_atoms <= 0 || !a->n_bas_atom || !a->n_fit_atom || !a->padf || !a->mo)
+  if (a->n_atoms <= 0 || !a->n_bas_atom || !a->n_fit_atom || !a->mo)
     return fail("AO-form job: n_atoms must be positive and the ao arrays non-NULL");
+  if (a->n_R < 0 || a->n_R > PadfLattice::kMax)
+    return fail("AO-form job: n_R must lie in [0, 128]");
+  if (a->n_R > 0) {
+    if (a->padf) return fail("AO-form job: give padf or the lattice form (n_R > 0), not both");
+    if (!a->lattice || !a->kfrac || !a->padf_R) return fail("AO-form job: lattice form needs lattice, kfrac, padf_R");
+    for (int r = 0; r < a->n_R; ++r)
+      if (!a->padf_R[r]) return fail("AO-form job: a padf_R pointer is NULL");
+    for (int k = 0; k < 3 * j->n_kpts; ++k) {
+      if (!isfinite(a->kfrac[k])) return fail("AO-form job: kfrac not finite");
+      if (!j->is_complex && a->kfrac[k] != floor(a->kfrac[k]))
+        return fail("AO-form job: real (Gamma-only) lattice-form jobs need integer kfrac");
+    }
+  } else if (!a->padf) {
+    return fail("AO-form job: padf is NULL and no lattice form given");
+  }
   long nb = 0, nf = 0, S = 0;
   for (int A = 0; A < a->n_atoms; ++A) {
     if (a->n_bas_atom[A] <= 0 || a->n_fit_atom[A] <= 0)
@@ -49,7 +66,7 @@ int ao_validate(const rpa_job* j, char* msg, size_t len) {
     return fail("AO-form job: n_mo must lie in [n_occ + n_virt, n_bas]");
   if (nb > 65536 || S > (1L << 30)) return fail("AO-form job: basis or PADF array too large");
   for (int k = 0; k < j->n_kpts; ++k)
-    if (!a->padf[k] || !a->mo[k]) return fail("AO-form job: a padf or mo pointer is NULL");
+    if ((a->n_R == 0 && !a->padf[k]) || !a->mo[k]) return fail("AO-form job: a padf or mo pointer is NULL");
   return RPA_OK;
 }
 
@@ -78,7 +95,9 @@ AoPlan ao_plan(const rpa_job* j) {
   p.occ_bytes = al256(es * (size_t)p.S * j->n_occ);
   p.virt_bytes = al256(es * (size_t)p.S * j->n_virt);
   p.cblk = es * (size_t)j->n_aux * j->n_occ * j->n_virt;
-  p.off_hocc = al256(sizeof(int4) * (size_t)j->n_aux);
+  p.off_padf = al256(sizeof(int4) * (size_t)j->n_aux);
+  p.padf_bytes = a->n_R > 0 ? al256(es * (size_t)p.n_bas * p.S) : 0;
+  p.off_hocc = p.off_padf + p.padf_bytes;
   p.off_hvirt = p.off_hocc + p.occ_bytes * p.n_occ_slots;
   p.off_c = p.off_hvirt + p.virt_bytes * p.n_virt_slots;
   p.bytes = p.off_c + al256(p.cblk * j->n_k);
@@ -91,6 +110,8 @@ size_t ao_input_bytes(const rpa_job* j) {
   if (!j->ao) return 0;
   const AoPlan p = ao_plan(j);
   const size_t es = j->is_complex ? 16 : 8;
+  if (j->ao->n_R > 0)
+    return 8 * (size_t)j->ao->n_R * p.n_bas * p.S + es * (size_t)j->n_kpts * p.n_bas * j->ao->n_mo;
   return es * (size_t)j->n_kpts * p.n_bas * ((size_t)p.S + j->ao->n_mo);
 }
 
@@ -115,17 +136,33 @@ rpa_status ao_enqueue_half(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const AoPl
       need_o[j->pair_k[(size_t)qq * j->n_k + jj]] = 1;
       need_v[j->pair_kq[(size_t)qq * j->n_k + jj]] = 1;
     }
+  PadfLattice lat{};
+  if (a->n_R > 0) {
+    lat.n_R = a->n_R;
+    for (int r = 0; r < a->n_R; ++r) {
+      for (int d = 0; d < 3; ++d) lat.R[r][d] = a->lattice[3 * r + d];
+      lat.C0[r] = (const double*)a->padf_R[r];
+    }
+  }
   int n = 0;
   prof_begin(ctx, pex, s);
   for (int k = 0; k < j->n_kpts; ++k) {
+    if (!need_o[k] && !need_v[k]) continue;
+    const double* P = (const double*)(a->n_R > 0 ? nullptr : a->padf[k]);
+    if (a->n_R > 0) {  // this k-point's array as the lattice sum, into the PADF slot
+      CKA(launch_padf_k(j->is_complex, lat, a->kfrac + 3 * k, (long)p.n_bas * p.S, (double*)(region + p.off_padf),
+                        s));
+      P = (const double*)(region + p.off_padf);
+      ++n;
+    }
     if (need_o[k]) {
-      CKA(launch_ao_half(j->is_complex, p.n_bas, p.S, a->n_mo, (const double*)a->padf[k], (const double*)a->mo[k], 0,
-                         j->n_occ, (double*)(region + p.off_hocc + p.occ_bytes * p.occ_slot[k]), s));
+      CKA(launch_ao_half(j->is_complex, p.n_bas, p.S, a->n_mo, P, (const double*)a->mo[k], 0, j->n_occ,
+                         (double*)(region + p.off_hocc + p.occ_bytes * p.occ_slot[k]), s));
       ++n;
     }
     if (need_v[k]) {
-      CKA(launch_ao_half(j->is_complex, p.n_bas, p.S, a->n_mo, (const double*)a->padf[k], (const double*)a->mo[k],
-                         j->n_occ, j->n_virt, (double*)(region + p.off_hvirt + p.virt_bytes * p.virt_slot[k]), s));
+      CKA(launch_ao_half(j->is_complex, p.n_bas, p.S, a->n_mo, P, (const double*)a->mo[k], j->n_occ, j->n_virt,
+                         (double*)(region + p.off_hvirt + p.virt_bytes * p.virt_slot[k]), s));
       ++n;
     }
   }

@@ -20,6 +20,7 @@ struct AoPlan {
   int n_occ_slots = 0, n_virt_slots = 0;
   size_t occ_bytes = 0, virt_bytes = 0;  // one slot
   size_t cblk = 0;                       // one C(q, k_j) block
+  size_t off_padf = 0, padf_bytes = 0;   // lattice form: one k-point's PADF array
   size_t off_hocc = 0, off_hvirt = 0, off_c = 0, bytes = 0;
 };
 

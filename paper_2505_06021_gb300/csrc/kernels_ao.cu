@@ -20,13 +20,20 @@
 // n_bas^2 n_aux n_occ n_virt for the direct double sum; the half-transforms
 // are done once per k-point, not once per pair.
 //
-// Both kernels are FP64 (DFMA): the result feeds the FP64 chi0 path directly
+// Lattice form: the k-dependent arrays are the lattice sums of the cell-pair
+// coefficients (Sec. 2.2), C(kappa) = sum_dR C^{0,dR} e^{2 pi i kappa.n},
+// formed one k-point at a time by padf_k_kernel just before its
+// half-transforms (HBM-bound: n_R real reads and one complex write per entry).
+//
+// The transform kernels are FP64 (DFMA): the result feeds the FP64 chi0 path directly
 // and the split-precision path through its own 31-bit slicing.  GB300 issues
 // about two DFMA per clock per SM, so the kernels are organised only to keep
 // that pipe busy: a 32 x 32 output tile per CTA, 2 x 2 outputs per thread,
 // operands staged through shared memory in K-steps of 16 with coalesced row
 // loads, every complex multiply-add four DFMAs.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "fp64_elem.cuh"
 #include "rpa_internal.h"
@@ -146,7 +153,47 @@ __global__ void __launch_bounds__(256) ao_assemble_kernel(const __grid_constant_
     }
 }
 
+// out[e] = sum_r C0[r][e] e^{2 pi i kappa . R_r}; real jobs keep the real part
+// (Gamma-equivalent k-points only, where every phase is 1).
+template <bool C>
+__global__ void __launch_bounds__(256) padf_k_kernel(const __grid_constant__ PadfLattice L, double k0, double k1,
+                                                     double k2, long n, double* __restrict__ out) {
+  __shared__ double cs[PadfLattice::kMax], sn[PadfLattice::kMax];
+  for (int r = threadIdx.x; r < L.n_R; r += blockDim.x) {
+    const double x = k0 * L.R[r][0] + k1 * L.R[r][1] + k2 * L.R[r][2];
+    sincospi(2.0 * x, &sn[r], &cs[r]);
+  }
+  __syncthreads();
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int r = 0; r < L.n_R; ++r) {
+      const double v = __ldcs(L.C0[r] + e);
+      re = fma(v, cs[r], re);
+      if constexpr (C) im = fma(v, sn[r], im);
+    }
+    if constexpr (C)
+      *reinterpret_cast<double2*>(out + 2 * e) = make_double2(re, im);
+    else
+      out[e] = re;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_padf_k(int cplx, const PadfLattice& L, const double* kfrac, long n, double* out,
+                          cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (L.n_R <= 0 || L.n_R > PadfLattice::kMax) return cudaErrorInvalidValue;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long blocks = std::min<long>((n + 255) / 256, (long)sms * 16);
+  if (cplx)
+    padf_k_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(L, kfrac[0], kfrac[1], kfrac[2], n, out);
+  else
+    padf_k_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(L, kfrac[0], kfrac[1], kfrac[2], n, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ao_half(int cplx, int n_bas, int S, int n_mo, const double* P, const double* c, int n0, int ncols,
                            double* H, cudaStream_t s) {

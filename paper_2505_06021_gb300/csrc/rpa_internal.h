@@ -76,6 +76,18 @@ cudaError_t launch_vinv(int cplx, int N, int n_q, const double* L, double* X, do
 cudaError_t launch_ao_half(int cplx, int n_bas, int S, int n_mo, const double* P, const double* c, int n0, int ncols,
                            double* H, cudaStream_t s);
 
+// Lattice form of the PADF coefficients: n_R integer lattice vectors and the
+// device arrays of their real cell-pair coefficients.
+struct PadfLattice {
+  static constexpr int kMax = 128;
+  int n_R;
+  int R[kMax][3];
+  const double* C0[kMax];
+};
+// out[e] = sum_r C0[r][e] e^{2 pi i kfrac . R_r} for e < n (complex128 out),
+// or the real part (cplx == 0, Gamma-equivalent k-points).
+cudaError_t launch_padf_k(int cplx, const PadfLattice& L, const double* kfrac, long n, double* out, cudaStream_t s);
+
 // Per (q, k) pair of one launch: MO coefficients at k and k+q, half-
 // transforms H_occ(k) (S x n_occ) and H_virt(k+q) (S x n_virt), output
 // C(q, k) (n_aux x n_occ*n_virt).

@@ -144,3 +144,27 @@ def test_ao_footprint_counts_padf_not_mo_basis_coefficients(lib):
     # q's MO-basis coefficients 0.94 GB; the job's 15 GB of C never resides
     assert 9.0e9 < fp < 15.0e9
     assert p.padf_bytes() == 16 * 256 * 65536 * 16
+
+
+def test_validate_lattice_form_ao_jobs(lib):
+    p = synth.config1_ao(n_bas_atom=(8, 6), n_fit_atom=(10, 14), n_occ=3, n_virt=9, lattice_radius=1)
+    R = [FakeTensor(0x400000 + 0x100 * r) for r in range(len(p.lattice))]
+    st, msg = _fake_ao_job(p, padf=None, padf_R=R).validate()
+    assert st == rpa.RPA_OK, msg
+    # both forms at once
+    j = _fake_ao_job(p, padf=[FakeTensor(0x200000 + 0x100 * k) for k in range(p.n_kpts)], padf_R=R)
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "not both" in msg
+    j = _fake_ao_job(p, padf=None, padf_R=R)
+    j._Rp[3] = None
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "padf_R" in msg
+    # a real Gamma-only job needs integer k-point coordinates
+    g = synth.make_ao_problem("g", is_complex=False, n_bas_atom=(4, 4), n_fit_atom=(6, 6), n_occ=2, n_virt=5,
+                              grid=synth.gamma_grid(), n_w=4, seed=3, lattice=synth.lattice_2d(1))
+    Rg = [FakeTensor(0x500000 + 0x100 * r) for r in range(len(g.lattice))]
+    j = _fake_ao_job(g, padf=None, padf_R=Rg)
+    assert j.validate()[0] == rpa.RPA_OK
+    j._kf[0] = 0.5
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "integer kfrac" in msg

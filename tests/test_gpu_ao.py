@@ -150,3 +150,50 @@ def test_batch_and_serving_refuse_ao_jobs(rpa):
         with pytest.raises(rpa.RpaError) as e:
             c.submit(job)
         assert e.value.status == rpa.RPA_E_INVAL
+
+
+# ---- lattice form: k-dependent PADF arrays as lattice sums on the device ----
+
+def _lattice(is_complex=True):
+    grid = synth.regular_kq_grid((2, 2, 1)) if is_complex else synth.gamma_grid()
+    return synth.make_ao_problem("ao-lat", is_complex=is_complex, n_bas_atom=(20, 14, 9), n_fit_atom=(26, 30, 16),
+                                 n_occ=7, n_virt=33, grid=grid, n_w=6, seed=63, lattice=synth.lattice_2d(2))
+
+
+@pytest.mark.parametrize("is_complex", [True, False])
+def test_lattice_form_ao2mo_matches_oracle(rpa, is_complex):
+    p = _lattice(is_complex)
+    t = rpa.upload_ao_problem(p)
+    job = rpa.job_from_ao_problem(p, t)
+    with rpa.Context(0) as c:
+        for q in range(p.n_q):
+            out = c.ao2mo(job, q)
+            torch.cuda.synchronize()
+            _check_blocks(out, p, q)
+
+
+def test_lattice_form_equals_k_form_given_the_lattice_sums(rpa):
+    """Isolates the lattice-sum kernel: the k form fed with the oracle's lattice
+    sums must give the lattice form's coefficients to rounding."""
+    p = _lattice()
+    t = rpa.upload_ao_problem(p)
+    jl = rpa.job_from_ao_problem(p, t)
+    tk = dict(t, padf=[torch.from_numpy(oracle.padf_of(p, k)).cuda() for k in range(p.n_kpts)], padf_R=None)
+    jk = rpa.job_from_ao_problem(synth.AOProblem(p, p.n_bas_atom, p.n_fit_atom), tk)
+    with rpa.Context(0) as c:
+        for q in (0, 3):
+            a = c.ao2mo(jl, q)
+            b = c.ao2mo(jk, q)
+            torch.cuda.synchronize()
+            scale = b.abs().max().item()
+            assert (a - b).abs().max().item() <= 1e-13 * scale, q
+
+
+def test_lattice_form_energy_matches_oracle_fp64(rpa):
+    p = _lattice()
+    ref = oracle.energy(p)
+    t = rpa.upload_ao_problem(p)
+    with rpa.Context(0) as c:
+        r = c.energy(rpa.job_from_ao_problem(p, t, prec=rpa.PREC_FP64))
+    assert np.all(np.abs(r["eps"] - ref["eps"]) <= TOL_TERM * np.abs(ref["eps"]))
+    assert abs(r["Ec"] - ref["Ec"]) <= TOL_TERM * abs(ref["Ec"])
