@@ -7,8 +7,8 @@
 //   PADF        lattice form only: one k-point's k-dependent PADF array
 //   H_occ       one S x n_occ slot per k-point that appears as k (pair_k)
 //   H_virt      one S x n_virt slot per k-point that appears as k+q (pair_kq)
-//   C           n_k blocks n_aux x n_occ*n_virt: the MO-basis coefficients of
-//               the q being processed (read by the chi0 step)
+//   C           qb x n_k blocks n_aux x n_occ*n_virt: the MO-basis
+//               coefficients of the q batch being processed (read by chi0)
 // The half-transforms depend on the k-point only, so rpa_energy forms them
 // once per job; each q then costs one assembly launch.
 #include <cuda_runtime.h>
@@ -70,7 +70,7 @@ int ao_validate(const rpa_job* j, char* msg, size_t len) {
   return RPA_OK;
 }
 
-AoPlan ao_plan(const rpa_job* j) {
+AoPlan ao_plan(const rpa_job* j, int qb) {
   AoPlan p;
   const rpa_ao* a = j->ao;
   const size_t es = j->is_complex ? 16 : 8;
@@ -100,15 +100,15 @@ AoPlan ao_plan(const rpa_job* j) {
   p.off_hocc = p.off_padf + p.padf_bytes;
   p.off_hvirt = p.off_hocc + p.occ_bytes * p.n_occ_slots;
   p.off_c = p.off_hvirt + p.virt_bytes * p.n_virt_slots;
-  p.bytes = p.off_c + al256(p.cblk * j->n_k);
+  p.bytes = p.off_c + al256(p.cblk * j->n_k * (size_t)std::max(qb, 1));
   return p;
 }
 
-size_t ao_region_bytes(const rpa_job* j) { return j->ao ? ao_plan(j).bytes : 0; }
+size_t ao_region_bytes(const rpa_job* j, int qb) { return j->ao ? ao_plan(j, qb).bytes : 0; }
 
 size_t ao_input_bytes(const rpa_job* j) {
   if (!j->ao) return 0;
-  const AoPlan p = ao_plan(j);
+  const AoPlan p = ao_plan(j, 1);
   const size_t es = j->is_complex ? 16 : 8;
   if (j->ao->n_R > 0)
     return 8 * (size_t)j->ao->n_R * p.n_bas * p.S + es * (size_t)j->n_kpts * p.n_bas * j->ao->n_mo;

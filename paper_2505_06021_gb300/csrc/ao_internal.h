@@ -26,9 +26,10 @@ struct AoPlan {
 
 // RPA_OK or RPA_E_INVAL with a message; j->ao must be non-null.
 int ao_validate(const rpa_job* j, char* msg, size_t len);
-AoPlan ao_plan(const rpa_job* j);
+// qb: q whose MO-basis coefficients the region holds at once.
+AoPlan ao_plan(const rpa_job* j, int qb);
 // Bytes of the AO workspace region (0 for jobs without ao).
-size_t ao_region_bytes(const rpa_job* j);
+size_t ao_region_bytes(const rpa_job* j, int qb);
 // Device bytes of the job's AO inputs (PADF and MO arrays of all k-points).
 size_t ao_input_bytes(const rpa_job* j);
 // Fit table upload and half-transforms of the k-points used by q (q < 0: by

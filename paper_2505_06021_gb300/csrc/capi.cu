@@ -221,41 +221,46 @@ static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 // Workspace cap of the synchronous calls (the serving lanes use a smaller one).
 size_t sync_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap, (size_t)64 << 30); }
 
-Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool mixed_ws) {
+Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool mixed_ws, int qt) {
   Layout L{};
+  if (qt < qb) qt = qb;
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
   const size_t nov = (size_t)j->n_occ * j->n_virt;
   const size_t npk = (size_t)j->n_q * j->n_k;
   const size_t nqw = (size_t)j->n_q * j->n_w;
   L.qb = qb;
+  L.qt = qt;
   L.meta = al(sizeof(void*) * npk + sizeof(int) * 2 * npk + 64) +
            al(sizeof(double) * (2 * j->n_w + 2 * j->n_q + 3 * nqw + 8) + 64);
   L.dtab = al(sizeof(double) * qb * j->n_k * j->n_w * nov);
-  L.chi = al(es * NN * qb * j->n_w);
+  L.chi = al(es * NN * qt * j->n_w);
   L.T = L.chi;
-  L.L = al(es * NN * qb);
+  L.L = al(es * NN * qt);
   if (j->mem == RPA_MEM_HOST) {
     L.stageC = al(es * j->n_aux * nov * qb * j->n_k);
     L.stageV = al(es * NN * qb);
     L.eps = al(sizeof(double) * (size_t)j->n_kpts * (j->n_occ + j->n_virt));
   }
   if (j->prec == RPA_PREC_MIXED) {
-    L.Vc = al(es * NN * qb);  // the inverse-form tail keeps a copy of V(q)
+    L.Vc = al(es * NN * qt);  // the inverse-form tail keeps a copy of V(q)
     if (mixed_ws) {
       BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, (int)nov, j->n_k, j->n_w, 1};
       L.slice_cap = ws_cap / 2;
       L.mixed = al(mixed_workspace_bytes(g, n_slices, L.slice_cap));
     }
   }
-  L.ao = al(ao_region_bytes(j));
+  L.ao = al(ao_region_bytes(j, qb));
   L.total = L.meta + L.dtab + L.chi + L.T + L.L + L.Vc + 2 * (L.stageC + L.stageV) + L.eps + L.mixed + L.ao;
   return L;
 }
 
 int choose_qb(const rpa_job* j, int n_slices, size_t cap) {
-  if (j->ao) return 1;  // one q's MO-basis coefficients at a time
   int qb = j->n_q;
+  if (j->ao) {  // AO form: the MO-basis coefficients of a few q at a time (<= 4 GB)
+    const size_t per_q = (j->is_complex ? 16 : 8) * (size_t)j->n_aux * j->n_occ * j->n_virt * j->n_k;
+    qb = (int)std::max<size_t>(1, std::min<size_t>((size_t)j->n_q, ((size_t)4 << 30) / std::max<size_t>(per_q, 1)));
+  }
   while (qb > 1 && plan_layout(j, qb, n_slices, cap, true).total > cap) qb = (qb + 1) / 2;
   // host-resident inputs: at least four q-batches, so that the copies of one
   // batch overlap the compute of the previous one
@@ -263,12 +268,24 @@ int choose_qb(const rpa_job* j, int n_slices, size_t cap) {
   return qb;
 }
 
+int choose_qt(const rpa_job* j, int qb, int n_slices, size_t cap) {
+  // host-staged and AO-form jobs compute chi0 per staging batch; their tail
+  // (V factor, log-det) runs over as many q as fit, so that its Cholesky
+  // launches fill the GPU
+  if (j->mem != RPA_MEM_HOST && !j->ao) return qb;
+  int m = (j->n_q + qb - 1) / qb;
+  while (m > 1 && plan_layout(j, qb, n_slices, cap, true, std::min(j->n_q, m * qb)).total > cap) m = (m + 1) / 2;
+  return std::min(j->n_q, m * qb);
+}
+
 size_t job_workspace(const rpa_job* j, int n_slices, size_t ws_cap) {
-  return plan_layout(j, choose_qb(j, n_slices, ws_cap), n_slices, ws_cap, true).total;
+  const int qb = choose_qb(j, n_slices, ws_cap);
+  return plan_layout(j, qb, n_slices, ws_cap, true, choose_qt(j, qb, n_slices, ws_cap)).total;
 }
 
 size_t job_footprint(const rpa_job* j, int n_slices, size_t ws_cap) {
-  Layout L = plan_layout(j, choose_qb(j, n_slices, ws_cap), n_slices, ws_cap, true);
+  const int qb = choose_qb(j, n_slices, ws_cap);
+  Layout L = plan_layout(j, qb, n_slices, ws_cap, true, choose_qt(j, qb, n_slices, ws_cap));
   size_t in = 0;
   if (j->mem == RPA_MEM_DEVICE) {
     const size_t es = j->is_complex ? 16 : 8;
@@ -393,16 +410,26 @@ rpa_status stage_dtab(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, 
 
 // The FP64 steps after chi0 for q in [q0, q0+nq), chi0 in b.chi: factor V,
 // sandwich, Cholesky log-det.  V of the batch at Vdev[0..nq).
-rpa_status stage_vside(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
-                       const void* const* Vdev, cudaStream_t s) {
+// V(q) of nq q-points into slots lo.. of L (and of the inverse form's copy Vc).
+static rpa_status vside_copy(rpa_ctx* ctx, const rpa_job* j, const Bufs& b, int lo, int nq, const void* const* Vdev,
+                             cudaStream_t s) {
+  const size_t es = j->is_complex ? 16 : 8;
+  const size_t NN = (size_t)j->n_aux * j->n_aux;
+  for (int qi = 0; qi < nq; ++qi) {
+    CK(cudaMemcpyAsync(b.L + (lo + qi) * NN * (es / 8), Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
+    if (b.Vc)
+      CK(cudaMemcpyAsync(b.Vc + (lo + qi) * NN * (es / 8), Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
+  }
+  return RPA_OK;
+}
+
+// V = L L^H for the q in [q0, q0+nq) held in slots 0..nq-1 of L (and, for the
+// inverse form, ln det V and -V^-1 over L).
+static rpa_status vside_factor(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
+                               cudaStream_t s) {
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
   const long mstride = (long)(NN * (es / 8));
-  // V(q) -> L, the lower Cholesky factor (V = L L^H), one matrix per q
-  for (int qi = 0; qi < nq; ++qi) {
-    CK(cudaMemcpyAsync(b.L + qi * NN * (es / 8), Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
-    if (b.Vc) CK(cudaMemcpyAsync(b.Vc + qi * NN * (es / 8), Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
-  }
   prof_begin(ctx, pex, s);
   CK(launch_cholesky(j->is_complex, j->n_aux, nq, b.L, mstride, 1, b.Vc ? b.ldV + q0 : nullptr, b.status,
                      (1 << 29) + q0, s));
@@ -418,12 +445,19 @@ rpa_status stage_vside(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b,
   return RPA_OK;
 }
 
-rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
-                      const void* const* Vdev, cudaStream_t s) {
+rpa_status stage_vside(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
+                       const void* const* Vdev, cudaStream_t s) {
+  if (rpa_status st = vside_copy(ctx, j, b, 0, nq, Vdev, s)) return st;
+  return vside_factor(ctx, pex, j, b, q0, nq, s);
+}
+
+// Log-det of every (q, w), q in [q0, q0+nq) held in slots 0..nq-1 of chi, L
+// and Vc (the V side done).
+static rpa_status stage_logdet(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
+                               cudaStream_t s) {
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
   const long mstride = (long)(NN * (es / 8));
-  if (rpa_status st = stage_vside(ctx, pex, j, b, q0, nq, Vdev, s)) return st;
   if (b.Vc) {
     // inverse form: one Cholesky of V^-1 - chi per (q, w); no sandwich
     prof_begin(ctx, pex, s);
@@ -447,17 +481,21 @@ rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, 
   return RPA_OK;
 }
 
-// Hot path for q in [q0, q0+nq).  Device tables are indexed by q*n_k + j;
-// V of the batch at Vdev[0..nq).  chi_user: write chi0 there and stop.
-static rpa_status run_qbatch(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
-                             const void* const* Vdev, const double* eps_occ, const double* eps_virt, cudaStream_t s,
-                             double* chi_user, int n_slices) {
+rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
+                      const void* const* Vdev, cudaStream_t s) {
+  if (rpa_status st = stage_vside(ctx, pex, j, b, q0, nq, Vdev, s)) return st;
+  return stage_logdet(ctx, pex, j, b, q0, nq, s);
+}
+
+// chi0 of q in [q0, q0+nq) into chi[0..nq) (device tables indexed by
+// q*n_k + j; the d table of the batch is built first).
+static rpa_status run_chi(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
+                          const double* eps_occ, const double* eps_virt, cudaStream_t s, double* chi, int n_slices) {
   const int nk = j->n_k;
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
   BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, j->n_occ * j->n_virt, nk, j->n_w, nq};
   if (rpa_status st = stage_dtab(ctx, pex, j, b, q0, nq, eps_occ, eps_virt, s)) return st;
-  double* chi = chi_user ? chi_user : b.chi;
   if (j->prec == RPA_PREC_MIXED) {
     struct HookCtx {
       rpa_ctx* ctx;
@@ -487,8 +525,7 @@ static rpa_status run_qbatch(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bu
     prof_end(ctx, pex, s, RPA_K_CHI0, 1);
     ctx->launches++;
   }
-  if (chi_user) return RPA_OK;
-  return stage_tail(ctx, pex, j, b, q0, nq, Vdev, s);
+  return RPA_OK;
 }
 
 rpa_status decode_status(rpa_ctx* ctx, int st, int n_w) {
@@ -518,7 +555,8 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
   CK(cudaSetDevice(ctx->device));
   cudaStream_t s = ex.s;
   const int qb = choose_qb(job, ctx->n_slices, ws_cap);
-  Layout L = plan_layout(job, qb, ctx->n_slices, ws_cap, true);
+  const int qt = choose_qt(job, qb, ctx->n_slices, ws_cap);
+  Layout L = plan_layout(job, qb, ctx->n_slices, ws_cap, true, qt);
   if (!ex.ensure_ws(L.total)) {
     ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", L.total);
     return RPA_E_NOMEM;
@@ -533,14 +571,14 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
   const int nbatch = (job->n_q + qb - 1) / qb;
 
   AoPlan aop;
-  if (job->ao) aop = ao_plan(job);
+  if (job->ao) aop = ao_plan(job, qb);
   std::vector<const void*> cp((size_t)job->n_q * job->n_k), vp(job->n_q);
   for (int q = 0; q < job->n_q; ++q) {
     const int bi = q / qb, slot = bi % 2, qi = q - bi * qb;
     for (int jj = 0; jj < job->n_k; ++jj) {
       const size_t i = (size_t)q * job->n_k + jj;
-      if (job->ao)  // qb == 1: every q's coefficients go to the same buffer
-        cp[i] = b.ao + aop.off_c + (size_t)jj * cblk;
+      if (job->ao)  // every batch's coefficients go to the same buffer
+        cp[i] = b.ao + aop.off_c + ((size_t)qi * job->n_k + jj) * cblk;
       else
         cp[i] = host ? (const void*)(b.stageC[slot] + ((size_t)qi * job->n_k + jj) * cblk) : job->C[i];
     }
@@ -578,11 +616,21 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
   }
   for (int bi = 0; bi < nbatch; ++bi) {
     const int q0 = bi * qb, nq = std::min(qb, job->n_q - q0), slot = bi % 2;
+    const int t0 = (q0 / qt) * qt, lo = q0 - t0, nt = std::min(qt, job->n_q - t0);
     if (host) CK(cudaStreamWaitEvent(s, ex.ready[slot], 0));
-    if (job->ao)
-      if (rpa_status st1 = ao_enqueue_assemble(ctx, &ex, job, aop, b.ao, q0, b.ao + aop.off_c, s)) return st1;
-    if (rpa_status st = run_qbatch(ctx, &ex, job, b, q0, nq, vp.data() + q0, eo, ev, s, nullptr, ctx->n_slices))
+    for (int qi = 0; job->ao && qi < nq; ++qi)
+      if (rpa_status st1 = ao_enqueue_assemble(ctx, &ex, job, aop, b.ao, q0 + qi,
+                                               b.ao + aop.off_c + (size_t)qi * job->n_k * cblk, s))
+        return st1;
+    if (rpa_status st = run_chi(ctx, &ex, job, b, q0, nq, eo, ev, s, b.chi + (size_t)lo * job->n_w * NN * (es / 8),
+                                ctx->n_slices))
       return st;
+    if (rpa_status st = vside_copy(ctx, job, b, lo, nq, vp.data() + q0, s)) return st;
+    // the tail once its batch of q is complete (chi, V of every q in place)
+    if (q0 + nq == t0 + nt) {
+      if (rpa_status st = vside_factor(ctx, &ex, job, b, t0, nt, s)) return st;
+      if (rpa_status st = stage_logdet(ctx, &ex, job, b, t0, nt, s)) return st;
+    }
     if (host) {
       CK(cudaEventRecord(ex.freed[slot], s));
       if (bi + 2 < nbatch)
@@ -742,7 +790,7 @@ rpa_status rpa_chi0(rpa_ctx* ctx, const rpa_job* job, int q, void* chi_out, void
   std::vector<const void*> cp;
   AoPlan aop;
   if (job->ao) {
-    aop = ao_plan(job);
+    aop = ao_plan(job, 1);
     cp.resize((size_t)job->n_q * job->n_k);
     for (size_t i = 0; i < cp.size(); ++i) cp[i] = b.ao + aop.off_c + (i % job->n_k) * aop.cblk;
   }
@@ -754,8 +802,8 @@ rpa_status rpa_chi0(rpa_ctx* ctx, const rpa_job* job, int q, void* chi_out, void
     if (rpa_status st1 = ao_enqueue_half(ctx, &ex, job, aop, b.ao, q, s)) return st1;
     if (rpa_status st1 = ao_enqueue_assemble(ctx, &ex, job, aop, b.ao, q, b.ao + aop.off_c, s)) return st1;
   }
-  if (rpa_status st = run_qbatch(ctx, &ex, job, b, q, 1, job->V + q, job->eps_occ, job->eps_virt, s,
-                                 (double*)chi_out, ctx->n_slices))
+  if (rpa_status st = run_chi(ctx, &ex, job, b, q, 1, job->eps_occ, job->eps_virt, s, (double*)chi_out,
+                              ctx->n_slices))
     return st;
   // the d table in the workspace is reused by the next call on this context
   CK(cudaEventRecord(ex.done, s));
@@ -779,7 +827,7 @@ rpa_status rpa_ao2mo(rpa_ctx* ctx, const rpa_job* job, int q, void* C_out, void*
   CK(cudaSetDevice(ctx->device));
   Exec& ex = ctx->ex;
   cudaStream_t s = (cudaStream_t)stream;
-  const AoPlan aop = ao_plan(job);
+  const AoPlan aop = ao_plan(job, 1);
   // only the AO region is used: fit table and half-transforms
   if (!ex.ensure_ws(aop.off_c + 256)) {
     ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", aop.off_c);

@@ -94,7 +94,8 @@ namespace rpa {
 struct Layout {
   size_t meta, dtab, chi, T, L, Vc, stageC, stageV, eps, mixed, ao, total;
   size_t slice_cap;  // mixed path: bytes for the weighted operand's digit planes
-  int qb;
+  int qb;            // q per staging batch (d table, host staging, AO coefficients)
+  int qt;            // q per tail batch (chi, L, Vc, T: V factor and log-det)
 };
 
 // Device pointers into a lane's workspace.
@@ -144,8 +145,10 @@ void prof_begin(rpa_ctx* ctx, Exec* ex, cudaStream_t s);
 void prof_end(rpa_ctx* ctx, Exec* ex, cudaStream_t s, int cls, int n_kernels);
 void prof_collect(rpa_ctx* ctx, Exec* ex);
 // mixed_ws: include the split-precision chi0 workspace (a batch supplies its own).
-Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool mixed_ws);
+// qt: q per tail batch (0: qt = qb).
+Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool mixed_ws, int qt = 0);
 int choose_qb(const rpa_job* j, int n_slices, size_t cap);
+int choose_qt(const rpa_job* j, int qb, int n_slices, size_t cap);
 Bufs carve(void* ws, const rpa_job* j, const Layout& L);
 size_t sync_ws_cap(rpa_ctx* ctx);
 size_t tables_bytes(const rpa_job* j);

@@ -140,10 +140,17 @@ def test_validate_ao_jobs(lib):
 def test_ao_footprint_counts_padf_not_mo_basis_coefficients(lib):
     p = synth.config1_ao()
     fp = _fake_ao_job(p).footprint()
-    # PADF arrays of the 16 k-points 4.3 GB + half-transforms 4.3 GB + one
-    # q's MO-basis coefficients 0.94 GB; the job's 15 GB of C never resides
-    assert 9.0e9 < fp < 15.0e9
+    # PADF arrays of the 16 k-points 4.3 GB + half-transforms 4.3 GB + the
+    # MO-basis coefficients of one batch of 4 q (3.8 GB) + the tail's chi0 of
+    # all q: the job's 15 GB of C never resides at once
+    fc = _fake_job(synth.config1()).footprint()
+    assert 9.0e9 < fp < fc
     assert p.padf_bytes() == 16 * 256 * 65536 * 16
+    # lattice form: 25 real cell-pair arrays instead of 16 complex k-point arrays
+    pl = synth.config1_ao(lattice_radius=2)
+    R = [FakeTensor(0x400000 + 0x100 * r) for r in range(len(pl.lattice))]
+    fl = _fake_ao_job(pl, padf=None, padf_R=R).footprint()
+    assert fl < fp
 
 
 def test_validate_lattice_form_ao_jobs(lib):
