@@ -6,6 +6,7 @@ or calls anything here, and nothing here imports the GPU library.
 
 Each function restates one step of the paper's method (arXiv 2505.06021):
 
+* :func:`projector` - periodic projector T(k) and regularised MO coefficients, Sec. 2.3
 * :func:`padf_k`    - k-dependent PADF coefficients from the cell-pair ones, Sec. 2.2
 * :func:`ao2mo`     - MO-basis fit coefficients C_{gamma,ia}(q, k) from the
                       k-dependent PADF and MO coefficients, Sec. 2.2
@@ -190,6 +191,34 @@ def jacobi_eigh(A: np.ndarray, max_sweeps: int = 100, tol: float = 1e-14) -> Tup
     if rc < 0:
         raise OracleError("jacobi rc=%d" % rc)
     return lam, U, rc
+
+
+def projector(S_list: Sequence[np.ndarray], eps_d: float, c_list: Sequence[np.ndarray]):
+    """Periodic projector method (Sec. 2.3), step by step:
+
+    1. S(k) = U(k) D(k) U(k)^H by the Jacobi eigendecomposition, eigenvalues in
+       ascending order (the order a Hermitian eigensolver reports);
+    2. R(k)_ii = Theta(D_ii(k) - eps_d), with Theta(0) = 1;
+    3. R~ = prod_k R(k) (diagonal matrices, so element by element);
+    4. T(k) = U(k) R~ U(k)^H;
+    5. c~(k) = T(k) c(k).
+
+    Returns (the list of c~(k), the number of diagonal zeros of R~, the list
+    of T(k), the sorted eigenvalues per k)."""
+    eigs = []
+    for S in S_list:
+        lam, U, _ = jacobi_eigh(S)
+        order = np.argsort(lam, kind="stable")
+        eigs.append((lam[order], U[:, order]))
+    Rt = np.ones(len(eigs[0][0]))
+    for lam, _ in eigs:
+        Rt = Rt * (lam - eps_d >= 0.0).astype(np.float64)
+    Ts, out = [], []
+    for (lam, U), c in zip(eigs, c_list):
+        T = (U * Rt[None, :]) @ U.conj().T
+        Ts.append(T)
+        out.append(T @ c)
+    return out, int(np.sum(Rt == 0.0)), Ts, [lam for lam, _ in eigs]
 
 
 def vhalf(V: np.ndarray) -> np.ndarray:

@@ -46,7 +46,7 @@ BASE_SEED = 20250506
 # random streams
 # ----------------------------------------------------------------------------
 
-_TAGS = {"eps": 1, "C": 2, "V": 3, "batch": 4, "serve": 5, "padf": 6, "mo": 7, "padfR": 8}
+_TAGS = {"eps": 1, "C": 2, "V": 3, "batch": 4, "serve": 5, "padf": 6, "mo": 7, "padfR": 8, "ovl": 9}
 
 
 def _rng(seed: int, tag: str, *idx: int) -> np.random.Generator:
@@ -378,6 +378,25 @@ class AOProblem(Problem):
         out = rng.standard_normal((self.n_bas, self.n_pf))
         out *= math.sqrt(var)
         return out
+
+    def overlap(self, kappa: int, n_small_max: int = 3) -> Tuple[np.ndarray, int]:
+        """Basis-set overlap S(kappa) = Q diag(lam) Q^H (Q Haar) with near-linear
+        dependencies: lam ~ U[0.3, 3] except 0..n_small_max of them (seeded per
+        k-point) ~ logU[1e-7, 1e-5].  Returns (S, number of small eigenvalues)."""
+        rng = _rng(self.seed, "ovl", kappa)
+        n = self.n_bas
+        if self.is_complex:
+            z = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / math.sqrt(2.0)
+        else:
+            z = rng.standard_normal((n, n))
+        Qm, R = np.linalg.qr(z)
+        Qm = Qm * (np.diagonal(R) / np.abs(np.diagonal(R)))[None, :]
+        lam = rng.uniform(0.3, 3.0, n)
+        n_small = int(rng.integers(0, n_small_max + 1))
+        lam[:n_small] = np.exp(rng.uniform(math.log(1e-7), math.log(1e-5), n_small))
+        S = (Qm * lam[None, :]) @ Qm.conj().T
+        S = 0.5 * (S + S.conj().T)
+        return np.ascontiguousarray(S.astype(self.dtype)), n_small
 
     def padf_bytes(self) -> int:
         if self.lattice is not None:
