@@ -116,6 +116,10 @@ typedef struct {
   const int *lattice;         /* host [n_R*3]: integer lattice vectors dR */
   const double *kfrac;        /* host [n_kpts*3]: fractional coordinates of the k-points */
   const void *const *padf_R;  /* host [n_R] of device pointers, real float64 n_bas x S each */
+  const void *const *overlap; /* NULL, or host [n_kpts] of device pointers: the basis overlap S(kappa),
+                                 n_bas x n_bas Hermitian positive definite; the MO coefficients are then
+                                 regularised by the periodic projector (rpa_projector) first */
+  double eps_d;               /* projector threshold on the eigenvalues of S(kappa) */
 } rpa_ao;
 
 typedef struct {
@@ -176,6 +180,21 @@ rpa_status rpa_chi0(rpa_ctx *ctx, const rpa_job *job, int q, void *chi_out, void
  * pair sums over the basis functions on gamma's atom.  Asynchronous on
  * `stream`; intermediate arrays live in the context's workspace. */
 rpa_status rpa_ao2mo(rpa_ctx *ctx, const rpa_job *job, int q, void *C_out, void *stream);
+
+/* The periodic projector of Sec. 2.3 (job->ao with overlap): with
+ * S(kappa) = U D U^H (eigenvalues ascending), R(kappa)_ii = Theta(D_ii - eps_d)
+ * (Theta(0) = 1), R~ = prod_kappa R(kappa) over the job's k-points and
+ * T(kappa) = U R~ U^H, writes c~(kappa) = T(kappa) c(kappa) into mo_out[kappa]
+ * (host array [n_kpts] of device pointers, n_bas x n_mo each; may be the
+ * job's own mo arrays).  Since the eigenvalues are ascending, R~ removes the
+ * m lowest eigen-directions of every S(kappa), m = the largest count of
+ * eigenvalues below eps_d; *n_removed (optional) receives m, eig_out
+ * (optional, host [n_kpts*n_bas]) the eigenvalues.  Eigenvectors by a
+ * one-sided Jacobi on the GPU (FP64); at most 256 k-points and
+ * n_bas <= 6144.  Synchronises `stream` (one host test per Jacobi sweep);
+ * RPA_E_TIMEOUT if 60 sweeps do not converge. */
+rpa_status rpa_projector(rpa_ctx *ctx, const rpa_job *job, void *const *mo_out, double *eig_out, int *n_removed,
+                         void *stream);
 
 /* Steps A4-A6 for one q: from chi (device [n_w][n_aux][n_aux], as written by
  * rpa_chi0) computes out[2*w] = ln det(1 - Pi) and out[2*w+1] = Tr Pi,
@@ -263,7 +282,8 @@ void *rpa_stream(rpa_ctx *ctx);
 #define RPA_K_SLICE 6    /* operand preparation of the split-precision path */
 #define RPA_K_CHI0_RED 7 /* split-K reduction of the tensor-core chi0 */
 #define RPA_K_AO2MO 8    /* AO -> MO transform of the fit coefficients (AO-form jobs) */
-#define RPA_K_COUNT 9
+#define RPA_K_PROJ 9     /* periodic projector (Jacobi sweeps, projection) */
+#define RPA_K_COUNT 10
 rpa_status rpa_profile(rpa_ctx *ctx, int enable);
 rpa_status rpa_profile_read(rpa_ctx *ctx, double *ms, uint64_t *launches);
 

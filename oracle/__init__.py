@@ -165,13 +165,29 @@ def padf_of(problem, kappa: int, n_threads: Optional[int] = None) -> np.ndarray:
     return C if problem.is_complex else np.ascontiguousarray(C.real)
 
 
+_proj_cache: Dict[tuple, list] = {}
+
+
+def mo_of(problem, kappa: int) -> np.ndarray:
+    """MO coefficients of k-point kappa as the transform uses them: the
+    problem's own, or (eps_d set) the periodic projector's c~."""
+    if getattr(problem, "eps_d", None) is None:
+        return problem.mo(kappa)
+    key = (id(problem), problem.seed, problem.eps_d, problem.n_bas, problem.n_mo, problem.n_kpts)
+    if key not in _proj_cache:
+        S = [problem.overlap(k)[0] for k in range(problem.n_kpts)]
+        _proj_cache.clear()
+        _proj_cache[key] = projector(S, problem.eps_d, [problem.mo(k) for k in range(problem.n_kpts)])[0]
+    return _proj_cache[key][kappa]
+
+
 def ao2mo_block(problem, q: int, j: int, entries: Optional[np.ndarray] = None,
                 n_threads: Optional[int] = None) -> np.ndarray:
     """C(q, k_j) of an AO-form problem (``synth.AOProblem``)."""
     k, kq = int(problem.grid.pair_k[q, j]), int(problem.grid.pair_kq[q, j])
     return ao2mo(problem.is_complex, problem.n_bas_atom, problem.n_fit_atom, problem.n_occ, problem.n_virt,
-                 padf_of(problem, k, n_threads), padf_of(problem, kq, n_threads), problem.mo(k), problem.mo(kq),
-                 entries, n_threads)
+                 padf_of(problem, k, n_threads), padf_of(problem, kq, n_threads), mo_of(problem, k),
+                 mo_of(problem, kq), entries, n_threads)
 
 
 def _blocks(problem, q: int, n_threads: Optional[int] = None):

@@ -25,12 +25,13 @@ STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "NOMEM", 3: "CUDA", 4: "NOTPD", 5: "TIME
 
 # Entry points declared in include/rpa.h
 EXPORTS = ("rpa_create", "rpa_destroy", "rpa_last_error", "rpa_job_validate", "rpa_job_footprint", "rpa_chi0",
-           "rpa_ao2mo", "rpa_logdet", "rpa_energy", "rpa_energy_batch", "rpa_submit", "rpa_poll", "rpa_wait",
+           "rpa_ao2mo", "rpa_projector", "rpa_logdet", "rpa_energy", "rpa_energy_batch", "rpa_submit", "rpa_poll", "rpa_wait",
            "rpa_serving_stats", "rpa_serving_peak", "rpa_test_drop_copy", "rpa_kernel_launches", "rpa_stream",
            "rpa_profile", "rpa_profile_read", "rpa_logdet_noalloc", "rpa_noalloc_last_error")
 
 # kernel classes of rpa_profile_read
-KERNEL_CLASSES = ("dtab", "chi0", "vfactor", "sandwich", "logdet", "reduce", "slice", "chi0_reduce", "ao2mo")
+KERNEL_CLASSES = ("dtab", "chi0", "vfactor", "sandwich", "logdet", "reduce", "slice", "chi0_reduce", "ao2mo",
+                  "proj")
 
 
 class RpaError(RuntimeError):
@@ -49,7 +50,8 @@ class rpa_ao(ctypes.Structure):
                 ("n_fit_atom", ctypes.POINTER(ctypes.c_int)), ("n_mo", ctypes.c_int),
                 ("padf", ctypes.POINTER(ctypes.c_void_p)), ("mo", ctypes.POINTER(ctypes.c_void_p)),
                 ("n_R", ctypes.c_int), ("lattice", ctypes.POINTER(ctypes.c_int)),
-                ("kfrac", ctypes.POINTER(ctypes.c_double)), ("padf_R", ctypes.POINTER(ctypes.c_void_p))]
+                ("kfrac", ctypes.POINTER(ctypes.c_double)), ("padf_R", ctypes.POINTER(ctypes.c_void_p)),
+                ("overlap", ctypes.POINTER(ctypes.c_void_p)), ("eps_d", ctypes.c_double)]
 
 
 class rpa_job(ctypes.Structure):
@@ -86,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "rpa_job_footprint": (I, [J, ctypes.POINTER(S)]),
         "rpa_chi0": (I, [P, J, I, P, P]),
         "rpa_ao2mo": (I, [P, J, I, P, P]),
+        "rpa_projector": (I, [P, J, ctypes.POINTER(P), ctypes.POINTER(D), ctypes.POINTER(I), P]),
         "rpa_logdet": (I, [P, J, I, P, ctypes.POINTER(D), P]),
         "rpa_energy": (I, [P, J, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
         "rpa_energy_batch": (I, [P, J, I, ctypes.POINTER(D)]),
@@ -127,7 +130,8 @@ class Job:
     ``n_fit_atom`` (per atom), and the per-k-point device tensors ``padf``
     [n_bas, S] and ``mo`` [n_bas, n_mo] (layouts of ``rpa_ao``); lattice form:
     ``padf`` None and ``padf_R`` (real [n_bas, S] per lattice vector),
-    ``lattice`` [n_R, 3] integers and ``kfrac`` [n_kpts, 3]."""
+    ``lattice`` [n_R, 3] integers and ``kfrac`` [n_kpts, 3]; projector:
+    ``overlap`` (device [n_bas, n_bas] per k-point) and ``eps_d``."""
 
     def __init__(self, *, is_complex: bool, n_aux: int, n_occ: int, n_virt: int, pair_k, pair_kq, w_q, zeta_k: float,
                  omega, zeta_w, eps_occ, eps_virt, C: Optional[Sequence], V: Sequence, prec: int = PREC_FP64,
@@ -176,6 +180,10 @@ class Job:
                 a.lattice = self._lat.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
                 a.kfrac = _dptr(self._kf)
                 a.padf_R = ctypes.cast(self._Rp, ctypes.POINTER(ctypes.c_void_p))
+            if ao.get("overlap") is not None:
+                self._Op = (ctypes.c_void_p * len(ao["overlap"]))(*[int(t.data_ptr()) for t in ao["overlap"]])
+                a.overlap = ctypes.cast(self._Op, ctypes.POINTER(ctypes.c_void_p))
+                a.eps_d = float(ao["eps_d"])
             self._ao = a
             s.ao = ctypes.pointer(a)
         self.s = s
@@ -225,6 +233,8 @@ def job_from_ao_problem(problem, tensors: Dict[str, object], prec: int = PREC_FP
           "mo": tensors["mo"]}
     if tensors.get("padf_R") is not None:
         ao.update(padf_R=tensors["padf_R"], lattice=problem.lattice, kfrac=problem.grid.kpts)
+    if tensors.get("overlap") is not None:
+        ao.update(overlap=tensors["overlap"], eps_d=problem.eps_d)
     return Job(is_complex=problem.is_complex, n_aux=problem.n_aux, n_occ=problem.n_occ, n_virt=problem.n_virt,
                pair_k=g.pair_k, pair_kq=g.pair_kq, w_q=g.w_q, zeta_k=g.zeta_k, omega=problem.omega,
                zeta_w=problem.zeta_w, eps_occ=tensors["eps_occ"], eps_virt=tensors["eps_virt"], C=None,
@@ -253,8 +263,11 @@ def upload_ao_problem(problem, device="cuda", threads: int = 0):
         padf_R = list(ex.map(lambda r: put(problem.padf_R(r)), range(len(problem.lattice)))) if lat else None
         mo = list(ex.map(lambda k: put(problem.mo(k)), range(problem.n_kpts)))
         V = list(ex.map(lambda q: put(problem.V(q)), range(problem.n_q)))
-    return {"padf": padf, "padf_R": padf_R, "mo": mo, "V": V, "eps_occ": put(problem.eps_occ.astype(np.float64)),
-            "eps_virt": put(problem.eps_virt.astype(np.float64))}
+        ovl = None
+        if getattr(problem, "eps_d", None) is not None:
+            ovl = list(ex.map(lambda k: put(problem.overlap(k)[0]), range(problem.n_kpts)))
+    return {"padf": padf, "padf_R": padf_R, "mo": mo, "V": V, "overlap": ovl,
+            "eps_occ": put(problem.eps_occ.astype(np.float64)), "eps_virt": put(problem.eps_virt.astype(np.float64))}
 
 
 def upload_problem(problem, device="cuda", qs: Optional[Sequence[int]] = None, pin: bool = False,
@@ -392,6 +405,24 @@ class Context:
         self._check(self.lib.rpa_ao2mo(self.h, ctypes.byref(job.s), int(q), ctypes.c_void_p(out.data_ptr()),
                                        ctypes.c_void_p(st_ptr)))
         return out
+
+    def projector(self, job: Job, out=None, stream=None):
+        """Periodic projector of an AO-form job with overlaps: (list of c~
+        device tensors per k-point, removed directions m, eigenvalues [n_kpts,
+        n_bas] ascending)."""
+        import torch
+
+        mo = job.ao_t["mo"]
+        if out is None:
+            out = [torch.empty_like(t) for t in mo]
+        ptrs = (ctypes.c_void_p * len(out))(*[int(t.data_ptr()) for t in out])
+        n_bas = int(mo[0].shape[0])
+        eig = np.zeros((len(out), n_bas))
+        m = ctypes.c_int()
+        st_ptr = (stream or torch.cuda.current_stream()).cuda_stream
+        self._check(self.lib.rpa_projector(self.h, ctypes.byref(job.s), ptrs, _dptr(eig), ctypes.byref(m),
+                                           ctypes.c_void_p(st_ptr)))
+        return out, int(m.value), eig
 
     def logdet(self, job: Job, q: int, chi, stream=None) -> np.ndarray:
         import torch

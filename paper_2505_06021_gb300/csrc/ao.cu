@@ -5,6 +5,8 @@
 // Workspace region (offsets from Bufs.ao):
 //   fit table   int4 per fit function gamma (see launch_ao_assemble)
 //   PADF        lattice form only: one k-point's k-dependent PADF array
+//   projector   with overlap matrices: the projector's workspace and the
+//               regularised MO coefficients c~ of every k-point
 //   H_occ       one S x n_occ slot per k-point that appears as k (pair_k)
 //   H_virt      one S x n_virt slot per k-point that appears as k+q (pair_kq)
 //   C           qb x n_k blocks n_aux x n_occ*n_virt: the MO-basis
@@ -19,6 +21,7 @@
 #include <vector>
 
 #include "ao_internal.h"
+#include "proj_internal.h"
 #include "rpa_internal.h"
 #include "rpa_runtime.h"
 
@@ -62,6 +65,13 @@ int ao_validate(const rpa_job* j, char* msg, size_t len) {
     S += (long)a->n_bas_atom[A] * a->n_fit_atom[A];
   }
   if (nf != j->n_aux) return fail("AO-form job: fit functions per atom must sum to n_aux");
+  if (a->overlap) {
+    if (j->n_kpts > ProjPtrs::kMax) return fail("AO-form job: the projector takes at most 256 k-points");
+    if (nb > 6144) return fail("AO-form job: the projector takes n_bas <= 6144");
+    if (!isfinite(a->eps_d) || a->eps_d < 0.0) return fail("AO-form job: eps_d must be finite and >= 0");
+    for (int k = 0; k < j->n_kpts; ++k)
+      if (!a->overlap[k]) return fail("AO-form job: an overlap pointer is NULL");
+  }
   if (a->n_mo < j->n_occ + j->n_virt || a->n_mo > nb)
     return fail("AO-form job: n_mo must lie in [n_occ + n_virt, n_bas]");
   if (nb > 65536 || S > (1L << 30)) return fail("AO-form job: basis or PADF array too large");
@@ -97,7 +107,14 @@ AoPlan ao_plan(const rpa_job* j, int qb) {
   p.cblk = es * (size_t)j->n_aux * j->n_occ * j->n_virt;
   p.off_padf = al256(sizeof(int4) * (size_t)j->n_aux);
   p.padf_bytes = a->n_R > 0 ? al256(es * (size_t)p.n_bas * p.S) : 0;
-  p.off_hocc = p.off_padf + p.padf_bytes;
+  p.off_proj = p.off_padf + p.padf_bytes;
+  size_t proj_bytes = 0;
+  if (a->overlap) {
+    proj_bytes = al256(proj_layout(j->is_complex, j->n_kpts, p.n_bas, a->n_mo).bytes);
+    p.cproj_bytes = al256(es * (size_t)p.n_bas * a->n_mo);
+  }
+  p.off_cproj = p.off_proj + proj_bytes;
+  p.off_hocc = p.off_cproj + p.cproj_bytes * (a->overlap ? j->n_kpts : 0);
   p.off_hvirt = p.off_hocc + p.occ_bytes * p.n_occ_slots;
   p.off_c = p.off_hvirt + p.virt_bytes * p.n_virt_slots;
   p.bytes = p.off_c + al256(p.cblk * j->n_k * (size_t)std::max(qb, 1));
@@ -123,6 +140,24 @@ size_t ao_input_bytes(const rpa_job* j) {
       return RPA_E_CUDA;                                                                             \
     }                                                                                                \
   } while (0)
+
+const double* ao_mo(const rpa_job* j, const AoPlan& p, const char* region, int k) {
+  if (j->ao->overlap) return (const double*)(region + p.off_cproj + p.cproj_bytes * (size_t)k);
+  return (const double*)j->ao->mo[k];
+}
+
+rpa_status ao_project(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const AoPlan& p, char* region, cudaStream_t s) {
+  const rpa_ao* a = j->ao;
+  if (!a->overlap) return RPA_OK;
+  std::vector<const double*> c(j->n_kpts);
+  std::vector<double*> out(j->n_kpts);
+  for (int k = 0; k < j->n_kpts; ++k) {
+    c[k] = (const double*)a->mo[k];
+    out[k] = (double*)(region + p.off_cproj + p.cproj_bytes * (size_t)k);
+  }
+  return run_projector(ctx, pex, j->is_complex, j->n_kpts, p.n_bas, a->n_mo, a->overlap, c.data(), out.data(),
+                       a->eps_d, region + p.off_proj, s, nullptr, nullptr);
+}
 
 rpa_status ao_enqueue_half(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const AoPlan& p, char* region, int q,
                            cudaStream_t s) {
@@ -156,12 +191,12 @@ rpa_status ao_enqueue_half(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const AoPl
       ++n;
     }
     if (need_o[k]) {
-      CKA(launch_ao_half(j->is_complex, p.n_bas, p.S, a->n_mo, P, (const double*)a->mo[k], 0, j->n_occ,
+      CKA(launch_ao_half(j->is_complex, p.n_bas, p.S, a->n_mo, P, ao_mo(j, p, region, k), 0, j->n_occ,
                          (double*)(region + p.off_hocc + p.occ_bytes * p.occ_slot[k]), s));
       ++n;
     }
     if (need_v[k]) {
-      CKA(launch_ao_half(j->is_complex, p.n_bas, p.S, a->n_mo, P, (const double*)a->mo[k], j->n_occ, j->n_virt,
+      CKA(launch_ao_half(j->is_complex, p.n_bas, p.S, a->n_mo, P, ao_mo(j, p, region, k), j->n_occ, j->n_virt,
                          (double*)(region + p.off_hvirt + p.virt_bytes * p.virt_slot[k]), s));
       ++n;
     }
@@ -182,8 +217,8 @@ rpa_status ao_enqueue_assemble(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const 
     for (int t = 0; t < np; ++t) {
       const size_t i = (size_t)q * j->n_k + j0 + t;
       const int k = j->pair_k[i], kq = j->pair_kq[i];
-      pr.mo_k[t] = (const double*)a->mo[k];
-      pr.mo_kq[t] = (const double*)a->mo[kq];
+      pr.mo_k[t] = ao_mo(j, p, region, k);
+      pr.mo_kq[t] = ao_mo(j, p, region, kq);
       pr.h_occ[t] = (const double*)(region + p.off_hocc + p.occ_bytes * p.occ_slot[k]);
       pr.h_virt[t] = (const double*)(region + p.off_hvirt + p.virt_bytes * p.virt_slot[kq]);
       pr.out[t] = (double*)(out + p.cblk * (size_t)(j0 + t));

@@ -21,6 +21,7 @@ struct AoPlan {
   size_t occ_bytes = 0, virt_bytes = 0;  // one slot
   size_t cblk = 0;                       // one C(q, k_j) block
   size_t off_padf = 0, padf_bytes = 0;   // lattice form: one k-point's PADF array
+  size_t off_proj = 0, off_cproj = 0, cproj_bytes = 0;  // projector: workspace, c~ per k-point
   size_t off_hocc = 0, off_hvirt = 0, off_c = 0, bytes = 0;
 };
 
@@ -36,6 +37,11 @@ size_t ao_input_bytes(const rpa_job* j);
 // every q) into `region`.
 rpa_status ao_enqueue_half(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const AoPlan& p, char* region, int q,
                            cudaStream_t s);
+// With overlap matrices: the periodic projector's c~ of every k-point into the
+// region (synchronises s); without: nothing.
+rpa_status ao_project(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const AoPlan& p, char* region, cudaStream_t s);
+// The MO coefficients the transform uses for k-point k (c~ or the job's c).
+const double* ao_mo(const rpa_job* j, const AoPlan& p, const char* region, int k);
 // C(q, k_j), j = 0..n_k-1, into out + j * cblk (half-transforms in place).
 rpa_status ao_enqueue_assemble(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const AoPlan& p, const char* region, int q,
                                char* out, cudaStream_t s);

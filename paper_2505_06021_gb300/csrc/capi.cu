@@ -585,8 +585,10 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
     vp[q] = host ? (const void*)(b.stageV[slot] + (size_t)qi * es * NN) : job->V[q];
   }
   if (rpa_status st0 = upload_tables(ctx, ex, job, b, cp.data())) return st0;
-  if (job->ao)
+  if (job->ao) {
+    if (rpa_status st1 = ao_project(ctx, &ex, job, aop, b.ao, s)) return st1;
     if (rpa_status st1 = ao_enqueue_half(ctx, &ex, job, aop, b.ao, -1, s)) return st1;
+  }
 
   const double* eo = job->eps_occ;
   const double* ev = job->eps_virt;
@@ -799,6 +801,7 @@ rpa_status rpa_chi0(rpa_ctx* ctx, const rpa_job* job, int q, void* chi_out, void
   CK(cudaEventRecord(ex.done, ex.s));
   CK(cudaStreamWaitEvent(s, ex.done, 0));
   if (job->ao) {
+    if (rpa_status st1 = ao_project(ctx, &ex, job, aop, b.ao, s)) return st1;
     if (rpa_status st1 = ao_enqueue_half(ctx, &ex, job, aop, b.ao, q, s)) return st1;
     if (rpa_status st1 = ao_enqueue_assemble(ctx, &ex, job, aop, b.ao, q, b.ao + aop.off_c, s)) return st1;
   }
@@ -834,6 +837,7 @@ rpa_status rpa_ao2mo(rpa_ctx* ctx, const rpa_job* job, int q, void* C_out, void*
     return RPA_E_NOMEM;
   }
   char* region = (char*)ex.ws;
+  if (rpa_status st = ao_project(ctx, &ex, job, aop, region, s)) return st;
   if (rpa_status st = ao_enqueue_half(ctx, &ex, job, aop, region, q, s)) return st;
   if (rpa_status st = ao_enqueue_assemble(ctx, &ex, job, aop, region, q, (char*)C_out, s)) return st;
   // the workspace is reused by the next call on this context

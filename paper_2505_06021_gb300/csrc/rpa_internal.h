@@ -104,6 +104,35 @@ struct AoPairs {
 cudaError_t launch_ao_assemble(int cplx, const AoPairs& pr, int n_pairs, const int4* fit, int n_aux, int n_occ,
                                int n_virt, int n_mo, cudaStream_t s);
 
+// ---- periodic projector (kernels_proj.cu) --------------------------------
+
+// Per k-point (up to kMax): the overlap S (N x N, Hermitian positive
+// definite), the MO coefficients c (N x n_mo) and the output c~ (may be c).
+struct ProjPtrs {
+  static constexpr int kMax = 256;
+  const double* S[kMax];
+  const double* c[kMax];
+  double* out[kMax];
+};
+// W[k] (Np columns of N, column-major) = S(k) and V[k] = I; Np = N rounded
+// up to even (a zero padding column).
+cudaError_t launch_proj_load(int cplx, const ProjPtrs& P, int n_mat, int N, int Np, double* W, double* V,
+                             cudaStream_t s);
+// Round r of a one-sided Jacobi sweep over every W[k] (rotations accumulated
+// in V[k]); pairs with |w_p^H w_q| / (|w_p| |w_q|) > thresh are rotated; the
+// largest such ratio is merged into *off_max (the bits of a non-negative
+// double).
+cudaError_t launch_jacobi_round(int cplx, int n_mat, int N, int Np, int r, double* W, double* V, double thresh,
+                                unsigned long long* off_max, cudaStream_t s);
+// Eigenvalues (column norms of W) in ascending order into lam_sorted
+// [n_mat][N], the column of each rank into by_rank, m = the largest count
+// below eps_d over the k-points (into *m, zeroed by the caller), then
+// out[k] = c[k] - U_m (U_m^H c[k]), U_m the columns of V of the m lowest
+// ranks (X: scratch of n_mat * N * n_mo elements).
+cudaError_t launch_proj_finish(int cplx, const ProjPtrs& P, int n_mat, int N, int Np, int n_mo, const double* W,
+                               const double* V, double eps_d, double* lam_sorted, int* by_rank, int* m, double* X,
+                               cudaStream_t s);
+
 // T[b] = chi[b] * L[b / n_w]   (L lower triangular, N x N).
 // Y[b] = -(L[b / n_w]^H T[b]), lower triangle only.
 cudaError_t launch_sandwich(int cplx, int N, int n_batch, int n_w, const double* chi, const double* L, double* T,

@@ -314,7 +314,7 @@ class AOProblem(Problem):
     """
 
     def __init__(self, base: Problem, n_bas_atom: Sequence[int], n_fit_atom: Sequence[int],
-                 lattice: Optional[np.ndarray] = None):
+                 lattice: Optional[np.ndarray] = None, eps_d: Optional[float] = None):
         super().__init__(**{f.name: getattr(base, f.name) for f in dataclasses.fields(Problem)})
         self.n_bas_atom = tuple(int(x) for x in n_bas_atom)
         self.n_fit_atom = tuple(int(x) for x in n_fit_atom)
@@ -323,6 +323,8 @@ class AOProblem(Problem):
         if self.n_occ + self.n_virt > self.n_bas:
             raise ValueError("n_occ + n_virt exceeds the basis size")
         self.lattice = None if lattice is None else np.ascontiguousarray(lattice, np.int32).reshape(-1, 3)
+        # periodic projector threshold (None: the MO coefficients are used as they are)
+        self.eps_d = eps_d
 
     @property
     def n_atoms(self) -> int:
@@ -410,10 +412,11 @@ def lattice_2d(radius: int) -> np.ndarray:
 
 
 def make_ao_problem(name: str, *, is_complex: bool, n_bas_atom: Sequence[int], n_fit_atom: Sequence[int],
-                    n_occ: int, n_virt: int, grid: KQGrid, n_w: int, seed: int, lattice=None, **kw) -> AOProblem:
+                    n_occ: int, n_virt: int, grid: KQGrid, n_w: int, seed: int, lattice=None, eps_d=None,
+                    **kw) -> AOProblem:
     base = make_problem(name, is_complex=is_complex, n_aux=int(sum(n_fit_atom)), n_occ=n_occ, n_virt=n_virt,
                         grid=grid, n_w=n_w, seed=seed, **kw)
-    return AOProblem(base, n_bas_atom, n_fit_atom, lattice)
+    return AOProblem(base, n_bas_atom, n_fit_atom, lattice, eps_d)
 
 
 def _bands(seed: int, grid: KQGrid, n_occ: int, n_virt: int, dispersion: float) -> Tuple[np.ndarray, np.ndarray]:

@@ -175,3 +175,19 @@ def test_validate_lattice_form_ao_jobs(lib):
     j._kf[0] = 0.5
     st, msg = j.validate()
     assert st == rpa.RPA_E_INVAL and "integer kfrac" in msg
+
+
+def test_validate_projector_ao_jobs(lib):
+    p = synth.config1_ao(n_bas_atom=(8, 6), n_fit_atom=(10, 14), n_occ=3, n_virt=9)
+    p.eps_d = 1e-4
+    ovl = [FakeTensor(0x600000 + 0x100 * k) for k in range(p.n_kpts)]
+    st, msg = _fake_ao_job(p, overlap=ovl).validate()
+    assert st == rpa.RPA_OK, msg
+    j = _fake_ao_job(p, overlap=ovl)
+    j._Op[2] = None
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "overlap" in msg
+    j = _fake_ao_job(p, overlap=ovl)
+    j._ao.eps_d = float("nan")
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "eps_d" in msg
