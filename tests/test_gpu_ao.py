@@ -197,3 +197,35 @@ def test_lattice_form_energy_matches_oracle_fp64(rpa):
         r = c.energy(rpa.job_from_ao_problem(p, t, prec=rpa.PREC_FP64))
     assert np.all(np.abs(r["eps"] - ref["eps"]) <= TOL_TERM * np.abs(ref["eps"]))
     assert abs(r["Ec"] - ref["Ec"]) <= TOL_TERM * abs(ref["Ec"])
+
+
+# ---- degenerate shapes -------------------------------------------------------
+
+@pytest.mark.parametrize("nb,nf,n_occ,n_virt", [
+    ((9,), (13,), 2, 7),              # a single atom: both PADF terms on every fit function
+    ((1, 12, 1), (3, 9, 1), 1, 13),   # one-function atoms, one occupied state
+    ((6, 6), (5, 5), 11, 1),          # one virtual state
+])
+def test_ao2mo_degenerate_shapes(rpa, nb, nf, n_occ, n_virt):
+    p = synth.make_ao_problem("ao-deg", is_complex=True, n_bas_atom=nb, n_fit_atom=nf, n_occ=n_occ, n_virt=n_virt,
+                              grid=synth.regular_kq_grid((2, 1, 1)), n_w=4, seed=64)
+    t = rpa.upload_ao_problem(p)
+    job = rpa.job_from_ao_problem(p, t)
+    with rpa.Context(0) as c:
+        for q in range(p.n_q):
+            out = c.ao2mo(job, q)
+            torch.cuda.synchronize()
+            _check_blocks(out, p, q)
+
+
+def test_lattice_form_single_vector(rpa):
+    """One lattice vector dR = 0: every k-point's array is the cell-pair array."""
+    p = synth.make_ao_problem("ao-lat1", is_complex=True, n_bas_atom=(7, 5), n_fit_atom=(8, 6), n_occ=3, n_virt=9,
+                              grid=synth.regular_kq_grid((2, 2, 1)), n_w=4, seed=65,
+                              lattice=np.zeros((1, 3), np.int32))
+    t = rpa.upload_ao_problem(p)
+    job = rpa.job_from_ao_problem(p, t)
+    with rpa.Context(0) as c:
+        out = c.ao2mo(job, 1)
+        torch.cuda.synchronize()
+    _check_blocks(out, p, 1)
