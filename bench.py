@@ -365,6 +365,18 @@ def run_ours(args):
         torch.cuda.empty_cache()
         th = rpa.upload_problem(p, "cpu", pin=True)
         jh = rpa.job_from_problem(p, th, prec=pc, mem=rpa.MEM_HOST)
+        # host -> device bandwidth of these pinned buffers (one q-batch's worth)
+        nb_probe = min(len(th["C"]), 4 * p.n_k)
+        dbuf = torch.empty(sum(t.numel() for t in th["C"][:nb_probe]), dtype=th["C"][0].dtype, device="cuda")
+        torch.cuda.synchronize()
+        h0 = time.perf_counter()
+        off = 0
+        for t in th["C"][:nb_probe]:
+            dbuf[off:off + t.numel()].copy_(t.reshape(-1), non_blocking=True)
+            off += t.numel()
+        torch.cuda.synchronize()
+        h2d_gbs = dbuf.numel() * dbuf.element_size() / (time.perf_counter() - h0) / 1e9
+        del dbuf
         ctx.energy(jh)
         barrier(world)
         torch.cuda.synchronize()
@@ -381,7 +393,8 @@ def run_ours(args):
         nqw = p.n_q * p.n_w
         line["e2e"] = {"value": world * args.e2e_steps / te, "unit": "jobs/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": 8 * (1 + 3 * nqw) + 4, "steps": args.e2e_steps,
-                       "step_s": step_s, "Ec_matches_device": bool(rh["Ec"] == res["Ec"])}
+                       "step_s": step_s, "h2d_gbs_of_inputs": h2d_gbs,
+                       "Ec_matches_device": bool(rh["Ec"] == res["Ec"])}
         del th, jh
     else:
         line["e2e"] = None
