@@ -203,6 +203,44 @@ def oracle_jobs_per_s(p, s):
     return 1.0 / job_s, job_s
 
 
+def gpu_local_cpus(dev_index):
+    """CPUs of the NUMA node the GPU hangs off (from sysfs), restricted to the
+    ones this process may use; (node, cpus) or (None, None) if unknown."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(dev_index), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        dom, bus, rest = out.split(":")
+        addr = "%04x:%s:%s" % (int(dom, 16), bus.lower(), rest.lower())
+        node = int(open("/sys/bus/pci/devices/%s/numa_node" % addr).read().strip())
+        if node < 0:
+            return None, None
+        cpus = set()
+        for part in open("/sys/devices/system/node/node%d/cpulist" % node).read().strip().split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        cpus &= os.sched_getaffinity(0)
+        return (node, cpus) if cpus else (node, None)
+    except Exception:
+        return None, None
+
+
+class near_gpu:
+    """Runs the enclosed host allocations (pinning, first touch) on the CPUs of
+    the GPU's NUMA node, so that pinned inputs are local to the GPU's host link."""
+
+    def __init__(self, dev_index):
+        self.node, self.cpus = gpu_local_cpus(dev_index)
+
+    def __enter__(self):
+        self.saved = os.sched_getaffinity(0)
+        if self.cpus:
+            os.sched_setaffinity(0, self.cpus)
+        return self
+
+    def __exit__(self, *a):
+        os.sched_setaffinity(0, self.saved)
+
+
 def traffic_for(kernel_key):
     """DRAM bytes per launch of `kernel_key` from the committed ncu summary,
     valid only while the kernel source is unchanged (hash recorded)."""
@@ -363,9 +401,11 @@ def run_ours(args):
             t.data = torch.empty(0, device=t.device)
         tens = None
         torch.cuda.empty_cache()
-        th = rpa.upload_problem(p, "cpu", pin=True)
+        with near_gpu(local) as ng:
+            th = rpa.upload_problem(p, "cpu", pin=True)
         jh = rpa.job_from_problem(p, th, prec=pc, mem=rpa.MEM_HOST)
-        # host -> device bandwidth of these pinned buffers (one q-batch's worth)
+        ctx.energy(jh)
+        # host -> device bandwidth of these pinned buffers (one q-batch's worth), warm
         nb_probe = min(len(th["C"]), 4 * p.n_k)
         dbuf = torch.empty(sum(t.numel() for t in th["C"][:nb_probe]), dtype=th["C"][0].dtype, device="cuda")
         torch.cuda.synchronize()
@@ -377,7 +417,6 @@ def run_ours(args):
         torch.cuda.synchronize()
         h2d_gbs = dbuf.numel() * dbuf.element_size() / (time.perf_counter() - h0) / 1e9
         del dbuf
-        ctx.energy(jh)
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -393,7 +432,8 @@ def run_ours(args):
         nqw = p.n_q * p.n_w
         line["e2e"] = {"value": world * args.e2e_steps / te, "unit": "jobs/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": 8 * (1 + 3 * nqw) + 4, "steps": args.e2e_steps,
-                       "step_s": step_s, "h2d_gbs_of_inputs": h2d_gbs,
+                       "step_s": step_s, "h2d_gbs_of_inputs": h2d_gbs, "host_numa_node": ng.node,
+                       "pinned_near_gpu": bool(ng.cpus),
                        "Ec_matches_device": bool(rh["Ec"] == res["Ec"])}
         del th, jh
     else:
@@ -858,9 +898,10 @@ def run_ao(args):
     if not args.no_e2e and not args.n_q:
         # host-resident AO inputs (pinned) copied to the device inside the timed region
         pin_src = tens["padf"] if tens["padf"] is not None else tens["padf_R"]
-        hp = [t.cpu().pin_memory() for t in pin_src]
-        hm = [t.cpu().pin_memory() for t in tens["mo"]]
-        hv = [t.cpu().pin_memory() for t in tens["V"]]
+        with near_gpu(local):
+            hp = [t.cpu().pin_memory() for t in pin_src]
+            hm = [t.cpu().pin_memory() for t in tens["mo"]]
+            hv = [t.cpu().pin_memory() for t in tens["V"]]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
