@@ -294,17 +294,22 @@ def upload_problem(problem, device="cuda", qs: Optional[Sequence[int]] = None, p
             return t.pin_memory() if pin else t
         return t.to(dev)
 
+    blocks = [(q, j) for q in qs for j in range(problem.n_k)]
+    # host inputs: one allocation for all blocks (pinned once, contiguous),
+    # the blocks are views of it
+    big = torch.empty((len(blocks), problem.n_aux, problem.n_ov), dtype=dt, pin_memory=pin) if on_host else None
+    index = {qj: i for i, qj in enumerate(blocks)}
+
     def make_c(qj):
         q, j = qj
         if on_host:
-            t = torch.empty((problem.n_aux, problem.n_ov), dtype=dt, pin_memory=pin)
+            t = big[index[qj]]
             problem.C(q, j, out=t.numpy())
             return t
         h = np.empty((problem.n_aux, problem.n_ov), npdt)
         problem.C(q, j, out=h)
         return torch.from_numpy(h).to(dev)
 
-    blocks = [(q, j) for q in qs for j in range(problem.n_k)]
     nthr = threads or min(16, os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(nthr) as ex:
         C = list(ex.map(make_c, blocks))
