@@ -645,9 +645,15 @@ __device__ __forceinline__ void chol_one(int N, double* __restrict__ A, int mode
   Team<CL>::sync();
 }
 
+// One-CTA-per-matrix Cholesky launches keep two matrices on each SM (128
+// registers per thread): while one CTA is in its serial phases (the diagonal
+// block in one warp, the panel solve, barriers) the other keeps the FP64 pipe
+// busy with its trailing update.
+constexpr int CHOL_CTAS_PER_SM = 2;
+
 // Batched: matrix b of the launch (team b / CL) at mats + b * bstride.
 template <bool C, int CL>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, CL == 1 ? CHOL_CTAS_PER_SM : 1)
     cholesky_kernel(int N, double* __restrict__ mats, long bstride, int mode, double* __restrict__ out,
                     int* __restrict__ status, int status_base, const double* __restrict__ Wn,
                     const double* __restrict__ Vc, const double* __restrict__ ldV, int n_w, int b0) {
@@ -661,6 +667,8 @@ __global__ void __launch_bounds__(256)
 
 // Ragged: one CTA per task, matrices of any size (tasks ordered largest
 // first by the caller, so the block scheduler packs them greedily).
+// (One CTA per SM: with uneven sizes the second CTA's register cap costs more
+// than the overlap gains; measured on the batched workload.)
 template <bool C>
 __global__ void __launch_bounds__(256) cholesky_ragged_kernel(const CholTask* __restrict__ tasks) {
   const CholTask t = tasks[blockIdx.x];
@@ -839,10 +847,10 @@ cudaError_t launch_chol_t(int N, int b0, int n_mat, double* mats, long bstride, 
 // The launch split of launch_chol_c: 0 = one CTA per matrix, 1 = a cluster
 // per matrix, 2 = one CTA per matrix except a short last wave on clusters.
 int chol_split(int N, int n_mat) {
-  const int P = num_sms_fp64();
+  const int P = num_sms_fp64(), W = P * CHOL_CTAS_PER_SM;  // W: matrices in one wave
   if (N >= 256 && n_mat * 2 < P) return 1;
-  const int r = n_mat % P;
-  if (N >= 256 && n_mat > P && r > 0 && r * 2 < P) return 2;
+  const int r = n_mat % W;
+  if (N >= 256 && n_mat > W && r > 0 && r * 2 < W) return 2;
   return 0;
 }
 
@@ -850,14 +858,14 @@ template <bool C>
 cudaError_t launch_chol_c(int N, int n_mat, double* mats, long bstride, int mode, double* out, int* status,
                           int status_base, cudaStream_t s, const double* Wn, const double* Vc, const double* ldV,
                           int n_w) {
-  const int P = num_sms_fp64();
+  const int W = num_sms_fp64() * CHOL_CTAS_PER_SM;
   const int split = chol_split(N, n_mat);
   // few large matrices: a cluster per matrix
   if (split == 1)
     return launch_chol_t<C, CL_BIG>(N, 0, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
   // one CTA per matrix; a short last wave (fewer than P/2 matrices) goes to
   // clusters instead, so that it does not run on a few SMs alone
-  const int r = n_mat % P;
+  const int r = n_mat % W;
   if (split == 2) {
     cudaError_t e = launch_chol_t<C, 1>(N, 0, n_mat - r, mats, bstride, mode, out, status, status_base, s, Wn, Vc,
                                         ldV, n_w);
