@@ -191,3 +191,19 @@ def test_validate_projector_ao_jobs(lib):
     j._ao.eps_d = float("nan")
     st, msg = j.validate()
     assert st == rpa.RPA_E_INVAL and "eps_d" in msg
+
+
+def test_mixed_frequency_limit(lib):
+    p32 = synth.make_problem("f", is_complex=True, n_aux=16, n_occ=2, n_virt=3, grid=synth.regular_kq_grid((2, 1, 1)),
+                             n_w=32, seed=1)
+    j = _fake_job(p32)
+    j.s.prec = rpa.PREC_MIXED
+    assert j.validate()[0] == rpa.RPA_OK
+    p33 = synth.make_problem("f", is_complex=True, n_aux=16, n_occ=2, n_virt=3, grid=synth.regular_kq_grid((2, 1, 1)),
+                             n_w=33, seed=1)
+    j = _fake_job(p33)
+    j.s.prec = rpa.PREC_MIXED
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "32" in msg
+    j.s.prec = rpa.PREC_FP64  # the FP64 path has no such limit
+    assert j.validate()[0] == rpa.RPA_OK

@@ -114,6 +114,19 @@ def test_mixed_energy_large_aux(rpa, ctx):
     assert np.max(np.abs(r["eps"] - ref["eps"]) / np.abs(ref["eps"])) <= 1e-8
 
 
+def test_mixed_energy_at_frequency_limit(rpa, ctx):
+    """32 frequencies (the split path's maximum: one persistent launch round
+    carries up to 32 frequency groups of a q)."""
+    p = synth.make_problem("m32", is_complex=True, n_aux=72, n_occ=2, n_virt=7,
+                           grid=synth.regular_kq_grid((2, 1, 1)), n_w=32, seed=46)
+    job = rpa.job_from_problem(p, rpa.upload_problem(p), prec=rpa.PREC_MIXED)
+    r = ctx.energy(job)
+    ref = oracle.energy(p)
+    assert abs(r["Ec"] - ref["Ec"]) <= TOL_EC, (r["Ec"], ref["Ec"])
+    # the largest nodes carry tiny terms: compare against the largest one
+    assert np.max(np.abs(r["eps"] - ref["eps"])) <= 1e-8 * np.max(np.abs(ref["eps"]))
+
+
 def test_mixed_deterministic_and_slice_count(rpa):
     p = synth.make_problem("m", is_complex=True, n_aux=96, n_occ=3, n_virt=20, grid=synth.regular_kq_grid((2, 1, 1)),
                            n_w=3, seed=44)
