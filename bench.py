@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "mixed"])
-    ap.add_argument("--slices", type=int, default=0, help="BF16 digit slices of the mixed path (2-4; 0: library default)")
+    ap.add_argument("--slices", type=int, default=0,
+                    help="BF16 digit slices of the mixed path (2-4; 0: library default)")
     ap.add_argument("--cap-gb", type=float, default=0.0,
                     help="periodic2d/slab: the context's HBM cap (bounds the workspace; profiling small cases)")
     ap.add_argument("--n-q", type=int, default=0, help="profiling only: restrict the job to its first n q-points")
@@ -533,7 +534,8 @@ def run_batch(args):
             "config": {"workload": "batch-uneven: %d independent Gamma-real / 2x2x1-complex instances, N_aux ~ "
                                    "U[128,1024], N_occ ~ U[8,64], N_virt = 4-15 x N_occ, 16 frequencies each; "
                                    "one rpa_energy_batch call per step (CUDA graph replay)" % n,
-                       "n_inst": n, "chi0_prec": prec, "chi0_slices": args.slices or 4, "c_gb": sum(p.c_bytes() for p in probs) / 1e9,
+                       "n_inst": n, "chi0_prec": prec, "chi0_slices": args.slices or 4,
+                       "c_gb": sum(p.c_bytes() for p in probs) / 1e9,
                        "l2": "inputs larger than L2", "parallelism": "one batch per GPU (weak scaling)"},
             "chi0_tflops": alg * world * args.steps / (ms / 1e3) / 1e12, "gpu_launches": launches,
             "kernel_ms_per_step": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
@@ -766,7 +768,8 @@ def run_serving(args):
                        "chi0_slices": args.slices or 4,
                        "arrival_rate_jobs_s": rate, "capacity_jobs_s": cap_jobs_s,
                        "capacity_sample": "closed loop over the %d admissible jobs of the stream, at most 8 in "
-                                          "flight, inputs made on the device meanwhile" % len(adm), "rejected_over_cap": len(rejected),
+                                          "flight, inputs made on the device meanwhile" % len(adm),
+                       "rejected_over_cap": len(rejected),
                        "failed_to_submit": len(failed), "failures": failed[:3],
                        "l2": "inputs larger than L2", "parallelism": "one serving context per GPU"},
             "latency_s": {"p50": st["lat_p50_s"], "p99": st["lat_p99_s"], "mean": st["lat_mean_s"]},

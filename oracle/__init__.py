@@ -63,8 +63,9 @@ def _load():
         lib.oracle_logabsdet_lu.argtypes = [i, i, _dp, _dp]
         lib.oracle_energy_sum.argtypes = [i, i, _dp, _dp, _dp, _dp]
         lib.oracle_max_threads.argtypes = []
-        for f in (lib.oracle_chi0, lib.oracle_ao2mo, lib.oracle_padf_k, lib.oracle_jacobi_eigh, lib.oracle_vhalf, lib.oracle_sandwich,
-                  lib.oracle_logdet_cholesky, lib.oracle_logabsdet_lu, lib.oracle_energy_sum, lib.oracle_max_threads):
+        for f in (lib.oracle_chi0, lib.oracle_ao2mo, lib.oracle_padf_k, lib.oracle_jacobi_eigh, lib.oracle_vhalf,
+                  lib.oracle_sandwich, lib.oracle_logdet_cholesky, lib.oracle_logabsdet_lu, lib.oracle_energy_sum,
+                  lib.oracle_max_threads):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib

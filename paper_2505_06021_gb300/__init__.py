@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "NOMEM", 3: "CUDA", 4: "NOTPD", 5: "TIME
 
 # Entry points declared in include/rpa.h
 EXPORTS = ("rpa_create", "rpa_destroy", "rpa_last_error", "rpa_job_validate", "rpa_job_footprint", "rpa_chi0",
-           "rpa_ao2mo", "rpa_projector", "rpa_logdet", "rpa_energy", "rpa_energy_batch", "rpa_submit", "rpa_poll", "rpa_wait",
+           "rpa_ao2mo", "rpa_projector", "rpa_logdet", "rpa_energy", "rpa_energy_batch", "rpa_submit", "rpa_poll",
+           "rpa_wait",
            "rpa_serving_stats", "rpa_serving_peak", "rpa_test_drop_copy", "rpa_kernel_launches", "rpa_stream",
            "rpa_profile", "rpa_profile_read", "rpa_logdet_noalloc", "rpa_noalloc_last_error")
 

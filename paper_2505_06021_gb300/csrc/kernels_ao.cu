@@ -103,9 +103,9 @@ __global__ void __launch_bounds__(256) ao_half_kernel(int n_bas, int S, int n_mo
 
 // One CTA: fit function gamma of pair p, a 32 x 32 tile of (i, a).
 template <bool C>
-__global__ void __launch_bounds__(256) ao_assemble_kernel(const __grid_constant__ AoPairs pr, const int4* __restrict__ fit,
-                                                          int n_aux, int n_occ, int n_virt, int n_mo, int n_ti,
-                                                          int n_ta) {
+__global__ void __launch_bounds__(256)
+    ao_assemble_kernel(const __grid_constant__ AoPairs pr, const int4* __restrict__ fit, int n_aux, int n_occ,
+                       int n_virt, int n_mo, int n_ti, int n_ta) {
   __shared__ Elem<C> As[AK][AT];
   __shared__ Elem<C> Bs[AK][AT];
   long bid = blockIdx.x;

@@ -96,7 +96,8 @@ rpa_status rpa_logdet_noalloc(int is_complex, int n_aux, int n_w, const void* V,
   int* status = reinterpret_cast<int*>(base + 3 * RPA_NOALLOC_MAT_BYTES);
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(L, V, es * NN, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = rpa::launch_cholesky(is_complex, n_aux, 1, L, (long)(NN * (es / 8)), 1, nullptr, status, 1 << 29, s);
+  if (e == cudaSuccess)
+    e = rpa::launch_cholesky(is_complex, n_aux, 1, L, (long)(NN * (es / 8)), 1, nullptr, status, 1 << 29, s);
   const double* chib = static_cast<const double*>(chi);
   for (int w = 0; w < n_w && e == cudaSuccess; ++w) {
     e = rpa::launch_sandwich(is_complex, n_aux, 1, 1, chib + (size_t)w * NN * (es / 8), L, T, Y, s);
