@@ -109,9 +109,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 // Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, K-major A and B,
-// M = 128, N = 128.
-__device__ __forceinline__ uint32_t idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// M = 128, N = 128 or 256.
+__device__ __forceinline__ uint32_t idesc(uint32_t n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 __device__ __forceinline__ void mma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t id, bool acc) {
   asm volatile(
@@ -172,7 +172,7 @@ struct TcParams {
   int drop_item;  // test hook: the first K-block of this work item is never
                   // loaded (-1: off), so one bounded wait runs out
   int* err;
-  int grp_mask;  // accumulator groups that receive MMAs (the host's copy of PairTable<s>::mask)
+  int grp_mask;  // accumulator groups that receive MMAs (the host's copy of MmaTable<s>::mask)
   TcSeg seg[MAX_SEGS];
 };
 static_assert(sizeof(TcParams) <= 32000, "kernel parameter block too large");
@@ -220,45 +220,86 @@ __device__ __forceinline__ ItemPos item_pos(const TcParams& p, int item) {
   return r;
 }
 
-// Slice pairs (i, j) of S digit planes: all levels i + j < S, and for S = 2
-// also (1, 1) (the largest term of level 2); accumulator group = min(level, 3);
-// `first` marks the first pair of its group in a stage (it starts the group's
-// sum at the first K-block of a chunk).  For S = 4 the dropped level-4 terms
-// are 2^-32 of level 0 (measured |dE_c| 2.9e-9 Ha on the 2-D periodic job).
+// The MMAs of one K-block.  Slice pairs (i, j) of S digit planes: all levels
+// i + j < S, and for S = 2 also (1, 1) (the largest term of level 2);
+// accumulator group = min(level, 3), TMEM columns [128 g, 128 g + 128).  For S
+// = 4 the dropped level-4 terms are 2^-32 of level 0 (measured |dE_c| 2.9e-9 Ha
+// on the 2-D periodic job).  Two pairs (i, j), (i, j + 1) whose groups are g,
+// g + 1 with g even share one MMA of N = 256: B's digit planes j and j + 1 are
+// adjacent in the stage (4 KB apart, the 8-row-group stride continuing), so
+// they form one 256-row operand, and the two groups one 256-column TMEM range
+// at a 256-aligned offset; the A tile is read from shared memory once for both.
+// `first` marks an MMA whose groups receive nothing earlier in the stage (it
+// starts their sums at the first K-block of a chunk); pairs are merged only
+// where that holds for both groups or for neither.  S = 4: 6 MMAs (4 wide)
+// for the 10 pairs; S = 3: 5 for 6; S = 2: 3 for 4.
 template <int S>
-struct PairTable {
-  static constexpr int N = S * (S + 1) / 2 + (S == 2 ? 1 : 0);
-  int i[16], j[16], g[16], first[16], mask;
-  constexpr PairTable() : i(), j(), g(), first(), mask(0) {
-    int n = 0;
-    for (int l = 0; l < S; ++l)
-      for (int a = 0; a <= l; ++a) {
+struct MmaTable {
+  int n, i[16], j[16], g[16], wide[16], first[16], mask;
+  static constexpr int grp(int level) { return level < NGROUPS - 1 ? level : NGROUPS - 1; }
+  static constexpr bool in(int a, int b) { return a < S && b < S && (a + b < S || (S == 2 && a == 1 && b == 1)); }
+  constexpr MmaTable() : n(0), i(), j(), g(), wide(), first(), mask(0) {
+    bool touched[NGROUPS] = {};
+    for (int a = 0; a < S; ++a)
+      for (int b = 0; b < S;) {
+        if (!in(a, b)) {
+          ++b;
+          continue;
+        }
+        const int g0 = grp(a + b);
+        const bool w = in(a, b + 1) && g0 % 2 == 0 && grp(a + b + 1) == g0 + 1 && touched[g0] == touched[g0 + 1];
         i[n] = a;
-        j[n] = l - a;
-        g[n] = l < NGROUPS - 1 ? l : NGROUPS - 1;
+        j[n] = b;
+        g[n] = g0;
+        wide[n] = w;
+        first[n] = !touched[g0];
+        touched[g0] = true;
+        mask |= 1 << g0;
+        if (w) {
+          touched[g0 + 1] = true;
+          mask |= 1 << (g0 + 1);
+        }
         ++n;
+        b += w ? 2 : 1;
       }
-    if (S == 2) {
-      i[n] = 1;
-      j[n] = 1;
-      g[n] = 2;
-      ++n;
-    }
-    for (int k = 0; k < n; ++k) {
-      first[k] = 1;
-      for (int m = 0; m < k; ++m)
-        if (g[m] == g[k]) first[k] = 0;
-      mask |= 1 << g[k];
-    }
   }
 };
 
+// Compile-time check of the table: every pair of the set lands in exactly one
+// MMA, in the group of its level, and `first` is set exactly on the first MMA
+// into each of its groups.
 template <int S>
-__device__ constexpr PairTable<S> kPairs{};
+constexpr bool mma_table_ok() {
+  constexpr MmaTable<S> t{};
+  using T = MmaTable<S>;
+  for (int a = 0; a < MAX_S; ++a)
+    for (int b = 0; b < MAX_S; ++b) {
+      int c = 0;
+      for (int m = 0; m < t.n; ++m)
+        if (t.i[m] == a && (t.j[m] == b || (t.wide[m] && t.j[m] + 1 == b))) {
+          ++c;
+          if (T::grp(a + b) != t.g[m] + b - t.j[m]) return false;
+        }
+      if (c != (T::in(a, b) ? 1 : 0)) return false;
+    }
+  for (int m = 0; m < t.n; ++m)
+    for (int h = 0; h <= t.wide[m]; ++h) {
+      bool earlier = false;
+      for (int k = 0; k < m; ++k)
+        if (t.g[k] == t.g[m] + h || (t.wide[k] && t.g[k] + 1 == t.g[m] + h)) earlier = true;
+      if (earlier == (t.first[m] != 0)) return false;
+    }
+  return true;
+}
+static_assert(mma_table_ok<2>() && mma_table_ok<3>() && mma_table_ok<4>(), "slice-pair MMA table is inconsistent");
+static_assert(MmaTable<4>{}.n == 6 && MmaTable<3>{}.n == 5 && MmaTable<2>{}.n == 3, "unexpected MMA counts");
+
+template <int S>
+__device__ constexpr MmaTable<S> kMmas{};
 
 template <int S>
 __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_constant__ TcParams p) {
-  constexpr const PairTable<S>& PT = kPairs<S>;
+  constexpr const MmaTable<S>& MT = kMmas<S>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -338,7 +379,7 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
       int stage = 0;
       uint32_t phase = 0, acc_phase = 0;
       bool ok = true;
-      const uint32_t id = idesc();
+      const uint32_t id128 = idesc(128), id256 = idesc(256);
       // descriptors: plane 0 of stage 0, advanced by byte offsets >> 4
       const uint64_t d0 = sdesc(smem_u32(smem));
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
@@ -356,9 +397,10 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
             const uint64_t db = da + (uint64_t)((MAX_S * PLANE_BYTES) >> 4);
             const bool first_kb = kb == c0;
 #pragma unroll
-            for (int pi = 0; pi < PairTable<S>::N; ++pi)
-              mma(tmem + 128u * (uint32_t)PT.g[pi], da + (uint64_t)((PT.i[pi] * PLANE_BYTES) >> 4),
-                  db + (uint64_t)((PT.j[pi] * PLANE_BYTES) >> 4), id, !(first_kb && PT.first[pi]));
+            for (int m = 0; m < MT.n; ++m)
+              mma(tmem + 128u * (uint32_t)MT.g[m], da + (uint64_t)((MT.i[m] * PLANE_BYTES) >> 4),
+                  db + (uint64_t)((MT.j[m] * PLANE_BYTES) >> 4), MT.wide[m] ? id256 : id128,
+                  !(first_kb && MT.first[m]));
             mma_commit(&empty[stage]);
             if (++stage == STAGES) {
               stage = 0;

@@ -469,16 +469,16 @@ MixedLayout mixed_layout(const BatchGeom& g, int s, int sms, size_t slice_cap) {
 }
 
 // Accumulator groups used by s slices: levels 0 .. s-1, plus level 2 for the
-// (1, 1) pair of s = 2, capped at the last group (PairTable's rule).
+// (1, 1) pair of s = 2, capped at the last group (MmaTable's rule).
 constexpr int group_mask(int s) {
   int m = 0;
   for (int lvl = 0; lvl < s; ++lvl) m |= 1 << (lvl < NGROUPS - 1 ? lvl : NGROUPS - 1);
   if (s == 2) m |= 1 << 2;
   return m;
 }
-static_assert(group_mask(2) == PairTable<2>{}.mask && group_mask(3) == PairTable<3>{}.mask &&
-                  group_mask(4) == PairTable<4>{}.mask,
-              "host and kernel pair tables disagree");
+static_assert(group_mask(2) == MmaTable<2>{}.mask && group_mask(3) == MmaTable<3>{}.mask &&
+                  group_mask(4) == MmaTable<4>{}.mask,
+              "host and kernel accumulator groups disagree");
 
 // ---------------------------------------------------- split-K planning ----
 // A launch's segments get their split-K depth from one common target item
