@@ -252,6 +252,16 @@ Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool m
   }
   L.ao = al(ao_region_bytes(j, qb));
   L.total = L.meta + L.dtab + L.chi + L.T + L.L + L.Vc + 2 * (L.stageC + L.stageV) + L.eps + L.mixed + L.ao;
+  if (L.mixed && qb >= 2) {
+    // two alternating regions (the next q's operand written during the
+    // current q's tensor-core launch) when they fit under the cap
+    BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, (int)nov, j->n_k, j->n_w, 1};
+    const size_t m2 = al(mixed_seq_workspace_bytes(g, n_slices, L.slice_cap));
+    if (m2 > L.mixed && L.total - L.mixed + m2 <= ws_cap) {
+      L.total += m2 - L.mixed;
+      L.mixed = m2;
+    }
+  }
   return L;
 }
 
@@ -510,15 +520,17 @@ static rpa_status run_chi(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs&
                       HookCtx* h = (HookCtx*)u;
                       prof_end(h->ctx, h->ex, st, cls, n);
                     }};
-    for (int qi = 0; qi < nq; ++qi) {
-      BatchGeom g1 = g;
-      g1.n_qb = 1;
-      uint64_t nl = 0;
-      CK(launch_chi0_mixed(g1, n_slices, (const double* const*)(b.Cptrs + (size_t)(q0 + qi) * nk),
-                           b.dtab + (size_t)qi * nk * j->n_w * g.n_ov, chi + (size_t)qi * j->n_w * NN * (es / 8),
-                           b.mixed, b.mixed_bytes, b.status, &nl, s, b.slice_cap, pex ? &hook : nullptr));
-      ctx->launches += nl;
-    }
+    BatchGeom g1 = g;
+    g1.n_qb = 1;
+    std::vector<MixedQ> mq(nq);
+    for (int qi = 0; qi < nq; ++qi)
+      mq[qi] = MixedQ{g1, (const double* const*)(b.Cptrs + (size_t)(q0 + qi) * nk),
+                      b.dtab + (size_t)qi * nk * j->n_w * g.n_ov, chi + (size_t)qi * j->n_w * NN * (es / 8),
+                      b.slice_cap};
+    uint64_t nl = 0;
+    CK(launch_chi0_mixed_seq(mq.data(), nq, n_slices, b.mixed, b.mixed_bytes, b.status, &nl, s,
+                             pex ? &hook : nullptr));
+    ctx->launches += nl;
   } else {
     prof_begin(ctx, pex, s);
     CK(launch_chi0_fp64(g, (const double* const*)(b.Cptrs + (size_t)q0 * nk), b.dtab, chi, s));

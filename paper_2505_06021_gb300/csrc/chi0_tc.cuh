@@ -7,7 +7,8 @@
 // of 16 real values; operands arrive by bulk copies of pre-blocked digit
 // planes (one contiguous 16 KB run per operand and K-block, no-swizzle
 // core-matrix layout), one elected thread issues tcgen05.mma, eight epilogue
-// warps drain TMEM with tcgen05.ld.  Slice pairs are grouped by level into
+// warps drain TMEM with tcgen05.ld, and two slicer warps may write another
+// q's weighted digit planes meanwhile (a side job without waits).  Slice pairs are grouped by level into
 // four TMEM accumulators (levels 0-2 exact, levels >= 3 FP32); every CHUNK t
 // the epilogue adds them into float-float register accumulators.  Every wait
 // is bounded (globaltimer); on a time-out the kernel raises an error flag,
@@ -16,17 +17,19 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "slice.cuh"
+
 namespace rpa {
 namespace {
 
 constexpr int KB = 16;              // real K per K-block (= MMA K for BF16)
 constexpr int CHUNK = 1024;         // complex t per exact accumulation (real: 2048 t)
 constexpr int STAGES = 6;
-constexpr int MAX_S = 4;
 constexpr int PLANE_BYTES = 128 * KB * 2;                 // 4096: one slice, 128 rows, 16 values
 constexpr int STAGE_BYTES = 2 * MAX_S * PLANE_BYTES;      // A + B = 32 KB
 constexpr int EPI_WARPS = 8;
-constexpr int THREADS = 64 + 32 * EPI_WARPS;              // producer, MMA, 8 epilogue warps
+constexpr int SLICE_WARPS = 2;
+constexpr int THREADS = 64 + 32 * EPI_WARPS + 32 * SLICE_WARPS;  // producer, MMA, epilogue, slicer warps
 constexpr int NGROUPS = 4;
 constexpr unsigned long long WAIT_NS = 2000000000ull;     // 2 s per wait
 
@@ -173,6 +176,11 @@ struct TcParams {
                   // loaded (-1: off), so one bounded wait runs out
   int* err;
   int grp_mask;  // accumulator groups that receive MMAs (the host's copy of MmaTable<s>::mask)
+  // Side job of the slicer warps: the weighted digit planes of another q
+  // (all its frequencies), written while this launch's MMAs run; its inputs
+  // and output share nothing with this launch's segments.
+  int side_on;
+  SliceArgs side;
   TcSeg seg[MAX_SEGS];
 };
 static_assert(sizeof(TcParams) <= 32000, "kernel parameter block too large");
@@ -417,7 +425,7 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
       while (!mbar_try(drain, 0) && gtime() - t0 < WAIT_NS) {
       }
     }
-  } else {
+  } else if (warp < 2 + EPI_WARPS) {
     // ------------------------------------------------ epilogue (8 warps)
     const int quad = warp & 3;
     const int half = (warp - 2) >> 2;  // columns [64 half, 64 half + 64)
@@ -463,6 +471,19 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
         *reinterpret_cast<float4*>(ph + u) = make_float4(hi[u], hi[u + 1], hi[u + 2], hi[u + 3]);
         *reinterpret_cast<float4*>(pl + u) = make_float4(lo[u], lo[u + 1], lo[u + 2], lo[u + 3]);
       }
+    }
+  } else if (p.side_on) {
+    // ------------------------------------------------ slicer (2 warps)
+    // no waits: independent loads and stores, consecutive threads on
+    // consecutive rows of one K-block as in the standalone slicing kernel
+    constexpr int NT = 32 * SLICE_WARPS;
+    const long total = (long)p.side.Npad * (p.side.Kr / 16);
+    const long stride = (long)gridDim.x * NT;
+    const long first = (long)blockIdx.x * NT + (threadIdx.x - (THREADS - NT));
+    if (p.side.cplx) {
+      for (long idx = first; idx < total; idx += stride) slice_unit<true, true>(p.side, idx);
+    } else {
+      for (long idx = first; idx < total; idx += stride) slice_unit<false, true>(p.side, idx);
     }
   }
   fence_before();

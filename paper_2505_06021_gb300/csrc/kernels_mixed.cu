@@ -48,10 +48,7 @@ namespace {
 // Fixed-point inputs, built once per q (C) and once per frequency table (w):
 //   c_fix = round(c 2^(30 - eC_P)), |c| < 2^eC_P for the whole row P, |c_fix| <= 2^30;
 //   w = w_m 2^(ew - 31) with w_m in [2^30, 2^31), one 31-bit mantissa per (k, t, w).
-// A digit set is produced from an integer F (|F| <= 2^30):
-//   F + 0x808080 = (d0 2^24) + (d1+128) 2^16 + (d2+128) 2^8 + (d3+128),
-// each biased byte b is turned into the BF16 of (b - 128) 2^(-8i) by the
-// exact float trick (2^23 + b) 2^(-8i) - (2^23 + 128) 2^(-8i) (one FFMA, no I2F).
+// Their digit planes are written by slice_unit (slice.cuh).
 
 // c_fix of one q: [Npad][Kr] int32, zero outside the data; eC per row.
 __global__ void __launch_bounds__(256) cfix_kernel(int cplx, int N, int Npad, int n_ov, int n_k, int Ktot, int Kr,
@@ -80,189 +77,13 @@ __global__ void __launch_bounds__(256) cfix_kernel(int cplx, int N, int Npad, in
   }
 }
 
-struct SliceArgs {
-  int cplx, Npad, n_ov, Ktot, Kr, s, n_w, w0, G, nxy;
-  const int* cfix;       // [Npad][Kr]
-  const int* eC;         // [Npad] exponent of c_fix
-  const unsigned long long* wx;  // [n_k][n_w][n_ov] weights (mantissa | exponent << 32), null: weight 1
-  const int* eA;         // [n_w][Npad] row exponents of A
-  uint16_t* S;           // digit planes, blocked (see store_planes)
-};
-
-// One thread per (row, 16 real values); it loops over the G frequencies of the
-// launch (the 16 fixed-point values of C are loaded once).  With wm == null
-// the digits of C itself are written (X and, for complex data, Y = (im, -re)).
-// Digit planes are stored in the order the tensor-core kernel consumes them,
-// so that one stage of operand data is a single contiguous 16 KB copy:
-//   weighted A: [g][I = P/128][kb][plane][m-core 16][k-core 2][8 rows][8 values]
-//   C (B side): [J][kb][plane][n-core 16][k-core 2][8 rows][8 values]
-// with J = P/64 for complex data (n-cores 0-7: X rows, 8-15: Y rows) and
-// J = P/128 for real data.  A 4 KB plane block is the no-swizzle K-major
-// core-matrix layout of a 128 x 16 BF16 operand tile (core matrix = 8 rows x
-// 16 bytes, K-adjacent cores 128 B apart, row-adjacent cores 256 B apart).
-__device__ __forceinline__ void store_core_rows(uint16_t* block, int row, const uint32_t (&v)[8]) {
-  uint4* d0 = reinterpret_cast<uint4*>(block + (((row >> 3) * 2 + 0) * 8 + (row & 7)) * 8);
-  uint4* d1 = reinterpret_cast<uint4*>(block + (((row >> 3) * 2 + 1) * 8 + (row & 7)) * 8);
-  *d0 = make_uint4(v[0], v[1], v[2], v[3]);
-  *d1 = make_uint4(v[4], v[5], v[6], v[7]);
-}
-
-__device__ __forceinline__ void store_planes(const SliceArgs& a, int P, int kb, const uint32_t (&px)[MAX_S][8],
-                                             const uint32_t (&py)[MAX_S][8]) {
-  const long n_kb = a.Kr / 16;
-  const int J = a.nxy == 2 ? (P >> 6) : (P >> 7);
-  const int nrow = a.nxy == 2 ? (P & 63) : (P & 127);
-#pragma unroll
-  for (int i = 0; i < MAX_S; ++i) {
-    if (i >= a.s) break;
-    uint16_t* blk = a.S + (((long)J * n_kb + kb) * a.s + i) * 2048;
-    store_core_rows(blk, nrow, px[i]);
-    if (a.nxy == 2) store_core_rows(blk, 64 + nrow, py[i]);
-  }
-}
-
-// X planes only (the weighted operand A has no Y part).
-__device__ __forceinline__ void store_planes_x(const SliceArgs& a, int g, int P, int kb,
-                                               const uint32_t (&px)[MAX_S][8]) {
-  const long n_kb = a.Kr / 16;
-  const long nI = a.Npad / 128;
-#pragma unroll
-  for (int i = 0; i < MAX_S; ++i) {
-    if (i >= a.s) break;
-    uint16_t* blk = a.S + ((((long)g * nI + (P >> 7)) * n_kb + kb) * a.s + i) * 2048;
-    store_core_rows(blk, P & 127, px[i]);
-  }
-}
-
-
-// BF16 digit i of a biased word G' = (F + 0x808080) ^ 2^31 (byte 3 - i holds
-// d_i + 128) as FP32 bits: one byte permute builds 2^23 + b, one FFMA scales
-// and removes the bias exactly.
-template <int I>
-__device__ __forceinline__ uint32_t digit_f(uint32_t Gp) {
-  const uint32_t bits = __byte_perm(Gp, 0x4B000000u, 0x7540u | (3 - I));
-  const float scale = __int_as_float((127 - 8 * I) << 23);
-  return __float_as_uint(fmaf(__uint_as_float(bits), scale, -8388736.0f * scale));
-}
-__device__ __forceinline__ uint32_t biased(int F) { return (uint32_t)(F + 0x808080) ^ 0x80000000u; }
-
-// X digit planes of two consecutive K values (F0 low half, F1 high half).
-__device__ __forceinline__ void pair_x(int F0, int F1, int up, int s, uint32_t (&px)[MAX_S][8]) {
-  const uint32_t G0 = biased(F0), G1 = biased(F1);
-  px[0][up] = __byte_perm(digit_f<0>(G0), digit_f<0>(G1), 0x7632);
-  px[1][up] = __byte_perm(digit_f<1>(G0), digit_f<1>(G1), 0x7632);
-  if (s > 2) px[2][up] = __byte_perm(digit_f<2>(G0), digit_f<2>(G1), 0x7632);
-  if (s > 3) px[3][up] = __byte_perm(digit_f<3>(G0), digit_f<3>(G1), 0x7632);
-}
-// X = (re, im) and Y = (im, -re) digit planes of one complex value.
-template <int I>
-__device__ __forceinline__ void cplx_xy(uint32_t Gre, uint32_t Gim, uint32_t& x, uint32_t& y) {
-  const uint32_t fr = digit_f<I>(Gre), fi = digit_f<I>(Gim);
-  x = __byte_perm(fr, fi, 0x7632);
-  y = __byte_perm(fi, fr ^ 0x80000000u, 0x7632);
-}
-
-// F = round(c w 2^-sh) for |c w| < 2^61; sh >= 1 by construction of the row
-// exponents (|F| <= 2^30); sh is clamped to 62, where the result is 0 anyway.
-__device__ __forceinline__ int round_shift(int c, long long wm, int sh) {
-  sh = min(max(sh, 1), 62);
-  const long long pr = (long long)c * wm;
-  return (int)((pr + (1ll << (sh - 1))) >> sh);
-}
-
 template <bool CPLX, bool WEIGHTED>
 __global__ void __launch_bounds__(256, 2) slice_kernel(SliceArgs a) {
-  const long ngroups = (long)a.Kr / 16;
-  const long total = (long)a.Npad * ngroups;
-  constexpr int tpg = CPLX ? 8 : 16;  // t per group of 16 real values
+  const long total = (long)a.Npad * (a.Kr / 16);
   // consecutive threads take consecutive rows of one K-block: coalesced
   // stores into the blocked layout, shared weight loads
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int P = (int)(idx % a.Npad);
-    const int tg = (int)(idx / a.Npad);
-    const int4* src = reinterpret_cast<const int4*>(a.cfix + (long)P * a.Kr + tg * 16);
-    int cv[16];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int4 x = src[v];
-      cv[4 * v] = x.x;
-      cv[4 * v + 1] = x.y;
-      cv[4 * v + 2] = x.z;
-      cv[4 * v + 3] = x.w;
-    }
-    if constexpr (!WEIGHTED) {
-      uint32_t px[MAX_S][8], py[MAX_S][8];
-#pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        if constexpr (CPLX) {
-          const uint32_t Gr = biased(cv[2 * v]), Gi = biased(cv[2 * v + 1]);
-          cplx_xy<0>(Gr, Gi, px[0][v], py[0][v]);
-          cplx_xy<1>(Gr, Gi, px[1][v], py[1][v]);
-          cplx_xy<2>(Gr, Gi, px[2][v], py[2][v]);
-          cplx_xy<3>(Gr, Gi, px[3][v], py[3][v]);
-        } else {
-          pair_x(cv[2 * v], cv[2 * v + 1], v, a.s, px);
-        }
-      }
-      store_planes(a, P, tg, px, py);
-      continue;
-    } else {
-      // the group's t = t0 .. t0 + tpg - 1 as (k-point j, pair tt): one
-      // division per group, then steps
-      const int t0 = tg * tpg;
-      const int j0 = t0 / a.n_ov, tt0 = t0 - j0 * a.n_ov;
-      const int eC = a.eC[P];
-      // (k-point, pair) offsets of the group's t, frequency-independent
-      long off[tpg];
-      {
-        int j = j0, tt = tt0;
-#pragma unroll
-        for (int v = 0; v < tpg; ++v) {
-          off[v] = (t0 + v < a.Ktot) ? ((long)j * a.n_w) * a.n_ov + tt : -1;
-          if (++tt == a.n_ov) {
-            tt = 0;
-            ++j;
-          }
-        }
-      }
-      unsigned long long xw[tpg];
-#pragma unroll
-      for (int v = 0; v < tpg; ++v) xw[v] = off[v] >= 0 ? __ldg(a.wx + off[v] + (long)a.w0 * a.n_ov) : 0ull;
-      int eAw = a.eA[(long)a.w0 * a.Npad + P];
-      for (int g = 0; g < a.G; ++g) {
-        const int w = a.w0 + g;
-        const int shbase = 30 + eAw - eC;
-        // next frequency's weights and row exponent, in flight during this one
-        unsigned long long xn[tpg];
-        const bool more = g + 1 < a.G;
-#pragma unroll
-        for (int v = 0; v < tpg; ++v)
-          xn[v] = (more && off[v] >= 0) ? __ldg(a.wx + off[v] + (long)(w + 1) * a.n_ov) : 0ull;
-        const int eAn = more ? a.eA[(long)(w + 1) * a.Npad + P] : 0;
-        uint32_t px[MAX_S][8];
-        long long wm_prev = 0;
-        int sh_prev = 0;
-#pragma unroll
-        for (int v = 0; v < tpg; ++v) {
-          const unsigned long long x = xw[v];
-          const long long wmv = (long long)(uint32_t)x;
-          const int shv = shbase - (int)(uint32_t)(x >> 32);
-          if constexpr (CPLX) {
-            pair_x(round_shift(cv[2 * v], wmv, shv), round_shift(cv[2 * v + 1], wmv, shv), v, a.s, px);
-          } else if ((v & 1) == 0) {
-            wm_prev = wmv;
-            sh_prev = shv;
-          } else {
-            pair_x(round_shift(cv[v - 1], wm_prev, sh_prev), round_shift(cv[v], wmv, shv), v >> 1, a.s, px);
-          }
-        }
-        store_planes_x(a, g, P, tg, px);
-#pragma unroll
-        for (int v = 0; v < tpg; ++v) xw[v] = xn[v];
-        eAw = eAn;
-      }
-    }
-  }
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x)
+    slice_unit<CPLX, WEIGHTED>(a, idx);
 }
 
 // Row exponents.  eA[w][P] = max_t (Ec_t + Ew_t) - 2044 + 1 (biased fields),
@@ -593,6 +414,83 @@ void launch_tc(int s, int grid, size_t smem, cudaStream_t st, const TcParams& tp
 
 size_t slice_cap_of(const MixedQ& q) { return q.slice_cap ? q.slice_cap : ((size_t)12 << 30); }
 
+constexpr size_t TC_SMEM = STAGES * STAGE_BYTES + 1024 + 256;  // stages, alignment pad, barriers
+
+cudaError_t tc_smem_attr() {
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [&] {
+    attr = cudaFuncSetAttribute(chi0_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(chi0_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(chi0_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+  });
+  return attr;
+}
+
+// One q's workspace region (layout L) carved from p.
+struct QState {
+  MixedLayout L;
+  uint16_t *S, *SC;
+  int *erow, *erowC, *cfix;
+  unsigned long long* wx;
+  int16_t* ew;
+  float* part;
+  int w_next, rounds_left;
+};
+
+QState carve_q(char* p, const MixedLayout& L, int n_w) {
+  QState q;
+  q.L = L;
+  q.S = (uint16_t*)p;
+  p += L.slices;
+  q.SC = (uint16_t*)p;
+  p += L.slicesC;
+  q.erow = (int*)p;
+  p += L.erow;
+  q.erowC = (int*)p;
+  p += L.erowC;
+  q.part = (float*)p;
+  p += L.part;
+  q.wx = (unsigned long long*)p;
+  p += L.wm;
+  q.ew = (int16_t*)p;
+  p += L.ew;
+  q.cfix = (int*)p;
+  q.w_next = 0;
+  q.rounds_left = (n_w + L.G - 1) / L.G;
+  return q;
+}
+
+unsigned slice_grid(const MixedLayout& L, int sms) {
+  const long tg = (long)L.Npad * (L.Kr / 16);
+  return (unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32);
+}
+
+// Per-q preparation (4 launches): packed weights, row exponents, fixed-point
+// C and the digit planes of C (the B operand).
+void prep_q(const QState& q, const MixedQ& m, int s, int sms, cudaStream_t st) {
+  const BatchGeom& g = m.g;
+  const long nwt = (long)g.n_k * g.n_w * g.n_ov;
+  wtab_kernel<<<(unsigned)std::min<long>((nwt + 255) / 256, (long)sms * 16), 256, 0, st>>>(nwt, m.dtab, q.wx, q.ew);
+  erow_kernel<<<q.L.Npad, 256, 0, st>>>(g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_k, g.n_w, m.Cptrs, q.ew, q.erow,
+                                         q.erowC);
+  const long tot = (long)q.L.Npad * q.L.Kr;
+  cfix_kernel<<<(unsigned)std::min<long>((tot + 255) / 256, (long)sms * 32), 256, 0, st>>>(
+      g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_k, q.L.Ktot, q.L.Kr, m.Cptrs, q.erowC, q.cfix);
+  SliceArgs sc{g.cplx, q.L.Npad, g.n_ov, q.L.Ktot, q.L.Kr, s, g.n_w, 0, 1, q.L.nxy, q.cfix, q.erowC,
+               nullptr, q.erow, q.SC};
+  launch_slice(g.cplx, slice_grid(q.L, sms), st, sc);
+}
+
+// Weighted digit planes of frequencies [w0, w0 + G) of q into q.S.
+SliceArgs weighted_args(const QState& q, const MixedQ& m, int s, int w0, int G) {
+  const BatchGeom& g = m.g;
+  return SliceArgs{g.cplx, q.L.Npad, g.n_ov, q.L.Ktot, q.L.Kr, s, g.n_w, w0, G, 1, q.cfix, q.erowC,
+                   q.wx, q.erow, q.S};
+}
+
 }  // namespace
 
 bool mixed_supported() { return true; }
@@ -638,28 +536,8 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
   if (n <= 0) return cudaSuccess;
   if (s < 2 || s > MAX_S) return cudaErrorInvalidValue;
   const int sms = num_sms();
-  const size_t smem = STAGES * STAGE_BYTES + 1024 + 256;  // stages, alignment pad, barriers
-  {
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [&] {
-      attr = cudaFuncSetAttribute(chi0_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (attr == cudaSuccess)
-        attr = cudaFuncSetAttribute(chi0_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (attr == cudaSuccess)
-        attr = cudaFuncSetAttribute(chi0_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    });
-    if (attr != cudaSuccess) return attr;
-  }
-  struct QState {
-    MixedLayout L;
-    uint16_t *S, *SC;
-    int *erow, *erowC, *cfix;
-    unsigned long long* wx;
-    int16_t* ew;
-    float* part;
-    int w_next, rounds_left;
-  };
+  const size_t smem = TC_SMEM;
+  if (cudaError_t ea = tc_smem_attr()) return ea;
   std::vector<QState> Q(n);
   char* p = (char*)work;
   int* err = (int*)p;
@@ -668,48 +546,18 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
   for (int i = 0; i < n; ++i) {
     const BatchGeom& g = qs[i].g;
     if (g.n_w > MAX_W || g.n_w <= 0) return cudaErrorInvalidValue;
-    QState& q = Q[i];
-    q.L = mixed_layout(g, s, sms, slice_cap_of(qs[i]));
-    used += q.L.total;
+    const MixedLayout L = mixed_layout(g, s, sms, slice_cap_of(qs[i]));
+    used += L.total;
     if (used > work_bytes) return cudaErrorMemoryAllocation;
-    q.S = (uint16_t*)p;
-    p += q.L.slices;
-    q.SC = (uint16_t*)p;
-    p += q.L.slicesC;
-    q.erow = (int*)p;
-    p += q.L.erow;
-    q.erowC = (int*)p;
-    p += q.L.erowC;
-    q.part = (float*)p;
-    p += q.L.part;
-    q.wx = (unsigned long long*)p;
-    p += q.L.wm;
-    q.ew = (int16_t*)p;
-    p += q.L.ew;
-    q.cfix = (int*)p;
-    p += q.L.cfix;
-    q.w_next = 0;
-    q.rounds_left = (g.n_w + q.L.G - 1) / q.L.G;
+    Q[i] = carve_q(p, L, g.n_w);
+    p += L.total;
   }
   uint64_t nl = 0;
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int) * 4, st);
   if (e != cudaSuccess) return e;
   hb();
   for (int i = 0; i < n; ++i) {
-    const BatchGeom& g = qs[i].g;
-    QState& q = Q[i];
-    const long nwt = (long)g.n_k * g.n_w * g.n_ov;
-    wtab_kernel<<<(unsigned)std::min<long>((nwt + 255) / 256, (long)sms * 16), 256, 0, st>>>(nwt, qs[i].dtab, q.wx,
-                                                                                               q.ew);
-    erow_kernel<<<q.L.Npad, 256, 0, st>>>(g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_k, g.n_w, qs[i].Cptrs, q.ew,
-                                           q.erow, q.erowC);
-    const long tot = (long)q.L.Npad * q.L.Kr;
-    cfix_kernel<<<(unsigned)std::min<long>((tot + 255) / 256, (long)sms * 32), 256, 0, st>>>(
-        g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_k, q.L.Ktot, q.L.Kr, qs[i].Cptrs, q.erowC, q.cfix);
-    SliceArgs sc{g.cplx, q.L.Npad, g.n_ov, q.L.Ktot, q.L.Kr, s, g.n_w, 0, 1, q.L.nxy, q.cfix, q.erowC,
-                 nullptr, q.erow, q.SC};
-    const long tg = (long)q.L.Npad * (q.L.Kr / 16);
-    launch_slice(g.cplx, (unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), st, sc);
+    prep_q(Q[i], qs[i], s, sms, st);
     nl += 4;
   }
   he(RPA_K_SLICE, 4 * n);
@@ -738,12 +586,7 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
     hb();
     for (size_t k = 0; k < who.size(); ++k) {
       const int i = who[k];
-      QState& q = Q[i];
-      const BatchGeom& g = qs[i].g;
-      SliceArgs sa{g.cplx, q.L.Npad, g.n_ov, q.L.Ktot, q.L.Kr, s, g.n_w, w0s[k], Gs[k], 1, q.cfix, q.erowC,
-                   q.wx, q.erow, q.S};
-      const long tg = (long)q.L.Npad * (q.L.Kr / 16);
-      launch_slice(g.cplx, (unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), st, sa);
+      launch_slice(qs[i].g.cplx, slice_grid(Q[i].L, sms), st, weighted_args(Q[i], qs[i], s, w0s[k], Gs[k]));
       ++nl;
     }
     he(RPA_K_SLICE, (int)who.size());
@@ -838,6 +681,137 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
     nl += 2;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+  }
+  if (status) {
+    err_merge_kernel<<<1, 32, 0, st>>>(err, status);
+    ++nl;
+  }
+  if (n_launch) *n_launch = nl;
+  return cudaSuccess;
+}
+
+size_t mixed_seq_workspace_bytes(const BatchGeom& g, int n_slices, size_t slice_cap) {
+  const MixedLayout L = mixed_layout(g, n_slices, num_sms(), slice_cap);
+  if (L.G < g.n_w) return 1024 + L.total;  // several rounds per q: one region
+  return 1024 + 2 * L.total;
+}
+
+// chi0 of n q of one geometry, one q after another, each in a single round
+// (all its frequencies).  Two workspace regions alternate; the slicer warps
+// of q's tensor-core launch write the weighted digit planes of the next q
+// into the other region while q's MMAs run, so only the first q's weighted
+// slicing is a launch of its own.  The next q's preparation (weights,
+// exponents, fixed-point C, digits of C) runs before q's launch.  Falls back
+// to one launch_chi0_mixed_multi call per q when the workspace cannot hold two
+// single-round regions, the q differ in shape, or a launch would not fill the
+// GPU (the two slicer warps of each CTA must share the slicing with every SM).
+cudaError_t launch_chi0_mixed_seq(const MixedQ* qs, int n, int s, void* work, size_t work_bytes, int* status,
+                                  uint64_t* n_launch, cudaStream_t st, const LaunchHook* hook) {
+  auto hb = [&]() {
+    if (hook) hook->begin(hook->user, st);
+  };
+  auto he = [&](int cls, int nk) {
+    if (hook) hook->end(hook->user, st, cls, nk);
+  };
+  if (n <= 0) return cudaSuccess;
+  if (s < 2 || s > MAX_S) return cudaErrorInvalidValue;
+  const int sms = num_sms();
+  const BatchGeom& g = qs[0].g;
+  const size_t cap = slice_cap_of(qs[0]);
+  const MixedLayout L = mixed_layout(g, s, sms, cap);
+  const std::vector<SegShape> shp{SegShape{L.n_chunks, g.n_w, L.n_tiles, L.nks_cap}};
+  int Lc = autotune_lookup(round_key(shp, s));
+  if (Lc <= 0) {
+    double best = 1e300;
+    for (int c : candidates(shp)) {
+      const double cost = plan_for(shp, c, sms).cost;
+      if (cost < best) {
+        best = cost;
+        Lc = c;
+      }
+    }
+  }
+  const SplitPlan pl = plan_for(shp, Lc, sms);
+  const int nks = pl.nks[0];
+  const int n_items = g.n_w * L.n_tiles * nks;
+  bool seq = n >= 2 && g.n_w > 0 && g.n_w <= MAX_W && L.G >= g.n_w && 1024 + 2 * L.total <= work_bytes &&
+             n_items >= sms;
+  for (int i = 1; i < n && seq; ++i) {
+    const BatchGeom& h = qs[i].g;
+    seq = h.cplx == g.cplx && h.n_aux == g.n_aux && h.n_occ == g.n_occ && h.n_virt == g.n_virt &&
+          h.n_ov == g.n_ov && h.n_k == g.n_k && h.n_w == g.n_w && slice_cap_of(qs[i]) == cap;
+  }
+  if (!seq) {
+    uint64_t tot = 0;
+    for (int i = 0; i < n; ++i) {
+      uint64_t nl = 0;
+      const cudaError_t e = launch_chi0_mixed_multi(&qs[i], 1, s, work, work_bytes, status, &nl, st, false, hook);
+      tot += nl;
+      if (e != cudaSuccess) {
+        if (n_launch) *n_launch = tot;
+        return e;
+      }
+    }
+    if (n_launch) *n_launch = tot;
+    return cudaSuccess;
+  }
+  if (cudaError_t ea = tc_smem_attr()) return ea;
+  char* p = (char*)work;
+  int* err = (int*)p;
+  QState R[2] = {carve_q(p + 1024, L, g.n_w), carve_q(p + 1024 + L.total, L, g.n_w)};
+  uint64_t nl = 0;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int) * 4, st);
+  if (e != cudaSuccess) return e;
+  hb();
+  prep_q(R[0], qs[0], s, sms, st);
+  launch_slice(g.cplx, slice_grid(L, sms), st, weighted_args(R[0], qs[0], s, 0, g.n_w));
+  he(RPA_K_SLICE, 5);
+  nl += 5;
+  const int cps = (L.n_chunks + nks - 1) / nks;
+  for (int i = 0; i < n; ++i) {
+    const QState& c = R[i & 1];
+    const bool more = i + 1 < n;
+    if (more) {
+      hb();
+      prep_q(R[(i + 1) & 1], qs[i + 1], s, sms, st);
+      he(RPA_K_SLICE, 4);
+      nl += 4;
+    }
+    TcParams tp;
+    RedParams rp;
+    memset(&tp, 0, sizeof tp);
+    memset(&rp, 0, sizeof rp);
+    tp.s = s;
+    tp.kb_per_chunk = KB_PER_CHUNK;
+    tp.drop_item = mixed_test_drop_take();
+    tp.err = err;
+    tp.grp_mask = group_mask(s);
+    tp.n_segs = 1;
+    TcSeg& S = tp.seg[0];
+    S.A = c.S;
+    S.B = c.SC;
+    S.nI = L.Npad / 128;
+    S.part = c.part;
+    S.cplx = g.cplx;
+    S.G = g.n_w;
+    S.n_tiles = L.n_tiles;
+    S.n_ksplit = nks;
+    S.kb_per_split = cps * KB_PER_CHUNK;
+    S.n_kb = L.n_kb;
+    S.item0 = 0;
+    tp.n_items = n_items;
+    tp.side_on = more ? 1 : 0;
+    if (more) tp.side = weighted_args(R[(i + 1) & 1], qs[i + 1], s, 0, g.n_w);
+    rp.n_segs = 1;
+    rp.seg[0] = RedSeg{g.cplx, g.n_aux, L.Npad, L.n_tiles, nks, 0, g.n_w, 0, c.part, c.erow, c.erowC, qs[i].chi};
+    hb();
+    launch_tc(s, std::min(n_items, sms), TC_SMEM, st, tp);
+    he(RPA_K_CHI0, 1);
+    hb();
+    reduce_kernel<<<g.n_w * L.n_tiles, 256, 0, st>>>(rp);
+    he(RPA_K_CHI0_RED, 1);
+    nl += 2;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (status) {
     err_merge_kernel<<<1, 32, 0, st>>>(err, status);

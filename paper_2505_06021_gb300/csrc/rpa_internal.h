@@ -175,6 +175,12 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int n_slices, void*
                                     int* status, uint64_t* n_launch, cudaStream_t s, bool tune,
                                     const LaunchHook* hook = nullptr);
 size_t mixed_multi_workspace_bytes(const MixedQ* qs, int n, int n_slices);
+// chi0 of n q of one geometry one after another, the next q's weighted digit
+// planes written by the tensor-core launch of the current one (two workspace
+// regions, mixed_seq_workspace_bytes); otherwise one q at a time.
+cudaError_t launch_chi0_mixed_seq(const MixedQ* qs, int n, int n_slices, void* work, size_t work_bytes,
+                                  int* status, uint64_t* n_launch, cudaStream_t s, const LaunchHook* hook);
+size_t mixed_seq_workspace_bytes(const BatchGeom& g, int n_slices, size_t slice_cap);
 // Autotuner cache (autotune.cu): the recorded split target for a shape-class
 // key, 0 if none; autotune_record stores a measured choice.
 int autotune_lookup(uint64_t key);

@@ -127,6 +127,29 @@ def test_mixed_energy_at_frequency_limit(rpa, ctx):
     assert np.max(np.abs(r["eps"] - ref["eps"])) <= 1e-8 * np.max(np.abs(ref["eps"]))
 
 
+def test_mixed_energy_pipelined_slicing(rpa):
+    """Several q of one shape whose tensor-core launches fill the GPU (4 q,
+    N_aux 384: 12 tiles x 16 frequencies = 192 work items): the weighted digit
+    planes of each next q are written by the slicer warps of the current q's
+    launch, so the job has one standalone weighted-slicing launch plus the
+    four preparation launches per q.  E_c and every term against the oracle,
+    and bit-identical on a second run."""
+    p = synth.make_problem("pipe", is_complex=True, n_aux=384, n_occ=4, n_virt=24,
+                           grid=synth.regular_kq_grid((2, 2, 1)), n_w=16, seed=47)
+    job = rpa.job_from_problem(p, rpa.upload_problem(p), prec=rpa.PREC_MIXED)
+    with rpa.Context(0) as c:
+        c.profile(True)
+        r = c.energy(job)
+        prof = c.profile_read()
+        r2 = c.energy(job)
+    assert prof["slice"][1] == 5 + 4 * (p.n_q - 1), prof["slice"]
+    assert prof["chi0"][1] == p.n_q
+    assert r["Ec"] == r2["Ec"] and np.array_equal(r["eps"], r2["eps"])
+    ref = oracle.energy(p)
+    assert abs(r["Ec"] - ref["Ec"]) <= TOL_EC, (r["Ec"], ref["Ec"])
+    assert np.max(np.abs(r["eps"] - ref["eps"])) <= 1e-8 * np.max(np.abs(ref["eps"]))
+
+
 def test_mixed_deterministic_and_slice_count(rpa):
     p = synth.make_problem("m", is_complex=True, n_aux=96, n_occ=3, n_virt=20, grid=synth.regular_kq_grid((2, 1, 1)),
                            n_w=3, seed=44)
