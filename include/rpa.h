@@ -138,7 +138,9 @@ typedef struct {
   const double *eps_occ;          /* [n_kpts*n_occ], device or host (mem) */
   const double *eps_virt;         /* [n_kpts*n_virt], device or host (mem) */
   const void *const *C;           /* host array [n_q*n_k] of pointers to C(q,k_j); NULL with ao */
-  const void *const *V;           /* host array [n_q] of pointers to V(q) */
+  const void *const *V;           /* host array [n_q] of pointers to V(q); with RPA_MEM_DEVICE every
+                                     C and V pointer is aligned to its element size (16 bytes
+                                     complex, 8 real), else RPA_E_INVAL */
   int prec;                       /* RPA_PREC_* */
   int mem;                        /* RPA_MEM_* */
   const rpa_ao *ao;               /* NULL, or the AO form of the fit coefficients (C must then be

@@ -201,11 +201,15 @@ rpa_status validate_job(const rpa_job* j, char* msg, size_t len) {
     if (j->pair_k[i] < 0 || j->pair_k[i] >= j->n_kpts || j->pair_kq[i] < 0 || j->pair_kq[i] >= j->n_kpts)
       return set_msg(msg, len, "pair index %ld out of range [0, %d)", i, j->n_kpts);
     if (!j->ao && !j->C[i]) return set_msg(msg, len, "C[%ld] is NULL", i);
+    if (!j->ao && j->mem == RPA_MEM_DEVICE && ((uintptr_t)j->C[i] & (j->is_complex ? 15u : 7u)))
+      return set_msg(msg, len, "C[%ld] is not aligned to its element size", i);
   }
   if (j->ao)
     if (int st = ao_validate(j, msg, len)) return st;
   for (int q = 0; q < j->n_q; ++q) {
     if (!j->V[q]) return set_msg(msg, len, "V[%d] is NULL", q);
+    if (j->mem == RPA_MEM_DEVICE && ((uintptr_t)j->V[q] & (j->is_complex ? 15u : 7u)))
+      return set_msg(msg, len, "V[%d] is not aligned to its element size", q);
     if (!isfinite(j->w_q[q])) return set_msg(msg, len, "w_q[%d] not finite", q);
   }
   for (int w = 0; w < j->n_w; ++w)

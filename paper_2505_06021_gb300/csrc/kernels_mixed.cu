@@ -51,29 +51,34 @@ namespace {
 // Their digit planes are written by slice_unit (slice.cuh).
 
 // c_fix of one q: [Npad][Kr] int32, zero outside the data; eC per row.
+// Rows along grid y, K along grid x (both grid-stride), so that no element
+// needs a 64-bit division; consecutive threads read consecutive values of C.
 __global__ void __launch_bounds__(256) cfix_kernel(int cplx, int N, int Npad, int n_ov, int n_k, int Ktot, int Kr,
                                                    const double* const* C, const int* eC, int* cfix) {
-  const long total = (long)Npad * Kr;
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-    const int P = (int)(idx / Kr), k = (int)(idx % Kr);
-    const int tglob = cplx ? (k >> 1) : k;
-    int v = 0;
-    if (P < N && tglob < Ktot) {
-      const int j = tglob / n_ov, t = tglob - j * n_ov;
-      const double c = cplx ? C[j][2 * ((long)P * n_ov + t) + (k & 1)] : C[j][(long)P * n_ov + t];
-      const unsigned long long cb = (unsigned long long)__double_as_longlong(c);
-      const int Ec = (int)((cb >> 52) & 0x7ff);
-      if (Ec != 0) {
-        // c = mant 2^(Ec - 1075); c_fix = c 2^(30 - eC) = mant >> (1045 - Ec + eC)
-        const int sh = 1045 - Ec + eC[P];
-        const unsigned long long mant = (cb & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        if (sh < 64) {
-          const int m = (int)((mant + (1ull << (sh - 1))) >> sh);
-          v = (cb >> 63) ? -m : m;
+  for (int P = blockIdx.y; P < Npad; P += gridDim.y) {
+    int* out = cfix + (long)P * Kr;
+    const int eP = P < N ? eC[P] : 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < Kr; k += gridDim.x * blockDim.x) {
+      const int tglob = cplx ? (k >> 1) : k;
+      int v = 0;
+      if (P < N && tglob < Ktot) {
+        const int j = tglob / n_ov, t = tglob - j * n_ov;
+        const double c = cplx ? C[j][2 * ((long)P * n_ov + t) + (k & 1)] : C[j][(long)P * n_ov + t];
+        const unsigned long long cb = (unsigned long long)__double_as_longlong(c);
+        const int Ec = (int)((cb >> 52) & 0x7ff);
+        if (Ec != 0) {
+          // c = mant 2^(Ec - 1075); c_fix = c 2^(30 - eC) = mant >> (1045 - Ec + eC), a shift of
+          // at least 23 since eC >= Ec - 1022
+          const int sh = 1045 - Ec + eP;
+          const unsigned long long mant = (cb & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+          if (sh < 64) {
+            const int m = (int)((mant + (1ull << (sh - 1))) >> sh);
+            v = (cb >> 63) ? -m : m;
+          }
         }
       }
+      out[k] = v;
     }
-    cfix[idx] = v;
   }
 }
 
@@ -88,75 +93,98 @@ __global__ void __launch_bounds__(256, 2) slice_kernel(SliceArgs a) {
 
 // Row exponents.  eA[w][P] = max_t (Ec_t + Ew_t) - 2044 + 1 (biased fields),
 // so |c w| < 2^(eA - 1) on row P; eC[P] = max_t Ec_t - 1022, so |c| < 2^eC.
-// One block per row; the weight exponents come from the 16-bit table ew.
+// Phase 1: block (row P, part kp) covers k-point j = kp / TP and its t8-chunks
+// [tp n8 / TP, (tp + 1) n8 / TP), tp = kp mod TP, and writes its raw maxima
+// (Ec_t + Ew_t + 1022 per frequency, Ec_t; 0 where no entry is nonzero) to
+// part[kp][g][P] (g = n_w: the Ec maximum); the weight exponents come from the
+// 16-bit table ew.  Phase 2 takes the maximum over the parts.
 constexpr int MAX_W = 32;
-__global__ void __launch_bounds__(256) erow_kernel(int cplx, int N, int Npad, int n_ov, int n_k, int n_w,
-                                                   const double* const* C, const int16_t* ew, int* eA, int* eC) {
-  const int P = blockIdx.x;
+__global__ void __launch_bounds__(256) erow_part_kernel(int cplx, int N, int Npad, int n_ov, int n_w, int TP,
+                                                        const double* const* C, const int16_t* ew, int* part) {
+  const int P = blockIdx.x, kp = blockIdx.y;
+  const int j = kp / TP, tp = kp - j * TP;
   int m[MAX_W];
   int mc = 0;
 #pragma unroll
   for (int g = 0; g < MAX_W; ++g) m[g] = 0;
   if (P < N) {
     const int n8 = (n_ov + 7) / 8;
-    for (int j = 0; j < n_k; ++j) {
-      const unsigned long long* row =
-          reinterpret_cast<const unsigned long long*>(C[j]) + (long)P * n_ov * (cplx ? 2 : 1);
-      for (int t8 = threadIdx.x; t8 < n8; t8 += blockDim.x) {
-        int ec[8];
-        int emax = 0;
+    const int c0 = (int)((long)tp * n8 / TP), c1 = (int)((long)(tp + 1) * n8 / TP);
+    const unsigned long long* row =
+        reinterpret_cast<const unsigned long long*>(C[j]) + (long)P * n_ov * (cplx ? 2 : 1);
+    const bool vec = (n_ov % 8 == 0);
+    for (int t8 = c0 + (int)threadIdx.x; t8 < c1; t8 += blockDim.x) {
+      int ec[8];
+      int emax = 0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int t = t8 * 8 + u;
-          ec[u] = -100000;
-          if (t < n_ov) {
-            int e = (int)((row[cplx ? 2 * t : t] >> 52) & 0x7ff);
-            if (cplx) e = max(e, (int)((row[2 * t + 1] >> 52) & 0x7ff));
-            if (e != 0) ec[u] = e;
-            emax = max(emax, e);
-          }
-        }
-        mc = max(mc, emax);
-        if (emax == 0) continue;
-        const int16_t* e0 = ew + (long)j * n_w * n_ov + t8 * 8;
-        const bool vec = (n_ov % 8 == 0);
-#pragma unroll
-        for (int g = 0; g < MAX_W; ++g) {
-          if (g >= n_w) break;
-          int16_t ev[8];
-          if (vec) {
-            const uint4 v = *reinterpret_cast<const uint4*>(e0 + (long)g * n_ov);
-            memcpy(ev, &v, 16);
+      for (int u = 0; u < 8; ++u) {
+        const int t = t8 * 8 + u;
+        ec[u] = -100000;
+        if (t < n_ov) {
+          int e;
+          if (cplx) {
+            const ulonglong2 x = reinterpret_cast<const ulonglong2*>(row)[t];
+            e = max((int)((x.x >> 52) & 0x7ff), (int)((x.y >> 52) & 0x7ff));
           } else {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) ev[u] = (t8 * 8 + u < n_ov) ? e0[(long)g * n_ov + u] : (int16_t)0;
+            e = (int)((row[t] >> 52) & 0x7ff);
           }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) m[g] = max(m[g], ec[u] + (int)ev[u] + 1022);
+          if (e != 0) ec[u] = e;
+          emax = max(emax, e);
         }
+      }
+      mc = max(mc, emax);
+      if (emax == 0) continue;
+      const int16_t* e0 = ew + (long)j * n_w * n_ov + t8 * 8;
+#pragma unroll
+      for (int g = 0; g < MAX_W; ++g) {
+        if (g >= n_w) break;
+        int16_t ev[8];
+        if (vec) {
+          const uint4 v = *reinterpret_cast<const uint4*>(e0 + (long)g * n_ov);
+          memcpy(ev, &v, 16);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) ev[u] = (t8 * 8 + u < n_ov) ? e0[(long)g * n_ov + u] : (int16_t)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) m[g] = max(m[g], ec[u] + (int)ev[u] + 1022);
       }
     }
   }
-  __shared__ int red[256];
+  // block maxima: one warp reduction per value, then across the 8 warps
+  __shared__ int red[MAX_W + 1][8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int g = 0; g < MAX_W; ++g) {
     if (g >= n_w) break;
-    red[threadIdx.x] = m[g];
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + o]);
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) eA[(long)g * Npad + P] = red[0] > 0 ? red[0] - 2044 + 1 : -2000;
-    __syncthreads();
+    const int r = __reduce_max_sync(0xffffffffu, m[g]);
+    if (lane == 0) red[g][warp] = r;
   }
-  red[threadIdx.x] = mc;
+  {
+    const int r = __reduce_max_sync(0xffffffffu, mc);
+    if (lane == 0) red[MAX_W][warp] = r;
+  }
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + o]);
-    __syncthreads();
+  if ((int)threadIdx.x <= n_w) {
+    const int g = (int)threadIdx.x < n_w ? (int)threadIdx.x : MAX_W;
+    int r = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) r = max(r, red[g][w]);
+    part[((long)kp * (n_w + 1) + threadIdx.x) * Npad + P] = r;
   }
-  if (threadIdx.x == 0) eC[P] = red[0] ? red[0] - 1022 : -2000;
+}
+
+__global__ void __launch_bounds__(256) erow_final_kernel(int n_w, int Npad, int KP, const int* part, int* eA,
+                                                         int* eC) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (n_w + 1) * Npad) return;
+  const int g = idx / Npad, P = idx - g * Npad;
+  int r = 0;
+  for (int kp = 0; kp < KP; ++kp) r = max(r, part[((long)kp * (n_w + 1) + g) * Npad + P]);
+  if (g < n_w)
+    eA[(long)g * Npad + P] = r > 0 ? r - 2044 + 1 : -2000;
+  else
+    eC[P] = r ? r - 1022 : -2000;
 }
 
 // w = zeta_k |d| as a 31-bit mantissa and exponent: w = wm 2^(ew - 31),
@@ -251,8 +279,8 @@ int num_sms() {
 // Workspace of one q: slices of A for up to G frequencies, slices of C,
 // exponents, fixed-point C, weights, split-K partials.
 struct MixedLayout {
-  int Npad, Ktot, Kr, nxy, G, n_tiles, n_kb, n_chunks, nks_cap;
-  size_t slices, slicesC, erow, erowC, part, wm, ew, cfix, total;
+  int Npad, Ktot, Kr, nxy, G, n_tiles, n_kb, n_chunks, nks_cap, TP, KP;
+  size_t slices, slicesC, erow, erowC, part, wm, ew, cfix, erowp, total;
 };
 
 constexpr int KB_PER_CHUNK = 2 * CHUNK / KB;
@@ -285,7 +313,11 @@ MixedLayout mixed_layout(const BatchGeom& g, int s, int sms, size_t slice_cap) {
   L.wm = al(sizeof(unsigned long long) * (size_t)g.n_k * g.n_w * g.n_ov);
   L.ew = al(sizeof(int16_t) * (size_t)g.n_k * g.n_w * g.n_ov);
   L.cfix = al(sizeof(int) * (size_t)L.Npad * L.Kr);
-  L.total = L.slices + L.slicesC + L.erow + L.erowC + L.part + L.wm + L.ew + L.cfix;
+  // row-exponent parts: at least 8 per row (a k-point's t range is cut in TP pieces)
+  L.TP = g.n_k >= 8 ? 1 : (8 + g.n_k - 1) / g.n_k;
+  L.KP = g.n_k * L.TP;
+  L.erowp = al(sizeof(int) * (size_t)L.KP * (g.n_w + 1) * L.Npad);
+  L.total = L.slices + L.slicesC + L.erow + L.erowC + L.part + L.wm + L.ew + L.cfix + L.erowp;
   return L;
 }
 
@@ -433,7 +465,7 @@ cudaError_t tc_smem_attr() {
 struct QState {
   MixedLayout L;
   uint16_t *S, *SC;
-  int *erow, *erowC, *cfix;
+  int *erow, *erowC, *cfix, *erowp;
   unsigned long long* wx;
   int16_t* ew;
   float* part;
@@ -458,27 +490,34 @@ QState carve_q(char* p, const MixedLayout& L, int n_w) {
   q.ew = (int16_t*)p;
   p += L.ew;
   q.cfix = (int*)p;
+  p += L.cfix;
+  q.erowp = (int*)p;
   q.w_next = 0;
   q.rounds_left = (n_w + L.G - 1) / L.G;
   return q;
 }
+
+constexpr int PREP_LAUNCHES = 5;
 
 unsigned slice_grid(const MixedLayout& L, int sms) {
   const long tg = (long)L.Npad * (L.Kr / 16);
   return (unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32);
 }
 
-// Per-q preparation (4 launches): packed weights, row exponents, fixed-point
-// C and the digit planes of C (the B operand).
+// Per-q preparation (PREP_LAUNCHES launches): packed weights, row exponents
+// (two phases), fixed-point C and the digit planes of C (the B operand).
 void prep_q(const QState& q, const MixedQ& m, int s, int sms, cudaStream_t st) {
   const BatchGeom& g = m.g;
   const long nwt = (long)g.n_k * g.n_w * g.n_ov;
   wtab_kernel<<<(unsigned)std::min<long>((nwt + 255) / 256, (long)sms * 16), 256, 0, st>>>(nwt, m.dtab, q.wx, q.ew);
-  erow_kernel<<<q.L.Npad, 256, 0, st>>>(g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_k, g.n_w, m.Cptrs, q.ew, q.erow,
-                                         q.erowC);
-  const long tot = (long)q.L.Npad * q.L.Kr;
-  cfix_kernel<<<(unsigned)std::min<long>((tot + 255) / 256, (long)sms * 32), 256, 0, st>>>(
-      g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_k, q.L.Ktot, q.L.Kr, m.Cptrs, q.erowC, q.cfix);
+  erow_part_kernel<<<dim3((unsigned)q.L.Npad, (unsigned)q.L.KP), 256, 0, st>>>(
+      g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_w, q.L.TP, m.Cptrs, q.ew, q.erowp);
+  erow_final_kernel<<<((g.n_w + 1) * q.L.Npad + 255) / 256, 256, 0, st>>>(g.n_w, q.L.Npad, q.L.KP, q.erowp, q.erow,
+                                                                           q.erowC);
+  const int gy = std::min(q.L.Npad, 65535);
+  const int gx = std::max(1, std::min((q.L.Kr + 255) / 256, sms * 32 / gy));
+  cfix_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_k,
+                                                                   q.L.Ktot, q.L.Kr, m.Cptrs, q.erowC, q.cfix);
   SliceArgs sc{g.cplx, q.L.Npad, g.n_ov, q.L.Ktot, q.L.Kr, s, g.n_w, 0, 1, q.L.nxy, q.cfix, q.erowC,
                nullptr, q.erow, q.SC};
   launch_slice(g.cplx, slice_grid(q.L, sms), st, sc);
@@ -558,9 +597,9 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
   hb();
   for (int i = 0; i < n; ++i) {
     prep_q(Q[i], qs[i], s, sms, st);
-    nl += 4;
+    nl += PREP_LAUNCHES;
   }
-  he(RPA_K_SLICE, 4 * n);
+  he(RPA_K_SLICE, PREP_LAUNCHES * n);
   TcParams tp;
   RedParams rp;
   while (true) {
@@ -765,8 +804,8 @@ cudaError_t launch_chi0_mixed_seq(const MixedQ* qs, int n, int s, void* work, si
   hb();
   prep_q(R[0], qs[0], s, sms, st);
   launch_slice(g.cplx, slice_grid(L, sms), st, weighted_args(R[0], qs[0], s, 0, g.n_w));
-  he(RPA_K_SLICE, 5);
-  nl += 5;
+  he(RPA_K_SLICE, PREP_LAUNCHES + 1);
+  nl += PREP_LAUNCHES + 1;
   const int cps = (L.n_chunks + nks - 1) / nks;
   for (int i = 0; i < n; ++i) {
     const QState& c = R[i & 1];
@@ -774,8 +813,8 @@ cudaError_t launch_chi0_mixed_seq(const MixedQ* qs, int n, int s, void* work, si
     if (more) {
       hb();
       prep_q(R[(i + 1) & 1], qs[i + 1], s, sms, st);
-      he(RPA_K_SLICE, 4);
-      nl += 4;
+      he(RPA_K_SLICE, PREP_LAUNCHES);
+      nl += PREP_LAUNCHES;
     }
     TcParams tp;
     RedParams rp;

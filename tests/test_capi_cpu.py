@@ -86,6 +86,22 @@ def test_validate_rejects_bad_jobs(lib):
     assert j.validate()[0] == rpa.RPA_E_INVAL
 
 
+def test_validate_rejects_misaligned_device_pointers(lib):
+    """Device-resident C and V are read as whole elements (16 bytes for
+    complex128): a pointer off that alignment is refused on the host."""
+    p = synth.config1(n_aux=32, n_occ=2, n_virt=5)
+    j = _fake_job(p, C=[FakeTensor(0x10008 + 0x100 * i) for i in range(p.n_q * p.n_k)])
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "C[0]" in msg and "aligned" in msg
+    j = _fake_job(p, V=[FakeTensor(0x90000 + 0x100 * i + (8 if i == 2 else 0)) for i in range(p.n_q)])
+    st, msg = j.validate()
+    assert st == rpa.RPA_E_INVAL and "V[2]" in msg and "aligned" in msg
+    # real (Gamma-only) data needs 8 bytes only
+    g = synth.config0()
+    j = _fake_job(g, C=[FakeTensor(0x10008 + 0x100 * i) for i in range(g.n_q * g.n_k)])
+    assert j.validate()[0] == rpa.RPA_OK
+
+
 def test_footprint_grows_with_size(lib):
     a = _fake_job(synth.config1(n_aux=64, n_occ=2, n_virt=5)).footprint()
     b = _fake_job(synth.config1(n_aux=128, n_occ=2, n_virt=5)).footprint()

@@ -132,7 +132,7 @@ def test_mixed_energy_pipelined_slicing(rpa):
     N_aux 384: 12 tiles x 16 frequencies = 192 work items): the weighted digit
     planes of each next q are written by the slicer warps of the current q's
     launch, so the job has one standalone weighted-slicing launch plus the
-    four preparation launches per q.  E_c and every term against the oracle,
+    five preparation launches per q.  E_c and every term against the oracle,
     and bit-identical on a second run."""
     p = synth.make_problem("pipe", is_complex=True, n_aux=384, n_occ=4, n_virt=24,
                            grid=synth.regular_kq_grid((2, 2, 1)), n_w=16, seed=47)
@@ -142,7 +142,7 @@ def test_mixed_energy_pipelined_slicing(rpa):
         r = c.energy(job)
         prof = c.profile_read()
         r2 = c.energy(job)
-    assert prof["slice"][1] == 5 + 4 * (p.n_q - 1), prof["slice"]
+    assert prof["slice"][1] == 6 + 5 * (p.n_q - 1), prof["slice"]
     assert prof["chi0"][1] == p.n_q
     assert r["Ec"] == r2["Ec"] and np.array_equal(r["eps"], r2["eps"])
     ref = oracle.energy(p)
