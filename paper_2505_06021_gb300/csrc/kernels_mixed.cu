@@ -93,27 +93,53 @@ __global__ void __launch_bounds__(256, 2) slice_kernel(SliceArgs a) {
 
 // Row exponents.  eA[w][P] = max_t (Ec_t + Ew_t) - 2044 + 1 (biased fields),
 // so |c w| < 2^(eA - 1) on row P; eC[P] = max_t Ec_t - 1022, so |c| < 2^eC.
-// Phase 1: block (row P, part kp) covers k-point j = kp / TP and its t8-chunks
-// [tp n8 / TP, (tp + 1) n8 / TP), tp = kp mod TP, and writes its raw maxima
+// Phase 1: block (rows 8 bx .. 8 bx + 7, part kp) covers k-point j = kp / TP
+// and its t8-chunks [tp n8 / TP, (tp + 1) n8 / TP), tp = kp mod TP; warp w
+// takes row 8 bx + w, lane l the l-th chunk of each group of 32 chunks.  The
+// 16-bit weight exponents of a group (all frequencies) are staged in shared
+// memory once for the block's 8 rows.  Each warp writes its row's raw maxima
 // (Ec_t + Ew_t + 1022 per frequency, Ec_t; 0 where no entry is nonzero) to
-// part[kp][g][P] (g = n_w: the Ec maximum); the weight exponents come from the
-// 16-bit table ew.  Phase 2 takes the maximum over the parts.
+// part[kp][g][P] (g = n_w: the Ec maximum).  Phase 2 takes the maximum over
+// the parts.
 constexpr int MAX_W = 32;
+constexpr int EROW_ROWS = 8;
 __global__ void __launch_bounds__(256) erow_part_kernel(int cplx, int N, int Npad, int n_ov, int n_w, int TP,
                                                         const double* const* C, const int16_t* ew, int* part) {
-  const int P = blockIdx.x, kp = blockIdx.y;
+  __shared__ uint4 ews[MAX_W][32];  // [frequency][chunk of the group]: 8 exponents each
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int P = blockIdx.x * EROW_ROWS + warp, kp = blockIdx.y;
   const int j = kp / TP, tp = kp - j * TP;
+  const int n8 = (n_ov + 7) / 8;
+  const int c0 = (int)((long)tp * n8 / TP), c1 = (int)((long)(tp + 1) * n8 / TP);
+  const bool vec = (n_ov % 8 == 0);
+  const int16_t* ewj = ew + (long)j * n_w * n_ov;
+  const unsigned long long* row =
+      P < N ? reinterpret_cast<const unsigned long long*>(C[j]) + (long)P * n_ov * (cplx ? 2 : 1) : nullptr;
   int m[MAX_W];
   int mc = 0;
 #pragma unroll
   for (int g = 0; g < MAX_W; ++g) m[g] = 0;
-  if (P < N) {
-    const int n8 = (n_ov + 7) / 8;
-    const int c0 = (int)((long)tp * n8 / TP), c1 = (int)((long)(tp + 1) * n8 / TP);
-    const unsigned long long* row =
-        reinterpret_cast<const unsigned long long*>(C[j]) + (long)P * n_ov * (cplx ? 2 : 1);
-    const bool vec = (n_ov % 8 == 0);
-    for (int t8 = c0 + (int)threadIdx.x; t8 < c1; t8 += blockDim.x) {
+  for (int g0 = c0; g0 < c1; g0 += 32) {
+    // stage the group's exponents: n_w x 32 chunks of 8 values
+    for (int u = threadIdx.x; u < n_w * 32; u += blockDim.x) {
+      const int g = u >> 5, ch = g0 + (u & 31);
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (ch < c1) {
+        const int16_t* src = ewj + (long)g * n_ov + (long)ch * 8;
+        if (vec) {
+          v = *reinterpret_cast<const uint4*>(src);
+        } else {
+          int16_t tmp[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) tmp[e] = (ch * 8 + e < n_ov) ? src[e] : (int16_t)0;
+          memcpy(&v, tmp, 16);
+        }
+      }
+      ews[g][u & 31] = v;
+    }
+    __syncthreads();
+    const int t8 = g0 + lane;
+    if (row && t8 < c1) {
       int ec[8];
       int emax = 0;
 #pragma unroll
@@ -133,45 +159,29 @@ __global__ void __launch_bounds__(256) erow_part_kernel(int cplx, int N, int Npa
         }
       }
       mc = max(mc, emax);
-      if (emax == 0) continue;
-      const int16_t* e0 = ew + (long)j * n_w * n_ov + t8 * 8;
+      if (emax != 0) {
 #pragma unroll
-      for (int g = 0; g < MAX_W; ++g) {
-        if (g >= n_w) break;
-        int16_t ev[8];
-        if (vec) {
-          const uint4 v = *reinterpret_cast<const uint4*>(e0 + (long)g * n_ov);
+        for (int g = 0; g < MAX_W; ++g) {
+          if (g >= n_w) break;
+          const uint4 v = ews[g][lane];
+          int16_t ev[8];
           memcpy(ev, &v, 16);
-        } else {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) ev[u] = (t8 * 8 + u < n_ov) ? e0[(long)g * n_ov + u] : (int16_t)0;
+          for (int u = 0; u < 8; ++u) m[g] = max(m[g], ec[u] + (int)ev[u] + 1022);
         }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) m[g] = max(m[g], ec[u] + (int)ev[u] + 1022);
       }
     }
+    __syncthreads();
   }
-  // block maxima: one warp reduction per value, then across the 8 warps
-  __shared__ int red[MAX_W + 1][8];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // row maxima: one warp reduction per value
 #pragma unroll
   for (int g = 0; g < MAX_W; ++g) {
     if (g >= n_w) break;
     const int r = __reduce_max_sync(0xffffffffu, m[g]);
-    if (lane == 0) red[g][warp] = r;
+    if (lane == 0 && P < Npad) part[((long)kp * (n_w + 1) + g) * Npad + P] = r;
   }
-  {
-    const int r = __reduce_max_sync(0xffffffffu, mc);
-    if (lane == 0) red[MAX_W][warp] = r;
-  }
-  __syncthreads();
-  if ((int)threadIdx.x <= n_w) {
-    const int g = (int)threadIdx.x < n_w ? (int)threadIdx.x : MAX_W;
-    int r = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) r = max(r, red[g][w]);
-    part[((long)kp * (n_w + 1) + threadIdx.x) * Npad + P] = r;
-  }
+  const int r = __reduce_max_sync(0xffffffffu, mc);
+  if (lane == 0 && P < Npad) part[((long)kp * (n_w + 1) + n_w) * Npad + P] = r;
 }
 
 __global__ void __launch_bounds__(256) erow_final_kernel(int n_w, int Npad, int KP, const int* part, int* eA,
@@ -510,7 +520,7 @@ void prep_q(const QState& q, const MixedQ& m, int s, int sms, cudaStream_t st) {
   const BatchGeom& g = m.g;
   const long nwt = (long)g.n_k * g.n_w * g.n_ov;
   wtab_kernel<<<(unsigned)std::min<long>((nwt + 255) / 256, (long)sms * 16), 256, 0, st>>>(nwt, m.dtab, q.wx, q.ew);
-  erow_part_kernel<<<dim3((unsigned)q.L.Npad, (unsigned)q.L.KP), 256, 0, st>>>(
+  erow_part_kernel<<<dim3((unsigned)((q.L.Npad + EROW_ROWS - 1) / EROW_ROWS), (unsigned)q.L.KP), 256, 0, st>>>(
       g.cplx, g.n_aux, q.L.Npad, g.n_ov, g.n_w, q.L.TP, m.Cptrs, q.ew, q.erowp);
   erow_final_kernel<<<((g.n_w + 1) * q.L.Npad + 255) / 256, 256, 0, st>>>(g.n_w, q.L.Npad, q.L.KP, q.erowp, q.erow,
                                                                            q.erowC);
