@@ -844,6 +844,46 @@ cudaError_t launch_chol_t(int N, int b0, int n_mat, double* mats, long bstride, 
   return cudaGetLastError();
 }
 
+// Clusters of CL CTAs of cholesky_kernel<C, CL> the device holds at once
+// (cudaOccupancyMaxActiveClusters), queried once; 0 if the query fails.
+template <bool C, int CL>
+int chol_max_clusters() {
+  static int n = -1;
+  if (n < 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(256);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int m = 0;
+    if (cudaOccupancyMaxActiveClusters(&m, cholesky_kernel<C, CL>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      m = 0;
+    }
+    n = m;
+  }
+  return n;
+}
+
+// A cluster per matrix: CL_BIG CTAs each when all the launch's clusters fit
+// on the device at once, else clusters of 4 when those do (one wave instead of
+// two: the serial diagonal and panel phases, not the trailing update, set a
+// cluster's time).
+template <bool C>
+cudaError_t launch_chol_clusters(int N, int b0, int n_mat, double* mats, long bstride, int mode, double* out,
+                                 int* status, int status_base, cudaStream_t s, const double* Wn, const double* Vc,
+                                 const double* ldV, int n_w) {
+  const int m8 = chol_max_clusters<C, CL_BIG>();
+  if (m8 > 0 && n_mat > m8 && chol_max_clusters<C, 4>() >= n_mat)
+    return launch_chol_t<C, 4>(N, b0, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
+  return launch_chol_t<C, CL_BIG>(N, b0, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
+}
+
 // The launch split of launch_chol_c: 0 = one CTA per matrix, 1 = a cluster
 // per matrix, 2 = one CTA per matrix except a short last wave on clusters.
 int chol_split(int N, int n_mat) {
@@ -862,7 +902,7 @@ cudaError_t launch_chol_c(int N, int n_mat, double* mats, long bstride, int mode
   const int split = chol_split(N, n_mat);
   // few large matrices: a cluster per matrix
   if (split == 1)
-    return launch_chol_t<C, CL_BIG>(N, 0, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
+    return launch_chol_clusters<C>(N, 0, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
   // one CTA per matrix; a short last wave (fewer than P/2 matrices) goes to
   // clusters instead, so that it does not run on a few SMs alone
   const int r = n_mat % W;
@@ -870,8 +910,8 @@ cudaError_t launch_chol_c(int N, int n_mat, double* mats, long bstride, int mode
     cudaError_t e = launch_chol_t<C, 1>(N, 0, n_mat - r, mats, bstride, mode, out, status, status_base, s, Wn, Vc,
                                         ldV, n_w);
     if (e != cudaSuccess) return e;
-    return launch_chol_t<C, CL_BIG>(N, n_mat - r, r, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV,
-                                    n_w);
+    return launch_chol_clusters<C>(N, n_mat - r, r, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV,
+                                   n_w);
   }
   return launch_chol_t<C, 1>(N, 0, n_mat, mats, bstride, mode, out, status, status_base, s, Wn, Vc, ldV, n_w);
 }
