@@ -1,15 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the RPA hot path on GB300.
 
-Default workload (periodic2d): a step is one whole RPA correlation-energy job
-of the 2-D periodic workload (complex128, 4x4x1 k- and q-grids = 16 q x 16 k,
-N_aux = 512, N_occ = 32, N_virt = 224, 20 imaginary frequencies): chi0 for
-every (q, omega), the sandwich, the Cholesky log-det and the quadrature,
-through the C ABI (rpa_energy) with inputs resident in HBM.  The mixed
-(split-precision chi0) path is timed, and one step of the plain FP64 path is
-timed beside it with |dE_c| between the two.  Prints one JSON line.
+Default workload (slab): a step is one whole RPA correlation-energy job of
+the slab dual-grid workload (complex128, coarse 3x3x1 q-grid without Gamma
+plus 4 near-Gamma points, dense 6x6x1 K_reg = 12 q x 36 k pairs, N_aux = 768,
+N_occ = 32, N_virt = 480, 16 imaginary frequencies): chi0 for every
+(q, omega), the V side, the Cholesky log-det and the quadrature, through the
+C ABI (rpa_energy) with inputs resident in HBM.  The mixed (split-precision
+chi0) path is timed, and one step of the plain FP64 path is timed beside it
+with |dE_c| and the per-term error between the two; a short Poisson stream
+of served jobs gives the p50/p99 latency beside it.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|mixed]
+    python bench.py --workload periodic2d  # the 2-D periodic job (4x4x1, N_aux 512, 20 frequencies)
     python bench.py --workload batch     # 64 uneven instances per step (rpa_energy_batch)
     python bench.py --workload serving   # Poisson stream of jobs (rpa_submit), p50/p99 latency
     python bench.py --workload periodic2d-ao  # the same job given as PADF + MO coefficients
@@ -31,6 +34,15 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+T_START = time.perf_counter()
+
+
+def log(msg):
+    """Progress note on stderr (stdout carries only the JSON line)."""
+    sys.stderr.write("[bench %7.1f s] %s\n" % (time.perf_counter() - T_START, msg))
+    sys.stderr.flush()
+
+
 METRIC = "χ0 TFLOP/s & E_c jobs/s, mixed vs FP64 at |ΔE_c|≤1µHa; p50/p99 job latency"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.259
 
@@ -49,9 +61,12 @@ def parse():
     ap.add_argument("--n-q", type=int, default=0, help="profiling only: restrict the job to its first n q-points")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", default="periodic2d", choices=["periodic2d", "slab", "batch", "serving",
-                                                                         "periodic2d-ao"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--workload", default="slab", choices=["periodic2d", "slab", "batch", "serving",
+                                                                   "periodic2d-ao"])
+    ap.add_argument("--lat-jobs", type=int, default=40,
+                    help="periodic2d/slab: jobs of the short served stream whose p50/p99 latency joins the line "
+                         "(0: none)")
     ap.add_argument("--no-fp64", action="store_true", help="periodic2d: skip the FP64 comparison step")
     ap.add_argument("--n-inst", type=int, default=64, help="batch: instances per step")
     ap.add_argument("--ao-scale", type=int, default=1,
@@ -182,26 +197,81 @@ def allreduce_max(x, world):
     return float(t.item())
 
 
-def cpu_oracle_sample(p, q=0, w=0):
-    """Times the oracle as it stands on the host cores on one (q, omega) term
-    plus the V(q)^(1/2) it needs; returns seconds for each and the threads."""
-    import oracle
+def oracle_terms(p, name):
+    """The (q, omega) terms the oracle samples on the large workloads: 2-D
+    periodic q in {Gamma, 5} x omega in {0, 10, 19}; slab dual grid q in
+    {first regular, first near-Gamma} x omega in {0, 8, 15}."""
+    import numpy as np
 
-    nthr = oracle.max_threads()
-    V = p.V(q)
-    t0 = time.perf_counter()
-    Vh = oracle.vhalf(V)
-    t1 = time.perf_counter()
-    C = [p.C(q, j) for j in range(p.n_k)]
-    t2 = time.perf_counter()
-    oracle.term(p, q, w, Vh=Vh, C_blocks=C)
-    t3 = time.perf_counter()
-    return {"vhalf_s": t1 - t0, "term_s": t3 - t2, "threads": nthr}
+    if name == "slab":
+        ng = np.asarray(p.grid.near_gamma, bool)
+        qs = [int(np.argmin(ng)), int(np.argmax(ng))]
+        ws = [0, p.n_w // 2, p.n_w - 1]
+    else:
+        qs = [0, min(5, p.n_q - 1)]
+        ws = [0, p.n_w // 2, p.n_w - 1]
+    return [(q, w) for q in qs for w in ws]
 
 
-def oracle_jobs_per_s(p, s):
-    job_s = p.n_q * s["vhalf_s"] + p.n_q * p.n_w * s["term_s"]
-    return 1.0 / job_s, job_s
+class OracleSampler:
+    """Times the oracle as it stands (the plain FP64 definition, OpenMP over
+    rows) on the host cores.  V(q)^1/2 (single-threaded Jacobi) is formed once
+    per sampled q, outside the sampled steps; a step is one (q, omega) term of
+    the stated subset with its chi0 over one k-pair (the pairs cycle from step
+    to step), then the sandwich and the Cholesky log-det of the full N x N
+    matrices.  A whole job is extrapolated as
+    n_q T_vhalf + n_q n_w (n_k T_chi0(one pair) + T_tail)."""
+
+    def __init__(self, p, name, n_vhalf=None):
+        import oracle
+
+        oracle.build()
+        self.p, self.terms = p, oracle_terms(p, name)
+        self.threads = oracle.max_threads()
+        self.Vh, self.vhalf_s = {}, []
+        qs = sorted(set(q for q, _ in self.terms))
+        for q in qs[:n_vhalf] if n_vhalf else qs:
+            t0 = time.perf_counter()
+            self.Vh[q] = oracle.vhalf(p.V(q))
+            self.vhalf_s.append(time.perf_counter() - t0)
+        self.terms = [(q, w) for q, w in self.terms if q in self.Vh]
+        self._C = {}
+        self.chi_s, self.tail_s = [], []
+
+    def step(self, i):
+        import oracle
+
+        p = self.p
+        q, w = self.terms[i % len(self.terms)]
+        j = (i // len(self.terms)) % p.n_k
+        if (q, j) not in self._C:
+            self._C[(q, j)] = p.C(q, j)
+        eo, ev = p.eps_pair(q, j)
+        t0 = time.perf_counter()
+        chi = oracle.chi0([self._C[(q, j)]], [eo], [ev], p.grid.zeta_k, float(p.omega[w]))
+        t1 = time.perf_counter()
+        Pi = oracle.sandwich(self.Vh[q], chi)
+        oracle.logdet(Pi)
+        t2 = time.perf_counter()
+        self.chi_s.append(t1 - t0)
+        self.tail_s.append(t2 - t1)
+        return t2 - t0
+
+    def job_s(self):
+        p = self.p
+        return (p.n_q * statistics.median(self.vhalf_s) +
+                p.n_q * p.n_w * (p.n_k * statistics.median(self.chi_s) + statistics.median(self.tail_s)))
+
+    def record(self):
+        js = self.job_s()
+        return {"value": 1.0 / js, "unit": "jobs/s", "cores": self.threads, "kind": "oracle",
+                "sample": "terms %s (q, w) of the job, each step chi0 over one k-pair (pairs cycling) + V^1/2 "
+                          "sandwich + Cholesky log-det at full N, OpenMP over rows; V(q)^1/2 Jacobi once per sampled "
+                          "q (single thread, outside the steps); whole job extrapolated as n_q*T_vhalf + "
+                          "n_q*n_w*(n_k*T_chi0_pair + T_tail)" % self.terms,
+                "extrapolated_job_s": js, "vhalf_s": statistics.median(self.vhalf_s),
+                "chi0_one_pair_s": statistics.median(self.chi_s), "tail_s": statistics.median(self.tail_s),
+                "steps_sampled": len(self.chi_s)}
 
 
 def gpu_local_cpus(dev_index):
@@ -267,30 +337,49 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    p = workload()
-    import oracle
-
-    oracle.build()
-    from paper_2505_06021_gb300 import synth
-
-    # warm-up steps touch the same code paths on the small Gamma-only case
+    name = args.workload if args.workload in ("periodic2d", "slab") else "slab"
+    p = workload(0, name)
+    smp = OracleSampler(p, name)
     for i in range(args.warmup):
-        cpu_oracle_sample(synth.config0(), q=0, w=i % 16)
-    times = [cpu_oracle_sample(p, q=(5 * i) % p.n_q, w=(7 * i) % p.n_w) for i in range(args.steps)]
-    vh = statistics.median(t["vhalf_s"] for t in times)
-    tm = statistics.median(t["term_s"] for t in times)
-    val, job_s = oracle_jobs_per_s(p, {"vhalf_s": vh, "term_s": tm})
-    sample = ("per step one (q, omega) term of the job (chi0 + V^1/2 sandwich + Cholesky log-det) plus the "
-              "V(q)^1/2 Jacobi it needs; job time extrapolated as n_q*T_vhalf + n_q*n_w*T_term")
+        smp.step(i)
+    smp.chi_s, smp.tail_s = [], []
+    step_s = [smp.step(args.warmup + i) for i in range(args.steps)]
+    rec = smp.record()
+    val = rec["value"]
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "jobs/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * (vh + tm),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(step_s),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded, shapes of the paper's periodic workloads)",
-            "config": config_of(p, "fp64", 0),
-            "cpu_baseline": {"value": val, "unit": "jobs/s", "cores": times[0]["threads"], "kind": "oracle",
-                             "sample": sample, "extrapolated_job_s": job_s, "vhalf_s": vh, "term_s": tm},
+            "config": config_of(p, "fp64", 0, name),
+            "cpu_baseline": rec,
             "e2e": {"value": val, "unit": "jobs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def host_mem_available():
+    """MemAvailable of this host in bytes (None if unknown)."""
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def served_latency(args, local, n_jobs):
+    """p50/p99 job latency of a short Poisson stream of served jobs (the
+    serving workload's 50/30/20 size mix, first n_jobs jobs) at 80 % of the
+    capacity measured on the same stream in a closed loop."""
+    a = argparse.Namespace(**vars(args))
+    a.serve_jobs, a.serve_load = n_jobs, 0.8
+    rec = serving_record(a, local)
+    return {"p50_s": rec["latency_s"]["p50"], "p99_s": rec["latency_s"]["p99"], "mean_s": rec["latency_s"]["mean"],
+            "jobs_s": rec["value"], "capacity_jobs_s": rec["config"]["capacity_jobs_s"],
+            "queue_wait_p99_s": rec["queue_wait_s"]["p99"], "jobs": rec["steps"],
+            "stream": "first %d jobs of the serving stream (50/30/20 Gamma-only N_aux 64 / 2-D periodic N_aux 512 / "
+                      "uneven instances, n x n x 1 k-grids), arrivals at 80 %% of the closed-loop capacity, "
+                      "rpa_submit/rpa_poll, mixed chi0" % n_jobs}
 
 
 def run_ours(args):
@@ -305,97 +394,115 @@ def run_ours(args):
     if prec == "auto":
         prec = "mixed" if rpa_mixed_available() else "fp64"
     pc = rpa.PREC_MIXED if prec == "mixed" else rpa.PREC_FP64
-    p = workload(args.n_q, args.workload)
+    name = args.workload
+    p = workload(args.n_q, name)
+    dev = "cuda:%d" % local
+    # end-to-end inputs: pinned host copies of the whole job (generated once;
+    # the device-resident job is copied from them)
+    want_e2e = not args.no_e2e and not args.n_q
+    e2e_skip = None
+    if want_e2e:
+        avail = host_mem_available()
+        need = 1.25 * p.c_bytes() * world + 16e9
+        if avail is not None and avail < need:
+            want_e2e, e2e_skip = False, "host memory: %.0f GB available, %.0f GB needed" % (avail / 1e9, need / 1e9)
     t_gen = time.perf_counter()
-    tens = rpa.upload_problem(p, "cuda:%d" % local)
+    th = None
+    if want_e2e:
+        with near_gpu(local) as ng:
+            th = rpa.upload_problem(p, "cpu", pin=True)
+        tens = {"C": [t.to(dev, non_blocking=True) for t in th["C"]], "V": [t.to(dev) for t in th["V"]],
+                "eps_occ": th["eps_occ"].to(dev), "eps_virt": th["eps_virt"].to(dev)}
+    else:
+        tens = rpa.upload_problem(p, dev)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
+    log("inputs ready (%.1f s)" % t_gen)
     job = rpa.job_from_problem(p, tens, prec=pc)
     ctx = rpa.Context(local, n_slices=args.slices, hbm_cap_bytes=int(args.cap_gb * 1e9))
     for _ in range(args.warmup):
         ctx.energy(job)
+    log("warm-up done")
     ext = torch.cuda.ExternalStream(ctx.stream_handle)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     clocks = ClockSampler(local)
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
     ctx.profile(True)
     n0 = ctx.launches
-    e0.record(ext)
+    ev[0].record(ext)
     res = None
-    for _ in range(args.steps):
+    for i in range(args.steps):
         res = ctx.energy(job)
-    e1.record(ext)
+        ev[i + 1].record(ext)
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
     prof = ctx.profile_read()
+    cnt = ctx.profile_counters()
     ctx.profile(False)
     launches = ctx.launches - n0
-    ms = e0.elapsed_time(e1)
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    ms = ev[0].elapsed_time(ev[args.steps])
     ms_max = allreduce_max(ms, world)
     jobs_per_s = world * args.steps / (ms_max / 1e3)
     chi0_flops_job = p.chi0_flops()
 
-    # dominant kernel: chi0 (one launch per q-batch in the FP64 path)
+    # dominant kernel: the chi0 contraction
     chi_ms, chi_n = prof["chi0"]
     chi_launch_ms = chi_ms / max(chi_n, 1)
     flops_per_launch = chi0_flops_job * args.steps / max(chi_n, 1)
     achieved = flops_per_launch / (chi_launch_ms / 1e3) / 1e12
+    counting = ("achieved = the method's algorithmic FP64-equivalent chi0 flops (Hermitian lower triangle, "
+                "4N(N+1)N_ov per (q, k, omega), complex; all n_w frequencies) per launch / the launch's mean "
+                "CUDA-event time")
     if prec == "fp64":
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": traffic_for("chi0_fp64") if args.workload == "periodic2d" else None,
+                "traffic": traffic_for("chi0_fp64") if name == "periodic2d" else None,
                 "kernel": "chi0_fp64_kernel", "peak_source": "derived FP64 DFMA peak: 152 SMs x 2 DFMA/clk x "
-                "2 flop x 2.07 GHz (microbenchmark measured 1.205 TFLOP/s)",
-                "note": "achieved counts the algorithmic Hermitian lower-triangle flops 4N(N+1)N_ov per (q,k,w); "
-                        "the kernel forms conj(C_P)C_Q once per t and reuses it over a group of frequencies, so "
+                "2 flop x 2.07 GHz (microbenchmark measured 1.205 TFLOP/s)", "counting": counting,
+                "note": "the kernel forms conj(C_P)C_Q once per t and reuses it over a group of frequencies, so "
                         "it executes fewer FP64 instructions than the algorithmic count"}
     else:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        tensor_flops = rpa_mixed_tensor_flops(p, ctx, args.slices or 4)
-        ach_t = tensor_flops * args.steps / max(chi_n, 1) / (chi_launch_ms / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": ach_t, "peak": peak, "unit": "TFLOP/s", "frac": ach_t / peak,
-                "traffic": traffic_for("chi0_mixed") if args.workload == "periodic2d" else None,
-                "kernel": "chi0 tcgen05 sliced",
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
-                "algorithmic_fp64_equiv_tflops": achieved}
+        ex_t = cnt["tensor_flops"] / (chi_ms / 1e3) / 1e12 if chi_ms > 0 else None
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic_for("chi0_mixed_" + name),
+                "kernel": "chi0_tc_kernel<%d> (tcgen05, BF16 digit slices)" % (args.slices or 4),
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; the kernel runs inside a "
+                               "long step)", "counting": counting,
+                "executed_tensor_tflops": ex_t, "executed_frac": ex_t / peak if ex_t else None,
+                "executed_note": "tensor-core flops the launches issue (slice pairs x padded tiles x padded K x "
+                                 "the contractions run), counted by the library, per second of chi0 launch time",
+                "launch_ms": chi_launch_ms, "launches_per_step": chi_n / max(args.steps, 1)}
     kernel_ms = {k: {"ms": v[0] / args.steps, "launches": v[1] // max(args.steps, 1)} for k, v in prof.items()
                  if v[1]}
     line = {"metric": METRIC, "value": jobs_per_s, "unit": "jobs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "bf16-slices->f64",
             "data": "synthetic (seeded, shapes of the paper's periodic workloads; no public data)",
-            "config": dict(config_of(p, prec, args.n_q, args.workload),
+            "config": dict(config_of(p, prec, args.n_q, name),
                            **({"chi0_slices": args.slices or 4} if prec == "mixed" else {})),
             "chi0_tflops": chi0_flops_job * world * args.steps / (ms_max / 1e3) / 1e12,
             "chi0_tflops_kernel": achieved, "Ec": res["Ec"], "gpu_launches": launches,
+            "latency_s": {"p50": float(np.percentile(step_ms, 50)) / 1e3,
+                          "p99": float(np.percentile(step_ms, 99)) / 1e3,
+                          "what": "per-job latency of the timed jobs (one job at a time, device-resident inputs, "
+                                  "CUDA events between jobs)"},
             "kernel_ms_per_step": kernel_ms, "roofline": roof, "clocks": clk, "input_gen_s": t_gen}
 
+    log("timed steps done: %.1f ms/step" % (ms_max / args.steps))
     # end to end through the public API with HOST buffers (pinned), copies inside
-    if not args.no_e2e and not args.n_q:
-        with near_gpu(local) as ng:
-            th = rpa.upload_problem(p, "cpu", pin=True)
+    if want_e2e:
         jh = rpa.job_from_problem(p, th, prec=pc, mem=rpa.MEM_HOST)
         ctx.energy(jh)
-        # host -> device bandwidth of these pinned buffers (one q-batch's worth), warm
-        nb_probe = min(len(th["C"]), 4 * p.n_k)
-        dbuf = torch.empty(sum(t.numel() for t in th["C"][:nb_probe]), dtype=th["C"][0].dtype, device="cuda")
-        torch.cuda.synchronize()
-        h0 = time.perf_counter()
-        off = 0
-        for t in th["C"][:nb_probe]:
-            dbuf[off:off + t.numel()].copy_(t.reshape(-1), non_blocking=True)
-            off += t.numel()
-        torch.cuda.synchronize()
-        h2d_gbs = dbuf.numel() * dbuf.element_size() / (time.perf_counter() - h0) / 1e9
-        del dbuf
         barrier(world)
         torch.cuda.synchronize()
+        ctx.profile(True)
         t0 = time.perf_counter()
         step_s = []
         for _ in range(args.e2e_steps):
@@ -404,46 +511,65 @@ def run_ours(args):
             step_s.append(time.perf_counter() - t1)
         torch.cuda.synchronize()
         te = allreduce_max(time.perf_counter() - t0, world)
+        hprof = ctx.profile_read()
+        hcnt = ctx.profile_counters()
+        ctx.profile(False)
         h2d = sum(t.numel() * t.element_size() for t in th["C"] + th["V"]) + 8 * (th["eps_occ"].numel() +
                                                                                     th["eps_virt"].numel())
         nqw = p.n_q * p.n_w
+        cp_ms = hprof["h2d"][0]
         line["e2e"] = {"value": world * args.e2e_steps / te, "unit": "jobs/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": 8 * (1 + 3 * nqw) + 4, "steps": args.e2e_steps,
-                       "step_s": step_s, "h2d_gbs_of_inputs": h2d_gbs, "host_numa_node": ng.node,
-                       "pinned_near_gpu": bool(ng.cpus),
+                       "step_s": step_s,
+                       "h2d_gbs_library": (hcnt["h2d_bytes"] / (cp_ms / 1e3) / 1e9) if cp_ms > 0 else None,
+                       "h2d_gbs_note": "bytes rpa_energy copied host->device / the copies' own time (CUDA events "
+                                       "around each q-batch's copies on the library's copy stream), over the "
+                                       "e2e steps",
+                       "h2d_bytes_library_per_step": hcnt["h2d_bytes"] / args.e2e_steps,
+                       "h2d_copy_ms_per_step": cp_ms / args.e2e_steps,
+                       "host_numa_node": ng.node, "pinned_near_gpu": bool(ng.cpus),
                        "Ec_matches_device": bool(rh["Ec"] == res["Ec"])}
-        del th, jh
+        del jh
     else:
-        line["e2e"] = None
+        line["e2e"] = None if e2e_skip is None else {"skipped": e2e_skip}
+    del th
 
+    log("e2e done")
     # one step of the plain FP64 path on the same job, and the mixed path's error
-    if prec == "mixed" and not args.no_fp64 and not args.n_q:
+    if prec == "mixed" and not args.no_fp64 and not args.n_q and world == 1:
         jf = job.with_prec(rpa.PREC_FP64)
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
-        barrier(world)
         torch.cuda.synchronize()
         f0.record(ext)
         rf = ctx.energy(jf)
         f1.record(ext)
         torch.cuda.synchronize()
-        fms = allreduce_max(f0.elapsed_time(f1), world)
+        fms = f0.elapsed_time(f1)
         rel = np.abs(res["eps"] - rf["eps"]) / np.abs(rf["eps"])
-        line["fp64"] = {"value": world / (fms / 1e3), "unit": "jobs/s", "ms_per_step": fms, "steps": 1,
+        line["fp64"] = {"value": 1.0 / (fms / 1e3), "unit": "jobs/s", "ms_per_step": fms, "steps": 1,
                         "warmup": 0, "Ec": rf["Ec"], "abs_dEc_mixed_vs_fp64_Ha": abs(res["Ec"] - rf["Ec"]),
                         "max_rel_err_per_term": float(rel.max()), "median_rel_err_per_term": float(np.median(rel))}
         line["speedup_mixed_vs_fp64"] = jobs_per_s / line["fp64"]["value"]
         del jf
-
-    if rank == 0 and not args.no_cpu_baseline and world == 1:
-        s = cpu_oracle_sample(p)
-        v, job_s = oracle_jobs_per_s(p, s)
-        line["cpu_baseline"] = {"value": v, "unit": "jobs/s", "cores": s["threads"], "kind": "oracle",
-                                "sample": "one (q=0, w=0) term (chi0 + V^1/2 sandwich + Cholesky log-det, OpenMP "
-                                          "over rows) plus one V(q)^1/2 Jacobi; job time extrapolated as "
-                                          "n_q*T_vhalf + n_q*n_w*T_term", "extrapolated_job_s": job_s,
-                                "vhalf_s": s["vhalf_s"], "term_s": s["term_s"]}
     ctx.close()
+    del job, tens
+    torch.cuda.empty_cache()
+
+    log("fp64 step done")
+    # p50/p99 of a short served stream (the metric's latency part)
+    if args.lat_jobs > 0 and not args.n_q and world == 1:
+        try:
+            line["serving"] = served_latency(args, local, args.lat_jobs)
+        except Exception as ex:  # recorded, the line still prints
+            line["serving"] = {"error": repr(ex)[:300]}
+
+    log("served stream done")
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        smp = OracleSampler(p, name, n_vhalf=1)
+        for i in range(3):
+            smp.step(i)
+        line["cpu_baseline"] = smp.record()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -454,10 +580,6 @@ def run_ours(args):
 
 def rpa_mixed_available():
     return True
-
-
-def tensor_flops_of(problems, s=4):
-    return sum(rpa_mixed_tensor_flops(p, None, s) for p in problems)
 
 
 def run_batch(args):
@@ -490,6 +612,7 @@ def run_batch(args):
     ctx.profile(True)
     ctx.energy_batch(jobs)
     prof = ctx.profile_read()
+    cnt = ctx.profile_counters()
     ctx.profile(False)
     ext = torch.cuda.ExternalStream(ctx.stream_handle)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -516,12 +639,15 @@ def run_batch(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     if prec == "mixed":
-        tf = tensor_flops_of(probs, args.slices or 4)
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        ach = tf / (chi_ms / 1e3) / 1e12
+        ach = alg / (chi_ms / 1e3) / 1e12
+        ex_t = cnt["tensor_flops"] / (chi_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": None, "kernel": "chi0 tcgen05 sliced (persistent, all segments of a round)",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                "counting": "achieved = the instances' algorithmic FP64-equivalent chi0 flops (Hermitian lower "
+                            "triangle) per second of tensor-core launch time",
+                "executed_tensor_tflops": ex_t, "executed_frac": ex_t / peak,
                 "timing": "one profiled eager batch step: CUDA events around every tensor-core launch"}
     else:
         ach = alg / (chi_ms / 1e3) / 1e12
@@ -645,6 +771,14 @@ def device_inputs(p, device, seed):
 
 
 def run_serving(args):
+    world, rank, local = dist_setup()
+    line = serving_record(args, local)
+    line["n_gpus"] = world
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serving_record(args, local):
     """Poisson stream of RPA energy jobs through rpa_submit / rpa_wait: sizes
     drawn 50/30/20 from Gamma-only (N_aux=64), 2-D periodic (N_aux=512) and
     uneven-instance shapes with n x n x 1 k-grids, n ~ U{1..4}; inputs made
@@ -652,10 +786,9 @@ def run_serving(args):
     footprint under the cap.  The arrival rate is a fraction of the capacity
     measured first by running the whole stream in a closed loop."""
     os.environ.setdefault("PYTORCH_ALLOC_CONF", "expandable_segments:True")
-    import numpy as np
     import torch
 
-    world, rank, local = dist_setup()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     torch.cuda.set_device(local)
     import paper_2505_06021_gb300 as rpa
     from paper_2505_06021_gb300 import synth
@@ -777,8 +910,7 @@ def run_serving(args):
             "peak_running_jobs": peak["max_running"], "peak_admitted_gb": peak["max_bytes"] / 1e9,
             "largest_micro_batch": peak["max_batch"],
             "gpu_launches": launches, "clocks": clk, "roofline": None, "e2e": None}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def ao_flops(p):
@@ -934,7 +1066,7 @@ def run_ao(args):
 
 
 def cpu_oracle_sample_ao(p):
-    """cpu_oracle_sample for an AO-form problem: the term's coefficient blocks
+    """Oracle timing sample for an AO-form problem: the term's coefficient blocks
     are random stand-ins of the right shape (the term's cost does not depend
     on their values; the transform is timed separately)."""
     import numpy as np
@@ -952,20 +1084,6 @@ def cpu_oracle_sample_ao(p):
     oracle.term(p, 0, 0, Vh=Vh, C_blocks=C)
     t3 = time.perf_counter()
     return {"vhalf_s": t1 - t0, "term_s": t3 - t2, "threads": nthr}
-
-
-def rpa_mixed_tensor_flops(p, ctx, s=4):
-    """Tensor-core flops the split-precision chi0 executes for the whole job:
-    slice pairs x padded 128 x 64 (complex) / 128 x 128 (real) lower tiles x
-    padded K, 2 flops per multiply-add."""
-    npad = -(-p.n_aux // 128) * 128
-    nb = npad // 128
-    kt = p.n_k * p.n_ov
-    chunk = 1024 if p.is_complex else 2048
-    kr = (-(-kt // chunk) * chunk) * (2 if p.is_complex else 1)
-    tiles = nb * (nb + 1) if p.is_complex else nb * (nb + 1) // 2
-    pairs = s * (s + 1) // 2 + (1 if s == 2 else 0)
-    return float(p.n_q) * p.n_w * tiles * (kr // 16) * pairs * 2.0 * 128 * 128 * 16
 
 
 def main():

@@ -285,9 +285,18 @@ void *rpa_stream(rpa_ctx *ctx);
 #define RPA_K_CHI0_RED 7 /* split-K reduction of the tensor-core chi0 */
 #define RPA_K_AO2MO 8    /* AO -> MO transform of the fit coefficients (AO-form jobs) */
 #define RPA_K_PROJ 9     /* periodic projector (Jacobi sweeps, projection) */
-#define RPA_K_COUNT 10
+#define RPA_K_H2D 10     /* host -> device staging copies of RPA_MEM_HOST jobs (copy stream; no kernels) */
+#define RPA_K_COUNT 11
 rpa_status rpa_profile(rpa_ctx *ctx, int enable);
 rpa_status rpa_profile_read(rpa_ctx *ctx, double *ms, uint64_t *launches);
+
+/* Work counters since the last rpa_profile(ctx, 1): *tensor_flops receives
+ * the tensor-core flops issued by split-precision chi0 launches (slice pairs x
+ * padded 128-row tiles x padded K, 2 flops per multiply-add; counted process
+ * wide, so concurrent contexts add up), *h2d_bytes the bytes this context's
+ * rpa_energy calls copied host -> device for RPA_MEM_HOST jobs.  Either
+ * pointer may be NULL. */
+rpa_status rpa_profile_counters(rpa_ctx *ctx, uint64_t *tensor_flops, uint64_t *h2d_bytes);
 
 /* The log-det step (A4-A6) for callers that cannot allocate device memory at
  * call time - e.g. code embedded in a framework that owns all GPU memory
@@ -297,16 +306,23 @@ rpa_status rpa_profile_read(rpa_ctx *ctx, double *ms, uint64_t *launches);
  *
  * Same results as rpa_logdet for one q, without a context: V (device,
  * n_aux x n_aux, Hermitian positive definite) and chi (device, n_w x n_aux x
- * n_aux, as written by rpa_chi0) are inputs; out (DEVICE, n_w x 2) receives
- * (ln det(1 - Pi), Tr Pi) per frequency.  Scratch is a fixed static device
- * array of 7,078,144 bytes that every GPU loading the library holds until
- * exit; nothing is allocated.  n_aux > 384 is rejected with RPA_E_INVAL.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current): make that first call before any stream
- * capture.  All calls share the array, so calls whose work overlaps on the GPU
+ * n_aux, as written by rpa_chi0) are inputs; out (DEVICE, unlike rpa_logdet's
+ * host array, n_w x 2 doubles) receives (ln det(1 - Pi), Tr Pi) per
+ * frequency.  V, chi and out must be device (or managed) memory of the
+ * current device, aligned to their element size (16 bytes complex, 8 real),
+ * else RPA_E_INVAL; their sizes cannot be checked here, so the caller
+ * guarantees n_aux^2, n_w n_aux^2 and 2 n_w elements.  Scratch is a fixed
+ * static device array of 7,078,144 bytes that every GPU loading the library
+ * holds until exit; nothing is allocated.  n_aux > 384 is rejected with
+ * RPA_E_INVAL.  The first call on a device looks up the array's device
+ * address (once per device, with that device current) and keeps it for the
+ * life of the process, so do not reset the device (cudaDeviceReset) between
+ * calls.  All calls share the array, so calls whose work overlaps on the GPU
  * (other streams or threads on the same device) race; serialise them.  The
- * call synchronises `stream` and returns RPA_E_NOTPD / RPA_E_CUDA / RPA_E_INVAL
- * with a message in rpa_noalloc_last_error() (per host thread). */
+ * call copies a status word to the host and synchronises `stream`, so it
+ * cannot be made while that stream (or, in global capture mode, any stream)
+ * is capturing.  Returns RPA_E_NOTPD / RPA_E_CUDA / RPA_E_INVAL with a message
+ * in rpa_noalloc_last_error() (per host thread). */
 rpa_status rpa_logdet_noalloc(int is_complex, int n_aux, int n_w, const void *V, const void *chi, double *out,
                               void *stream);
 const char *rpa_noalloc_last_error(void);

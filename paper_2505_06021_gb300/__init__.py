@@ -28,11 +28,12 @@ EXPORTS = ("rpa_create", "rpa_destroy", "rpa_last_error", "rpa_job_validate", "r
            "rpa_ao2mo", "rpa_projector", "rpa_logdet", "rpa_energy", "rpa_energy_batch", "rpa_submit", "rpa_poll",
            "rpa_wait",
            "rpa_serving_stats", "rpa_serving_peak", "rpa_test_drop_copy", "rpa_kernel_launches", "rpa_stream",
-           "rpa_profile", "rpa_profile_read", "rpa_logdet_noalloc", "rpa_noalloc_last_error")
+           "rpa_profile", "rpa_profile_read", "rpa_profile_counters", "rpa_logdet_noalloc",
+           "rpa_noalloc_last_error")
 
 # kernel classes of rpa_profile_read
 KERNEL_CLASSES = ("dtab", "chi0", "vfactor", "sandwich", "logdet", "reduce", "slice", "chi0_reduce", "ao2mo",
-                  "proj")
+                  "proj", "h2d")
 
 
 class RpaError(RuntimeError):
@@ -103,6 +104,7 @@ def load_library(path: str = LIB_PATH):
         "rpa_stream": (P, [P]),
         "rpa_profile": (I, [P, I]),
         "rpa_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(u64)]),
+        "rpa_profile_counters": (I, [P, ctypes.POINTER(u64), ctypes.POINTER(u64)]),
         "rpa_logdet_noalloc": (I, [I, I, I, P, P, P, P]),
         "rpa_noalloc_last_error": (ctypes.c_char_p, []),
     }
@@ -322,10 +324,19 @@ def upload_problem(problem, device="cuda", qs: Optional[Sequence[int]] = None, p
 
 def logdet_noalloc(is_complex: bool, n_aux: int, n_w: int, V, chi, out, stream=None) -> None:
     """rpa_logdet_noalloc: the log-det step with the library's static scratch
-    (no device allocation).  V, chi and out are device tensors; out is
-    float64 [n_w, 2]."""
+    (no device allocation).  V, chi and out are contiguous device tensors of
+    the current device: V [n_aux, n_aux] and chi [n_w, n_aux, n_aux] in
+    complex128 (is_complex) or float64, out float64 with 2 n_w elements."""
     import torch
 
+    dt = torch.complex128 if is_complex else torch.float64
+    dev = torch.cuda.current_device()
+    for name, t, want, n in (("V", V, dt, n_aux * n_aux), ("chi", chi, dt, n_w * n_aux * n_aux),
+                             ("out", out, torch.float64, 2 * n_w)):
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError("%s must be a tensor on the current CUDA device %d" % (name, dev))
+        if t.dtype != want or not t.is_contiguous() or t.numel() < n:
+            raise ValueError("%s must be a contiguous %s tensor of at least %d elements" % (name, want, n))
     lib = load_library()
     st_ptr = (stream or torch.cuda.current_stream()).cuda_stream
     st = lib.rpa_logdet_noalloc(int(is_complex), int(n_aux), int(n_w), ctypes.c_void_p(V.data_ptr()),
@@ -386,6 +397,14 @@ class Context:
         n = (ctypes.c_uint64 * len(KERNEL_CLASSES))()
         self._check(self.lib.rpa_profile_read(self.h, ms, n))
         return {k: (ms[i], int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def profile_counters(self) -> Dict[str, int]:
+        """Tensor-core flops issued (process wide) and host -> device bytes
+        staged by this context since profiling was switched on."""
+        f = ctypes.c_uint64()
+        h = ctypes.c_uint64()
+        self._check(self.lib.rpa_profile_counters(self.h, ctypes.byref(f), ctypes.byref(h)))
+        return {"tensor_flops": int(f.value), "h2d_bytes": int(h.value)}
 
     def chi0(self, job: Job, q: int, out=None, stream=None):
         import torch

@@ -120,6 +120,24 @@ rpa_status wait_event(rpa_ctx* ctx, cudaEvent_t ev, double timeout_s) {
   }
 }
 
+int device_sm_count() {
+  static std::mutex mu;
+  static int cache[MAX_DEVICES] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= MAX_DEVICES) dev = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache[dev] <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      n = 148;
+    }
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
 // ------------------------------------------------------------- tracing ----
 
 cudaEvent_t Exec::take_event() {
@@ -613,11 +631,14 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
   auto issue_copy = [&](int bi) -> rpa_status {
     const int q0 = bi * qb, nq = std::min(qb, job->n_q - q0), slot = bi % 2;
     CK(cudaStreamWaitEvent(ex.cs, ex.freed[slot], 0));
+    prof_begin(ctx, &ex, ex.cs);
     for (int i = 0; i < nq * job->n_k; ++i)
       CK(cudaMemcpyAsync(b.stageC[slot] + i * cblk, job->C[(size_t)q0 * job->n_k + i], cblk, cudaMemcpyHostToDevice,
                          ex.cs));
     for (int i = 0; i < nq; ++i)
       CK(cudaMemcpyAsync(b.stageV[slot] + i * es * NN, job->V[q0 + i], es * NN, cudaMemcpyHostToDevice, ex.cs));
+    prof_end(ctx, &ex, ex.cs, RPA_K_H2D, 0);
+    ctx->h2d_bytes += (uint64_t)nq * job->n_k * cblk + (uint64_t)nq * es * NN;
     CK(cudaEventRecord(ex.ready[slot], ex.cs));
     return RPA_OK;
   };
@@ -763,6 +784,18 @@ rpa_status rpa_profile(rpa_ctx* ctx, int enable) {
     ctx->prof_ms[i] = 0.0;
     ctx->prof_n[i] = 0;
   }
+  if (ctx->prof) {
+    ctx->flops0 = mixed_tensor_flops_issued();
+    ctx->h2d_bytes = 0;
+  }
+  return RPA_OK;
+}
+
+rpa_status rpa_profile_counters(rpa_ctx* ctx, uint64_t* tensor_flops, uint64_t* h2d_bytes) {
+  if (!ctx) return RPA_E_INVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (tensor_flops) *tensor_flops = mixed_tensor_flops_issued() - ctx->flops0;
+  if (h2d_bytes) *h2d_bytes = ctx->h2d_bytes.load();
   return RPA_OK;
 }
 

@@ -20,6 +20,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "fp64_elem.cuh"
 #include "rpa_internal.h"
 
@@ -28,16 +30,7 @@ namespace {
 
 // ---------------------------------------------------------------- helpers --
 
-int num_sms_fp64() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
-  return n;
-}
+int num_sms_fp64() { return device_sm_count(); }
 
 // Lower-triangular tile index -> (I, J), J <= I.
 __device__ __forceinline__ void tri_index(int t, int& I, int& J) {
@@ -844,12 +837,19 @@ cudaError_t launch_chol_t(int N, int b0, int n_mat, double* mats, long bstride, 
   return cudaGetLastError();
 }
 
-// Clusters of CL CTAs of cholesky_kernel<C, CL> the device holds at once
-// (cudaOccupancyMaxActiveClusters), queried once; 0 if the query fails.
+// Clusters of CL CTAs of cholesky_kernel<C, CL> the current device holds at
+// once (cudaOccupancyMaxActiveClusters), queried once per device (under a
+// lock); 0 if the query fails.
 template <bool C, int CL>
 int chol_max_clusters() {
-  static int n = -1;
-  if (n < 0) {
+  static std::mutex mu;
+  static int cache[MAX_DEVICES];
+  static bool have[MAX_DEVICES] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 0 || dev >= MAX_DEVICES) dev = 0;
+  if (!have[dev]) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CL);
     cfg.blockDim = dim3(256);
@@ -865,9 +865,10 @@ int chol_max_clusters() {
       cudaGetLastError();
       m = 0;
     }
-    n = m;
+    cache[dev] = m;
+    have[dev] = true;
   }
-  return n;
+  return cache[dev];
 }
 
 // A cluster per matrix: CL_BIG CTAs each when all the launch's clusters fit

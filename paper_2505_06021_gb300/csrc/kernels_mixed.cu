@@ -275,16 +275,7 @@ __global__ void err_merge_kernel(const int* err, int* status) {
 
 // ------------------------------------------------------------ host side --
 
-int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
-  return n;
-}
+int num_sms() { return device_sm_count(); }
 
 // Workspace of one q: slices of A for up to G frequencies, slices of C,
 // exponents, fixed-point C, weights, split-K partials.
@@ -445,7 +436,17 @@ void launch_slice(int cplx, unsigned grid, cudaStream_t st, const SliceArgs& a) 
   }
 }
 
+// Tensor-core flops issued by every chi0_tc_kernel launch of this process
+// (slice pairs x padded tiles x padded K of each segment).
+std::atomic<unsigned long long> g_tc_flops{0};
+
 void launch_tc(int s, int grid, size_t smem, cudaStream_t st, const TcParams& tp) {
+  const unsigned long long pairs = (unsigned long long)(s * (s + 1) / 2 + (s == 2 ? 1 : 0));
+  unsigned long long f = 0;
+  for (int i = 0; i < tp.n_segs; ++i)
+    f += (unsigned long long)tp.seg[i].G * tp.seg[i].n_tiles * (unsigned long long)tp.seg[i].n_kb * pairs * 2ull *
+         128ull * 128ull * (unsigned long long)KB;
+  g_tc_flops += f;
   if (s == 2)
     chi0_tc_kernel<2><<<grid, THREADS, smem, st>>>(tp);
   else if (s == 3)
@@ -543,6 +544,8 @@ SliceArgs weighted_args(const QState& q, const MixedQ& m, int s, int w0, int G) 
 }  // namespace
 
 bool mixed_supported() { return true; }
+
+uint64_t mixed_tensor_flops_issued() { return g_tc_flops.load(); }
 
 // Test hook (rpa_test_drop_copy): the next tensor-core launch in this process
 // leaves the first K-block of one work item unloaded.

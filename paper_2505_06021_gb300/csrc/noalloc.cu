@@ -19,6 +19,7 @@
 // other's results.  Each call clears the status word before use; the matrices
 // are fully rewritten before they are read.
 #include <cuda_runtime.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -81,6 +82,40 @@ rpa_status rpa_logdet_noalloc(int is_complex, int n_aux, int n_w, const void* V,
     snprintf(d, sizeof d, "n_aux = %d exceeds the static scratch limit %d", n_aux, RPA_NOALLOC_MAX_NAUX);
     set_msg("too large", d);
     return RPA_E_INVAL;
+  }
+  // V, chi and out must be device (or managed) memory of the current device,
+  // aligned to their element size: a host pointer here would make the kernels
+  // read or write memory the GPU cannot (or should not) reach.
+  {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      cudaGetLastError();
+      set_msg("no current CUDA device", nullptr);
+      return RPA_E_CUDA;
+    }
+    const void* ptrs[3] = {V, chi, out};
+    const char* names[3] = {"V", "chi", "out"};
+    const size_t align[3] = {is_complex ? (size_t)16 : (size_t)8, is_complex ? (size_t)16 : (size_t)8, 8};
+    for (int i = 0; i < 3; ++i) {
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, ptrs[i]) != cudaSuccess) {
+        cudaGetLastError();
+        set_msg("pointer query failed", names[i]);
+        return RPA_E_INVAL;
+      }
+      if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev) {
+        char d[96];
+        snprintf(d, sizeof d, "%s is not device memory of the current device %d", names[i], dev);
+        set_msg("invalid pointer", d);
+        return RPA_E_INVAL;
+      }
+      if (reinterpret_cast<uintptr_t>(ptrs[i]) % align[i]) {
+        char d[96];
+        snprintf(d, sizeof d, "%s is not aligned to %zu bytes", names[i], align[i]);
+        set_msg("invalid pointer", d);
+        return RPA_E_INVAL;
+      }
+    }
   }
   char* base = static_cast<char*>(scratch_for_current_device());
   if (!base) {

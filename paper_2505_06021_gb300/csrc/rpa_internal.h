@@ -10,6 +10,12 @@
 
 namespace rpa {
 
+// Devices whose attributes the library caches (ordinals at or above fall back
+// to the entry of device 0).
+constexpr int MAX_DEVICES = 64;
+// Multiprocessor count of the current device, queried once per device.
+int device_sm_count();
+
 // Geometry of one q-batch handed to the kernels.  All pointers are device
 // memory.  Matrices are row-major, complex data interleaved (re, im).
 struct BatchGeom {
@@ -192,5 +198,7 @@ int mixed_test_drop_take();
 // Tensor-core flops the split-precision chi0 of one q executes (slice pairs
 // x padded tiles x padded K).
 uint64_t mixed_tensor_flops(const BatchGeom& g, int n_slices);
+// Tensor-core flops issued by all split-precision chi0 launches of this process so far.
+uint64_t mixed_tensor_flops_issued();
 
 }  // namespace rpa

@@ -86,6 +86,8 @@ struct rpa_ctx {
   bool prof = false;
   double prof_ms[RPA_K_COUNT] = {0};
   uint64_t prof_n[RPA_K_COUNT] = {0};
+  uint64_t flops0 = 0;                 // process-wide tensor flops at rpa_profile(ctx, 1)
+  std::atomic<uint64_t> h2d_bytes{0};  // host -> device staging bytes since then
 };
 
 namespace rpa {

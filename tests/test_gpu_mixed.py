@@ -173,13 +173,17 @@ def test_slab_dual_grid_full_size_subset(rpa):
     """The slab dual-grid workload at full size (N_aux=768, 32 occ, 480 virt,
     36 k per q, 16 freq) on two of its q-points, the first regular one and the
     first near-Gamma one (the dual grid's displaced point, whose V has the
-    scaled leading eigenvalue): split-precision chi0 against the FP64 path per
-    (q, w) and on their weighted energy, and the FP64 path against the oracle
-    on one sampled term."""
+    scaled leading eigenvalue), both paths in the benchmark's launch
+    configuration: every term of the sampled subset q x w in {0, 8, 15}
+    against the oracle, the FP64 path at 1e-10 and the split-precision path at
+    1e-8 relative per term; the split path against the FP64 path on all
+    terms of the two q and on their weighted energy."""
     from paper_2505_06021_gb300 import shard
 
     p = synth.config2()
-    qs = [0, 8]
+    ng = np.asarray(p.grid.near_gamma, bool)
+    qs = [int(np.argmin(ng)), int(np.argmax(ng))]
+    ws = [0, 8, 15]
     t = rpa.upload_problem(p, qs=qs)
     g = p.grid
     sel = [q * p.n_k + j for q in qs for j in range(p.n_k)]
@@ -197,8 +201,12 @@ def test_slab_dual_grid_full_size_subset(rpa):
     rel = np.abs(rm["eps"] - rf["eps"]) / np.abs(rf["eps"])
     assert rel.max() <= 1e-8, rel.max()
     assert abs(rm["Ec"] - rf["Ec"]) <= TOL_EC
-    ref = oracle.term(p, 8, 8)
-    assert abs(rf["eps"][1, 8] - ref["eps"]) <= 1e-10 * abs(ref["eps"])
+    ref = oracle.energy(p, qs=qs, ws=ws)
+    for i, q in enumerate(qs):
+        for w in ws:
+            for key in ("eps", "lndet", "trPi"):
+                assert abs(rf[key][i, w] - ref[key][q, w]) <= 1e-10 * abs(ref[key][q, w]), (q, w, key)
+            assert abs(rm["eps"][i, w] - ref["eps"][q, w]) <= 1e-8 * abs(ref["eps"][q, w]), (q, w)
     assert shard.quadrature(rf["eps"], g.w_q[qs], p.zeta_w) == pytest.approx(rf["Ec"], rel=1e-12)
 
 

@@ -208,7 +208,7 @@ def test_kernel_launch_count(rpa, ctx):
 def test_periodic_config_full_size_sampled(rpa):
     """The 2-D periodic workload at full size (N_aux=512, 32 occ, 224 virt,
     16 k x 16 q, 20 freq) through the same launch configuration as the
-    benchmark; the oracle recomputes sampled (q, w) terms one by one."""
+    benchmark; the oracle recomputes the six sampled (q, w) terms."""
     p = synth.config1()
     t = rpa.upload_problem(p)
     job = rpa.job_from_problem(p, t)
@@ -216,11 +216,13 @@ def test_periodic_config_full_size_sampled(rpa):
         r = c.energy(job)
     del t
     torch.cuda.empty_cache()
-    for q, w in ((0, 0), (5, 19)):
-        ref = oracle.term(p, q, w)
-        assert abs(r["eps"][q, w] - ref["eps"]) <= TOL_TERM * abs(ref["eps"]), (q, w)
-        assert abs(r["lndet"][q, w] - ref["lndet"]) <= TOL_TERM * abs(ref["lndet"])
-        assert abs(r["trPi"][q, w] - ref["trPi"]) <= TOL_TERM * abs(ref["trPi"])
+    # the sampled subset: q in {Gamma, 5} x w in {0, 10, 19}
+    qs, ws = [0, 5], [0, 10, 19]
+    ref = oracle.energy(p, qs=qs, ws=ws)
+    for q in qs:
+        for w in ws:
+            for key in ("eps", "lndet", "trPi"):
+                assert abs(r[key][q, w] - ref[key][q, w]) <= TOL_TERM * abs(ref[key][q, w]), (q, w, key)
     # properties that hold at any size
     assert r["Ec"] < 0 and np.all(r["eps"] < 0)
     assert np.all(r["lndet"] > 0) and np.all(r["trPi"] < 0)

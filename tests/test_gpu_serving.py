@@ -5,18 +5,22 @@ Each result must be the same alone and in the mix: FP64 jobs bit for bit (the
 same kernels run on the job's own lane, whatever else shares the device),
 mixed-precision jobs within 1e-9 Ha (far inside the 1 microhartree bar; the
 split-K plan of a q may differ between the synchronous and the lane
-workspace).  Jobs submitted together must overlap on the device, admission
+workspace).  Every served result is also checked against the CPU oracle:
+FP64 jobs at 1e-10 relative, mixed jobs within 1 microhartree.  Jobs submitted together must overlap on the device, admission
 must respect the HBM cap, and the latency statistics must be filled in.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2505_06021_gb300 import synth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL_MIX = 1e-9  # Hartree
+TOL_MIX = 1e-9  # Hartree, served vs alone
+TOL_ORACLE_FP64 = 1e-10  # relative
+TOL_ORACLE_MIX = 1e-6  # Hartree
 
 
 @pytest.fixture(scope="module")
@@ -30,16 +34,27 @@ def rpa():
     return m
 
 
-def _jobs(rpa, n=10, seed=91):
+def _jobs(rpa, n=10, seed=91, problems=None):
     out = []
     for i, (_, p) in enumerate(synth.serving_stream(n_jobs=n, rate_per_s=1.0, seed=seed, scale=0.1)):
         prec = rpa.PREC_FP64 if i % 4 == 3 else rpa.PREC_MIXED
         out.append(rpa.job_from_problem(p, rpa.upload_problem(p), prec=prec))
+        if problems is not None:
+            problems.append(p)
     return out
 
 
+def _check_oracle(rpa, job, p, Ec):
+    ref = oracle.energy(p)["Ec"]
+    if job.s.prec == rpa.PREC_FP64:
+        assert abs(Ec - ref) <= TOL_ORACLE_FP64 * abs(ref), (p.name, Ec, ref)
+    else:
+        assert abs(Ec - ref) <= TOL_ORACLE_MIX, (p.name, Ec, ref)
+
+
 def test_served_results_equal_alone(rpa):
-    jobs = _jobs(rpa)
+    probs = []
+    jobs = _jobs(rpa, problems=probs)
     with rpa.Context(0) as c:
         alone = [c.energy(j)["Ec"] for j in jobs]
     with rpa.Context(0, max_inflight=8) as c:
@@ -47,11 +62,12 @@ def test_served_results_equal_alone(rpa):
         served = [c.wait(t, 300.0)[0] for t in tickets]
         st = c.serving_stats()
         peak = c.serving_peak()
-    for j, a, s in zip(jobs, alone, served):
+    for j, a, s, p in zip(jobs, alone, served, probs):
         if j.s.prec == rpa.PREC_FP64:
             assert s == a
         else:
             assert abs(s - a) <= TOL_MIX, (s, a)
+        _check_oracle(rpa, j, p, s)
     assert st["jobs_done"] == len(jobs)
     assert 0.0 < st["lat_p50_s"] <= st["lat_p99_s"]
     assert peak["max_running"] >= 2  # submitted together: they overlap on the device
