@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--prec", default="auto", choices=["auto", "fp64", "mixed"])
     ap.add_argument("--slices", type=int, default=0,
                     help="BF16 digit slices of the mixed path (2-4; 0: library default)")
+    ap.add_argument("--chi0-freq", type=int, default=0, choices=[0, 1, 2],
+                    help="mixed chi0: 0 frequency-batched when it saves work (library default), 1 every frequency "
+                         "contracted, 2 always frequency-batched")
     ap.add_argument("--cap-gb", type=float, default=0.0,
                     help="periodic2d/slab: the context's HBM cap (bounds the workspace; profiling small cases)")
     ap.add_argument("--n-q", type=int, default=0, help="profiling only: restrict the job to its first n q-points")
@@ -419,7 +422,7 @@ def run_ours(args):
     t_gen = time.perf_counter() - t_gen
     log("inputs ready (%.1f s)" % t_gen)
     job = rpa.job_from_problem(p, tens, prec=pc)
-    ctx = rpa.Context(local, n_slices=args.slices, hbm_cap_bytes=int(args.cap_gb * 1e9))
+    ctx = rpa.Context(local, n_slices=args.slices, hbm_cap_bytes=int(args.cap_gb * 1e9), chi0_freq=args.chi0_freq)
     for _ in range(args.warmup):
         ctx.energy(job)
     log("warm-up done")
@@ -486,9 +489,12 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "bf16-slices->f64",
             "data": "synthetic (seeded, shapes of the paper's periodic workloads; no public data)",
             "config": dict(config_of(p, prec, args.n_q, name),
-                           **({"chi0_slices": args.slices or 4} if prec == "mixed" else {})),
+                           **({"chi0_slices": args.slices or 4, "chi0_freq": ["auto", "per-frequency",
+                                                                               "frequency-batched"][args.chi0_freq]}
+                              if prec == "mixed" else {})),
             "chi0_tflops": chi0_flops_job * world * args.steps / (ms_max / 1e3) / 1e12,
             "chi0_tflops_kernel": achieved, "Ec": res["Ec"], "gpu_launches": launches,
+            "chi0_freq_plan": plan_of(rpa, p, args.chi0_freq) if prec == "mixed" else None,
             "latency_s": {"p50": float(np.percentile(step_ms, 50)) / 1e3,
                           "p99": float(np.percentile(step_ms, 99)) / 1e3,
                           "what": "per-job latency of the timed jobs (one job at a time, device-resident inputs, "
@@ -710,6 +716,24 @@ def run_batch(args):
 
 
 _V_CACHE = {}  # V(q) depends only on the shape here: shared by jobs of one shape
+
+
+def plan_of(rpa, p, mode):
+    """The frequency-batched chi0 plan of a problem (rpa_freq_plan on a host
+    descriptor with placeholder C/V pointers: the plan reads only the shapes,
+    pairs, frequencies and band energies)."""
+    import numpy as np
+    import torch
+
+    ph = torch.empty(1)
+    t = {"C": [ph] * (p.n_q * p.n_k), "V": [ph] * p.n_q,
+         "eps_occ": torch.from_numpy(np.ascontiguousarray(p.eps_occ, np.float64)),
+         "eps_virt": torch.from_numpy(np.ascontiguousarray(p.eps_virt, np.float64))}
+    pl = rpa.job_from_problem(p, t, prec=rpa.PREC_MIXED, mem=rpa.MEM_HOST).freq_plan(2 if mode == 2 else 0)
+    if mode == 1 or pl["n_bins"] == 0:
+        return {"used": False}
+    return {"used": True, "n_bins": pl["n_bins"], "rank": [int(x) for x in pl["rank"]],
+            "max_residual": float(pl["err"].max()), "work_ratio": pl["work_ratio"]}
 
 
 def footprint_of(rpa, p, prec):

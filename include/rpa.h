@@ -79,6 +79,9 @@ typedef struct {
   int n_slices;         /* BF16 slices per operand in RPA_PREC_MIXED (2..4; 0 = 4) */
   double timeout_s;     /* limit of every bounded wait (0 = 60 s) */
   int max_inflight;     /* serving: jobs admitted at once (0 = 64) */
+  int chi0_freq;        /* RPA_PREC_MIXED chi0 of rpa_energy / rpa_chi0: 0 = frequency-batched when its
+                           plan saves work (rpa_freq_plan), 1 = every frequency contracted, 2 = always
+                           frequency-batched */
 } rpa_config;
 
 /* Atomic-orbital form of a job's fit coefficients (Sec. 2.2, PADF in
@@ -162,6 +165,27 @@ const char *rpa_last_error(const rpa_ctx *ctx);
 /* Host-only check of a job description (no device access; usable without a
  * GPU).  Writes a message into msg (if msg_len > 0) on failure. */
 rpa_status rpa_job_validate(const rpa_job *job, char *msg, size_t msg_len);
+
+/* Host-only: the frequency-batched form of the split-precision chi0 for this
+ * job (job->mem must be RPA_MEM_HOST so that the band energies are readable
+ * here; usable without a GPU).  chi0(w) of Sec. 2.2 weighs transition t by
+ * d_t(w) = -4 D_t/(D_t^2 + w^2), a smooth function of its energy D_t, and
+ * Algorithm 1 contracts once per frequency.  The library instead splits the
+ * transitions of every q into n_bins windows of D (geometric, interior edges
+ * edges[0..n_bins-2] ascending, D in bin b when exactly b edges are <= D) and
+ * represents, inside bin b,
+ *     d(D, omega_w) = sum_{r < rank[b]} coef[b][r][w] d(D, omega_{skel[b][r]})
+ * (an interpolative decomposition over rank[b] of the job's own frequency
+ * nodes, residual err[b] <= 1e-10 of the bin's largest |d(., omega_w)| on a
+ * dense check grid), so chi0 needs rank[b] contractions over bin b instead of
+ * n_w: chi0(w) = sum_b sum_r coef[b][r][w] X_{b,r}, X_{b,r} the contraction of
+ * bin b's transitions at omega_{skel[b][r]}.  mode: 0 automatic (n_bins = 0
+ * when the plan saves no work), 2 always.  Outputs (any may be NULL):
+ * edges [16], rank [16], err [16], skel [16][n_w] (-1 past rank[b]), coef
+ * [16][n_w][n_w] (row r of bin b), *work_ratio = modelled sum_b rank[b] K_b /
+ * (n_w K).  RPA_E_INVAL for an invalid job or mem != RPA_MEM_HOST. */
+rpa_status rpa_freq_plan(const rpa_job *job, int mode, int *n_bins, double *edges, int *rank, int *skel,
+                         double *coef, double *err, double *work_ratio);
 
 /* Host-only: device bytes the job occupies while it runs (its inputs when
  * mem == RPA_MEM_DEVICE plus the workspace of one q-batch) - the admission

@@ -24,7 +24,8 @@ MEM_DEVICE, MEM_HOST = 0, 1
 STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "NOMEM", 3: "CUDA", 4: "NOTPD", 5: "TIMEOUT", 6: "BUSY", 7: "NOTREADY"}
 
 # Entry points declared in include/rpa.h
-EXPORTS = ("rpa_create", "rpa_destroy", "rpa_last_error", "rpa_job_validate", "rpa_job_footprint", "rpa_chi0",
+EXPORTS = ("rpa_create", "rpa_destroy", "rpa_last_error", "rpa_job_validate", "rpa_job_footprint", "rpa_freq_plan",
+           "rpa_chi0",
            "rpa_ao2mo", "rpa_projector", "rpa_logdet", "rpa_energy", "rpa_energy_batch", "rpa_submit", "rpa_poll",
            "rpa_wait",
            "rpa_serving_stats", "rpa_serving_peak", "rpa_test_drop_copy", "rpa_kernel_launches", "rpa_stream",
@@ -44,7 +45,7 @@ class RpaError(RuntimeError):
 
 class rpa_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("hbm_cap_bytes", ctypes.c_size_t), ("n_slices", ctypes.c_int),
-                ("timeout_s", ctypes.c_double), ("max_inflight", ctypes.c_int)]
+                ("timeout_s", ctypes.c_double), ("max_inflight", ctypes.c_int), ("chi0_freq", ctypes.c_int)]
 
 
 class rpa_ao(ctypes.Structure):
@@ -88,6 +89,8 @@ def load_library(path: str = LIB_PATH):
         "rpa_last_error": (ctypes.c_char_p, [P]),
         "rpa_job_validate": (I, [J, ctypes.c_char_p, S]),
         "rpa_job_footprint": (I, [J, ctypes.POINTER(S)]),
+        "rpa_freq_plan": (I, [J, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(I),
+                              ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D)]),
         "rpa_chi0": (I, [P, J, I, P, P]),
         "rpa_ao2mo": (I, [P, J, I, P, P]),
         "rpa_projector": (I, [P, J, ctypes.POINTER(P), ctypes.POINTER(D), ctypes.POINTER(I), P]),
@@ -211,6 +214,28 @@ class Job:
         buf = ctypes.create_string_buffer(512)
         st = load_library().rpa_job_validate(ctypes.byref(self.s), buf, 512)
         return st, buf.value.decode()
+
+    def freq_plan(self, mode: int = 0) -> Dict[str, object]:
+        """rpa_freq_plan (host-only; needs a MEM_HOST job): the frequency
+        factorisation of the split-precision chi0."""
+        nb = ctypes.c_int()
+        nw = self.s.n_w
+        edges = np.zeros(16)
+        rank = np.zeros(16, np.int32)
+        skel = np.zeros(16 * nw, np.int32)
+        coef = np.zeros(16 * nw * nw)
+        err = np.zeros(16)
+        wr = ctypes.c_double()
+        ip = ctypes.POINTER(ctypes.c_int)
+        st = load_library().rpa_freq_plan(ctypes.byref(self.s), int(mode), ctypes.byref(nb), _dptr(edges),
+                                          rank.ctypes.data_as(ip), skel.ctypes.data_as(ip), _dptr(coef), _dptr(err),
+                                          ctypes.byref(wr))
+        if st:
+            raise RpaError(st, "rpa_freq_plan failed")
+        n = int(nb.value)
+        return {"n_bins": n, "edges": edges[:max(0, n - 1)].copy(), "rank": rank[:n].copy(),
+                "skel": skel.reshape(16, nw)[:n].copy(), "coef": coef.reshape(16, nw, nw)[:n].copy(),
+                "err": err[:n].copy(), "work_ratio": float(wr.value)}
 
     def footprint(self) -> int:
         out = ctypes.c_size_t()
@@ -350,9 +375,9 @@ class Context:
     """An ``rpa_ctx`` on one device."""
 
     def __init__(self, device: int = 0, hbm_cap_bytes: int = 0, n_slices: int = 0, timeout_s: float = 0.0,
-                 max_inflight: int = 0):
+                 max_inflight: int = 0, chi0_freq: int = 0):
         self.lib = load_library()
-        cfg = rpa_config(device, hbm_cap_bytes, n_slices, timeout_s, max_inflight)
+        cfg = rpa_config(device, hbm_cap_bytes, n_slices, timeout_s, max_inflight, chi0_freq)
         h = ctypes.c_void_p()
         st = self.lib.rpa_create(ctypes.byref(cfg), ctypes.byref(h))
         if st:

@@ -79,6 +79,7 @@ void Exec::destroy() {
   s = cs = nullptr;
   done = nullptr;
   hstage.release();
+  hbin.release();
   hres.release();
 }
 
@@ -243,7 +244,7 @@ static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 // Workspace cap of the synchronous calls (the serving lanes use a smaller one).
 size_t sync_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap, (size_t)64 << 30); }
 
-Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool mixed_ws, int qt) {
+Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool mixed_ws, int qt, const BinJob* bj) {
   Layout L{};
   if (qt < qb) qt = qb;
   const size_t es = j->is_complex ? 16 : 8;
@@ -264,17 +265,33 @@ Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool m
     L.stageV = al(es * NN * qb);
     L.eps = al(sizeof(double) * (size_t)j->n_kpts * (j->n_occ + j->n_virt));
   }
+  const bool binned = bj && bj->on && j->prec == RPA_PREC_MIXED;
+  if (binned) L.dtab = 0;  // the frequency-batched chi0 forms its own weights
   if (j->prec == RPA_PREC_MIXED) {
     L.Vc = al(es * NN * qt);  // the inverse-form tail keeps a copy of V(q)
     if (mixed_ws) {
       BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, (int)nov, j->n_k, j->n_w, 1};
       L.slice_cap = ws_cap / 2;
-      L.mixed = al(mixed_workspace_bytes(g, n_slices, L.slice_cap));
+      L.mixed = binned ? al(binned_workspace_bytes(g, bj->plan, bj->Kt_max, bj->np_max, n_slices, L.slice_cap,
+                                                   false))
+                       : al(mixed_workspace_bytes(g, n_slices, L.slice_cap));
     }
   }
   L.ao = al(ao_region_bytes(j, qb));
   L.total = L.meta + L.dtab + L.chi + L.T + L.L + L.Vc + 2 * (L.stageC + L.stageV) + L.eps + L.mixed + L.ao;
-  if (L.mixed && qb >= 2) {
+  if (L.mixed && qb >= 2 && binned) {
+    // two alternating regions (the next q's weighted planes written during the
+    // current q's tensor-core launch) when all skeletons fit in one round
+    BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, (int)nov, j->n_k, j->n_w, 1};
+    if (binned_one_round(g, bj->plan, bj->Kt_max, bj->np_max, n_slices, L.slice_cap)) {
+      const size_t m2 =
+          al(binned_workspace_bytes(g, bj->plan, bj->Kt_max, bj->np_max, n_slices, L.slice_cap, true));
+      if (m2 > L.mixed && L.total - L.mixed + m2 <= ws_cap) {
+        L.total += m2 - L.mixed;
+        L.mixed = m2;
+      }
+    }
+  } else if (L.mixed && qb >= 2) {
     // two alternating regions (the next q's operand written during the
     // current q's tensor-core launch) when they fit under the cap
     BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, (int)nov, j->n_k, j->n_w, 1};
@@ -287,26 +304,27 @@ Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool m
   return L;
 }
 
-int choose_qb(const rpa_job* j, int n_slices, size_t cap) {
+int choose_qb(const rpa_job* j, int n_slices, size_t cap, const BinJob* bj) {
   int qb = j->n_q;
   if (j->ao) {  // AO form: the MO-basis coefficients of a few q at a time (<= 4 GB)
     const size_t per_q = (j->is_complex ? 16 : 8) * (size_t)j->n_aux * j->n_occ * j->n_virt * j->n_k;
     qb = (int)std::max<size_t>(1, std::min<size_t>((size_t)j->n_q, ((size_t)4 << 30) / std::max<size_t>(per_q, 1)));
   }
-  while (qb > 1 && plan_layout(j, qb, n_slices, cap, true).total > cap) qb = (qb + 1) / 2;
+  while (qb > 1 && plan_layout(j, qb, n_slices, cap, true, 0, bj).total > cap) qb = (qb + 1) / 2;
   // host-resident inputs: at least four q-batches, so that the copies of one
   // batch overlap the compute of the previous one
   if (j->mem == RPA_MEM_HOST) qb = std::min(qb, std::max(1, (j->n_q + 3) / 4));
   return qb;
 }
 
-int choose_qt(const rpa_job* j, int qb, int n_slices, size_t cap) {
+int choose_qt(const rpa_job* j, int qb, int n_slices, size_t cap, const BinJob* bj) {
   // host-staged and AO-form jobs compute chi0 per staging batch; their tail
   // (V factor, log-det) runs over as many q as fit, so that its Cholesky
   // launches fill the GPU
   if (j->mem != RPA_MEM_HOST && !j->ao) return qb;
   int m = (j->n_q + qb - 1) / qb;
-  while (m > 1 && plan_layout(j, qb, n_slices, cap, true, std::min(j->n_q, m * qb)).total > cap) m = (m + 1) / 2;
+  while (m > 1 && plan_layout(j, qb, n_slices, cap, true, std::min(j->n_q, m * qb), bj).total > cap)
+    m = (m + 1) / 2;
   return std::min(j->n_q, m * qb);
 }
 
@@ -522,11 +540,42 @@ rpa_status stage_tail(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, 
 // chi0 of q in [q0, q0+nq) into chi[0..nq) (device tables indexed by
 // q*n_k + j; the d table of the batch is built first).
 static rpa_status run_chi(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, int q0, int nq,
-                          const double* eps_occ, const double* eps_virt, cudaStream_t s, double* chi, int n_slices) {
+                          const double* eps_occ, const double* eps_virt, cudaStream_t s, double* chi, int n_slices,
+                          const BinJob* bj = nullptr) {
   const int nk = j->n_k;
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
   BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, j->n_occ * j->n_virt, nk, j->n_w, nq};
+  if (j->prec == RPA_PREC_MIXED && bj && bj->on) {
+    struct HookCtx {
+      rpa_ctx* ctx;
+      Exec* ex;
+    } hc{ctx, pex};
+    LaunchHook hook{&hc,
+                    [](void* u, cudaStream_t st) {
+                      HookCtx* h = (HookCtx*)u;
+                      prof_begin(h->ctx, h->ex, st);
+                    },
+                    [](void* u, cudaStream_t st, int cls, int n) {
+                      HookCtx* h = (HookCtx*)u;
+                      prof_end(h->ctx, h->ex, st, cls, n);
+                    }};
+    BatchGeom g1 = g;
+    g1.n_qb = 1;
+    std::vector<MixedBinQ> mq(nq);
+    for (int qi = 0; qi < nq; ++qi) {
+      const int q = q0 + qi;
+      mq[qi] = MixedBinQ{g1, (const double* const*)(b.Cptrs + (size_t)q * nk),
+                         chi + (size_t)qi * j->n_w * NN * (es / 8),
+                         &bj->qh[q], eps_occ, eps_virt, b.kidx + (size_t)q * nk, b.kqidx + (size_t)q * nk,
+                         j->zeta_k, b.status};
+    }
+    uint64_t nl = 0;
+    CK(launch_chi0_binned(mq.data(), nq, bj->plan, n_slices, b.mixed, b.mixed_bytes, b.slice_cap, b.status, &nl, s,
+                          pex ? &hook : nullptr));
+    ctx->launches += nl;
+    return RPA_OK;
+  }
   if (rpa_status st = stage_dtab(ctx, pex, j, b, q0, nq, eps_occ, eps_virt, s)) return st;
   if (j->prec == RPA_PREC_MIXED) {
     struct HookCtx {
@@ -565,6 +614,10 @@ static rpa_status run_chi(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs&
 rpa_status decode_status(rpa_ctx* ctx, int st, int n_w) {
   if (st == 0) return RPA_OK;
   const int code = st - 1;
+  if (code == STATUS_CODE_PLAN) {
+    ctx_set_error(ctx, "frequency-batched chi0: the device's transition counts disagree with the host plan");
+    return RPA_E_CUDA;
+  }
   if (code >= (1 << 30)) {
     ctx_set_error(ctx, "tensor-core chi0 kernel gave up waiting (code %d)", code - (1 << 30));
     return RPA_E_TIMEOUT;
@@ -576,7 +629,55 @@ rpa_status decode_status(rpa_ctx* ctx, int st, int n_w) {
   return RPA_E_NOTPD;
 }
 
-rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_cap) {
+rpa_status bin_job_build(rpa_ctx* ctx, Exec& ex, const rpa_job* j, BinJob& bj) {
+  bj = BinJob{};
+  if (j->prec != RPA_PREC_MIXED || ctx->chi0_freq == 1) return RPA_OK;
+  const size_t no = (size_t)j->n_kpts * j->n_occ, nv = (size_t)j->n_kpts * j->n_virt;
+  std::vector<double> eo, ev;
+  const double* peo = j->eps_occ;
+  const double* pev = j->eps_virt;
+  if (j->mem == RPA_MEM_DEVICE) {
+    eo.resize(no);
+    ev.resize(nv);
+    CK(cudaMemcpyAsync(eo.data(), j->eps_occ, sizeof(double) * no, cudaMemcpyDeviceToHost, ex.s));
+    CK(cudaMemcpyAsync(ev.data(), j->eps_virt, sizeof(double) * nv, cudaMemcpyDeviceToHost, ex.s));
+    CK(cudaStreamSynchronize(ex.s));
+    peo = eo.data();
+    pev = ev.data();
+  }
+  if (!freq_plan_build(j, peo, pev, ctx->chi0_freq, &bj.plan)) return RPA_OK;
+  const std::vector<double> evs = freq_sorted_virt(j, pev);
+  std::vector<std::vector<int>> img(j->n_q);
+  bj.qh.resize(j->n_q);
+  size_t n_i = 0;
+  for (int q = 0; q < j->n_q; ++q) {
+    freq_bin_q(j, bj.plan, q, peo, evs.data(), bj.qh[q], img[q]);
+    n_i += (img[q].size() + 15) & ~(size_t)15;
+    bj.Kt_max = std::max(bj.Kt_max, bj.qh[q].Kt);
+    bj.np_max = std::max(bj.np_max, bj.qh[q].n_parts);
+  }
+  std::vector<double> md;
+  freq_meta_d(j, bj.plan, md);
+  if (!ex.hbin.reserve(sizeof(int) * n_i + sizeof(double) * md.size() + 64)) {
+    ctx_set_error(ctx, "cannot allocate pinned host staging");
+    return RPA_E_NOMEM;
+  }
+  double* hd = (double*)ex.hbin.ptr;
+  memcpy(hd, md.data(), sizeof(double) * md.size());
+  int* hi = (int*)(hd + md.size());
+  for (int q = 0; q < j->n_q; ++q) {
+    memcpy(hi, img[q].data(), sizeof(int) * img[q].size());
+    bj.qh[q].meta_i = hi;
+    bj.qh[q].n_meta_i = img[q].size();
+    bj.qh[q].meta_d = hd;
+    bj.qh[q].n_meta_d = md.size();
+    hi += (img[q].size() + 15) & ~(size_t)15;
+  }
+  bj.on = true;
+  return RPA_OK;
+}
+
+rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_cap, bool allow_bin) {
   char msg[512];
   if (validate_job(job, msg, sizeof msg)) {
     ctx_set_error(ctx, "%s", msg);
@@ -588,9 +689,12 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
   }
   CK(cudaSetDevice(ctx->device));
   cudaStream_t s = ex.s;
-  const int qb = choose_qb(job, ctx->n_slices, ws_cap);
-  const int qt = choose_qt(job, qb, ctx->n_slices, ws_cap);
-  Layout L = plan_layout(job, qb, ctx->n_slices, ws_cap, true, qt);
+  BinJob bj;
+  if (allow_bin)
+    if (rpa_status stb = bin_job_build(ctx, ex, job, bj)) return stb;
+  const int qb = choose_qb(job, ctx->n_slices, ws_cap, &bj);
+  const int qt = choose_qt(job, qb, ctx->n_slices, ws_cap, &bj);
+  Layout L = plan_layout(job, qb, ctx->n_slices, ws_cap, true, qt, &bj);
   if (!ex.ensure_ws(L.total)) {
     ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", L.total);
     return RPA_E_NOMEM;
@@ -662,7 +766,7 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
                                                b.ao + aop.off_c + (size_t)qi * job->n_k * cblk, s))
         return st1;
     if (rpa_status st = run_chi(ctx, &ex, job, b, q0, nq, eo, ev, s, b.chi + (size_t)lo * job->n_w * NN * (es / 8),
-                                ctx->n_slices))
+                                ctx->n_slices, &bj))
       return st;
     if (rpa_status st = vside_copy(ctx, job, b, lo, nq, vp.data() + q0, s)) return st;
     // the tail once its batch of q is complete (chi, V of every q in place)
@@ -735,6 +839,12 @@ rpa_status rpa_create(const rpa_config* cfg, rpa_ctx** out) {
   ctx->cap = c.hbm_cap_bytes ? c.hbm_cap_bytes : (size_t)120 << 30;
   ctx->timeout_s = c.timeout_s > 0 ? c.timeout_s : 60.0;
   ctx->max_inflight = c.max_inflight > 0 ? c.max_inflight : 64;
+  if (c.chi0_freq < 0 || c.chi0_freq > 2) {
+    g_create_error = "chi0_freq must be 0, 1 or 2";
+    delete ctx;
+    return RPA_E_INVAL;
+  }
+  ctx->chi0_freq = c.chi0_freq;
   if (cudaSetDevice(c.device) != cudaSuccess || !ctx->ex.init()) {
     g_create_error = std::string("stream/event creation failed: ") + cudaGetErrorString(cudaGetLastError());
     ctx->ex.destroy();
@@ -832,7 +942,9 @@ rpa_status rpa_chi0(rpa_ctx* ctx, const rpa_job* job, int q, void* chi_out, void
   CK(cudaSetDevice(ctx->device));
   Exec& ex = ctx->ex;
   cudaStream_t s = (cudaStream_t)stream;
-  Layout L = plan_layout(job, 1, ctx->n_slices, sync_ws_cap(ctx), true);
+  BinJob bj;
+  if (rpa_status stb = bin_job_build(ctx, ex, job, bj)) return stb;
+  Layout L = plan_layout(job, 1, ctx->n_slices, sync_ws_cap(ctx), true, 0, &bj);
   if (!ex.ensure_ws(L.total)) {
     ctx_set_error(ctx, "cannot allocate %zu bytes of workspace", L.total);
     return RPA_E_NOMEM;
@@ -855,13 +967,16 @@ rpa_status rpa_chi0(rpa_ctx* ctx, const rpa_job* job, int q, void* chi_out, void
     if (rpa_status st1 = ao_enqueue_assemble(ctx, &ex, job, aop, b.ao, q, b.ao + aop.off_c, s)) return st1;
   }
   if (rpa_status st = run_chi(ctx, &ex, job, b, q, 1, job->eps_occ, job->eps_virt, s, (double*)chi_out,
-                              ctx->n_slices))
+                              ctx->n_slices, &bj))
     return st;
   // the d table in the workspace is reused by the next call on this context
   CK(cudaEventRecord(ex.done, s));
   rpa_status wst = wait_event(ctx, ex.done, ctx->timeout_s + 600.0);
   prof_collect(ctx, &ex);
-  return wst;
+  if (wst) return wst;
+  int stw = 0;
+  CK(cudaMemcpy(&stw, b.status, sizeof(int), cudaMemcpyDeviceToHost));
+  return decode_status(ctx, stw, job->n_w);
 }
 
 rpa_status rpa_ao2mo(rpa_ctx* ctx, const rpa_job* job, int q, void* C_out, void* stream) {
@@ -963,7 +1078,7 @@ rpa_status rpa_test_drop_copy(rpa_ctx* ctx, int item) {
 rpa_status rpa_energy(rpa_ctx* ctx, const rpa_job* job, double* Ec, double* eps_qw, double* parts) {
   if (!ctx || !Ec) return RPA_E_INVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
-  if (rpa_status st = rpa::energy_enqueue(ctx, ctx->ex, job, rpa::sync_ws_cap(ctx))) return st;
+  if (rpa_status st = rpa::energy_enqueue(ctx, ctx->ex, job, rpa::sync_ws_cap(ctx), true)) return st;
   // bounded wait: scaled with the job's chi0 work at a conservative 0.2 TFLOP/s
   const double work = 8.0 * job->n_aux * (double)job->n_aux * job->n_occ * job->n_virt * job->n_q * job->n_k *
                       job->n_w / (job->is_complex ? 1.0 : 4.0);

@@ -1,0 +1,675 @@
+// Frequency-batched split-precision chi0 (device side and launcher).
+//
+// For one q the plan (freq_plan.cu) splits the transitions t = (k-pair, i, a)
+// into bins of their energy D_t and gives each bin b a few skeleton
+// frequencies; chi0(w) = sum_b sum_r coef[b][r][w] X_{b,r} with X_{b,r} the
+// weighted contraction of bin b's transitions at skeleton r.  On the device:
+//   1. ecrow_kernel     row maxima of C's exponent field (natural order);
+//   2. perm_kernel      every transition's position in bin order (a warp per
+//                       (k-pair, i) row, ranks by warp matching, stable);
+//   3. wskel_kernel     the skeleton weights zeta_k |d(D_u, w_skel)| per
+//                       position, packed as 31-bit mantissa and exponent;
+//   4. cfix_bin_kernel  fixed-point C gathered into bin order and the row
+//                       maxima of the weighted operand per (bin, skeleton);
+//   5. slice_kernel     the digit planes of C (the B operand, unchanged code);
+//   6. per round: slice_bin_kernel (bin b's weighted planes for its skeletons
+//      of the round) and one chi0_tc_kernel whose segments are the bins (each
+//      reads B at its own K offset);
+//   7. reduce_bin_kernel: per element the split-K partials of every (b, r),
+//      scaled by their exponents and combined with coef into all n_w
+//      frequencies in FP64, Hermitian store.
+// With all skeletons in one round and two workspace regions, q+1's weighted
+// planes are written by the slicer warps of q's tensor-core launch (its
+// steps 1-5 run before that launch).  Included by kernels_mixed.cu.
+#pragma once
+
+namespace rpa {
+namespace {
+
+static_assert(SB_MAX_BINS == FREQ_MAX_BINS, "bin limits of the slicer and the plan differ");
+constexpr int BIN_MAX_RANK = 32;  // skeletons per bin at most (= the frequency limit)
+constexpr int STATUS_PLAN = STATUS_CODE_PLAN;  // device bin counts disagree with the plan
+
+struct BinEdges {
+  double edge[SB_MAX_BINS];
+};
+
+// Row maxima of the FP64 exponent field of C over all k-pairs of the q.
+// Block: 8 rows (a warp each) x one part of one k-pair's row.
+__global__ void __launch_bounds__(256) ecrow_kernel(int cplx, int N, int n_ov, int TP, const double* const* C,
+                                                    int* eCraw) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int P = blockIdx.x * 8 + warp;
+  if (P >= N) return;
+  const int j = blockIdx.y / TP, tp = blockIdx.y - j * TP;
+  const long nv = (long)n_ov * (cplx ? 2 : 1);
+  const long v0 = tp * nv / TP, v1 = (tp + 1) * nv / TP;
+  const unsigned long long* row = reinterpret_cast<const unsigned long long*>(C[j]) + (long)P * nv;
+  int m = 0;
+  for (long v = v0 + lane; v < v1; v += 32) m = max(m, (int)((row[v] >> 52) & 0x7ff));
+  m = __reduce_max_sync(0xffffffffu, m);
+  if (lane == 0 && m > 0) atomicMax(eCraw + P, m);
+}
+
+// Position of every transition in bin order.  One warp per (k-pair jj,
+// occupied i) row; bin b's transitions of the row go, in order of a, to
+// rowoff[row][b] .. rowoff[row][b] + cnt[row][b] - 1 (both from the host
+// plan).  A count that disagrees with the plan sets the status word and the
+// position is not written (no access outside the bin's range).
+__global__ void __launch_bounds__(256) perm_kernel(int n_k, int n_occ, int n_virt, int nb,
+                                                   const __grid_constant__ BinEdges e, const double* eps_occ,
+                                                   const double* eps_virt, const int* kidx, const int* kqidx,
+                                                   const int* rowtab, int* perm, double* dpos, int* status) {
+  __shared__ int run[8][SB_MAX_BINS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long nrow = (long)n_k * n_occ;
+  const long row = (long)blockIdx.x * 8 + warp;
+  if (row >= nrow) return;
+  const int jj = (int)(row / n_occ), i = (int)(row - (long)jj * n_occ);
+  if (lane < SB_MAX_BINS) run[warp][lane] = 0;
+  __syncwarp();
+  const double eo = eps_occ[(long)kidx[jj] * n_occ + i];
+  const double* ev = eps_virt + (long)kqidx[jj] * n_virt;
+  const int* off = rowtab + row * nb;
+  const int* cnt = rowtab + (nrow + row) * nb;
+  const int n_ov = n_occ * n_virt;
+  for (int a0 = 0; a0 < n_virt; a0 += 32) {
+    const int a = a0 + lane;
+    const bool act = a < n_virt;
+    double D = 0.0;
+    int b = -1;
+    if (act) {
+      D = ev[a] - eo;
+      b = 0;
+      while (b < nb - 1 && D >= e.edge[b]) ++b;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    const int below = __popc(peers & ((1u << lane) - 1u));
+    if (act) {
+      const int r = run[warp][b] + below;
+      if (r < cnt[b]) {
+        const long pos = (long)off[b] + r;
+        perm[pos] = jj * n_ov + i * n_virt + a;
+        dpos[pos] = D;
+      } else {
+        atomicCAS(status, 0, 1 + STATUS_PLAN);
+      }
+    }
+    __syncwarp();
+    if (act && below == 0) run[warp][b] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+struct BinPos {
+  int u0[SB_MAX_BINS + 1];  // first position of each bin
+  int rank[SB_MAX_BINS];
+};
+
+// Skeleton weights w = zeta_k |d(D_u, w_skel[b][g])| of every position u and
+// slot g < rmax (zero for padding and for slots past the bin's rank), as a
+// 31-bit mantissa and exponent: w = wm 2^(ew - 31), wx = wm | ew << 32.
+__global__ void __launch_bounds__(256) wskel_kernel(int Kt, int rmax, int nb, BinPos bp, const int* perm,
+                                                    const double* dpos, const double* skel_om, double zeta_k,
+                                                    unsigned long long* wx) {
+  const long total = (long)rmax * Kt;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int g = (int)(idx / Kt), u = (int)(idx - (long)g * Kt);
+    int b = 0;
+    while (b + 1 < nb && bp.u0[b + 1] <= u) ++b;
+    unsigned long long out = (unsigned long long)(uint32_t)(-2000) << 32;
+    if (g < bp.rank[b] && perm[u] >= 0) {
+      const double D = dpos[u], om = skel_om[b * rmax + g];
+      const double w = zeta_k * (4.0 * D / (D * D + om * om));
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(w);
+      const int E = (int)((bits >> 52) & 0x7ff);
+      if (E) {
+        unsigned long long m = (((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) + (1ull << 21)) >> 22;
+        int ee = E - 1022;
+        if (m >> 31) {
+          m >>= 1;
+          ++ee;
+        }
+        out = m | ((unsigned long long)(uint32_t)ee << 32);
+      }
+    }
+    wx[idx] = out;
+  }
+}
+
+// c_fix = round(c 2^(30 - eC)) of one FP64 value (eC: the row's exponent).
+__device__ __forceinline__ int fix_of(unsigned long long cb, int eC) {
+  const int Ec = (int)((cb >> 52) & 0x7ff);
+  if (Ec == 0) return 0;
+  const int sh = 1045 - Ec + eC;  // >= 23 since eC >= Ec - 1022
+  if (sh >= 64) return 0;
+  const unsigned long long mant = (cb & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int m = (int)((mant + (1ull << (sh - 1))) >> sh);
+  return (cb >> 63) ? -m : m;
+}
+
+// Fixed-point C in bin order and the raw row maxima of the weighted operand
+// (exponent field of c + exponent of w + 1022) per (bin, skeleton slot).
+// Block: 8 rows (a warp each) x one part (a position range inside one bin;
+// parts[3 y] = bin, parts[3 y + 1 .. 3 y + 2] = range).
+__global__ void __launch_bounds__(256) cfix_bin_kernel(int cplx, int N, int Npad, int n_ov, int Kr, int Kt, int rmax,
+                                                       const int* parts, const int* rankb, const double* const* C,
+                                                       const int* perm, const int* eCraw,
+                                                       const unsigned long long* wx, int* cfix, int* eAraw) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int P = blockIdx.x * 8 + warp;
+  if (P >= Npad) return;
+  const int b = parts[3 * blockIdx.y], u0 = parts[3 * blockIdx.y + 1], u1 = parts[3 * blockIdx.y + 2];
+  const int R = rankb[b];
+  const int rc = P < N ? eCraw[P] : 0;
+  const int eC = rc ? rc - 1022 : -2000;
+  int m[BIN_MAX_RANK];
+#pragma unroll
+  for (int g = 0; g < BIN_MAX_RANK; ++g) m[g] = 0;
+  int* out = cfix + (long)P * Kr;
+  for (int u = u0 + lane; u < u1; u += 32) {
+    const int pt = perm[u];
+    int v0 = 0, v1 = 0, Ec = 0;
+    if (P < N && pt >= 0) {
+      const int j = pt / n_ov, t = pt - j * n_ov;
+      if (cplx) {
+        const ulonglong2 x = reinterpret_cast<const ulonglong2*>(C[j])[(long)P * n_ov + t];
+        v0 = fix_of(x.x, eC);
+        v1 = fix_of(x.y, eC);
+        Ec = max((int)((x.x >> 52) & 0x7ff), (int)((x.y >> 52) & 0x7ff));
+      } else {
+        const unsigned long long x = reinterpret_cast<const unsigned long long*>(C[j])[(long)P * n_ov + t];
+        v0 = fix_of(x, eC);
+        Ec = (int)((x >> 52) & 0x7ff);
+      }
+    }
+    if (cplx)
+      *reinterpret_cast<int2*>(out + 2 * (long)u) = make_int2(v0, v1);
+    else
+      out[u] = v0;
+    if (Ec) {
+#pragma unroll
+      for (int g = 0; g < BIN_MAX_RANK; ++g) {
+        if (g >= R) break;
+        const int ee = (int)(uint32_t)(__ldg(wx + (long)g * Kt + u) >> 32);
+        m[g] = max(m[g], Ec + ee + 1022);
+      }
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < BIN_MAX_RANK; ++g) {
+    if (g >= R) break;
+    const int r = __reduce_max_sync(0xffffffffu, m[g]);
+    if (lane == 0 && r > 0) atomicMax(eAraw + ((long)b * rmax + g) * Npad + P, r);
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) slice_bin_kernel(SliceBinArgs a) {
+  const long total = (long)a.Npad * a.n_kb;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    if (a.cplx)
+      slice_unit_bin<true>(a, idx);
+    else
+      slice_unit_bin<false>(a, idx);
+  }
+}
+
+// chi0(w) for every frequency from the partials of every (bin, skeleton):
+// one thread per element of a lower tile.
+struct RedBin {
+  int cplx, N, Npad, n_tiles, nb, rmax, n_w, G;  // G: skeleton slots per round
+  int rank[SB_MAX_BINS], nks[SB_MAX_BINS];
+  long base[SB_MAX_BINS];  // item index of bin b's first round
+  const float* part;
+  const int* eAraw;
+  const int* eCraw;
+  const double* coef;  // [nb][rmax][n_w]
+  double* chi;         // [n_w][N][N]
+};
+
+__global__ void __launch_bounds__(256) reduce_bin_kernel(const __grid_constant__ RedBin rb) {
+  extern __shared__ double cs[];
+  const int ncoef = rb.nb * rb.rmax * rb.n_w;
+  for (int i = threadIdx.x; i < ncoef; i += blockDim.x) cs[i] = rb.coef[i];
+  __syncthreads();
+  const int ncols = rb.cplx ? 64 : 128;
+  const int per_tile = 128 * ncols / 256;
+  const int tile = blockIdx.x / per_tile;
+  const int e = (blockIdx.x - tile * per_tile) * 256 + threadIdx.x;
+  const int r = e / ncols, c = e - (e / ncols) * ncols;
+  int I, J;
+  tile_ij(rb.cplx, tile, I, J);
+  const int P = I * 128 + r, Q = J * ncols + c;
+  if (P >= rb.N || Q >= rb.N || Q > P) return;
+  double are[BIN_MAX_RANK], aim[BIN_MAX_RANK];
+#pragma unroll
+  for (int w = 0; w < BIN_MAX_RANK; ++w) are[w] = aim[w] = 0.0;
+  const int rq = rb.eCraw[Q];
+  const int eCQ = rq ? rq - 1022 : -2000;
+  for (int b = 0; b < rb.nb; ++b) {
+    for (int g = 0; g < rb.rank[b]; ++g) {
+      const int g0 = g / rb.G * rb.G, Gs = min(rb.G, rb.rank[b] - g0), gl = g - g0;
+      const long it0 = rb.base[b] + (long)g0 * rb.nks[b] * rb.n_tiles;
+      double re = 0.0, im = 0.0;
+      for (int ks = 0; ks < rb.nks[b]; ++ks) {
+        const long item = it0 + ((long)ks * Gs + gl) * rb.n_tiles + tile;
+        const float* pp = rb.part + item * 2 * 128 * 128 + (long)r * 128;
+        re += (double)pp[c] + (double)pp[128 * 128 + c];
+        if (rb.cplx) im += (double)pp[64 + c] + (double)pp[128 * 128 + 64 + c];
+      }
+      const int ra = rb.eAraw[((long)b * rb.rmax + g) * rb.Npad + P];
+      const int eA = ra > 0 ? ra - 2044 + 1 : -2000;
+      const double sc = -ldexp(1.0, eA + eCQ + 1 - 14);  // x = 2^(e - 7) sum v; chi = -sum conj(a) c
+      re *= sc;
+      im *= sc;
+      const double* cf = cs + ((long)b * rb.rmax + g) * rb.n_w;
+#pragma unroll
+      for (int w = 0; w < BIN_MAX_RANK; ++w) {
+        if (w >= rb.n_w) break;
+        are[w] = fma(cf[w], re, are[w]);
+        aim[w] = fma(cf[w], im, aim[w]);
+      }
+    }
+  }
+  const long NN = (long)rb.N * rb.N;
+#pragma unroll
+  for (int w = 0; w < BIN_MAX_RANK; ++w) {
+    if (w >= rb.n_w) break;
+    if (rb.cplx) {
+      double2* out = reinterpret_cast<double2*>(rb.chi) + (long)w * NN;
+      const double im = P == Q ? 0.0 : aim[w];
+      out[(long)P * rb.N + Q] = make_double2(are[w], im);
+      if (P != Q) out[(long)Q * rb.N + P] = make_double2(are[w], -im);
+    } else {
+      double* out = rb.chi + (long)w * NN;
+      out[(long)P * rb.N + Q] = are[w];
+      if (P != Q) out[(long)Q * rb.N + P] = are[w];
+    }
+  }
+}
+
+// ------------------------------------------------------------ host side --
+
+// Workspace of one q of the frequency-batched path.
+struct BinLayout {
+  int Npad, Kt, Kr, n_kb, nb, rmax, G, n_tiles, n_parts, meta_ints;
+  long items;  // partial items (sum over bins of rank x nks_cap x tiles)
+  size_t meta, perm, dpos, wx, eC, eA, cfix, SC, S, part, total;
+};
+
+BinLayout bin_layout(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int s, size_t slice_cap,
+                     int sms) {
+  BinLayout L{};
+  auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+  L.Npad = (g.n_aux + 127) / 128 * 128;
+  L.Kt = Kt_max;
+  L.Kr = g.cplx ? 2 * Kt_max : Kt_max;
+  L.n_kb = L.Kr / KB;
+  L.nb = p.n_bins;
+  L.rmax = p.rmax;
+  L.n_parts = n_parts_max;
+  const int nbk = L.Npad / 128;
+  L.n_tiles = g.cplx ? nbk * (nbk + 1) : nbk * (nbk + 1) / 2;
+  const size_t per_slot = (size_t)s * L.Npad * L.Kr * 2;  // every bin's weighted planes of one slot
+  L.G = (int)std::max<size_t>(1, std::min<size_t>((size_t)L.rmax, slice_cap / std::max<size_t>(per_slot, 1)));
+  // split-K cap per bin: enough items to fill the GPU (the partial buffer is sized for it)
+  long items = 0;
+  const int chunks = (L.n_kb + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
+  for (int b = 0; b < L.nb; ++b) {
+    const int Gb = std::min(L.G, p.rank[b]);
+    const int cap = std::max(1, std::min(chunks, (4 * sms + Gb * L.n_tiles - 1) / std::max(1, Gb * L.n_tiles)));
+    items += (long)p.rank[b] * cap * L.n_tiles;
+  }
+  L.items = items;
+  L.meta_ints = 2 * g.n_k * g.n_occ * L.nb + 3 * L.n_parts + SB_MAX_BINS;
+  L.meta = al(sizeof(int) * (size_t)L.meta_ints + 64) + al(sizeof(double) * (size_t)L.nb * L.rmax * (1 + g.n_w));
+  L.perm = al(sizeof(int) * (size_t)L.Kt);
+  L.dpos = al(sizeof(double) * (size_t)L.Kt);
+  L.wx = al(sizeof(unsigned long long) * (size_t)L.rmax * L.Kt);
+  L.eC = al(sizeof(int) * (size_t)L.Npad);
+  L.eA = al(sizeof(int) * (size_t)L.nb * L.rmax * L.Npad);
+  L.cfix = al(sizeof(int) * (size_t)L.Npad * L.Kr);
+  L.SC = al(per_slot * (g.cplx ? 2 : 1));
+  L.S = al(per_slot * L.G);
+  L.part = al(sizeof(float) * 2 * 128 * 128 * (size_t)items);
+  L.total = L.meta + L.perm + L.dpos + L.wx + L.eC + L.eA + L.cfix + L.SC + L.S + L.part;
+  return L;
+}
+
+struct BinRegion {
+  BinLayout L;
+  int* meta_i;  // rowtab [2][n_k n_occ nb] | parts [n_parts][3] | rank [16]
+  double* meta_d;  // skel_om [nb][rmax] | coef [nb][rmax][n_w]
+  int *perm, *eC, *eA, *cfix;
+  double* dpos;
+  unsigned long long* wx;
+  uint16_t *SC, *S;
+  float* part;
+};
+
+BinRegion carve_bin(char* p, const BinLayout& L) {
+  BinRegion r;
+  r.L = L;
+  auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+  r.meta_i = (int*)p;
+  r.meta_d = (double*)(p + al(sizeof(int) * (size_t)L.meta_ints + 64));
+  p += L.meta;
+  r.perm = (int*)p;
+  p += L.perm;
+  r.dpos = (double*)p;
+  p += L.dpos;
+  r.wx = (unsigned long long*)p;
+  p += L.wx;
+  r.eC = (int*)p;
+  p += L.eC;
+  r.eA = (int*)p;
+  p += L.eA;
+  r.cfix = (int*)p;
+  p += L.cfix;
+  r.SC = (uint16_t*)p;
+  p += L.SC;
+  r.S = (uint16_t*)p;
+  p += L.S;
+  r.part = (float*)p;
+  return r;
+}
+
+constexpr int BIN_PREP_LAUNCHES = 6;  // ecrow, perm, wskel, cfix_bin, slice of C (+ the memsets are not kernels)
+
+// Steps 1-5 for one q into region R (its meta image already copied there).
+cudaError_t bin_prep(const BinRegion& R, const MixedBinQ& q, const FreqPlan& p, int s, int sms, cudaStream_t st) {
+  const BatchGeom& g = q.g;
+  const BinQHost& h = *q.host;
+  const BinLayout& L = R.L;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(R.perm, 0xFF, sizeof(int) * (size_t)h.Kt, st))) return e;
+  if ((e = cudaMemsetAsync(R.eC, 0, sizeof(int) * (size_t)L.Npad, st))) return e;
+  if ((e = cudaMemsetAsync(R.eA, 0, sizeof(int) * (size_t)L.nb * L.rmax * L.Npad, st))) return e;
+  const int TP = g.n_k >= 8 ? 1 : (8 + g.n_k - 1) / g.n_k;
+  ecrow_kernel<<<dim3((unsigned)((g.n_aux + 7) / 8), (unsigned)(g.n_k * TP)), 256, 0, st>>>(g.cplx, g.n_aux, g.n_ov,
+                                                                                          TP, q.Cptrs, R.eC);
+  BinEdges be{};
+  for (int b = 0; b + 1 < p.n_bins; ++b) be.edge[b] = p.edges[b];
+  const long nrow = (long)g.n_k * g.n_occ;
+  perm_kernel<<<(unsigned)((nrow + 7) / 8), 256, 0, st>>>(g.n_k, g.n_occ, g.n_virt, p.n_bins, be, q.eps_occ,
+                                                          q.eps_virt, q.kidx, q.kqidx, R.meta_i, R.perm, R.dpos,
+                                                          q.status);
+  BinPos bp{};
+  for (int b = 0; b <= p.n_bins; ++b) bp.u0[b] = h.tb0[b];
+  for (int b = p.n_bins + 1; b <= SB_MAX_BINS; ++b) bp.u0[b] = h.Kt;
+  for (int b = 0; b < p.n_bins; ++b) bp.rank[b] = p.rank[b];
+  const long nw = (long)L.rmax * h.Kt;
+  wskel_kernel<<<(unsigned)std::min<long>((nw + 255) / 256, (long)sms * 16), 256, 0, st>>>(
+      h.Kt, L.rmax, p.n_bins, bp, R.perm, R.dpos, R.meta_d, q.zeta_k, R.wx);
+  const int n_parts = h.n_parts;
+  const int* parts = R.meta_i + 2 * nrow * p.n_bins;
+  const int* rankb = parts + 3 * n_parts;
+  cfix_bin_kernel<<<dim3((unsigned)(L.Npad / 8), (unsigned)n_parts), 256, 0, st>>>(
+      g.cplx, g.n_aux, L.Npad, g.n_ov, h.Kr, h.Kt, L.rmax, parts, rankb, q.Cptrs, R.perm, R.eC, R.wx, R.cfix, R.eA);
+  // digits of C (the B operand) in bin order
+  SliceArgs sc{g.cplx, L.Npad, g.n_ov, h.Kt, h.Kr, s, g.n_w, 0, 1, g.cplx ? 2 : 1, R.cfix, nullptr,
+               nullptr, nullptr, R.SC};
+  const long tg = (long)L.Npad * (h.Kr / 16);
+  launch_slice(g.cplx, (unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), st, sc);
+  return cudaGetLastError();
+}
+
+// Weighted planes of round k (slots [k G, k G + G) of every bin) of one q.
+SliceBinArgs bin_slice_args(const BinRegion& R, const MixedBinQ& q, const FreqPlan& p, int s, int k) {
+  const BinQHost& h = *q.host;
+  const BinLayout& L = R.L;
+  SliceBinArgs a{};
+  a.cplx = q.g.cplx;
+  a.Npad = L.Npad;
+  a.Kr = h.Kr;
+  a.s = s;
+  a.n_kb = h.Kr / KB;
+  a.nb = p.n_bins;
+  a.g0 = k * L.G;
+  a.rmax = L.rmax;
+  a.Kt = h.Kt;
+  a.cfix = R.cfix;
+  a.eC = R.eC;
+  a.wx = R.wx;
+  a.eAraw = R.eA;
+  a.S = R.S;
+  const long nI = L.Npad / 128;
+  long off = 0;
+  const int tpk = q.g.cplx ? 8 : 16;
+  for (int b = 0; b < SB_MAX_BINS; ++b) {
+    const bool in = b < p.n_bins;
+    a.kb0[b] = in ? h.tb0[b] / tpk : a.n_kb;
+    a.G[b] = in ? std::max(0, std::min(L.G, p.rank[b] - a.g0)) : 0;
+    a.aoff[b] = off;
+    if (in) off += (long)a.G[b] * nI * ((h.tb0[b + 1] - h.tb0[b]) / tpk) * s * 2048;
+  }
+  a.kb0[SB_MAX_BINS] = a.n_kb;
+  return a;
+}
+
+// Split-K depth of every bin for q (fixed over its rounds): the cost model of
+// the per-frequency path over the first round's segments, or the recorded
+// autotuner choice for this shape class.
+void bin_splits(const BinLayout& L, const MixedBinQ& q, const FreqPlan& p, int s, int sms, int* nks) {
+  const BinQHost& h = *q.host;
+  const int tpk = q.g.cplx ? 8 : 16;
+  std::vector<SegShape> shp;
+  std::vector<int> who;
+  for (int b = 0; b < p.n_bins; ++b) {
+    const int nkb = (h.tb0[b + 1] - h.tb0[b]) / tpk;
+    nks[b] = 1;
+    if (nkb == 0) continue;
+    const int chunks = (nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
+    const int Gb = std::min(L.G, p.rank[b]);
+    const int cap = std::max(1, std::min(chunks, (4 * sms + Gb * L.n_tiles - 1) / std::max(1, Gb * L.n_tiles)));
+    shp.push_back(SegShape{chunks, Gb, L.n_tiles, cap});
+    who.push_back(b);
+  }
+  if (shp.empty()) return;
+  int Lc = autotune_lookup(round_key(shp, s) ^ 0x5bd1e995ull);
+  if (Lc <= 0) {
+    double best = 1e300;
+    for (int c : candidates(shp)) {
+      const double cost = plan_for(shp, c, sms).cost;
+      if (cost < best) {
+        best = cost;
+        Lc = c;
+      }
+    }
+  }
+  const SplitPlan pl = plan_for(shp, Lc, sms);
+  for (size_t i = 0; i < who.size(); ++i) nks[who[i]] = pl.nks[i];
+}
+
+// The tensor-core launch of round k of q (segments: the bins with slots in it).
+int bin_tc_params(const BinRegion& R, const MixedBinQ& q, const FreqPlan& p, int s, int k, const int* nks,
+                  const long* base, int* err, TcParams& tp) {
+  const BinQHost& h = *q.host;
+  const BinLayout& L = R.L;
+  const int tpk = q.g.cplx ? 8 : 16;
+  memset(&tp, 0, sizeof tp);
+  tp.s = s;
+  tp.kb_per_chunk = KB_PER_CHUNK;
+  tp.drop_item = mixed_test_drop_take();
+  tp.err = err;
+  tp.grp_mask = group_mask(s);
+  const SliceBinArgs sa = bin_slice_args(R, q, p, s, k);
+  int items = 0;
+  for (int b = 0; b < p.n_bins; ++b) {
+    const int nkb = (h.tb0[b + 1] - h.tb0[b]) / tpk;
+    const int Gs = sa.G[b];
+    if (Gs <= 0 || nkb == 0) continue;
+    const int chunks = (nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
+    const int cps = (chunks + nks[b] - 1) / nks[b];
+    TcSeg& S = tp.seg[tp.n_segs++];
+    S.A = R.S + sa.aoff[b];
+    S.B = R.SC;
+    S.nI = L.Npad / 128;
+    S.part = R.part + (base[b] + (long)sa.g0 * nks[b] * L.n_tiles) * 2 * 128 * 128;
+    S.cplx = q.g.cplx;
+    S.G = Gs;
+    S.n_tiles = L.n_tiles;
+    S.n_ksplit = nks[b];
+    S.kb_per_split = cps * KB_PER_CHUNK;
+    S.n_kb = nkb;
+    S.kb_off = sa.kb0[b];
+    S.ldb = sa.n_kb;
+    S.item0 = items;
+    items += Gs * L.n_tiles * nks[b];
+  }
+  tp.n_items = items;
+  return items;
+}
+
+size_t bin_region_bytes(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int s, size_t slice_cap) {
+  return bin_layout(g, p, Kt_max, n_parts_max, s, slice_cap, num_sms()).total;
+}
+
+}  // namespace
+
+size_t binned_workspace_bytes(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int n_slices,
+                              size_t slice_cap, bool two_regions) {
+  const size_t one = bin_region_bytes(g, p, Kt_max, n_parts_max, n_slices, slice_cap);
+  return 1024 + (two_regions ? 2 : 1) * one;
+}
+
+bool binned_one_round(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int n_slices,
+                      size_t slice_cap) {
+  return bin_layout(g, p, Kt_max, n_parts_max, n_slices, slice_cap, num_sms()).G >= p.rmax;
+}
+
+// chi0 of n q (one geometry) through the frequency-batched plan, one q after
+// another; with a single round per q and room for two regions, q+1's weighted
+// planes are written inside q's tensor-core launch.
+cudaError_t launch_chi0_binned(const MixedBinQ* qs, int n, const FreqPlan& p, int s, void* work, size_t work_bytes,
+                               size_t slice_cap, int* status, uint64_t* n_launch, cudaStream_t st,
+                               const LaunchHook* hook) {
+  auto hb = [&]() {
+    if (hook) hook->begin(hook->user, st);
+  };
+  auto he = [&](int cls, int nk) {
+    if (hook) hook->end(hook->user, st, cls, nk);
+  };
+  if (n <= 0) return cudaSuccess;
+  if (s < 2 || s > MAX_S || p.n_bins <= 0 || p.rmax > BIN_MAX_RANK) return cudaErrorInvalidValue;
+  if ((size_t)p.n_bins * p.rmax * qs[0].g.n_w * sizeof(double) > 48 * 1024) return cudaErrorInvalidValue;
+  const int sms = num_sms();
+  if (cudaError_t ea = tc_smem_attr()) return ea;
+  int Kt_max = 0, np_max = 0;
+  for (int i = 0; i < n; ++i) {
+    Kt_max = std::max(Kt_max, qs[i].host->Kt);
+    np_max = std::max(np_max, qs[i].host->n_parts);
+  }
+  const BinLayout L = bin_layout(qs[0].g, p, Kt_max, np_max, s, slice_cap, sms);
+  const bool pipe = n >= 2 && L.G >= p.rmax && 1024 + 2 * L.total <= work_bytes;
+  if (1024 + L.total > work_bytes) return cudaErrorMemoryAllocation;
+  char* base = (char*)work;
+  int* err = (int*)base;
+  BinRegion R[2] = {carve_bin(base + 1024, L), carve_bin(base + 1024 + (pipe ? L.total : 0), L)};
+  uint64_t nl = 0;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int) * 4, st);
+  if (e != cudaSuccess) return e;
+  auto meta_copy = [&](const BinRegion& r, const MixedBinQ& q) -> cudaError_t {
+    const BinQHost& h = *q.host;
+    cudaError_t ee = cudaMemcpyAsync(r.meta_i, h.meta_i, sizeof(int) * h.n_meta_i, cudaMemcpyHostToDevice, st);
+    if (ee == cudaSuccess)
+      ee = cudaMemcpyAsync(r.meta_d, h.meta_d, sizeof(double) * h.n_meta_d, cudaMemcpyHostToDevice, st);
+    return ee;
+  };
+  // first q's preparation
+  hb();
+  if ((e = meta_copy(R[0], qs[0]))) return e;
+  if ((e = bin_prep(R[0], qs[0], p, s, sms, st))) return e;
+  he(RPA_K_SLICE, BIN_PREP_LAUNCHES - 1);
+  nl += BIN_PREP_LAUNCHES - 1;
+  const int rounds = (p.rmax + L.G - 1) / L.G;
+  for (int i = 0; i < n; ++i) {
+    const BinRegion& C = R[pipe ? (i & 1) : 0];
+    const MixedBinQ& q = qs[i];
+    const bool more = pipe && i + 1 < n;
+    int nks[SB_MAX_BINS];
+    long bbase[SB_MAX_BINS];
+    bin_splits(L, q, p, s, sms, nks);
+    long items = 0;
+    for (int b = 0; b < p.n_bins; ++b) {
+      bbase[b] = items;
+      items += (long)p.rank[b] * nks[b] * L.n_tiles;
+    }
+    if (items > L.items) return cudaErrorInvalidValue;
+    if (i > 0 && !pipe) {  // one region: this q's preparation after the previous q finished with it
+      hb();
+      if ((e = meta_copy(C, q))) return e;
+      if ((e = bin_prep(C, q, p, s, sms, st))) return e;
+      he(RPA_K_SLICE, BIN_PREP_LAUNCHES - 1);
+      nl += BIN_PREP_LAUNCHES - 1;
+    }
+    if (more) {  // the next q's preparation in the other region, before this q's launch
+      hb();
+      if ((e = meta_copy(R[(i + 1) & 1], qs[i + 1]))) return e;
+      if ((e = bin_prep(R[(i + 1) & 1], qs[i + 1], p, s, sms, st))) return e;
+      he(RPA_K_SLICE, BIN_PREP_LAUNCHES - 1);
+      nl += BIN_PREP_LAUNCHES - 1;
+    }
+    for (int k = 0; k < rounds; ++k) {
+      if (!(pipe && i > 0)) {  // weighted planes of this round (a launch of its own)
+        hb();
+        const SliceBinArgs sa = bin_slice_args(C, q, p, s, k);
+        const long tg = (long)L.Npad * sa.n_kb;
+        slice_bin_kernel<<<(unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), 256, 0, st>>>(sa);
+        he(RPA_K_SLICE, 1);
+        ++nl;
+      }
+      TcParams tp;
+      const int n_items = bin_tc_params(C, q, p, s, k, nks, bbase, err, tp);
+      if (more && k == rounds - 1) {
+        tp.side_on = 2;
+        tp.sideb = bin_slice_args(R[(i + 1) & 1], qs[i + 1], p, s, 0);
+      }
+      if (n_items > 0) {
+        hb();
+        launch_tc(s, std::min(n_items, sms), TC_SMEM, st, tp);
+        he(RPA_K_CHI0, 1);
+        ++nl;
+      } else if (more && k == rounds - 1) {  // nothing to contract: slice the next q standalone
+        const SliceBinArgs& sa = tp.sideb;
+        const long tg = (long)L.Npad * sa.n_kb;
+        slice_bin_kernel<<<(unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), 256, 0, st>>>(sa);
+        ++nl;
+      }
+    }
+    RedBin rb{};
+    rb.cplx = q.g.cplx;
+    rb.N = q.g.n_aux;
+    rb.Npad = L.Npad;
+    rb.n_tiles = L.n_tiles;
+    rb.nb = p.n_bins;
+    rb.rmax = L.rmax;
+    rb.n_w = q.g.n_w;
+    rb.G = L.G;
+    for (int b = 0; b < p.n_bins; ++b) {
+      rb.rank[b] = (q.host->tb0[b + 1] > q.host->tb0[b]) ? p.rank[b] : 0;
+      rb.nks[b] = nks[b];
+      rb.base[b] = bbase[b];
+    }
+    rb.part = C.part;
+    rb.eAraw = C.eA;
+    rb.eCraw = C.eC;
+    rb.coef = C.meta_d + (size_t)p.n_bins * L.rmax;
+    rb.chi = q.chi;
+    const int per_tile = 128 * (q.g.cplx ? 64 : 128) / 256;
+    hb();
+    reduce_bin_kernel<<<(unsigned)(L.n_tiles * per_tile), 256,
+                        sizeof(double) * (size_t)p.n_bins * L.rmax * q.g.n_w, st>>>(rb);
+    he(RPA_K_CHI0_RED, 1);
+    ++nl;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (status) {
+    err_merge_kernel<<<1, 32, 0, st>>>(err, status);
+    ++nl;
+  }
+  if (n_launch) *n_launch = nl;
+  return cudaSuccess;
+}
+
+}  // namespace rpa

@@ -165,9 +165,10 @@ constexpr int MAX_SEGS = 96;
 
 struct TcSeg {
   const uint16_t* A;  // weighted digit planes, [g][I][kb][plane][4 KB block]
-  const uint16_t* B;  // digit planes of C, [J][kb][plane][4 KB block]
+  const uint16_t* B;  // digit planes of C, [J][ldb][plane][4 KB block]; this segment reads K-blocks kb_off + kb
   float* part;        // [item][2 (hi, lo)][128 rows][128 cols]
   int cplx, G, n_tiles, n_ksplit, kb_per_split, n_kb, item0, nI;
+  int kb_off, ldb;    // the segment's K range within B, B's K-blocks per column block
 };
 
 struct TcParams {
@@ -179,8 +180,9 @@ struct TcParams {
   // Side job of the slicer warps: the weighted digit planes of another q
   // (all its frequencies), written while this launch's MMAs run; its inputs
   // and output share nothing with this launch's segments.
-  int side_on;
+  int side_on;        // 1: side (per-frequency operand), 2: sideb (frequency-batched operand)
   SliceArgs side;
+  SliceBinArgs sideb;
   TcSeg seg[MAX_SEGS];
 };
 static_assert(sizeof(TcParams) <= 32000, "kernel parameter block too large");
@@ -365,7 +367,8 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
           // A: X slices of rows I*128.. ; B: [X; Y] slices of columns J*64.. (real: X of J*128..)
           bulk_load(sa, SG.A + (((size_t)it.g * SG.nI + it.I) * SG.n_kb + kb) * (S * 2048), S * PLANE_BYTES,
                     &full[stage]);
-          bulk_load(sb, SG.B + ((size_t)it.J * SG.n_kb + kb) * (S * 2048), S * PLANE_BYTES, &full[stage]);
+          bulk_load(sb, SG.B + ((size_t)it.J * SG.ldb + SG.kb_off + kb) * (S * 2048), S * PLANE_BYTES,
+                    &full[stage]);
           armed[stage] = (int)phase;
           if (++stage == STAGES) {
             stage = 0;
@@ -472,7 +475,7 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
         *reinterpret_cast<float4*>(pl + u) = make_float4(lo[u], lo[u + 1], lo[u + 2], lo[u + 3]);
       }
     }
-  } else if (p.side_on) {
+  } else if (p.side_on == 1) {
     // ------------------------------------------------ slicer (2 warps)
     // no waits: independent loads and stores, consecutive threads on
     // consecutive rows of one K-block as in the standalone slicing kernel
@@ -484,6 +487,17 @@ __global__ void __launch_bounds__(THREADS, 1) chi0_tc_kernel(const __grid_consta
       for (long idx = first; idx < total; idx += stride) slice_unit<true, true>(p.side, idx);
     } else {
       for (long idx = first; idx < total; idx += stride) slice_unit<false, true>(p.side, idx);
+    }
+  } else if (p.side_on == 2) {
+    // the same for the frequency-batched operand of another q
+    constexpr int NT = 32 * SLICE_WARPS;
+    const long total = (long)p.sideb.Npad * p.sideb.n_kb;
+    const long stride = (long)gridDim.x * NT;
+    const long first = (long)blockIdx.x * NT + (threadIdx.x - (THREADS - NT));
+    if (p.sideb.cplx) {
+      for (long idx = first; idx < total; idx += stride) slice_unit_bin<true>(p.sideb, idx);
+    } else {
+      for (long idx = first; idx < total; idx += stride) slice_unit_bin<false>(p.sideb, idx);
     }
   }
   fence_before();

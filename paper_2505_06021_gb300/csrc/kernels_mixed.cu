@@ -681,6 +681,8 @@ cudaError_t launch_chi0_mixed_multi(const MixedQ* qs, int n, int s, void* work, 
         S.n_ksplit = nks;
         S.kb_per_split = cps * KB_PER_CHUNK;
         S.n_kb = q.L.n_kb;
+        S.kb_off = 0;
+        S.ldb = q.L.n_kb;
         S.item0 = items;
         items += Gs[k] * q.L.n_tiles * nks;
         rp.seg[rp.n_segs++] = RedSeg{g.cplx, g.n_aux, q.L.Npad, q.L.n_tiles, nks, w0s[k], Gs[k], blocks,
@@ -850,6 +852,8 @@ cudaError_t launch_chi0_mixed_seq(const MixedQ* qs, int n, int s, void* work, si
     S.n_ksplit = nks;
     S.kb_per_split = cps * KB_PER_CHUNK;
     S.n_kb = L.n_kb;
+    S.kb_off = 0;
+    S.ldb = L.n_kb;
     S.item0 = 0;
     tp.n_items = n_items;
     tp.side_on = more ? 1 : 0;
@@ -881,3 +885,5 @@ cudaError_t launch_chi0_mixed(const BatchGeom& g, int s, const double* const* Cp
 }
 
 }  // namespace rpa
+
+#include "chi0_binned.cuh"

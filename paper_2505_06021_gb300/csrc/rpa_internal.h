@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/rpa.h"
 
@@ -187,6 +188,82 @@ size_t mixed_multi_workspace_bytes(const MixedQ* qs, int n, int n_slices);
 cudaError_t launch_chi0_mixed_seq(const MixedQ* qs, int n, int n_slices, void* work, size_t work_bytes,
                                   int* status, uint64_t* n_launch, cudaStream_t s, const LaunchHook* hook);
 size_t mixed_seq_workspace_bytes(const BatchGeom& g, int n_slices, size_t slice_cap);
+// ---- frequency-batched chi0 (freq_plan.cu) --------------------------------
+// Transitions are split into windows (bins) of the transition energy D; in
+// bin b the weight of every frequency node is a combination of the weights of
+// rank[b] skeleton nodes, d(D, w) ~= sum_r coef[b][r][w] d(D, w_skel[b][r]),
+// to FREQ_TOL of the bin's largest |d(., w)|.
+constexpr int FREQ_MAX_BINS = 16;
+constexpr double FREQ_TOL = 1e-10;
+constexpr double FREQ_AMP = 16.0;
+struct FreqPlan {
+  int n_bins = 0;                         // 0: no plan (every frequency contracted)
+  double edges[FREQ_MAX_BINS - 1] = {};   // interior edges, ascending: bin(D) = #{e : D >= e}
+  int rank[FREQ_MAX_BINS] = {};
+  double err[FREQ_MAX_BINS] = {};         // residual on the check grid / column maximum
+  double amp[FREQ_MAX_BINS] = {};         // max over nodes of the scaled coefficient sum
+  int rmax = 0;
+  std::vector<int> skel;                  // [n_bins][rmax] node index (-1 unused)
+  std::vector<double> coef;               // [n_bins][rmax][n_w]
+  double work_ratio = 1.0;                // modelled sum_b rank K_b / (n_w K)
+  double dlo = 0.0, dhi = 0.0;            // transition-energy window of the job
+};
+// Builds the plan from host copies of the band energies; mode 0 automatic
+// (false when it saves no work), 1 off, 2 always.  Returns whether a plan is
+// to be used.
+bool freq_plan_build(const rpa_job* j, const double* eps_occ_h, const double* eps_virt_h, int mode, FreqPlan* out);
+// cnt[(jj n_occ + i) n_bins + b]: virtual states of row (k-pair jj, occupied
+// i) of q whose transition falls in bin b.  evs: virtual energies of every
+// k-point sorted ascending.
+void freq_counts(const rpa_job* j, const FreqPlan& p, int q, const double* eo, const double* evs, int* cnt);
+int freq_bin_of(const FreqPlan& p, double D);
+
+// One q of the frequency-batched chi0: positions of the bins (each padded to
+// whole K-blocks) and the image of its device tables (pinned host memory):
+//   ints:    row offsets [n_k n_occ][n_bins] | row counts [n_k n_occ][n_bins] |
+//            parts [n_parts][3] (bin, first, end position; FREQ_PART at most) | rank [16]
+//   doubles: skeleton frequencies [n_bins][rmax] | coef [n_bins][rmax][n_w] (shared by all q)
+constexpr int FREQ_PART = 2048;
+struct BinQHost {
+  int Kt = 0, Kr = 0;  // positions, real K values (complex: 2 Kt)
+  int tb0[FREQ_MAX_BINS + 1] = {};
+  int n_parts = 0;
+  const int* meta_i = nullptr;
+  size_t n_meta_i = 0;
+  const double* meta_d = nullptr;
+  size_t n_meta_d = 0;
+};
+// Fills h (except the meta pointers) and the int image of q.
+void freq_bin_q(const rpa_job* j, const FreqPlan& p, int q, const double* eo, const double* evs, BinQHost& h,
+                std::vector<int>& img);
+// The double image shared by all q (skeleton frequencies, coefficients).
+void freq_meta_d(const rpa_job* j, const FreqPlan& p, std::vector<double>& img);
+// Virtual energies of every k-point sorted ascending.
+std::vector<double> freq_sorted_virt(const rpa_job* j, const double* ev);
+
+// One q of a frequency-batched launch.
+struct MixedBinQ {
+  BatchGeom g;                 // n_qb = 1
+  const double* const* Cptrs;  // device table of the q's n_k C blocks
+  double* chi;                 // device output [n_w][N][N]
+  const BinQHost* host;
+  const double* eps_occ;       // device band energies and this q's pair indices
+  const double* eps_virt;
+  const int* kidx;
+  const int* kqidx;
+  double zeta_k;
+  int* status;                 // device status word (plan mismatch)
+};
+size_t binned_workspace_bytes(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int n_slices,
+                              size_t slice_cap, bool two_regions);
+bool binned_one_round(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int n_slices,
+                      size_t slice_cap);
+cudaError_t launch_chi0_binned(const MixedBinQ* qs, int n, const FreqPlan& p, int n_slices, void* work,
+                               size_t work_bytes, size_t slice_cap, int* status, uint64_t* n_launch, cudaStream_t s,
+                               const LaunchHook* hook);
+// Status word code of a device bin count that disagrees with the plan.
+constexpr int STATUS_CODE_PLAN = 1 << 28;
+
 // Autotuner cache (autotune.cu): the recorded split target for a shape-class
 // key, 0 if none; autotune_record stores a measured choice.
 int autotune_lookup(uint64_t key);

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/rpa.h"
+#include "rpa_internal.h"
 
 namespace rpa {
 
@@ -57,12 +58,22 @@ struct Exec {
   std::vector<cudaEvent_t> ev_pool;
   cudaEvent_t take_event();
   HostStage hstage;  // uploads (tables)
+  HostStage hbin;    // uploads (tables of the frequency-batched chi0)
   HostStage hres;    // downloads: [int status | pad | Ec | eps[nqw] | parts[2 nqw]]
   bool init();
   void destroy();
   bool ensure_ws(size_t bytes);
   int& status_word() { return *reinterpret_cast<int*>(hres.ptr); }
   double* results() { return reinterpret_cast<double*>(reinterpret_cast<char*>(hres.ptr) + 64); }
+};
+
+// The frequency-batched chi0 of one job: the plan and every q's tables
+// (their images in the lane's pinned buffer hbin).
+struct BinJob {
+  bool on = false;
+  FreqPlan plan;
+  std::vector<BinQHost> qh;  // per q
+  int Kt_max = 0, np_max = 0;
 };
 
 struct ServeState;  // serving.cu
@@ -76,6 +87,7 @@ struct rpa_ctx {
   size_t cap = 0;
   double timeout_s = 60.0;
   int max_inflight = 64;
+  int chi0_freq = 0;  // rpa_config.chi0_freq
   rpa::Exec ex;  // default lane for the synchronous entry points
   std::atomic<uint64_t> launches{0};
   std::mutex mu;  // serialises the synchronous entry points on this context
@@ -135,7 +147,9 @@ size_t job_footprint(const rpa_job* j, int n_slices, size_t ws_cap);
 size_t job_workspace(const rpa_job* j, int n_slices, size_t ws_cap);
 // Enqueues the whole hot path of `job` on lane `ex` (no host wait) and records
 // ex.done after the results were copied into ex.hres.
-rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_cap);
+// allow_bin: use the frequency-batched chi0 when the context's setting and
+// the job's plan allow it (the synchronous entry point; serving lanes do not).
+rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_cap, bool allow_bin = false);
 // After ex.done has completed: decodes the device status and copies results.
 rpa_status energy_finish(rpa_ctx* ctx, Exec& ex, const rpa_job* job, double* Ec, double* eps_qw, double* parts);
 // Bounded wait for an event (RPA_E_TIMEOUT after timeout_s).
@@ -147,10 +161,15 @@ void prof_begin(rpa_ctx* ctx, Exec* ex, cudaStream_t s);
 void prof_end(rpa_ctx* ctx, Exec* ex, cudaStream_t s, int cls, int n_kernels);
 void prof_collect(rpa_ctx* ctx, Exec* ex);
 // mixed_ws: include the split-precision chi0 workspace (a batch supplies its own).
-// qt: q per tail batch (0: qt = qb).
-Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool mixed_ws, int qt = 0);
-int choose_qb(const rpa_job* j, int n_slices, size_t cap);
-int choose_qt(const rpa_job* j, int qb, int n_slices, size_t cap);
+// qt: q per tail batch (0: qt = qb).  bj: the job's frequency-batched chi0, if any.
+Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool mixed_ws, int qt = 0,
+                   const BinJob* bj = nullptr);
+int choose_qb(const rpa_job* j, int n_slices, size_t cap, const BinJob* bj = nullptr);
+int choose_qt(const rpa_job* j, int qb, int n_slices, size_t cap, const BinJob* bj = nullptr);
+// Builds the frequency-batched plan of a split-precision job (band energies
+// read back from the device when they live there) and its per-q tables in
+// ex.hbin; bj.on stays false when the context turns it off or it saves nothing.
+rpa_status bin_job_build(rpa_ctx* ctx, Exec& ex, const rpa_job* j, BinJob& bj);
 Bufs carve(void* ws, const rpa_job* j, const Layout& L);
 size_t sync_ws_cap(rpa_ctx* ctx);
 size_t tables_bytes(const rpa_job* j);

@@ -199,5 +199,83 @@ __device__ __forceinline__ void slice_unit(const SliceArgs& a, long idx) {
   }
 }
 
+// ------------------------------------------- frequency-batched operand ----
+// The transitions of a q are grouped into bins of their energy (positions u
+// of a permuted K range, bin b holding [u0[b], u0[b+1]), padded to whole
+// K-blocks); bin b's weighted operand is needed only for its own skeleton
+// frequencies (slots).  One launch writes slots [g0, g0 + G[b]) of every
+// bin: the digit planes of bin b go to S + aoff[b], blocked as
+//   [slot g - g0][I = P/128][K-block of the bin][plane][4 KB core-matrix block],
+// i.e. each bin is a weighted operand of its own over its K range.
+constexpr int SB_MAX_BINS = 16;
+struct SliceBinArgs {
+  int cplx, Npad, Kr, s, n_kb, nb, g0, rmax, Kt;
+  const int* cfix;               // [Npad][Kr], positions in bin order
+  const int* eC;                 // [Npad] raw row maxima of the FP64 exponent field of C
+  const unsigned long long* wx;  // [rmax][Kt] skeleton weights (mantissa | exponent << 32)
+  const int* eAraw;              // [nb][rmax][Npad] raw row maxima of (exponent of c) + (exponent of w)
+  uint16_t* S;
+  int kb0[SB_MAX_BINS + 1];  // first K-block of each bin (kb0[nb] = n_kb)
+  int G[SB_MAX_BINS];        // slots of each bin in this launch
+  long aoff[SB_MAX_BINS];    // bin's plane offset in S (uint16 units)
+};
+
+template <bool CPLX>
+__device__ __forceinline__ void slice_unit_bin(const SliceBinArgs& a, long idx) {
+  constexpr int tpg = CPLX ? 8 : 16;  // positions per K-block
+  const int P = (int)(idx % a.Npad);
+  const int kb = (int)(idx / a.Npad);
+  int b = 0;
+  while (b + 1 < a.nb && a.kb0[b + 1] <= kb) ++b;
+  const int G = a.G[b];
+  if (G <= 0) return;
+  const int kbl = kb - a.kb0[b];
+  const long nkb = a.kb0[b + 1] - a.kb0[b];
+  const long nI = a.Npad / 128;
+  const int4* src = reinterpret_cast<const int4*>(a.cfix + (long)P * a.Kr + (long)kb * 16);
+  int cv[16];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int4 x = src[v];
+    cv[4 * v] = x.x;
+    cv[4 * v + 1] = x.y;
+    cv[4 * v + 2] = x.z;
+    cv[4 * v + 3] = x.w;
+  }
+  const int rc = a.eC[P];
+  const int eC = rc ? rc - 1022 : -2000;
+  const long u0 = (long)kb * tpg;
+  for (int gl = 0; gl < G; ++gl) {
+    const int g = a.g0 + gl;
+    const int ra = a.eAraw[((long)b * a.rmax + g) * a.Npad + P];
+    const int eA = ra > 0 ? ra - 2044 + 1 : -2000;
+    const int shbase = 30 + eA - eC;
+    const unsigned long long* wr = a.wx + (long)g * a.Kt + u0;
+    uint32_t px[MAX_S][8];
+    long long wm_prev = 0;
+    int sh_prev = 0;
+#pragma unroll
+    for (int v = 0; v < tpg; ++v) {
+      const unsigned long long x = __ldg(wr + v);
+      const long long wmv = (long long)(uint32_t)x;
+      const int shv = shbase - (int)(uint32_t)(x >> 32);
+      if constexpr (CPLX) {
+        pair_x(round_shift(cv[2 * v], wmv, shv), round_shift(cv[2 * v + 1], wmv, shv), v, a.s, px);
+      } else if ((v & 1) == 0) {
+        wm_prev = wmv;
+        sh_prev = shv;
+      } else {
+        pair_x(round_shift(cv[v - 1], wm_prev, sh_prev), round_shift(cv[v], wmv, shv), v >> 1, a.s, px);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < MAX_S; ++i) {
+      if (i >= a.s) break;
+      uint16_t* blk = a.S + a.aoff[b] + ((((long)gl * nI + (P >> 7)) * nkb + kbl) * a.s + i) * 2048;
+      store_core_rows(blk, P & 127, px[i]);
+    }
+  }
+}
+
 }  // namespace
 }  // namespace rpa

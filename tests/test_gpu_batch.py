@@ -5,7 +5,8 @@ tensor-core launches, replayed from a captured CUDA graph.
   per-element arithmetic order).
 * Mixed jobs: the exact accumulator levels make chi0 independent of the split-K
   plan up to the FP32 level-3 group and the float-float flush, so the batch and
-  the single-job E_c agree far inside the 1 microhartree bar; 1e-9 Ha here.
+  the single-job E_c (per-frequency chi0, chi0_freq = 1, as in the batch)
+  agree far inside the 1 microhartree bar; 1e-9 Ha here.
 * The graph replay gives the same numbers as the eager first call, and picks
   up new frequency tables (same shapes and pointers) written before the replay.
 """
@@ -44,7 +45,7 @@ def test_batch_matches_single_jobs(rpa):
     for i, p in enumerate(probs):
         t = rpa.upload_problem(p)
         jobs.append(rpa.job_from_problem(p, t, prec=rpa.PREC_MIXED if i % 3 != 2 else rpa.PREC_FP64))
-    with rpa.Context(0) as c:
+    with rpa.Context(0, chi0_freq=1) as c:
         single = np.array([c.energy(j)["Ec"] for j in jobs])
         n0 = c.launches
         e1 = c.energy_batch(jobs)  # eager, tuned, then captured
@@ -68,7 +69,7 @@ def test_batch_matches_single_jobs(rpa):
 def test_batch_replay_reads_new_tables(rpa):
     probs = _instances()[:3]
     jobs = [rpa.job_from_problem(p, rpa.upload_problem(p), prec=rpa.PREC_MIXED) for p in probs]
-    with rpa.Context(0) as c:
+    with rpa.Context(0, chi0_freq=1) as c:
         c.energy_batch(jobs)
         c.energy_batch(jobs)
         # same shapes and device pointers, new frequency grid: a replay must see it

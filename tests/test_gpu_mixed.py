@@ -133,11 +133,13 @@ def test_mixed_energy_pipelined_slicing(rpa):
     planes of each next q are written by the slicer warps of the current q's
     launch, so the job has one standalone weighted-slicing launch plus the
     five preparation launches per q.  E_c and every term against the oracle,
-    and bit-identical on a second run."""
+    and bit-identical on a second run.  Per-frequency chi0 (chi0_freq = 1);
+    the frequency-batched form of the same pipeline is tested in
+    test_gpu_freq.py."""
     p = synth.make_problem("pipe", is_complex=True, n_aux=384, n_occ=4, n_virt=24,
                            grid=synth.regular_kq_grid((2, 2, 1)), n_w=16, seed=47)
     job = rpa.job_from_problem(p, rpa.upload_problem(p), prec=rpa.PREC_MIXED)
-    with rpa.Context(0) as c:
+    with rpa.Context(0, chi0_freq=1) as c:
         c.profile(True)
         r = c.energy(job)
         prof = c.profile_read()

@@ -5,9 +5,11 @@ Each result must be the same alone and in the mix: FP64 jobs bit for bit (the
 same kernels run on the job's own lane, whatever else shares the device),
 mixed-precision jobs within 1e-9 Ha (far inside the 1 microhartree bar; the
 split-K plan of a q may differ between the synchronous and the lane
-workspace).  Every served result is also checked against the CPU oracle:
-FP64 jobs at 1e-10 relative, mixed jobs within 1 microhartree.  Jobs submitted together must overlap on the device, admission
-must respect the HBM cap, and the latency statistics must be filled in.
+workspace).  The solo runs use the per-frequency chi0 of the served path
+(chi0_freq = 1).  Every served result is also checked against the CPU
+oracle: FP64 jobs at 1e-10 relative, mixed jobs within 1 microhartree.
+Jobs submitted together must overlap on the device, admission must respect
+the HBM cap, and the latency statistics must be filled in.
 """
 import numpy as np
 import pytest
@@ -55,7 +57,7 @@ def _check_oracle(rpa, job, p, Ec):
 def test_served_results_equal_alone(rpa):
     probs = []
     jobs = _jobs(rpa, problems=probs)
-    with rpa.Context(0) as c:
+    with rpa.Context(0, chi0_freq=1) as c:
         alone = [c.energy(j)["Ec"] for j in jobs]
     with rpa.Context(0, max_inflight=8) as c:
         tickets = [c.submit(j) for j in jobs]
@@ -103,7 +105,7 @@ def test_failed_job_does_not_disturb_the_others(rpa):
     """A job whose V(q) is indefinite fails alone (RPA_E_NOTPD with its q) while
     the jobs around it in the stream complete with their solo results."""
     jobs = _jobs(rpa, n=5, seed=94)
-    with rpa.Context(0) as c:
+    with rpa.Context(0, chi0_freq=1) as c:
         alone = [c.energy(j)["Ec"] for j in jobs]
     p = synth.make_problem("bad", is_complex=True, n_aux=48, n_occ=2, n_virt=5, grid=synth.regular_kq_grid((2, 1, 1)),
                            n_w=4, seed=95)

@@ -27,11 +27,17 @@ def rpa():
 
 
 def _sharded(ctx, job, world):
+    """Each rank's rows as energy_sharded computes them (its q-block through
+    gpu_rows over sub_job), summed as the all-reduce of the ranks' tables
+    would, then the fixed-order quadrature."""
     n_q, n_w = job.s.n_q, job.s.n_w
+    rows = shard.gpu_rows(ctx, job)
     table = np.zeros((n_q, n_w))
-    for rank in range(world):
-        _, t = shard.energy_sharded(n_q, n_w, job.w_q, job.zeta_w, shard.gpu_rows(ctx, job), rank, world)
-        table += t  # what the all-reduce of the ranks' tables adds up
+    for qs in shard.q_blocks(n_q, world):
+        part = np.zeros((n_q, n_w))
+        if len(qs):
+            part[qs[0]:qs[-1] + 1] = rows(list(qs))
+        table += part
     return shard.quadrature(table, job.w_q, job.zeta_w), table
 
 
@@ -53,7 +59,8 @@ def test_sharded_mixed_close_to_unsharded(rpa):
     p = synth.make_problem("shm", is_complex=True, n_aux=96, n_occ=3, n_virt=12,
                            grid=synth.regular_kq_grid((2, 2, 1)), n_w=4, seed=72)
     job = rpa.job_from_problem(p, rpa.upload_problem(p), prec=rpa.PREC_MIXED)
-    with rpa.Context(0) as c:
+    # per-frequency chi0: the frequency-batched plan depends on the q-points of the (sub-)job
+    with rpa.Context(0, chi0_freq=1) as c:
         full = c.energy(job)
         Ec, table = _sharded(c, job, 2)
     assert abs(Ec - full["Ec"]) <= 1e-9
