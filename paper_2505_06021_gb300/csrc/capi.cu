@@ -242,7 +242,7 @@ rpa_status validate_job(const rpa_job* j, char* msg, size_t len) {
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace cap of the synchronous calls (the serving lanes use a smaller one).
-size_t sync_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap, (size_t)64 << 30); }
+size_t sync_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap, (size_t)96 << 30); }
 
 Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool mixed_ws, int qt, const BinJob* bj) {
   Layout L{};
@@ -269,28 +269,20 @@ Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool m
   if (binned) L.dtab = 0;  // the frequency-batched chi0 forms its own weights
   if (j->prec == RPA_PREC_MIXED) {
     L.Vc = al(es * NN * qt);  // the inverse-form tail keeps a copy of V(q)
-    if (mixed_ws) {
+    if (mixed_ws && !binned) {
       BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, (int)nov, j->n_k, j->n_w, 1};
       L.slice_cap = ws_cap / 2;
-      L.mixed = binned ? al(binned_workspace_bytes(g, bj->plan, bj->Kt_max, bj->np_max, n_slices, L.slice_cap,
-                                                   false))
-                       : al(mixed_workspace_bytes(g, n_slices, L.slice_cap));
+      L.mixed = al(mixed_workspace_bytes(g, n_slices, L.slice_cap));
     }
   }
   L.ao = al(ao_region_bytes(j, qb));
   L.total = L.meta + L.dtab + L.chi + L.T + L.L + L.Vc + 2 * (L.stageC + L.stageV) + L.eps + L.mixed + L.ao;
-  if (L.mixed && qb >= 2 && binned) {
-    // two alternating regions (the next q's weighted planes written during the
-    // current q's tensor-core launch) when all skeletons fit in one round
+  if (mixed_ws && binned) {
+    // the frequency-batched chi0 takes what the cap leaves (pipelined when that suffices)
     BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, (int)nov, j->n_k, j->n_w, 1};
-    if (binned_one_round(g, bj->plan, bj->Kt_max, bj->np_max, n_slices, L.slice_cap)) {
-      const size_t m2 =
-          al(binned_workspace_bytes(g, bj->plan, bj->Kt_max, bj->np_max, n_slices, L.slice_cap, true));
-      if (m2 > L.mixed && L.total - L.mixed + m2 <= ws_cap) {
-        L.total += m2 - L.mixed;
-        L.mixed = m2;
-      }
-    }
+    const size_t budget = ws_cap > L.total ? ws_cap - L.total : 0;
+    L.mixed = al(binned_workspace_bytes(g, bj->plan, bj->Kt_max, bj->np_max, n_slices, budget));
+    L.total += L.mixed;
   } else if (L.mixed && qb >= 2) {
     // two alternating regions (the next q's operand written during the
     // current q's tensor-core launch) when they fit under the cap
@@ -571,7 +563,7 @@ static rpa_status run_chi(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs&
                          j->zeta_k, b.status};
     }
     uint64_t nl = 0;
-    CK(launch_chi0_binned(mq.data(), nq, bj->plan, n_slices, b.mixed, b.mixed_bytes, b.slice_cap, b.status, &nl, s,
+    CK(launch_chi0_binned(mq.data(), nq, bj->plan, n_slices, b.mixed, b.mixed_bytes, b.status, &nl, s,
                           pex ? &hook : nullptr));
     ctx->launches += nl;
     return RPA_OK;

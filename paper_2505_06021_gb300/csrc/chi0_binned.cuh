@@ -6,21 +6,24 @@
 // weighted contraction of bin b's transitions at skeleton r.  On the device:
 //   1. ecrow_kernel     row maxima of C's exponent field (natural order);
 //   2. perm_kernel      every transition's position in bin order (a warp per
-//                       (k-pair, i) row, ranks by warp matching, stable);
+//                       (k-pair, i) row, ranks by warp matching, stable) and
+//                       its energy at that position;
 //   3. wskel_kernel     the skeleton weights zeta_k |d(D_u, w_skel)| per
 //                       position, packed as 31-bit mantissa and exponent;
-//   4. cfix_bin_kernel  fixed-point C gathered into bin order and the row
-//                       maxima of the weighted operand per (bin, skeleton);
-//   5. slice_kernel     the digit planes of C (the B operand, unchanged code);
-//   6. per round: slice_bin_kernel (bin b's weighted planes for its skeletons
+//   4. cfix_scatter_kernel  fixed-point C, read in its natural order
+//                       (coalesced) and written to the bin-order positions;
+//   5. erow_bin_kernel  the row maxima of the weighted operand per (bin,
+//                       skeleton), from the fixed-point values in bin order;
+//   6. slice_kernel     the digit planes of C (the B operand, unchanged code);
+//   7. per round: slice_bin_kernel (bin b's weighted planes for its skeletons
 //      of the round) and one chi0_tc_kernel whose segments are the bins (each
 //      reads B at its own K offset);
-//   7. reduce_bin_kernel: per element the split-K partials of every (b, r),
+//   8. reduce_bin_kernel: per element the split-K partials of every (b, r),
 //      scaled by their exponents and combined with coef into all n_w
 //      frequencies in FP64, Hermitian store.
 // With all skeletons in one round and two workspace regions, q+1's weighted
 // planes are written by the slicer warps of q's tensor-core launch (its
-// steps 1-5 run before that launch).  Included by kernels_mixed.cu.
+// steps 1-6 run before that launch).  Included by kernels_mixed.cu.
 #pragma once
 
 namespace rpa {
@@ -54,12 +57,14 @@ __global__ void __launch_bounds__(256) ecrow_kernel(int cplx, int N, int n_ov, i
 // Position of every transition in bin order.  One warp per (k-pair jj,
 // occupied i) row; bin b's transitions of the row go, in order of a, to
 // rowoff[row][b] .. rowoff[row][b] + cnt[row][b] - 1 (both from the host
-// plan).  A count that disagrees with the plan sets the status word and the
-// position is not written (no access outside the bin's range).
+// plan): inv[jj n_ov + t] = position (-1 if not placed), dpos[position] = D
+// (dpos stays 0 at padding positions).  A count that disagrees with the plan
+// sets the status word and the position is not written (no access outside
+// the bin's range).
 __global__ void __launch_bounds__(256) perm_kernel(int n_k, int n_occ, int n_virt, int nb,
                                                    const __grid_constant__ BinEdges e, const double* eps_occ,
                                                    const double* eps_virt, const int* kidx, const int* kqidx,
-                                                   const int* rowtab, int* perm, double* dpos, int* status) {
+                                                   const int* rowtab, int* inv, double* dpos, int* status) {
   __shared__ int run[8][SB_MAX_BINS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long nrow = (long)n_k * n_occ;
@@ -87,13 +92,14 @@ __global__ void __launch_bounds__(256) perm_kernel(int n_k, int n_occ, int n_vir
     const int below = __popc(peers & ((1u << lane) - 1u));
     if (act) {
       const int r = run[warp][b] + below;
+      int pos = -1;
       if (r < cnt[b]) {
-        const long pos = (long)off[b] + r;
-        perm[pos] = jj * n_ov + i * n_virt + a;
+        pos = off[b] + r;
         dpos[pos] = D;
       } else {
         atomicCAS(status, 0, 1 + STATUS_PLAN);
       }
+      inv[(long)jj * n_ov + i * n_virt + a] = pos;
     }
     __syncwarp();
     if (act && below == 0) run[warp][b] += __popc(peers);
@@ -107,19 +113,20 @@ struct BinPos {
 };
 
 // Skeleton weights w = zeta_k |d(D_u, w_skel[b][g])| of every position u and
-// slot g < rmax (zero for padding and for slots past the bin's rank), as a
-// 31-bit mantissa and exponent: w = wm 2^(ew - 31), wx = wm | ew << 32.
-__global__ void __launch_bounds__(256) wskel_kernel(int Kt, int rmax, int nb, BinPos bp, const int* perm,
-                                                    const double* dpos, const double* skel_om, double zeta_k,
-                                                    unsigned long long* wx) {
+// slot g < rmax (zero for padding, D = 0, and for slots past the bin's rank),
+// as a 31-bit mantissa and exponent: w = wm 2^(ew - 31), wx = wm | ew << 32.
+__global__ void __launch_bounds__(256) wskel_kernel(int Kt, int rmax, int nb, BinPos bp, const double* dpos,
+                                                    const double* skel_om, double zeta_k, unsigned long long* wx,
+                                                    int16_t* ewx) {
   const long total = (long)rmax * Kt;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
     const int g = (int)(idx / Kt), u = (int)(idx - (long)g * Kt);
     int b = 0;
     while (b + 1 < nb && bp.u0[b + 1] <= u) ++b;
     unsigned long long out = (unsigned long long)(uint32_t)(-2000) << 32;
-    if (g < bp.rank[b] && perm[u] >= 0) {
-      const double D = dpos[u], om = skel_om[b * rmax + g];
+    const double D = dpos[u];
+    if (g < bp.rank[b] && D > 0.0) {
+      const double om = skel_om[b * rmax + g];
       const double w = zeta_k * (4.0 * D / (D * D + om * om));
       const unsigned long long bits = (unsigned long long)__double_as_longlong(w);
       const int E = (int)((bits >> 52) & 0x7ff);
@@ -134,6 +141,7 @@ __global__ void __launch_bounds__(256) wskel_kernel(int Kt, int rmax, int nb, Bi
       }
     }
     wx[idx] = out;
+    ewx[idx] = (int16_t)(int)(uint32_t)(out >> 32);
   }
 }
 
@@ -148,59 +156,122 @@ __device__ __forceinline__ int fix_of(unsigned long long cb, int eC) {
   return (cb >> 63) ? -m : m;
 }
 
-// Fixed-point C in bin order and the raw row maxima of the weighted operand
-// (exponent field of c + exponent of w + 1022) per (bin, skeleton slot).
-// Block: 8 rows (a warp each) x one part (a position range inside one bin;
-// parts[3 y] = bin, parts[3 y + 1 .. 3 y + 2] = range).
-__global__ void __launch_bounds__(256) cfix_bin_kernel(int cplx, int N, int Npad, int n_ov, int Kr, int Kt, int rmax,
-                                                       const int* parts, const int* rankb, const double* const* C,
-                                                       const int* perm, const int* eCraw,
-                                                       const unsigned long long* wx, int* cfix, int* eAraw) {
+// Fixed-point C in bin order: C read in its natural order (coalesced, a k-pair
+// and t range per block, 8 rows of a warp each), each value written to its
+// bin-order position (a row's values of one bin are contiguous there).  Rows
+// N..Npad-1 are written as zeros; padding positions are zeroed by
+// erow_bin_kernel.
+__global__ void __launch_bounds__(256) cfix_scatter_kernel(int cplx, int N, int Npad, int n_ov, int Kr, int TP,
+                                                           const double* const* C, const int* inv, const int* eCraw,
+                                                           int* cfix) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int P = blockIdx.x * 8 + warp;
   if (P >= Npad) return;
-  const int b = parts[3 * blockIdx.y], u0 = parts[3 * blockIdx.y + 1], u1 = parts[3 * blockIdx.y + 2];
-  const int R = rankb[b];
+  const int j = blockIdx.y / TP, tp = blockIdx.y - j * TP;
+  const int t0 = (int)((long)tp * n_ov / TP), t1 = (int)((long)(tp + 1) * n_ov / TP);
   const int rc = P < N ? eCraw[P] : 0;
   const int eC = rc ? rc - 1022 : -2000;
-  int m[BIN_MAX_RANK];
-#pragma unroll
-  for (int g = 0; g < BIN_MAX_RANK; ++g) m[g] = 0;
+  const int* invj = inv + (long)j * n_ov;
   int* out = cfix + (long)P * Kr;
-  for (int u = u0 + lane; u < u1; u += 32) {
-    const int pt = perm[u];
-    int v0 = 0, v1 = 0, Ec = 0;
-    if (P < N && pt >= 0) {
-      const int j = pt / n_ov, t = pt - j * n_ov;
-      if (cplx) {
+  for (int t = t0 + lane; t < t1; t += 32) {
+    const int pos = invj[t];
+    if (pos < 0) continue;
+    if (cplx) {
+      int2 v = make_int2(0, 0);
+      if (P < N) {
         const ulonglong2 x = reinterpret_cast<const ulonglong2*>(C[j])[(long)P * n_ov + t];
-        v0 = fix_of(x.x, eC);
-        v1 = fix_of(x.y, eC);
-        Ec = max((int)((x.x >> 52) & 0x7ff), (int)((x.y >> 52) & 0x7ff));
-      } else {
-        const unsigned long long x = reinterpret_cast<const unsigned long long*>(C[j])[(long)P * n_ov + t];
-        v0 = fix_of(x, eC);
-        Ec = (int)((x >> 52) & 0x7ff);
+        v = make_int2(fix_of(x.x, eC), fix_of(x.y, eC));
       }
-    }
-    if (cplx)
-      *reinterpret_cast<int2*>(out + 2 * (long)u) = make_int2(v0, v1);
-    else
-      out[u] = v0;
-    if (Ec) {
-#pragma unroll
-      for (int g = 0; g < BIN_MAX_RANK; ++g) {
-        if (g >= R) break;
-        const int ee = (int)(uint32_t)(__ldg(wx + (long)g * Kt + u) >> 32);
-        m[g] = max(m[g], Ec + ee + 1022);
-      }
+      *reinterpret_cast<int2*>(out + 2 * (long)pos) = v;
+    } else {
+      int v = 0;
+      if (P < N) v = fix_of(reinterpret_cast<const unsigned long long*>(C[j])[(long)P * n_ov + t], eC);
+      out[pos] = v;
     }
   }
+}
+
+// Raw row maxima of the weighted operand per (bin, skeleton slot) from the
+// fixed-point values: |c_fix| < 2^bitlen, |w| < 2^ee, so
+// raw = max (bitlen + ee) + eC + 2014 bounds |c w| < 2^(raw - 2044) for the
+// values the slicing actually converts (the convention of the per-frequency
+// path, where raw = exponent field of c + ee + 1022).  Block: EROW_BIN_ROWS
+// rows (each warp several) x one part (a position range inside one bin); the
+// part's weight exponents are staged in shared memory once for all its rows
+// (slot 0's exponent is -2000 exactly at padding positions, which are zeroed
+// here).
+constexpr int EROW_BIN_ROWS = 64;
+constexpr int EROW_ILP = 4;
+__global__ void __launch_bounds__(256) erow_bin_kernel(int cplx, int Npad, int Kr, int Kt, int rmax,
+                                                       const int* parts, const int* rankb, const int* eCraw,
+                                                       const int16_t* ewx, int* cfix, int* eAraw) {
+  extern __shared__ int16_t ees[];  // [R][part length]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = parts[3 * blockIdx.y], u0 = parts[3 * blockIdx.y + 1], u1 = parts[3 * blockIdx.y + 2];
+  const int len = u1 - u0;
+  const int R = rankb[b];
+  // positions and parts are multiples of 8, Kt too: 16-byte copies of the exponents
+  const int len8 = len >> 3;
+  for (int i = threadIdx.x; i < R * len8; i += blockDim.x) {
+    const int g = i / len8, c = i - g * len8;
+    *reinterpret_cast<uint4*>(ees + g * len + 8 * c) =
+        __ldg(reinterpret_cast<const uint4*>(ewx + (long)g * Kt + u0) + c);
+  }
+  __syncthreads();
+  for (int rr = 0; rr < EROW_BIN_ROWS / 8; ++rr) {
+    const int P = blockIdx.x * EROW_BIN_ROWS + rr * 8 + warp;
+    if (P >= Npad) break;
+    int m[BIN_MAX_RANK];
 #pragma unroll
-  for (int g = 0; g < BIN_MAX_RANK; ++g) {
-    if (g >= R) break;
-    const int r = __reduce_max_sync(0xffffffffu, m[g]);
-    if (lane == 0 && r > 0) atomicMax(eAraw + ((long)b * rmax + g) * Npad + P, r);
+    for (int g = 0; g < BIN_MAX_RANK; ++g) m[g] = -100000;
+    int* row = cfix + (long)P * Kr;
+    // EROW_ILP positions per lane per step: their loads are issued together
+    for (int ub = 0; ub < len; ub += 32 * EROW_ILP) {
+      int av[EROW_ILP];
+#pragma unroll
+      for (int k = 0; k < EROW_ILP; ++k) {
+        const int uu = ub + k * 32 + lane;
+        av[k] = 0;
+        if (uu < len && ees[uu] != -2000) {
+          const long u = u0 + uu;
+          if (cplx) {
+            const int2 v = *reinterpret_cast<const int2*>(row + 2 * u);
+            av[k] = max(abs(v.x), abs(v.y));
+          } else {
+            av[k] = abs(row[u]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < EROW_ILP; ++k) {
+        const int uu = ub + k * 32 + lane;
+        if (uu >= len) break;
+        if (ees[uu] == -2000) {  // padding position
+          const long u = u0 + uu;
+          if (cplx)
+            *reinterpret_cast<int2*>(row + 2 * u) = make_int2(0, 0);
+          else
+            row[u] = 0;
+          continue;
+        }
+        if (av[k] == 0) continue;
+        const int bitlen = 32 - __clz(av[k]);
+#pragma unroll
+        for (int g = 0; g < BIN_MAX_RANK; ++g) {
+          if (g >= R) break;
+          m[g] = max(m[g], bitlen + (int)ees[g * len + uu]);
+        }
+      }
+    }
+    const int rc = eCraw[P];
+    if (!rc) continue;  // an all-zero row: no weighted contributions
+    const int eC = rc - 1022;
+#pragma unroll
+    for (int g = 0; g < BIN_MAX_RANK; ++g) {
+      if (g >= R) break;
+      const int r = __reduce_max_sync(0xffffffffu, m[g]);
+      if (lane == 0 && r > -100000) atomicMax(eAraw + ((long)b * rmax + g) * Npad + P, max(0, r + eC + 2014));
+    }
   }
 }
 
@@ -215,7 +286,13 @@ __global__ void __launch_bounds__(256, 2) slice_bin_kernel(SliceBinArgs a) {
 }
 
 // chi0(w) for every frequency from the partials of every (bin, skeleton):
-// one thread per element of a lower tile.
+// one thread per element of a lower tile.  The combination sum_{b,r} coef x
+// (n_w x sum_b rank_b multiply-adds per element) runs in float-float
+// arithmetic on the FP32 pipe (GB300's FP64 pipe is 1/58 of it): coef is held
+// as an unevaluated sum of two floats, each product is formed exactly by
+// Dekker's TwoProd (fmaf), and sums use Knuth's TwoSum; about 2^-44 relative,
+// far below the split-precision error of the partials.  Frequencies are
+// taken in groups of at most RED_WG along grid y (registers).
 struct RedBin {
   int cplx, N, Npad, n_tiles, nb, rmax, n_w, G;  // G: skeleton slots per round
   int rank[SB_MAX_BINS], nks[SB_MAX_BINS];
@@ -225,12 +302,28 @@ struct RedBin {
   const int* eCraw;
   const double* coef;  // [nb][rmax][n_w]
   double* chi;         // [n_w][N][N]
+  int wg;              // frequencies per group (grid y = groups)
 };
+constexpr int RED_WG = 10;
 
-__global__ void __launch_bounds__(256) reduce_bin_kernel(const __grid_constant__ RedBin rb) {
-  extern __shared__ double cs[];
+// (h, l) += a + b (a, b: a float-float product), Knuth TwoSum then renormalise.
+__device__ __forceinline__ void ff_acc(float& h, float& l, float ph, float pl) {
+  const float s = h + ph;
+  const float bb = s - h;
+  const float e = (h - (s - bb)) + (ph - bb);
+  const float t = e + pl + l;
+  h = s + t;
+  l = t - (h - s);
+}
+
+__global__ void __launch_bounds__(256, 2) reduce_bin_kernel(const __grid_constant__ RedBin rb) {
+  extern __shared__ float2 cs[];  // coefficients as (hi, lo) floats
   const int ncoef = rb.nb * rb.rmax * rb.n_w;
-  for (int i = threadIdx.x; i < ncoef; i += blockDim.x) cs[i] = rb.coef[i];
+  for (int i = threadIdx.x; i < ncoef; i += blockDim.x) {
+    const double c = rb.coef[i];
+    const float h = (float)c;
+    cs[i] = make_float2(h, (float)(c - (double)h));
+  }
   __syncthreads();
   const int ncols = rb.cplx ? 64 : 128;
   const int per_tile = 128 * ncols / 256;
@@ -241,64 +334,82 @@ __global__ void __launch_bounds__(256) reduce_bin_kernel(const __grid_constant__
   tile_ij(rb.cplx, tile, I, J);
   const int P = I * 128 + r, Q = J * ncols + c;
   if (P >= rb.N || Q >= rb.N || Q > P) return;
-  double are[BIN_MAX_RANK], aim[BIN_MAX_RANK];
+  const int w0 = blockIdx.y * rb.wg, nw = min(rb.wg, rb.n_w - w0);
+  float rh[RED_WG], rl[RED_WG], ih[RED_WG], il[RED_WG];
 #pragma unroll
-  for (int w = 0; w < BIN_MAX_RANK; ++w) are[w] = aim[w] = 0.0;
+  for (int w = 0; w < RED_WG; ++w) rh[w] = rl[w] = ih[w] = il[w] = 0.f;
   const int rq = rb.eCraw[Q];
   const int eCQ = rq ? rq - 1022 : -2000;
   for (int b = 0; b < rb.nb; ++b) {
     for (int g = 0; g < rb.rank[b]; ++g) {
+      const int ra = rb.eAraw[((long)b * rb.rmax + g) * rb.Npad + P];
+      if (ra <= 0 || rq == 0) continue;  // a zero row or column: no contribution
       const int g0 = g / rb.G * rb.G, Gs = min(rb.G, rb.rank[b] - g0), gl = g - g0;
       const long it0 = rb.base[b] + (long)g0 * rb.nks[b] * rb.n_tiles;
-      double re = 0.0, im = 0.0;
+      // x = sum over the split-K partials of (hi + lo), as a float-float pair
+      float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f;
       for (int ks = 0; ks < rb.nks[b]; ++ks) {
         const long item = it0 + ((long)ks * Gs + gl) * rb.n_tiles + tile;
         const float* pp = rb.part + item * 2 * 128 * 128 + (long)r * 128;
-        re += (double)pp[c] + (double)pp[128 * 128 + c];
-        if (rb.cplx) im += (double)pp[64 + c] + (double)pp[128 * 128 + 64 + c];
+        ff_acc(xh, xl, pp[c], pp[128 * 128 + c]);
+        if (rb.cplx) ff_acc(yh, yl, pp[64 + c], pp[128 * 128 + 64 + c]);
       }
-      const int ra = rb.eAraw[((long)b * rb.rmax + g) * rb.Npad + P];
-      const int eA = ra > 0 ? ra - 2044 + 1 : -2000;
-      const double sc = -ldexp(1.0, eA + eCQ + 1 - 14);  // x = 2^(e - 7) sum v; chi = -sum conj(a) c
-      re *= sc;
-      im *= sc;
-      const double* cf = cs + ((long)b * rb.rmax + g) * rb.n_w;
+      // scale 2^(eA + eC + 1 - 14) with the sign of chi = -sum conj(a) c (exact)
+      const int sh = (ra - 2044 + 1) + eCQ + 1 - 14;
+      xh = -ldexpf(xh, sh);
+      xl = -ldexpf(xl, sh);
+      yh = -ldexpf(yh, sh);
+      yl = -ldexpf(yl, sh);
+      const float2* cf = cs + ((long)b * rb.rmax + g) * rb.n_w + w0;
 #pragma unroll
-      for (int w = 0; w < BIN_MAX_RANK; ++w) {
-        if (w >= rb.n_w) break;
-        are[w] = fma(cf[w], re, are[w]);
-        aim[w] = fma(cf[w], im, aim[w]);
+      for (int w = 0; w < RED_WG; ++w) {
+        if (w >= nw) break;
+        const float2 k = cf[w];
+        float ph = k.x * xh;
+        float pl = fmaf(k.x, xh, -ph) + fmaf(k.x, xl, k.y * xh);
+        ff_acc(rh[w], rl[w], ph, pl);
+        if (rb.cplx) {
+          ph = k.x * yh;
+          pl = fmaf(k.x, yh, -ph) + fmaf(k.x, yl, k.y * yh);
+          ff_acc(ih[w], il[w], ph, pl);
+        }
       }
     }
   }
   const long NN = (long)rb.N * rb.N;
 #pragma unroll
-  for (int w = 0; w < BIN_MAX_RANK; ++w) {
-    if (w >= rb.n_w) break;
+  for (int w = 0; w < RED_WG; ++w) {
+    if (w >= nw) break;
+    const double re = (double)rh[w] + (double)rl[w];
     if (rb.cplx) {
-      double2* out = reinterpret_cast<double2*>(rb.chi) + (long)w * NN;
-      const double im = P == Q ? 0.0 : aim[w];
-      out[(long)P * rb.N + Q] = make_double2(are[w], im);
-      if (P != Q) out[(long)Q * rb.N + P] = make_double2(are[w], -im);
+      double2* out = reinterpret_cast<double2*>(rb.chi) + (long)(w0 + w) * NN;
+      const double im = P == Q ? 0.0 : (double)ih[w] + (double)il[w];
+      out[(long)P * rb.N + Q] = make_double2(re, im);
+      if (P != Q) out[(long)Q * rb.N + P] = make_double2(re, -im);
     } else {
-      double* out = rb.chi + (long)w * NN;
-      out[(long)P * rb.N + Q] = are[w];
-      if (P != Q) out[(long)Q * rb.N + P] = are[w];
+      double* out = rb.chi + (long)(w0 + w) * NN;
+      out[(long)P * rb.N + Q] = re;
+      if (P != Q) out[(long)Q * rb.N + P] = re;
     }
   }
 }
 
 // ------------------------------------------------------------ host side --
 
-// Workspace of one q of the frequency-batched path.
+// Workspace of the frequency-batched path: per-q regions (the q's tables,
+// fixed-point C, digit planes of C, split-K partials) and weighted-operand
+// buffers (G skeleton slots of every bin).  Pipelined: two of each, so that
+// every tensor-core launch (a round of one q) writes the next round's weighted
+// planes in its slicer warps while the next q's preparation sits in the other
+// region; otherwise one of each and standalone slicing launches.
 struct BinLayout {
-  int Npad, Kt, Kr, n_kb, nb, rmax, G, n_tiles, n_parts, meta_ints;
-  long items;  // partial items (sum over bins of rank x nks_cap x tiles)
-  size_t meta, perm, dpos, wx, eC, eA, cfix, SC, S, part, total;
+  int Npad, Kt, Kr, n_kb, nb, rmax, G, n_tiles, n_parts, meta_ints, nreg;
+  long items;  // partial items of one q (sum over bins of rank x split-K cap x tiles)
+  size_t meta, inv, dpos, wx, ewx, eC, eA, cfix, SC, part, qreg, abuf, total;
 };
 
-BinLayout bin_layout(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int s, size_t slice_cap,
-                     int sms) {
+BinLayout bin_layout_g(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int s, int G, int nreg,
+                       int sms) {
   BinLayout L{};
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
   L.Npad = (g.n_aux + 127) / 128 * 128;
@@ -307,59 +418,83 @@ BinLayout bin_layout(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_pa
   L.n_kb = L.Kr / KB;
   L.nb = p.n_bins;
   L.rmax = p.rmax;
+  L.G = G;
+  L.nreg = nreg;
   L.n_parts = n_parts_max;
   const int nbk = L.Npad / 128;
   L.n_tiles = g.cplx ? nbk * (nbk + 1) : nbk * (nbk + 1) / 2;
   const size_t per_slot = (size_t)s * L.Npad * L.Kr * 2;  // every bin's weighted planes of one slot
-  L.G = (int)std::max<size_t>(1, std::min<size_t>((size_t)L.rmax, slice_cap / std::max<size_t>(per_slot, 1)));
   // split-K cap per bin: enough items to fill the GPU (the partial buffer is sized for it)
   long items = 0;
   const int chunks = (L.n_kb + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
   for (int b = 0; b < L.nb; ++b) {
-    const int Gb = std::min(L.G, p.rank[b]);
+    const int Gb = std::min(G, p.rank[b]);
     const int cap = std::max(1, std::min(chunks, (4 * sms + Gb * L.n_tiles - 1) / std::max(1, Gb * L.n_tiles)));
     items += (long)p.rank[b] * cap * L.n_tiles;
   }
   L.items = items;
   L.meta_ints = 2 * g.n_k * g.n_occ * L.nb + 3 * L.n_parts + SB_MAX_BINS;
   L.meta = al(sizeof(int) * (size_t)L.meta_ints + 64) + al(sizeof(double) * (size_t)L.nb * L.rmax * (1 + g.n_w));
-  L.perm = al(sizeof(int) * (size_t)L.Kt);
+  L.inv = al(sizeof(int) * (size_t)g.n_k * g.n_ov);
   L.dpos = al(sizeof(double) * (size_t)L.Kt);
   L.wx = al(sizeof(unsigned long long) * (size_t)L.rmax * L.Kt);
+  L.ewx = al(sizeof(int16_t) * (size_t)L.rmax * L.Kt);
   L.eC = al(sizeof(int) * (size_t)L.Npad);
   L.eA = al(sizeof(int) * (size_t)L.nb * L.rmax * L.Npad);
   L.cfix = al(sizeof(int) * (size_t)L.Npad * L.Kr);
   L.SC = al(per_slot * (g.cplx ? 2 : 1));
-  L.S = al(per_slot * L.G);
   L.part = al(sizeof(float) * 2 * 128 * 128 * (size_t)items);
-  L.total = L.meta + L.perm + L.dpos + L.wx + L.eC + L.eA + L.cfix + L.SC + L.S + L.part;
+  L.qreg = L.meta + L.inv + L.dpos + L.wx + L.ewx + L.eC + L.eA + L.cfix + L.SC + L.part;
+  L.abuf = al(per_slot * G);
+  L.total = 1024 + nreg * (L.qreg + L.abuf);
   return L;
 }
 
+// Within `budget`: pipelined with every skeleton in one round per q; else one
+// region with every skeleton in one round; else one region with the largest
+// round that fits (G = 1 when nothing fits: the caller reports the shortfall).
+// Pipelining several rounds of one q was measured slower on the slab job (the
+// slicer warps' stores pull the power-capped clock down by more than the
+// standalone slicing costs), so it is not used.
+BinLayout bin_layout(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int s, size_t budget,
+                     int sms) {
+  for (int nreg = 2; nreg >= 1; --nreg) {
+    const BinLayout L = bin_layout_g(g, p, Kt_max, n_parts_max, s, p.rmax, nreg, sms);
+    if (L.total <= budget) return L;
+  }
+  for (int G = p.rmax - 1; G >= 1; --G) {
+    const BinLayout L = bin_layout_g(g, p, Kt_max, n_parts_max, s, G, 1, sms);
+    if (L.total <= budget) return L;
+  }
+  return bin_layout_g(g, p, Kt_max, n_parts_max, s, 1, 1, sms);
+}
+
+// One q's region: tables, exponents, fixed-point C, digit planes of C, partials.
 struct BinRegion {
-  BinLayout L;
-  int* meta_i;  // rowtab [2][n_k n_occ nb] | parts [n_parts][3] | rank [16]
+  int* meta_i;     // rowtab [2][n_k n_occ nb] | parts [n_parts][3] | rank [16]
   double* meta_d;  // skel_om [nb][rmax] | coef [nb][rmax][n_w]
-  int *perm, *eC, *eA, *cfix;
+  int *inv, *eC, *eA, *cfix;
   double* dpos;
   unsigned long long* wx;
-  uint16_t *SC, *S;
+  int16_t* ewx;
+  uint16_t* SC;
   float* part;
 };
 
 BinRegion carve_bin(char* p, const BinLayout& L) {
   BinRegion r;
-  r.L = L;
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
   r.meta_i = (int*)p;
   r.meta_d = (double*)(p + al(sizeof(int) * (size_t)L.meta_ints + 64));
   p += L.meta;
-  r.perm = (int*)p;
-  p += L.perm;
+  r.inv = (int*)p;
+  p += L.inv;
   r.dpos = (double*)p;
   p += L.dpos;
   r.wx = (unsigned long long*)p;
   p += L.wx;
+  r.ewx = (int16_t*)p;
+  p += L.ewx;
   r.eC = (int*)p;
   p += L.eC;
   r.eA = (int*)p;
@@ -368,21 +503,22 @@ BinRegion carve_bin(char* p, const BinLayout& L) {
   p += L.cfix;
   r.SC = (uint16_t*)p;
   p += L.SC;
-  r.S = (uint16_t*)p;
-  p += L.S;
   r.part = (float*)p;
   return r;
 }
 
-constexpr int BIN_PREP_LAUNCHES = 6;  // ecrow, perm, wskel, cfix_bin, slice of C (+ the memsets are not kernels)
+constexpr int BIN_PREP_LAUNCHES = 6;  // ecrow, perm, wskel, cfix_scatter, erow_bin, slice of C
 
-// Steps 1-5 for one q into region R (its meta image already copied there).
-cudaError_t bin_prep(const BinRegion& R, const MixedBinQ& q, const FreqPlan& p, int s, int sms, cudaStream_t st) {
+// Steps 1-6 for one q into region R, after copying its table image there.
+cudaError_t bin_prep(const BinRegion& R, const BinLayout& L, const MixedBinQ& q, const FreqPlan& p, int s, int sms,
+                     cudaStream_t st) {
   const BatchGeom& g = q.g;
   const BinQHost& h = *q.host;
-  const BinLayout& L = R.L;
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(R.perm, 0xFF, sizeof(int) * (size_t)h.Kt, st))) return e;
+  cudaError_t e = cudaMemcpyAsync(R.meta_i, h.meta_i, sizeof(int) * h.n_meta_i, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(R.meta_d, h.meta_d, sizeof(double) * h.n_meta_d, cudaMemcpyHostToDevice, st);
+  if (e) return e;
+  if ((e = cudaMemsetAsync(R.dpos, 0, sizeof(double) * (size_t)h.Kt, st))) return e;
   if ((e = cudaMemsetAsync(R.eC, 0, sizeof(int) * (size_t)L.Npad, st))) return e;
   if ((e = cudaMemsetAsync(R.eA, 0, sizeof(int) * (size_t)L.nb * L.rmax * L.Npad, st))) return e;
   const int TP = g.n_k >= 8 ? 1 : (8 + g.n_k - 1) / g.n_k;
@@ -392,7 +528,7 @@ cudaError_t bin_prep(const BinRegion& R, const MixedBinQ& q, const FreqPlan& p, 
   for (int b = 0; b + 1 < p.n_bins; ++b) be.edge[b] = p.edges[b];
   const long nrow = (long)g.n_k * g.n_occ;
   perm_kernel<<<(unsigned)((nrow + 7) / 8), 256, 0, st>>>(g.n_k, g.n_occ, g.n_virt, p.n_bins, be, q.eps_occ,
-                                                          q.eps_virt, q.kidx, q.kqidx, R.meta_i, R.perm, R.dpos,
+                                                          q.eps_virt, q.kidx, q.kqidx, R.meta_i, R.inv, R.dpos,
                                                           q.status);
   BinPos bp{};
   for (int b = 0; b <= p.n_bins; ++b) bp.u0[b] = h.tb0[b];
@@ -400,12 +536,15 @@ cudaError_t bin_prep(const BinRegion& R, const MixedBinQ& q, const FreqPlan& p, 
   for (int b = 0; b < p.n_bins; ++b) bp.rank[b] = p.rank[b];
   const long nw = (long)L.rmax * h.Kt;
   wskel_kernel<<<(unsigned)std::min<long>((nw + 255) / 256, (long)sms * 16), 256, 0, st>>>(
-      h.Kt, L.rmax, p.n_bins, bp, R.perm, R.dpos, R.meta_d, q.zeta_k, R.wx);
+      h.Kt, L.rmax, p.n_bins, bp, R.dpos, R.meta_d, q.zeta_k, R.wx, R.ewx);
+  cfix_scatter_kernel<<<dim3((unsigned)(L.Npad / 8), (unsigned)(g.n_k * TP)), 256, 0, st>>>(
+      g.cplx, g.n_aux, L.Npad, g.n_ov, h.Kr, TP, q.Cptrs, R.inv, R.eC, R.cfix);
   const int n_parts = h.n_parts;
   const int* parts = R.meta_i + 2 * nrow * p.n_bins;
   const int* rankb = parts + 3 * n_parts;
-  cfix_bin_kernel<<<dim3((unsigned)(L.Npad / 8), (unsigned)n_parts), 256, 0, st>>>(
-      g.cplx, g.n_aux, L.Npad, g.n_ov, h.Kr, h.Kt, L.rmax, parts, rankb, q.Cptrs, R.perm, R.eC, R.wx, R.cfix, R.eA);
+  erow_bin_kernel<<<dim3((unsigned)((L.Npad + EROW_BIN_ROWS - 1) / EROW_BIN_ROWS), (unsigned)n_parts), 256,
+                    sizeof(int16_t) * (size_t)L.rmax * FREQ_PART, st>>>(g.cplx, L.Npad, h.Kr, h.Kt, L.rmax, parts,
+                                                                        rankb, R.eC, R.ewx, R.cfix, R.eA);
   // digits of C (the B operand) in bin order
   SliceArgs sc{g.cplx, L.Npad, g.n_ov, h.Kt, h.Kr, s, g.n_w, 0, 1, g.cplx ? 2 : 1, R.cfix, nullptr,
                nullptr, nullptr, R.SC};
@@ -414,10 +553,10 @@ cudaError_t bin_prep(const BinRegion& R, const MixedBinQ& q, const FreqPlan& p, 
   return cudaGetLastError();
 }
 
-// Weighted planes of round k (slots [k G, k G + G) of every bin) of one q.
-SliceBinArgs bin_slice_args(const BinRegion& R, const MixedBinQ& q, const FreqPlan& p, int s, int k) {
+// Weighted planes of round k (slots [k G, k G + G) of every bin) of one q into A.
+SliceBinArgs bin_slice_args(const BinRegion& R, uint16_t* A, const BinLayout& L, const MixedBinQ& q,
+                            const FreqPlan& p, int s, int k) {
   const BinQHost& h = *q.host;
-  const BinLayout& L = R.L;
   SliceBinArgs a{};
   a.cplx = q.g.cplx;
   a.Npad = L.Npad;
@@ -432,7 +571,7 @@ SliceBinArgs bin_slice_args(const BinRegion& R, const MixedBinQ& q, const FreqPl
   a.eC = R.eC;
   a.wx = R.wx;
   a.eAraw = R.eA;
-  a.S = R.S;
+  a.S = A;
   const long nI = L.Npad / 128;
   long off = 0;
   const int tpk = q.g.cplx ? 8 : 16;
@@ -447,6 +586,11 @@ SliceBinArgs bin_slice_args(const BinRegion& R, const MixedBinQ& q, const FreqPl
   return a;
 }
 
+void launch_slice_bin(const SliceBinArgs& sa, int Npad, int sms, cudaStream_t st) {
+  const long tg = (long)Npad * sa.n_kb;
+  slice_bin_kernel<<<(unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), 256, 0, st>>>(sa);
+}
+
 // Split-K depth of every bin for q (fixed over its rounds): the cost model of
 // the per-frequency path over the first round's segments, or the recorded
 // autotuner choice for this shape class.
@@ -455,14 +599,15 @@ void bin_splits(const BinLayout& L, const MixedBinQ& q, const FreqPlan& p, int s
   const int tpk = q.g.cplx ? 8 : 16;
   std::vector<SegShape> shp;
   std::vector<int> who;
+  const int chunks_all = (L.n_kb + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
   for (int b = 0; b < p.n_bins; ++b) {
     const int nkb = (h.tb0[b + 1] - h.tb0[b]) / tpk;
     nks[b] = 1;
     if (nkb == 0) continue;
     const int chunks = (nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
     const int Gb = std::min(L.G, p.rank[b]);
-    const int cap = std::max(1, std::min(chunks, (4 * sms + Gb * L.n_tiles - 1) / std::max(1, Gb * L.n_tiles)));
-    shp.push_back(SegShape{chunks, Gb, L.n_tiles, cap});
+    const int cap = std::max(1, std::min(chunks_all, (4 * sms + Gb * L.n_tiles - 1) / std::max(1, Gb * L.n_tiles)));
+    shp.push_back(SegShape{chunks, Gb, L.n_tiles, std::min(cap, chunks)});
     who.push_back(b);
   }
   if (shp.empty()) return;
@@ -482,10 +627,9 @@ void bin_splits(const BinLayout& L, const MixedBinQ& q, const FreqPlan& p, int s
 }
 
 // The tensor-core launch of round k of q (segments: the bins with slots in it).
-int bin_tc_params(const BinRegion& R, const MixedBinQ& q, const FreqPlan& p, int s, int k, const int* nks,
-                  const long* base, int* err, TcParams& tp) {
+int bin_tc_params(const BinRegion& R, const uint16_t* A, const BinLayout& L, const MixedBinQ& q, const FreqPlan& p,
+                  int s, int k, const int* nks, const long* base, int* err, TcParams& tp) {
   const BinQHost& h = *q.host;
-  const BinLayout& L = R.L;
   const int tpk = q.g.cplx ? 8 : 16;
   memset(&tp, 0, sizeof tp);
   tp.s = s;
@@ -493,7 +637,7 @@ int bin_tc_params(const BinRegion& R, const MixedBinQ& q, const FreqPlan& p, int
   tp.drop_item = mixed_test_drop_take();
   tp.err = err;
   tp.grp_mask = group_mask(s);
-  const SliceBinArgs sa = bin_slice_args(R, q, p, s, k);
+  const SliceBinArgs sa = bin_slice_args(R, const_cast<uint16_t*>(A), L, q, p, s, k);
   int items = 0;
   for (int b = 0; b < p.n_bins; ++b) {
     const int nkb = (h.tb0[b + 1] - h.tb0[b]) / tpk;
@@ -502,7 +646,7 @@ int bin_tc_params(const BinRegion& R, const MixedBinQ& q, const FreqPlan& p, int
     const int chunks = (nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
     const int cps = (chunks + nks[b] - 1) / nks[b];
     TcSeg& S = tp.seg[tp.n_segs++];
-    S.A = R.S + sa.aoff[b];
+    S.A = A + sa.aoff[b];
     S.B = R.SC;
     S.nI = L.Npad / 128;
     S.part = R.part + (base[b] + (long)sa.g0 * nks[b] * L.n_tiles) * 2 * 128 * 128;
@@ -521,29 +665,20 @@ int bin_tc_params(const BinRegion& R, const MixedBinQ& q, const FreqPlan& p, int
   return items;
 }
 
-size_t bin_region_bytes(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int s, size_t slice_cap) {
-  return bin_layout(g, p, Kt_max, n_parts_max, s, slice_cap, num_sms()).total;
-}
-
 }  // namespace
 
 size_t binned_workspace_bytes(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int n_slices,
-                              size_t slice_cap, bool two_regions) {
-  const size_t one = bin_region_bytes(g, p, Kt_max, n_parts_max, n_slices, slice_cap);
-  return 1024 + (two_regions ? 2 : 1) * one;
+                              size_t budget) {
+  return bin_layout(g, p, Kt_max, n_parts_max, n_slices, budget, num_sms()).total;
 }
 
-bool binned_one_round(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int n_slices,
-                      size_t slice_cap) {
-  return bin_layout(g, p, Kt_max, n_parts_max, n_slices, slice_cap, num_sms()).G >= p.rmax;
-}
-
-// chi0 of n q (one geometry) through the frequency-batched plan, one q after
-// another; with a single round per q and room for two regions, q+1's weighted
-// planes are written inside q's tensor-core launch.
+// chi0 of n q (one geometry) through the frequency-batched plan.  The launches
+// run as a sequence of units (q, round); with the pipelined layout each
+// tensor-core launch writes the next unit's weighted planes in its slicer
+// warps (the first unit's are a launch of their own), and the next q's
+// preparation runs before the last launch of the current q.
 cudaError_t launch_chi0_binned(const MixedBinQ* qs, int n, const FreqPlan& p, int s, void* work, size_t work_bytes,
-                               size_t slice_cap, int* status, uint64_t* n_launch, cudaStream_t st,
-                               const LaunchHook* hook) {
+                               int* status, uint64_t* n_launch, cudaStream_t st, const LaunchHook* hook) {
   auto hb = [&]() {
     if (hook) hook->begin(hook->user, st);
   };
@@ -555,113 +690,125 @@ cudaError_t launch_chi0_binned(const MixedBinQ* qs, int n, const FreqPlan& p, in
   if ((size_t)p.n_bins * p.rmax * qs[0].g.n_w * sizeof(double) > 48 * 1024) return cudaErrorInvalidValue;
   const int sms = num_sms();
   if (cudaError_t ea = tc_smem_attr()) return ea;
+  {
+    static std::once_flag once;
+    static cudaError_t ea2 = cudaSuccess;
+    std::call_once(once, [] {
+      ea2 = cudaFuncSetAttribute(erow_bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(int16_t) * BIN_MAX_RANK * FREQ_PART));
+    });
+    if (ea2) return ea2;
+  }
   int Kt_max = 0, np_max = 0;
   for (int i = 0; i < n; ++i) {
     Kt_max = std::max(Kt_max, qs[i].host->Kt);
     np_max = std::max(np_max, qs[i].host->n_parts);
   }
-  const BinLayout L = bin_layout(qs[0].g, p, Kt_max, np_max, s, slice_cap, sms);
-  const bool pipe = n >= 2 && L.G >= p.rmax && 1024 + 2 * L.total <= work_bytes;
-  if (1024 + L.total > work_bytes) return cudaErrorMemoryAllocation;
+  const BinLayout L = bin_layout(qs[0].g, p, Kt_max, np_max, s, work_bytes, sms);
+  if (L.total > work_bytes) return cudaErrorMemoryAllocation;
+  const bool pipe = L.nreg == 2;
   char* base = (char*)work;
   int* err = (int*)base;
-  BinRegion R[2] = {carve_bin(base + 1024, L), carve_bin(base + 1024 + (pipe ? L.total : 0), L)};
+  BinRegion R[2];
+  uint16_t* AB[2];
+  for (int r = 0; r < L.nreg; ++r) {
+    R[r] = carve_bin(base + 1024 + r * L.qreg, L);
+    AB[r] = (uint16_t*)(base + 1024 + L.nreg * L.qreg + r * L.abuf);
+  }
+  if (!pipe) {
+    R[1] = R[0];
+    AB[1] = AB[0];
+  }
   uint64_t nl = 0;
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int) * 4, st);
   if (e != cudaSuccess) return e;
-  auto meta_copy = [&](const BinRegion& r, const MixedBinQ& q) -> cudaError_t {
-    const BinQHost& h = *q.host;
-    cudaError_t ee = cudaMemcpyAsync(r.meta_i, h.meta_i, sizeof(int) * h.n_meta_i, cudaMemcpyHostToDevice, st);
-    if (ee == cudaSuccess)
-      ee = cudaMemcpyAsync(r.meta_d, h.meta_d, sizeof(double) * h.n_meta_d, cudaMemcpyHostToDevice, st);
-    return ee;
-  };
-  // first q's preparation
-  hb();
-  if ((e = meta_copy(R[0], qs[0]))) return e;
-  if ((e = bin_prep(R[0], qs[0], p, s, sms, st))) return e;
-  he(RPA_K_SLICE, BIN_PREP_LAUNCHES - 1);
-  nl += BIN_PREP_LAUNCHES - 1;
   const int rounds = (p.rmax + L.G - 1) / L.G;
-  for (int i = 0; i < n; ++i) {
-    const BinRegion& C = R[pipe ? (i & 1) : 0];
+  const int n_units = n * rounds;
+  // the first q's preparation and the first unit's weighted planes
+  hb();
+  if ((e = bin_prep(R[0], L, qs[0], p, s, sms, st))) return e;
+  launch_slice_bin(bin_slice_args(R[0], AB[0], L, qs[0], p, s, 0), L.Npad, sms, st);
+  he(RPA_K_SLICE, BIN_PREP_LAUNCHES + 1);
+  nl += BIN_PREP_LAUNCHES + 1;
+  int nks[SB_MAX_BINS];
+  long bbase[SB_MAX_BINS];
+  for (int u = 0; u < n_units; ++u) {
+    const int i = u / rounds, k = u - i * rounds;
     const MixedBinQ& q = qs[i];
-    const bool more = pipe && i + 1 < n;
-    int nks[SB_MAX_BINS];
-    long bbase[SB_MAX_BINS];
-    bin_splits(L, q, p, s, sms, nks);
-    long items = 0;
-    for (int b = 0; b < p.n_bins; ++b) {
-      bbase[b] = items;
-      items += (long)p.rank[b] * nks[b] * L.n_tiles;
-    }
-    if (items > L.items) return cudaErrorInvalidValue;
-    if (i > 0 && !pipe) {  // one region: this q's preparation after the previous q finished with it
+    const BinRegion& C = R[i & 1];
+    uint16_t* A = AB[u & 1];
+    if (!pipe && u > 0) {  // one region and one buffer: preparation and slicing as launches of their own
       hb();
-      if ((e = meta_copy(C, q))) return e;
-      if ((e = bin_prep(C, q, p, s, sms, st))) return e;
-      he(RPA_K_SLICE, BIN_PREP_LAUNCHES - 1);
-      nl += BIN_PREP_LAUNCHES - 1;
+      int nk = 1;
+      if (k == 0) {
+        if ((e = bin_prep(C, L, q, p, s, sms, st))) return e;
+        nk += BIN_PREP_LAUNCHES;
+      }
+      launch_slice_bin(bin_slice_args(C, A, L, q, p, s, k), L.Npad, sms, st);
+      he(RPA_K_SLICE, nk);
+      nl += nk;
     }
-    if (more) {  // the next q's preparation in the other region, before this q's launch
+    if (k == 0) {
+      bin_splits(L, q, p, s, sms, nks);
+      long items = 0;
+      for (int b = 0; b < p.n_bins; ++b) {
+        bbase[b] = items;
+        items += (long)p.rank[b] * nks[b] * L.n_tiles;
+      }
+      if (items > L.items) return cudaErrorInvalidValue;
+    }
+    const bool has_next = pipe && u + 1 < n_units;
+    const int i2 = (u + 1) / rounds, k2 = (u + 1) - i2 * rounds;
+    if (has_next && i2 != i) {  // the next q's preparation in the other region
       hb();
-      if ((e = meta_copy(R[(i + 1) & 1], qs[i + 1]))) return e;
-      if ((e = bin_prep(R[(i + 1) & 1], qs[i + 1], p, s, sms, st))) return e;
-      he(RPA_K_SLICE, BIN_PREP_LAUNCHES - 1);
-      nl += BIN_PREP_LAUNCHES - 1;
+      if ((e = bin_prep(R[i2 & 1], L, qs[i2], p, s, sms, st))) return e;
+      he(RPA_K_SLICE, BIN_PREP_LAUNCHES);
+      nl += BIN_PREP_LAUNCHES;
     }
-    for (int k = 0; k < rounds; ++k) {
-      if (!(pipe && i > 0)) {  // weighted planes of this round (a launch of its own)
-        hb();
-        const SliceBinArgs sa = bin_slice_args(C, q, p, s, k);
-        const long tg = (long)L.Npad * sa.n_kb;
-        slice_bin_kernel<<<(unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), 256, 0, st>>>(sa);
-        he(RPA_K_SLICE, 1);
-        ++nl;
-      }
-      TcParams tp;
-      const int n_items = bin_tc_params(C, q, p, s, k, nks, bbase, err, tp);
-      if (more && k == rounds - 1) {
-        tp.side_on = 2;
-        tp.sideb = bin_slice_args(R[(i + 1) & 1], qs[i + 1], p, s, 0);
-      }
-      if (n_items > 0) {
-        hb();
-        launch_tc(s, std::min(n_items, sms), TC_SMEM, st, tp);
-        he(RPA_K_CHI0, 1);
-        ++nl;
-      } else if (more && k == rounds - 1) {  // nothing to contract: slice the next q standalone
-        const SliceBinArgs& sa = tp.sideb;
-        const long tg = (long)L.Npad * sa.n_kb;
-        slice_bin_kernel<<<(unsigned)std::min<long>((tg + 255) / 256, (long)sms * 32), 256, 0, st>>>(sa);
-        ++nl;
-      }
+    TcParams tp;
+    const int n_items = bin_tc_params(C, A, L, q, p, s, k, nks, bbase, err, tp);
+    if (has_next) {
+      tp.side_on = 2;
+      tp.sideb = bin_slice_args(R[i2 & 1], AB[(u + 1) & 1], L, qs[i2], p, s, k2);
     }
-    RedBin rb{};
-    rb.cplx = q.g.cplx;
-    rb.N = q.g.n_aux;
-    rb.Npad = L.Npad;
-    rb.n_tiles = L.n_tiles;
-    rb.nb = p.n_bins;
-    rb.rmax = L.rmax;
-    rb.n_w = q.g.n_w;
-    rb.G = L.G;
-    for (int b = 0; b < p.n_bins; ++b) {
-      rb.rank[b] = (q.host->tb0[b + 1] > q.host->tb0[b]) ? p.rank[b] : 0;
-      rb.nks[b] = nks[b];
-      rb.base[b] = bbase[b];
+    if (n_items > 0) {
+      hb();
+      launch_tc(s, std::min(n_items, sms), TC_SMEM, st, tp);
+      he(RPA_K_CHI0, 1);
+      ++nl;
+    } else if (has_next) {  // nothing to contract: the next unit's planes standalone
+      launch_slice_bin(tp.sideb, L.Npad, sms, st);
+      ++nl;
     }
-    rb.part = C.part;
-    rb.eAraw = C.eA;
-    rb.eCraw = C.eC;
-    rb.coef = C.meta_d + (size_t)p.n_bins * L.rmax;
-    rb.chi = q.chi;
-    const int per_tile = 128 * (q.g.cplx ? 64 : 128) / 256;
-    hb();
-    reduce_bin_kernel<<<(unsigned)(L.n_tiles * per_tile), 256,
-                        sizeof(double) * (size_t)p.n_bins * L.rmax * q.g.n_w, st>>>(rb);
-    he(RPA_K_CHI0_RED, 1);
-    ++nl;
+    if (k == rounds - 1) {
+      RedBin rb{};
+      rb.cplx = q.g.cplx;
+      rb.N = q.g.n_aux;
+      rb.Npad = L.Npad;
+      rb.n_tiles = L.n_tiles;
+      rb.nb = p.n_bins;
+      rb.rmax = L.rmax;
+      rb.n_w = q.g.n_w;
+      rb.G = L.G;
+      for (int b = 0; b < p.n_bins; ++b) {
+        rb.rank[b] = (q.host->tb0[b + 1] > q.host->tb0[b]) ? p.rank[b] : 0;
+        rb.nks[b] = nks[b];
+        rb.base[b] = bbase[b];
+      }
+      rb.part = C.part;
+      rb.eAraw = C.eA;
+      rb.eCraw = C.eC;
+      rb.coef = C.meta_d + (size_t)p.n_bins * L.rmax;
+      rb.chi = q.chi;
+      const int per_tile = 128 * (q.g.cplx ? 64 : 128) / 256;
+      const int n_groups = (q.g.n_w + RED_WG - 1) / RED_WG;
+      rb.wg = (q.g.n_w + n_groups - 1) / n_groups;
+      hb();
+      reduce_bin_kernel<<<dim3((unsigned)(L.n_tiles * per_tile), (unsigned)n_groups), 256,
+                          sizeof(float2) * (size_t)p.n_bins * L.rmax * q.g.n_w, st>>>(rb);
+      he(RPA_K_CHI0_RED, 1);
+      ++nl;
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (status) {

@@ -62,4 +62,60 @@ __device__ __forceinline__ void mac(Elem<C>& acc, Elem<C> a, Elem<C> b) {
   }
 }
 
+// Float-float form of an element (an unevaluated sum hi + lo of two floats per
+// real component, the same size as Elem<C>): the trailing updates of the
+// inverse-form log-det run on the FP32 pipe in this arithmetic.
+template <bool C>
+struct FFE;
+template <>
+struct FFE<true> {
+  float rh, rl, ih, il;
+};
+template <>
+struct FFE<false> {
+  float rh, rl;
+};
+static_assert(sizeof(FFE<true>) == sizeof(Elem<true>) && sizeof(FFE<false>) == sizeof(Elem<false>),
+              "float-float and FP64 elements share shared-memory arrays");
+
+template <bool C>
+__device__ __forceinline__ FFE<C> to_ff(Elem<C> e) {
+  FFE<C> f;
+  f.rh = __double2float_rn(e.re);
+  f.rl = __double2float_rn(e.re - (double)f.rh);
+  if constexpr (C) {
+    f.ih = __double2float_rn(e.im);
+    f.il = __double2float_rn(e.im - (double)f.ih);
+  }
+  return f;
+}
+
+// (h, l) += (ah + al)(bh + bl): the product's rounding error by one fmaf
+// (Dekker's TwoProd), the cross terms by two more, the sum's error by Knuth's
+// TwoSum; error terms gather in l (renormalised by the caller at the end).
+// Explicitly rounded intrinsics keep the compiler from contracting the
+// TwoSum into an fma.
+__device__ __forceinline__ void ff_mac(float& h, float& l, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float s = __fadd_rn(h, p);
+  const float v = __fsub_rn(s, h);
+  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, v)), __fsub_rn(p, v));
+  l = __fadd_rn(l, __fadd_rn(err, e));
+  h = s;
+}
+
+// acc += a * b in float-float (complex: four real products).
+template <bool C>
+__device__ __forceinline__ void ff_mac_e(FFE<C>& acc, const FFE<C>& a, const FFE<C>& b) {
+  ff_mac(acc.rh, acc.rl, a.rh, a.rl, b.rh, b.rl);
+  if constexpr (C) {
+    ff_mac(acc.rh, acc.rl, -a.ih, -a.il, b.ih, b.il);
+    ff_mac(acc.ih, acc.il, a.rh, a.rl, b.ih, b.il);
+    ff_mac(acc.ih, acc.il, a.ih, a.il, b.rh, b.rl);
+  }
+}
+
 }  // namespace rpa

@@ -109,10 +109,16 @@ BinFit fit_bin(double lo, double hi, const double* omega, int n_w, double tol, d
     x[i] = 0.5 * (lo + hi) + 0.5 * (hi - lo) * cos(M_PI * (i + 0.5) / N_FIT);
   for (int i = 0; i < N_CHECK; ++i) xc[i] = lo + (hi - lo) * (double)i / (N_CHECK - 1);
   // column scale: the largest |d| of each node over the bin (check grid and fit points)
-  for (int w = 0; w < n_w; ++w) {
-    for (int i = 0; i < N_CHECK; ++i) s[w] = std::max(s[w], fabs(weight(xc[i], omega[w])));
+  std::vector<double> Mc((size_t)N_CHECK * n_w);
+  for (int i = 0; i < N_CHECK; ++i)
+    for (int w = 0; w < n_w; ++w) {
+      Mc[(size_t)i * n_w + w] = weight(xc[i], omega[w]);
+      s[w] = std::max(s[w], fabs(Mc[(size_t)i * n_w + w]));
+    }
+  for (int w = 0; w < n_w; ++w)
     for (int i = 0; i < N_FIT; ++i) s[w] = std::max(s[w], fabs(weight(x[i], omega[w])));
-  }
+  for (int i = 0; i < N_CHECK; ++i)
+    for (int w = 0; w < n_w; ++w) Mc[(size_t)i * n_w + w] /= s[w];
   std::vector<double> A((size_t)N_FIT * n_w);
   for (int i = 0; i < N_FIT; ++i)
     for (int w = 0; w < n_w; ++w) A[(size_t)i * n_w + w] = weight(x[i], omega[w]) / s[w];
@@ -120,48 +126,81 @@ BinFit fit_bin(double lo, double hi, const double* omega, int n_w, double tol, d
   std::vector<double> R = A;
   qrcp(N_FIT, n_w, R, piv);
   const int kmax = std::min(n_w, N_FIT);
-  for (int r = 1; r <= kmax; ++r) {
-    // T = R11^-1 R12 (scaled coefficients of the non-skeleton columns)
-    std::vector<double> T((size_t)r * n_w, 0.0);  // [r][w] in original column order
-    bool ok = true;
+  // scaled coefficients T ([r][w], original column order) of the rank-r
+  // decomposition, T = R11^-1 R12 for the non-skeleton columns; false if R11
+  // is singular
+  auto coeffs = [&](int r, std::vector<double>& T) -> bool {
+    T.assign((size_t)r * n_w, 0.0);
     for (int k = 0; k < r; ++k) T[(size_t)k * n_w + piv[k]] = 1.0;
-    for (int c = r; c < n_w && ok; ++c) {
-      std::vector<double> y(r);
+    std::vector<double> y(r);
+    for (int c = r; c < n_w; ++c) {
       for (int k = r - 1; k >= 0; --k) {
         double acc = R[(size_t)k * n_w + c];
         for (int l = k + 1; l < r; ++l) acc -= R[(size_t)k * n_w + l] * y[l];
         const double dkk = R[(size_t)k * n_w + k];
-        if (dkk == 0.0) {
-          ok = false;
-          break;
-        }
+        if (dkk == 0.0) return false;
         y[k] = acc / dkk;
       }
-      for (int k = 0; k < r && ok; ++k) T[(size_t)k * n_w + piv[c]] = y[k];
+      for (int k = 0; k < r; ++k) T[(size_t)k * n_w + piv[c]] = y[k];
     }
-    if (!ok) break;
-    double amp = 0.0, err = 0.0;
+    return true;
+  };
+  // residual on the check grid and the coefficient sum; false when the rank fails the bars
+  auto passes = [&](int r, std::vector<double>& T, double& err, double& amp) -> bool {
+    if (!coeffs(r, T)) return false;
+    amp = 0.0;
     for (int w = 0; w < n_w; ++w) {
       double a = 0.0;
       for (int k = 0; k < r; ++k) a += fabs(T[(size_t)k * n_w + w]);
       amp = std::max(amp, a);
     }
-    for (int i = 0; i < N_CHECK && amp <= amp_max; ++i)
+    if (amp > amp_max) return false;
+    err = 0.0;
+    for (int i = 0; i < N_CHECK; ++i) {
+      const double* m = &Mc[(size_t)i * n_w];
       for (int w = 0; w < n_w; ++w) {
-        double v = weight(xc[i], omega[w]) / s[w];
-        for (int k = 0; k < r; ++k) v -= T[(size_t)k * n_w + w] * weight(xc[i], omega[piv[k]]) / s[piv[k]];
+        double v = m[w];
+        for (int k = 0; k < r; ++k) v -= T[(size_t)k * n_w + w] * m[piv[k]];
         err = std::max(err, fabs(v));
+        if (err > tol) return false;
       }
-    if (amp <= amp_max && err <= tol) {
-      f.rank = r;
-      f.err = err;
-      f.amp = amp;
-      f.skel.assign(piv.begin(), piv.begin() + r);
-      f.coef.assign((size_t)r * n_w, 0.0);
-      for (int k = 0; k < r; ++k)
-        for (int w = 0; w < n_w; ++w) f.coef[(size_t)k * n_w + w] = T[(size_t)k * n_w + w] * s[w] / s[piv[k]];
-      return f;
     }
+    return true;
+  };
+  // first guess from the pivots' decay, then the smallest rank that passes
+  const double r00 = fabs(R[0]);
+  int r0 = kmax;
+  for (int k = 1; k < kmax; ++k)
+    if (fabs(R[(size_t)k * n_w + k]) <= tol * r00) {
+      r0 = k;
+      break;
+    }
+  std::vector<double> T, Tbest;
+  double err = 0.0, amp = 0.0, ebest = 0.0, abest = 0.0;
+  int rbest = 0;
+  for (int r = r0; r <= kmax; ++r)
+    if (passes(r, T, err, amp)) {
+      rbest = r;
+      Tbest = T;
+      ebest = err;
+      abest = amp;
+      break;
+    }
+  while (rbest > 1 && passes(rbest - 1, T, err, amp)) {
+    --rbest;
+    Tbest = T;
+    ebest = err;
+    abest = amp;
+  }
+  if (rbest > 0) {
+    f.rank = rbest;
+    f.err = ebest;
+    f.amp = abest;
+    f.skel.assign(piv.begin(), piv.begin() + rbest);
+    f.coef.assign((size_t)rbest * n_w, 0.0);
+    for (int k = 0; k < rbest; ++k)
+      for (int w = 0; w < n_w; ++w) f.coef[(size_t)k * n_w + w] = Tbest[(size_t)k * n_w + w] * s[w] / s[piv[k]];
+    return f;
   }
   // no truncation reaches the bar: every node is its own skeleton
   f.rank = n_w;

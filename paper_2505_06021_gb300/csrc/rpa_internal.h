@@ -254,12 +254,12 @@ struct MixedBinQ {
   double zeta_k;
   int* status;                 // device status word (plan mismatch)
 };
+// Workspace of the frequency-batched chi0 within `budget` bytes (pipelined
+// with two q regions and two weighted-operand buffers when they fit).
 size_t binned_workspace_bytes(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int n_slices,
-                              size_t slice_cap, bool two_regions);
-bool binned_one_round(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int n_slices,
-                      size_t slice_cap);
+                              size_t budget);
 cudaError_t launch_chi0_binned(const MixedBinQ* qs, int n, const FreqPlan& p, int n_slices, void* work,
-                               size_t work_bytes, size_t slice_cap, int* status, uint64_t* n_launch, cudaStream_t s,
+                               size_t work_bytes, int* status, uint64_t* n_launch, cudaStream_t s,
                                const LaunchHook* hook);
 // Status word code of a device bin count that disagrees with the plan.
 constexpr int STATUS_CODE_PLAN = 1 << 28;

@@ -126,7 +126,7 @@ def test_binned_is_default_when_it_saves_work(rpa):
 def test_binned_pipelined_launch_count_and_determinism(rpa):
     """Several q of one shape with all skeletons in one round: the weighted
     planes of each next q are written inside the current q's tensor-core
-    launch, so a job has one standalone weighted-slicing launch, five
+    launch, so a job has one standalone weighted-slicing launch, six
     preparation launches per q and one tensor-core launch per q."""
     p = synth.make_problem("pipeb", is_complex=True, n_aux=384, n_occ=4, n_virt=24,
                            grid=synth.regular_kq_grid((2, 2, 1)), n_w=16, seed=47)
@@ -136,9 +136,46 @@ def test_binned_pipelined_launch_count_and_determinism(rpa):
         r = c.energy(job)
         prof = c.profile_read()
         r2 = c.energy(job)
-    assert prof["slice"][1] == 1 + 5 * p.n_q, prof["slice"]
+    assert prof["slice"][1] == 1 + 6 * p.n_q, prof["slice"]
     assert prof["chi0"][1] == p.n_q
     assert r["Ec"] == r2["Ec"] and np.array_equal(r["eps"], r2["eps"])
     ref = oracle.energy(p)
     assert abs(r["Ec"] - ref["Ec"]) <= TOL_EC, (r["Ec"], ref["Ec"])
     assert np.max(np.abs(r["eps"] - ref["eps"]) / np.abs(ref["eps"])) <= 1e-6
+
+
+def test_binned_wait_runs_out_and_context_recovers(rpa):
+    """Failure path of the frequency-batched launch without a GPU fault: one
+    work item's operand copies are never issued, the bounded wait runs out,
+    the call reports a time-out, and the same context then gives the same
+    energy as before."""
+    import time
+
+    p = _periodic(n_aux=96, n_occ=3, n_virt=30, kdims=(2, 1, 1), seed=57)
+    job = rpa.job_from_problem(p, rpa.upload_problem(p), prec=rpa.PREC_MIXED)
+    with rpa.Context(0, chi0_freq=2) as c:
+        good = c.energy(job)["Ec"]
+        c.test_drop_copy(0)
+        t0 = time.perf_counter()
+        with pytest.raises(rpa.RpaError) as e:
+            c.energy(job)
+        assert e.value.status == rpa.RPA_E_TIMEOUT
+        assert time.perf_counter() - t0 < 60.0
+        assert c.energy(job)["Ec"] == good
+
+
+def test_binned_not_positive_definite_reported(rpa):
+    """An indefinite V(q) planted on the host is reported with its q by the
+    frequency-batched path as well, and the context keeps working."""
+    p = _periodic(n_aux=80, n_occ=3, n_virt=24, kdims=(2, 1, 1), seed=58)
+    t = rpa.upload_problem(p)
+    Vbad = t["V"][1].clone()
+    Vbad[5, 5] = -60.0
+    t2 = dict(t)
+    t2["V"] = [t["V"][0], Vbad]
+    with rpa.Context(0, chi0_freq=2) as c:
+        with pytest.raises(rpa.RpaError) as e:
+            c.energy(rpa.job_from_problem(p, t2, prec=rpa.PREC_MIXED))
+        assert e.value.status == rpa.RPA_E_NOTPD and "V(q=1)" in str(e.value)
+        r = c.energy(rpa.job_from_problem(p, t, prec=rpa.PREC_MIXED))
+    assert abs(r["Ec"] - oracle.energy(p)["Ec"]) <= TOL_EC
