@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(256) cfix_scatter_kernel(int cplx, int N, int 
 // here).
 constexpr int EROW_BIN_ROWS = 64;
 constexpr int EROW_ILP = 4;
+template <int MR>  // skeletons per bin at most (register array size)
 __global__ void __launch_bounds__(256) erow_bin_kernel(int cplx, int Npad, int Kr, int Kt, int rmax,
                                                        const int* parts, const int* rankb, const int* eCraw,
                                                        const int16_t* ewx, int* cfix, int* eAraw) {
@@ -221,9 +222,9 @@ __global__ void __launch_bounds__(256) erow_bin_kernel(int cplx, int Npad, int K
   for (int rr = 0; rr < EROW_BIN_ROWS / 8; ++rr) {
     const int P = blockIdx.x * EROW_BIN_ROWS + rr * 8 + warp;
     if (P >= Npad) break;
-    int m[BIN_MAX_RANK];
+    int m[MR];
 #pragma unroll
-    for (int g = 0; g < BIN_MAX_RANK; ++g) m[g] = -100000;
+    for (int g = 0; g < MR; ++g) m[g] = -100000;
     int* row = cfix + (long)P * Kr;
     // EROW_ILP positions per lane per step: their loads are issued together
     for (int ub = 0; ub < len; ub += 32 * EROW_ILP) {
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(256) erow_bin_kernel(int cplx, int Npad, int K
         if (av[k] == 0) continue;
         const int bitlen = 32 - __clz(av[k]);
 #pragma unroll
-        for (int g = 0; g < BIN_MAX_RANK; ++g) {
+        for (int g = 0; g < MR; ++g) {
           if (g >= R) break;
           m[g] = max(m[g], bitlen + (int)ees[g * len + uu]);
         }
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(256) erow_bin_kernel(int cplx, int Npad, int K
     if (!rc) continue;  // an all-zero row: no weighted contributions
     const int eC = rc - 1022;
 #pragma unroll
-    for (int g = 0; g < BIN_MAX_RANK; ++g) {
+    for (int g = 0; g < MR; ++g) {
       if (g >= R) break;
       const int r = __reduce_max_sync(0xffffffffu, m[g]);
       if (lane == 0 && r > -100000) atomicMax(eAraw + ((long)b * rmax + g) * Npad + P, max(0, r + eC + 2014));
@@ -542,9 +543,17 @@ cudaError_t bin_prep(const BinRegion& R, const BinLayout& L, const MixedBinQ& q,
   const int n_parts = h.n_parts;
   const int* parts = R.meta_i + 2 * nrow * p.n_bins;
   const int* rankb = parts + 3 * n_parts;
-  erow_bin_kernel<<<dim3((unsigned)((L.Npad + EROW_BIN_ROWS - 1) / EROW_BIN_ROWS), (unsigned)n_parts), 256,
-                    sizeof(int16_t) * (size_t)L.rmax * FREQ_PART, st>>>(g.cplx, L.Npad, h.Kr, h.Kt, L.rmax, parts,
-                                                                        rankb, R.eC, R.ewx, R.cfix, R.eA);
+  const dim3 eg((unsigned)((L.Npad + EROW_BIN_ROWS - 1) / EROW_BIN_ROWS), (unsigned)n_parts);
+  const size_t esm = sizeof(int16_t) * (size_t)L.rmax * FREQ_PART;
+  if (L.rmax <= 8)
+    erow_bin_kernel<8><<<eg, 256, esm, st>>>(g.cplx, L.Npad, h.Kr, h.Kt, L.rmax, parts, rankb, R.eC, R.ewx, R.cfix,
+                                             R.eA);
+  else if (L.rmax <= 16)
+    erow_bin_kernel<16><<<eg, 256, esm, st>>>(g.cplx, L.Npad, h.Kr, h.Kt, L.rmax, parts, rankb, R.eC, R.ewx,
+                                              R.cfix, R.eA);
+  else
+    erow_bin_kernel<32><<<eg, 256, esm, st>>>(g.cplx, L.Npad, h.Kr, h.Kt, L.rmax, parts, rankb, R.eC, R.ewx,
+                                              R.cfix, R.eA);
   // digits of C (the B operand) in bin order
   SliceArgs sc{g.cplx, L.Npad, g.n_ov, h.Kt, h.Kr, s, g.n_w, 0, 1, g.cplx ? 2 : 1, R.cfix, nullptr,
                nullptr, nullptr, R.SC};
@@ -694,8 +703,12 @@ cudaError_t launch_chi0_binned(const MixedBinQ* qs, int n, const FreqPlan& p, in
     static std::once_flag once;
     static cudaError_t ea2 = cudaSuccess;
     std::call_once(once, [] {
-      ea2 = cudaFuncSetAttribute(erow_bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(int16_t) * BIN_MAX_RANK * FREQ_PART));
+      const int bytes = (int)(sizeof(int16_t) * BIN_MAX_RANK * FREQ_PART);
+      ea2 = cudaFuncSetAttribute(erow_bin_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (ea2 == cudaSuccess)
+        ea2 = cudaFuncSetAttribute(erow_bin_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (ea2 == cudaSuccess)
+        ea2 = cudaFuncSetAttribute(erow_bin_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     });
     if (ea2) return ea2;
   }
