@@ -473,8 +473,7 @@ static rpa_status vside_factor(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const 
   const size_t NN = (size_t)j->n_aux * j->n_aux;
   const long mstride = (long)(NN * (es / 8));
   prof_begin(ctx, pex, s);
-  // the inverse form (split-precision path, b.Vc set) factors V with float-float updates (mode 3)
-  CK(launch_cholesky(j->is_complex, j->n_aux, nq, b.L, mstride, b.Vc ? 3 : 1, b.Vc ? b.ldV + q0 : nullptr, b.status,
+  CK(launch_cholesky(j->is_complex, j->n_aux, nq, b.L, mstride, 1, b.Vc ? b.ldV + q0 : nullptr, b.status,
                      (1 << 29) + q0, s));
   prof_end(ctx, pex, s, RPA_K_VFACTOR, cholesky_launches(j->n_aux, nq));
   ctx->launches += cholesky_launches(j->n_aux, nq);

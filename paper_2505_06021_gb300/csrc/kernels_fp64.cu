@@ -219,9 +219,7 @@ cudaError_t chi0_dispatch(const BatchGeom& g, const double* const* Cptrs, const 
 constexpr int GT = 64;
 constexpr int GK = 16;
 
-// FF: the products in float-float arithmetic on the FP32 pipe (the inverse
-// form's V^-1 = X^H X of the split-precision path); FP64 otherwise.
-template <bool C, int MODE, bool FF = false>
+template <bool C, int MODE>
 __global__ void __launch_bounds__(256)
     sandwich_kernel(int N, int n_w, const double* __restrict__ Xb, const double* __restrict__ Lb,
                     double* __restrict__ Ob, int n_tiles_row, int tiles_per_mat) {
@@ -244,14 +242,10 @@ __global__ void __launch_bounds__(256)
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
 
   Elem<C> acc[4][4];
-  FFE<C> facc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      acc[u][v] = zero_elem<C>();
-      facc[u][v] = to_ff<C>(zero_elem<C>());
-    }
+    for (int v = 0; v < 4; ++v) acc[u][v] = zero_elem<C>();
 
   const int k_begin = (MODE == 0 ? J : I) * GT;
   for (int k0 = k_begin; k0 < N; k0 += GK) {
@@ -272,42 +266,17 @@ __global__ void __launch_bounds__(256)
       }
     }
     __syncthreads();
-    if constexpr (FF) {
-      // the tile's values to float-float in place (same element size)
-      FFE<C>(*Af)[GT] = reinterpret_cast<FFE<C>(*)[GT]>(As);
-      FFE<C>(*Bf)[GT] = reinterpret_cast<FFE<C>(*)[GT]>(Bs);
-      for (int idx = tid; idx < GK * GT; idx += 256) {
-        const int kk = idx / GT, c = idx % GT;
-        const Elem<C> ea = As[kk][c], eb = Bs[kk][c];
-        Af[kk][c] = to_ff<C>(ea);
-        Bf[kk][c] = to_ff<C>(eb);
-      }
-      __syncthreads();
-#pragma unroll 2
-      for (int kk = 0; kk < GK; ++kk) {
-        FFE<C> a[4], bv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = Af[kk][ty + 16 * u];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) bv[v] = Bf[kk][tx + 16 * v];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) ff_mac_e<C>(facc[u][v], a[u], bv[v]);
-      }
-    } else {
 #pragma unroll 4
-      for (int kk = 0; kk < GK; ++kk) {
-        Elem<C> a[4], bv[4];
+    for (int kk = 0; kk < GK; ++kk) {
+      Elem<C> a[4], bv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
+      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) bv[v] = Bs[kk][tx + 16 * v];
+      for (int v = 0; v < 4; ++v) bv[v] = Bs[kk][tx + 16 * v];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) mac<C>(acc[u][v], a[u], bv[v]);
-      }
+        for (int v = 0; v < 4; ++v) mac<C>(acc[u][v], a[u], bv[v]);
     }
     __syncthreads();
   }
@@ -318,10 +287,6 @@ __global__ void __launch_bounds__(256)
       const int P = I * GT + ty + 16 * u, Q = J * GT + tx + 16 * v;
       if (P >= N || Q >= N) continue;
       Elem<C> e = acc[u][v];
-      if constexpr (FF) {
-        e.re = (double)facc[u][v].rh + (double)facc[u][v].rl;
-        if constexpr (C) e.im = (double)facc[u][v].ih + (double)facc[u][v].il;
-      }
       if (MODE == 1) {
         e.re = -e.re;
         if constexpr (C) e.im = -e.im;
@@ -440,9 +405,6 @@ __device__ void team_sum(double s, double* red, double* part) {
 //         triangle), factorised; ln det(1 - Pi) = ln det M + ln det V
 //         (ldV[q]) and Tr Pi = Tr(chi V) = sum_PQ Re(chi_PQ conj(V_PQ)) from
 //         the copy Vc of V(q).
-// mode 3: mode 1 for the inverse form (split-precision path).
-// Modes 2 and 3 run the trailing updates in float-float arithmetic on the
-// FP32 pipe; modes 0 and 1 (the FP64 path) in FP64.
 // One matrix A (N x N) in `mode`; out: 1 double (mode 1) or 2 (ln det, Tr);
 // on a non-positive pivot *status becomes `code` (if still 0).  Mode 2 reads
 // Wq = -V^-1 and Vq = V of the matrix's q and ldv = ln det V.
@@ -601,7 +563,7 @@ __device__ __forceinline__ void chol_one(int N, double* __restrict__ A, int mode
     // (iii) trailing update of the lower part of A[kb+nb:, kb+nb:]
     const int m0 = kb + nb;
     const int m = N - m0;
-    if (m > 0 && (mode == 2 || mode == 3)) {
+    if (m > 0 && mode == 2) {
       // inverse form (split-precision path): the update in float-float on the
       // FP32 pipe, about 2^-46 relative per product, five times the rate of
       // the FP64 pipe; the diagonal block and the panel stay FP64
@@ -696,11 +658,11 @@ __device__ __forceinline__ void chol_one(int N, double* __restrict__ A, int mode
       if (status) atomicCAS(status, 0, code);
       if (out) {
         out[0] = nan("");
-        if (mode != 1 && mode != 3) out[1] = nan("");
+        if (mode != 1) out[1] = nan("");
       }
     }
   } else {
-    if (mode == 1 || mode == 3) {
+    if (mode == 1) {
       for (long idx = gtid; idx < (long)N * N; idx += GSTRIDE) {
         const int r = (int)(idx / N), c = (int)(idx % N);
         if (c > r) st_elem<C>(A, idx, zero_elem<C>());
@@ -737,8 +699,7 @@ __global__ void __launch_bounds__(256, CL == 1 ? CHOL_CTAS_PER_SM : 1)
   const int b = b0 + (int)(blockIdx.x / CL);
   const long q = mode == 2 ? b / n_w : 0;
   const long NN = (long)N * N * (C ? 2 : 1);
-  const bool vmode = mode == 1 || mode == 3;
-  chol_one<C, CL>(N, mats + (long)b * bstride, mode, out ? out + (vmode ? b : 2 * b) : nullptr, status,
+  chol_one<C, CL>(N, mats + (long)b * bstride, mode, out ? out + (mode == 1 ? b : 2 * b) : nullptr, status,
                   1 + status_base + b, mode == 2 ? Wn + q * NN : nullptr, mode == 2 ? Vc + q * NN : nullptr,
                   mode == 2 ? ldV + q : nullptr);
 }
@@ -756,9 +717,7 @@ __global__ void __launch_bounds__(256) cholesky_ragged_kernel(const CholTask* __
 // X = L^-1 for lower-triangular L (real positive diagonal), one CTA per
 // (matrix, 32-column block): block forward substitution down the rows,
 // X_r = L_rr^-1 (E_r - sum_{cb <= s < r} L_rs X_s); X is lower triangular.
-// FF: the block products in float-float arithmetic on the FP32 pipe (the
-// split-precision path); the diagonal-block substitution stays FP64.
-template <bool C, bool FF = false>
+template <bool C>
 __global__ void __launch_bounds__(256) trinv_kernel(int N, const double* __restrict__ Lb, double* __restrict__ Xb) {
   __shared__ Elem<C> Ls[CB][CB + 1];
   __shared__ Elem<C> Xs[CB][CB + 1];
@@ -777,51 +736,23 @@ __global__ void __launch_bounds__(256) trinv_kernel(int N, const double* __restr
   for (int rb = cb; rb < nt; ++rb) {
     const int r0 = rb * CB;
     Elem<C> acc[4];
-    FFE<C> facc[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      acc[u] = zero_elem<C>();
-      facc[u] = to_ff<C>(zero_elem<C>());
-    }
+    for (int u = 0; u < 4; ++u) acc[u] = zero_elem<C>();
     for (int sb = cb; sb < rb; ++sb) {
       const int s0 = sb * CB;
-      if constexpr (FF) {
-        FFE<C>(*Lf)[CB + 1] = reinterpret_cast<FFE<C>(*)[CB + 1]>(Ls);
-        FFE<C>(*Xf)[CB + 1] = reinterpret_cast<FFE<C>(*)[CB + 1]>(Xs);
-        for (int idx = tid; idx < CB * CB; idx += 256) {
-          const int r = idx / CB, c = idx % CB;
-          Lf[r][c] = to_ff<C>((r0 + r < N) ? ld_elem<C>(L, (long)(r0 + r) * N + s0 + c) : zero_elem<C>());
-          Xf[r][c] = to_ff<C>((c < ncol) ? ld_elem<C>(X, (long)(s0 + r) * N + c0 + c) : zero_elem<C>());
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int k = 0; k < CB; ++k) {
-          const FFE<C> xv = Xf[k][tx];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) ff_mac_e<C>(facc[u], Lf[ty + 8 * u][k], xv);
-        }
-      } else {
-        for (int idx = tid; idx < CB * CB; idx += 256) {
-          const int r = idx / CB, c = idx % CB;
-          Ls[r][c] = (r0 + r < N) ? ld_elem<C>(L, (long)(r0 + r) * N + s0 + c) : zero_elem<C>();
-          Xs[r][c] = (c < ncol) ? ld_elem<C>(X, (long)(s0 + r) * N + c0 + c) : zero_elem<C>();
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < CB; ++k) {
-          const Elem<C> xv = Xs[k][tx];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) mac<C>(acc[u], Ls[ty + 8 * u][k], xv);
-        }
+      for (int idx = tid; idx < CB * CB; idx += 256) {
+        const int r = idx / CB, c = idx % CB;
+        Ls[r][c] = (r0 + r < N) ? ld_elem<C>(L, (long)(r0 + r) * N + s0 + c) : zero_elem<C>();
+        Xs[r][c] = (c < ncol) ? ld_elem<C>(X, (long)(s0 + r) * N + c0 + c) : zero_elem<C>();
       }
       __syncthreads();
-    }
-    if constexpr (FF) {
+#pragma unroll 8
+      for (int k = 0; k < CB; ++k) {
+        const Elem<C> xv = Xs[k][tx];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        acc[u].re = (double)facc[u].rh + (double)facc[u].rl;
-        if constexpr (C) acc[u].im = (double)facc[u].ih + (double)facc[u].il;
+        for (int u = 0; u < 4; ++u) mac<C>(acc[u], Ls[ty + 8 * u][k], xv);
       }
+      __syncthreads();
     }
     // right-hand side E_r - acc, and the diagonal block of L
 #pragma unroll
@@ -1057,11 +988,11 @@ cudaError_t launch_vinv(int cplx, int N, int n_q, const double* L, double* X, do
   const int nb = (N + CB - 1) / CB;
   const int nt = (N + GT - 1) / GT, tri = nt * (nt + 1) / 2;
   if (cplx) {
-    trinv_kernel<true, true><<<n_q * nb, 256, 0, s>>>(N, L, X);
-    sandwich_kernel<true, 1, true><<<n_q * tri, 256, 0, s>>>(N, 1, X, X, Wn, nt, tri);
+    trinv_kernel<true><<<n_q * nb, 256, 0, s>>>(N, L, X);
+    sandwich_kernel<true, 1><<<n_q * tri, 256, 0, s>>>(N, 1, X, X, Wn, nt, tri);
   } else {
-    trinv_kernel<false, true><<<n_q * nb, 256, 0, s>>>(N, L, X);
-    sandwich_kernel<false, 1, true><<<n_q * tri, 256, 0, s>>>(N, 1, X, X, Wn, nt, tri);
+    trinv_kernel<false><<<n_q * nb, 256, 0, s>>>(N, L, X);
+    sandwich_kernel<false, 1><<<n_q * tri, 256, 0, s>>>(N, 1, X, X, Wn, nt, tri);
   }
   return cudaGetLastError();
 }
