@@ -533,6 +533,7 @@ def run_ours(args):
                                        "e2e steps",
                        "h2d_bytes_library_per_step": hcnt["h2d_bytes"] / args.e2e_steps,
                        "h2d_copy_ms_per_step": cp_ms / args.e2e_steps,
+                       "kernel_ms_per_step": {k: v[0] / args.e2e_steps for k, v in hprof.items() if v[1]},
                        "host_numa_node": ng.node, "pinned_near_gpu": bool(ng.cpus),
                        "abs_dEc_e2e_vs_device_Ha": abs(rh["Ec"] - res["Ec"]),
                        "dEc_note": "the host-staged job runs its chi0 in other q-batches and workspace rounds than "

@@ -242,7 +242,7 @@ rpa_status validate_job(const rpa_job* j, char* msg, size_t len) {
 static size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Workspace cap of the synchronous calls (the serving lanes use a smaller one).
-size_t sync_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap, (size_t)96 << 30); }
+size_t sync_ws_cap(rpa_ctx* ctx) { return std::min<size_t>(ctx->cap, (size_t)192 << 30); }
 
 Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool mixed_ws, int qt, const BinJob* bj) {
   Layout L{};
@@ -304,8 +304,23 @@ int choose_qb(const rpa_job* j, int n_slices, size_t cap, const BinJob* bj) {
   }
   while (qb > 1 && plan_layout(j, qb, n_slices, cap, true, 0, bj).total > cap) qb = (qb + 1) / 2;
   // host-resident inputs: at least four q-batches, so that the copies of one
-  // batch overlap the compute of the previous one
-  if (j->mem == RPA_MEM_HOST) qb = std::min(qb, std::max(1, (j->n_q + 3) / 4));
+  // batch overlap the compute of the previous one; with the frequency-batched
+  // chi0, fewer q per batch while that keeps all skeletons in one round (the
+  // staging buffers and the chi0 workspace share the cap)
+  if (j->mem == RPA_MEM_HOST) {
+    qb = std::min(qb, std::max(1, (j->n_q + 3) / 4));
+    if (bj && bj->on && j->prec == RPA_PREC_MIXED) {
+      auto one_round = [&](int b) {
+        const Layout L = plan_layout(j, b, n_slices, cap, false, j->n_q, nullptr);
+        const size_t budget = cap > L.total ? cap - L.total : 0;
+        const BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, j->n_occ * j->n_virt, j->n_k, j->n_w, 1};
+        int slots = 0;
+        binned_workspace_bytes(g, bj->plan, bj->Kt_max, bj->np_max, n_slices, budget, &slots);
+        return slots >= bj->plan.rmax;
+      };
+      while (qb > 1 && !one_round(qb)) --qb;
+    }
+  }
   return qb;
 }
 

@@ -257,7 +257,7 @@ struct MixedBinQ {
 // Workspace of the frequency-batched chi0 within `budget` bytes (pipelined
 // with two q regions and two weighted-operand buffers when they fit).
 size_t binned_workspace_bytes(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int n_slices,
-                              size_t budget);
+                              size_t budget, int* slots = nullptr);
 cudaError_t launch_chi0_binned(const MixedBinQ* qs, int n, const FreqPlan& p, int n_slices, void* work,
                                size_t work_bytes, int* status, uint64_t* n_launch, cudaStream_t s,
                                const LaunchHook* hook);
