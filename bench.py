@@ -19,7 +19,9 @@ of served jobs gives the p50/p99 latency beside it.  Prints one JSON line.
     python bench.py --impl reference ... # the CPU oracle as reference arm
 
 Under torchrun (N > 1) every rank runs its own job on its own GPU (weak
-scaling, no collective on the data path); rank 0 prints.
+scaling, no collective on the data path); rank 0 prints.  With --q-shard one
+job is split over the ranks by q-blocks instead (strong scaling, one
+all-reduce of the integrand table per job).
 """
 import argparse
 import json
@@ -63,6 +65,9 @@ def parse():
                     help="periodic2d/slab: the context's HBM cap (bounds the workspace; profiling small cases)")
     ap.add_argument("--n-q", type=int, default=0, help="profiling only: restrict the job to its first n q-points")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--q-shard", action="store_true",
+                    help="periodic2d/slab: one job split over the ranks by q-blocks (strong scaling) instead of "
+                         "one job per rank")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--workload", default="slab", choices=["periodic2d", "slab", "batch", "serving",
@@ -197,6 +202,17 @@ def allreduce_max(x, world):
 
     t = torch.tensor([x], dtype=torch.float64, device="cuda")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -385,6 +401,121 @@ def served_latency(args, local, n_jobs):
                       "rpa_submit/rpa_poll, mixed chi0" % n_jobs}
 
 
+def chi0_roofline(prec, prof, cnt, chi0_flops, steps, name, slices):
+    """Roofline record of the dominant kernel (the chi0 contraction) from the
+    library's CUDA-event profile: `chi0_flops` algorithmic FP64-equivalent
+    flops over the profiled launches.  Returns (record, achieved TFLOP/s)."""
+    chi_ms, chi_n = prof["chi0"]
+    chi_launch_ms = chi_ms / max(chi_n, 1)
+    flops_per_launch = chi0_flops / max(chi_n, 1)
+    achieved = flops_per_launch / (chi_launch_ms / 1e3) / 1e12 if chi_ms > 0 else 0.0
+    counting = ("achieved = the method's algorithmic FP64-equivalent chi0 flops (Hermitian lower triangle, "
+                "4N(N+1)N_ov per (q, k, omega), complex; all n_w frequencies) per launch / the launch's mean "
+                "CUDA-event time")
+    if prec == "fp64":
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": traffic_for("chi0_fp64") if name == "periodic2d" else None,
+                "kernel": "chi0_fp64_kernel", "peak_source": "derived FP64 DFMA peak: 152 SMs x 2 DFMA/clk x "
+                "2 flop x 2.07 GHz (microbenchmark measured 1.205 TFLOP/s)", "counting": counting,
+                "note": "the kernel forms conj(C_P)C_Q once per t and reuses it over a group of frequencies, so "
+                        "it executes fewer FP64 instructions than the algorithmic count"}, achieved
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    ex_t = cnt["tensor_flops"] / (chi_ms / 1e3) / 1e12 if chi_ms > 0 else None
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic_for("chi0_mixed_" + name),
+            "kernel": "chi0_tc_kernel<%d> (tcgen05, BF16 digit slices)" % (slices or 4),
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; the kernel runs inside a "
+                           "long step)", "counting": counting,
+            "executed_tensor_tflops": ex_t, "executed_frac": ex_t / peak if ex_t else None,
+            "executed_note": "tensor-core flops the launches issue (slice pairs x padded tiles x padded K x "
+                             "the contractions run), counted by the library, per second of chi0 launch time",
+            "launch_ms": chi_launch_ms, "launches_per_step": chi_n / max(steps, 1)}, achieved
+
+
+def run_qshard(args):
+    """One job split over the ranks by q-blocks (strong scaling): each rank
+    materialises and computes only its own q-points through rpa_energy, the
+    integrand table eps[q][w] is summed over ranks (one all-reduce of
+    n_q x n_w doubles) and every rank forms E_c by the fixed-order
+    quadrature.  A step is one whole job; time is host wall time between
+    barriers with the device synchronised on both sides, max over ranks."""
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    import paper_2505_06021_gb300 as rpa
+    from paper_2505_06021_gb300 import shard
+
+    prec = args.prec
+    if prec == "auto":
+        prec = "mixed" if rpa_mixed_available() else "fp64"
+    pc = rpa.PREC_MIXED if prec == "mixed" else rpa.PREC_FP64
+    name = args.workload
+    p = workload(args.n_q, name)
+    qs = list(shard.q_blocks(p.n_q, world)[rank])
+    dev = "cuda:%d" % local
+    t_gen = time.perf_counter()
+    job = shard.block_job(p, rpa.upload_problem(p, dev, qs=qs), qs, pc) if qs else None
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    log("inputs of q %s ready (%.1f s)" % (qs, t_gen))
+    ctx = rpa.Context(local, n_slices=args.slices, hbm_cap_bytes=int(args.cap_gb * 1e9), chi0_freq=args.chi0_freq)
+
+    def rows(_qs):
+        return ctx.energy(job)["eps"]
+
+    def step():
+        return shard.energy_sharded(p.n_q, p.n_w, p.grid.w_q, p.zeta_w, rows, rank, world)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.profile(True)
+    n0 = ctx.launches
+    t0 = time.perf_counter()
+    Ec = None
+    for _ in range(args.steps):
+        Ec, _table = step()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    barrier(world)
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    cnt = ctx.profile_counters()
+    ctx.profile(False)
+    launches = int(allreduce_sum(ctx.launches - n0, world))
+    t_max = allreduce_max(t, world)
+    flops_rank = p.chi0_flops() * len(qs) / p.n_q * args.steps
+    roof, achieved = chi0_roofline(prec, prof, cnt, flops_rank, args.steps, name, args.slices)
+    roof["note_qshard"] = "rank 0's chi0 launches (its own q-block)"
+    if rank != 0:
+        return
+    cfg = dict(config_of(p, prec, args.n_q, name), parallelism="one job q-sharded over %d ranks (strong scaling; "
+               "one all-reduce of the n_q x n_w integrand table per job)" % world)
+    if prec == "mixed":
+        cfg.update(chi0_slices=args.slices or 4,
+                   chi0_freq=["auto", "per-frequency", "frequency-batched"][args.chi0_freq])
+    line = {"metric": METRIC, "value": args.steps / t_max, "unit": "jobs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "bf16-slices->f64",
+            "data": "synthetic (seeded, shapes of the paper's periodic workloads; no public data)", "config": cfg,
+            "chi0_tflops": p.chi0_flops() * args.steps / t_max / 1e12, "chi0_tflops_kernel": achieved,
+            "Ec": Ec, "gpu_launches": launches, "q_block_rank0": qs,
+            "kernel_ms_per_step_rank0": {k: {"ms": v[0] / args.steps, "launches": v[1] // max(args.steps, 1)}
+                                         for k, v in prof.items() if v[1]},
+            "roofline": roof, "clocks": clk, "input_gen_s": t_gen,
+            "e2e": {"skipped": "q-sharded mode: device-resident inputs only (the end-to-end leg is in the "
+                               "default mode)"},
+            "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -452,36 +583,7 @@ def run_ours(args):
     jobs_per_s = world * args.steps / (ms_max / 1e3)
     chi0_flops_job = p.chi0_flops()
 
-    # dominant kernel: the chi0 contraction
-    chi_ms, chi_n = prof["chi0"]
-    chi_launch_ms = chi_ms / max(chi_n, 1)
-    flops_per_launch = chi0_flops_job * args.steps / max(chi_n, 1)
-    achieved = flops_per_launch / (chi_launch_ms / 1e3) / 1e12
-    counting = ("achieved = the method's algorithmic FP64-equivalent chi0 flops (Hermitian lower triangle, "
-                "4N(N+1)N_ov per (q, k, omega), complex; all n_w frequencies) per launch / the launch's mean "
-                "CUDA-event time")
-    if prec == "fp64":
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": traffic_for("chi0_fp64") if name == "periodic2d" else None,
-                "kernel": "chi0_fp64_kernel", "peak_source": "derived FP64 DFMA peak: 152 SMs x 2 DFMA/clk x "
-                "2 flop x 2.07 GHz (microbenchmark measured 1.205 TFLOP/s)", "counting": counting,
-                "note": "the kernel forms conj(C_P)C_Q once per t and reuses it over a group of frequencies, so "
-                        "it executes fewer FP64 instructions than the algorithmic count"}
-    else:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        ex_t = cnt["tensor_flops"] / (chi_ms / 1e3) / 1e12 if chi_ms > 0 else None
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic_for("chi0_mixed_" + name),
-                "kernel": "chi0_tc_kernel<%d> (tcgen05, BF16 digit slices)" % (args.slices or 4),
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; the kernel runs inside a "
-                               "long step)", "counting": counting,
-                "executed_tensor_tflops": ex_t, "executed_frac": ex_t / peak if ex_t else None,
-                "executed_note": "tensor-core flops the launches issue (slice pairs x padded tiles x padded K x "
-                                 "the contractions run), counted by the library, per second of chi0 launch time",
-                "launch_ms": chi_launch_ms, "launches_per_step": chi_n / max(args.steps, 1)}
+    roof, achieved = chi0_roofline(prec, prof, cnt, chi0_flops_job * args.steps, args.steps, name, args.slices)
     kernel_ms = {k: {"ms": v[0] / args.steps, "launches": v[1] // max(args.steps, 1)} for k, v in prof.items()
                  if v[1]}
     line = {"metric": METRIC, "value": jobs_per_s, "unit": "jobs/s", "n_gpus": world, "steps": args.steps,
@@ -533,7 +635,8 @@ def run_ours(args):
                                        "e2e steps",
                        "h2d_bytes_library_per_step": hcnt["h2d_bytes"] / args.e2e_steps,
                        "h2d_copy_ms_per_step": cp_ms / args.e2e_steps,
-                       "kernel_ms_per_step": {k: v[0] / args.e2e_steps for k, v in hprof.items() if v[1]},
+                       "kernel_ms_per_step": {k: {"ms": v[0] / args.e2e_steps, "launches": v[1] / args.e2e_steps}
+                                              for k, v in hprof.items() if v[1]},
                        "host_numa_node": ng.node, "pinned_near_gpu": bool(ng.cpus),
                        "abs_dEc_e2e_vs_device_Ha": abs(rh["Ec"] - res["Ec"]),
                        "dEc_note": "the host-staged job runs its chi0 in other q-batches and workspace rounds than "
@@ -1123,8 +1226,10 @@ def main():
         run_serving(args)
     elif args.workload == "periodic2d-ao":
         run_ao(args)
+    elif args.q_shard:
+        run_qshard(args)
     else:
-        run_ours(args)  # periodic2d (default) or slab
+        run_ours(args)  # slab (default) or periodic2d
 
 
 if __name__ == "__main__":

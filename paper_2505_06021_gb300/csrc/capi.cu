@@ -276,7 +276,9 @@ Layout plan_layout(const rpa_job* j, int qb, int n_slices, size_t ws_cap, bool m
     }
   }
   L.ao = al(ao_region_bytes(j, qb));
-  L.total = L.meta + L.dtab + L.chi + L.T + L.L + L.Vc + 2 * (L.stageC + L.stageV) + L.eps + L.mixed + L.ao;
+  if (binned) L.binmeta = al(bj->meta_bytes);
+  L.total = L.meta + L.dtab + L.chi + L.T + L.L + L.Vc + 2 * (L.stageC + L.stageV) + L.eps + L.mixed + L.ao +
+            L.binmeta;
   if (mixed_ws && binned) {
     // the frequency-batched chi0 takes what the cap leaves (pipelined when that suffices)
     BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, (int)nov, j->n_k, j->n_w, 1};
@@ -406,6 +408,8 @@ Bufs carve(void* ws, const rpa_job* j, const Layout& L) {
   b.slice_cap = L.slice_cap;
   p += L.mixed;
   b.ao = L.ao ? p : nullptr;
+  p += L.ao;
+  b.binmeta = L.binmeta ? p : nullptr;
   return b;
 }
 
@@ -680,6 +684,7 @@ rpa_status bin_job_build(rpa_ctx* ctx, Exec& ex, const rpa_job* j, BinJob& bj) {
     bj.qh[q].n_meta_d = md.size();
     hi += (img[q].size() + 15) & ~(size_t)15;
   }
+  bj.meta_bytes = (size_t)((char*)hi - (char*)ex.hbin.ptr);
   bj.on = true;
   return RPA_OK;
 }
@@ -730,6 +735,15 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
     vp[q] = host ? (const void*)(b.stageV[slot] + (size_t)qi * es * NN) : job->V[q];
   }
   if (rpa_status st0 = upload_tables(ctx, ex, job, b, cp.data())) return st0;
+  if (b.binmeta) {
+    // every q's bin tables in one copy, queued before the staging copies of
+    // the inputs (a small copy behind those waits for the copy engine)
+    CK(cudaMemcpyAsync(b.binmeta, ex.hbin.ptr, bj.meta_bytes, cudaMemcpyHostToDevice, s));
+    for (int q = 0; q < job->n_q; ++q) {
+      bj.qh[q].dmeta_i = (const int*)(b.binmeta + ((const char*)bj.qh[q].meta_i - (const char*)ex.hbin.ptr));
+      bj.qh[q].dmeta_d = (const double*)(b.binmeta + ((const char*)bj.qh[q].meta_d - (const char*)ex.hbin.ptr));
+    }
+  }
   if (job->ao) {
     if (rpa_status st1 = ao_project(ctx, &ex, job, aop, b.ao, s)) return st1;
     if (rpa_status st1 = ao_enqueue_half(ctx, &ex, job, aop, b.ao, -1, s)) return st1;

@@ -510,15 +510,29 @@ BinRegion carve_bin(char* p, const BinLayout& L) {
 
 constexpr int BIN_PREP_LAUNCHES = 6;  // ecrow, perm, wskel, cfix_scatter, erow_bin, slice of C
 
+// Region R as q's kernels see it: the tables read in place when the job's
+// copy of them is on the device already.
+BinRegion region_of(const BinRegion& R, const MixedBinQ& q) {
+  BinRegion r = R;
+  if (q.host->dmeta_i && q.host->dmeta_d) {
+    r.meta_i = const_cast<int*>(q.host->dmeta_i);
+    r.meta_d = const_cast<double*>(q.host->dmeta_d);
+  }
+  return r;
+}
+
 // Steps 1-6 for one q into region R, after copying its table image there.
 cudaError_t bin_prep(const BinRegion& R, const BinLayout& L, const MixedBinQ& q, const FreqPlan& p, int s, int sms,
                      cudaStream_t st) {
   const BatchGeom& g = q.g;
   const BinQHost& h = *q.host;
-  cudaError_t e = cudaMemcpyAsync(R.meta_i, h.meta_i, sizeof(int) * h.n_meta_i, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(R.meta_d, h.meta_d, sizeof(double) * h.n_meta_d, cudaMemcpyHostToDevice, st);
-  if (e) return e;
+  cudaError_t e = cudaSuccess;
+  if (R.meta_i != h.dmeta_i) {
+    e = cudaMemcpyAsync(R.meta_i, h.meta_i, sizeof(int) * h.n_meta_i, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(R.meta_d, h.meta_d, sizeof(double) * h.n_meta_d, cudaMemcpyHostToDevice, st);
+    if (e) return e;
+  }
   if ((e = cudaMemsetAsync(R.dpos, 0, sizeof(double) * (size_t)h.Kt, st))) return e;
   if ((e = cudaMemsetAsync(R.eC, 0, sizeof(int) * (size_t)L.Npad, st))) return e;
   if ((e = cudaMemsetAsync(R.eA, 0, sizeof(int) * (size_t)L.nb * L.rmax * L.Npad, st))) return e;
@@ -741,8 +755,8 @@ cudaError_t launch_chi0_binned(const MixedBinQ* qs, int n, const FreqPlan& p, in
   const int n_units = n * rounds;
   // the first q's preparation and the first unit's weighted planes
   hb();
-  if ((e = bin_prep(R[0], L, qs[0], p, s, sms, st))) return e;
-  launch_slice_bin(bin_slice_args(R[0], AB[0], L, qs[0], p, s, 0), L.Npad, sms, st);
+  if ((e = bin_prep(region_of(R[0], qs[0]), L, qs[0], p, s, sms, st))) return e;
+  launch_slice_bin(bin_slice_args(region_of(R[0], qs[0]), AB[0], L, qs[0], p, s, 0), L.Npad, sms, st);
   he(RPA_K_SLICE, BIN_PREP_LAUNCHES + 1);
   nl += BIN_PREP_LAUNCHES + 1;
   int nks[SB_MAX_BINS];
@@ -750,7 +764,7 @@ cudaError_t launch_chi0_binned(const MixedBinQ* qs, int n, const FreqPlan& p, in
   for (int u = 0; u < n_units; ++u) {
     const int i = u / rounds, k = u - i * rounds;
     const MixedBinQ& q = qs[i];
-    const BinRegion& C = R[i & 1];
+    const BinRegion C = region_of(R[i & 1], q);
     uint16_t* A = AB[u & 1];
     if (!pipe && u > 0) {  // one region and one buffer: preparation and slicing as launches of their own
       hb();
@@ -776,7 +790,7 @@ cudaError_t launch_chi0_binned(const MixedBinQ* qs, int n, const FreqPlan& p, in
     const int i2 = (u + 1) / rounds, k2 = (u + 1) - i2 * rounds;
     if (has_next && i2 != i) {  // the next q's preparation in the other region
       hb();
-      if ((e = bin_prep(R[i2 & 1], L, qs[i2], p, s, sms, st))) return e;
+      if ((e = bin_prep(region_of(R[i2 & 1], qs[i2]), L, qs[i2], p, s, sms, st))) return e;
       he(RPA_K_SLICE, BIN_PREP_LAUNCHES);
       nl += BIN_PREP_LAUNCHES;
     }
@@ -784,7 +798,7 @@ cudaError_t launch_chi0_binned(const MixedBinQ* qs, int n, const FreqPlan& p, in
     const int n_items = bin_tc_params(C, A, L, q, p, s, k, nks, bbase, err, tp);
     if (has_next) {
       tp.side_on = 2;
-      tp.sideb = bin_slice_args(R[i2 & 1], AB[(u + 1) & 1], L, qs[i2], p, s, k2);
+      tp.sideb = bin_slice_args(region_of(R[i2 & 1], qs[i2]), AB[(u + 1) & 1], L, qs[i2], p, s, k2);
     }
     if (n_items > 0) {
       hb();

@@ -74,6 +74,7 @@ struct BinJob {
   FreqPlan plan;
   std::vector<BinQHost> qh;  // per q
   int Kt_max = 0, np_max = 0;
+  size_t meta_bytes = 0;  // the pinned image block (doubles, then every q's ints)
 };
 
 struct ServeState;  // serving.cu
@@ -106,7 +107,7 @@ namespace rpa {
 
 // Workspace of one lane for a job processed in q-batches of qb q-points.
 struct Layout {
-  size_t meta, dtab, chi, T, L, Vc, stageC, stageV, eps, mixed, ao, total;
+  size_t meta, dtab, chi, T, L, Vc, stageC, stageV, eps, mixed, ao, binmeta, total;
   size_t slice_cap;  // mixed path: bytes for the weighted operand's digit planes
   int qb;            // q per staging batch (d table, host staging, AO coefficients)
   int qt;            // q per tail batch (chi, L, Vc, T: V factor and log-det)
@@ -137,7 +138,8 @@ struct Bufs {
   void* mixed;
   size_t mixed_bytes;
   size_t slice_cap;
-  char* ao;  // AO-form jobs: fit table, half-transforms, one q's C (ao_internal.h)
+  char* ao;       // AO-form jobs: fit table, half-transforms, one q's C (ao_internal.h)
+  char* binmeta;  // frequency-batched chi0: the job's bin tables, or null
 };
 
 void ctx_set_error(rpa_ctx* ctx, const char* fmt, ...);

@@ -77,6 +77,24 @@ def sub_job(job, qs: Sequence[int]):
                C=[job.C_t[i] for i in sel], V=[job.V_t[q] for q in qs], prec=job.s.prec, mem=job.s.mem)
 
 
+def block_job(problem, tensors, qs: Sequence[int], prec: int, mem: int = 0):
+    """The job of the q-points `qs` (a contiguous block) of a synthetic
+    problem whose tensors hold those q only (``upload_problem(..., qs=qs)``):
+    a rank materialises and keeps just its own C(q, k) blocks and V(q)."""
+    from . import Job
+
+    g = problem.grid
+    n_k = problem.n_k
+    sel = [q * n_k + j for q in qs for j in range(n_k)]
+    if len(tensors["C"]) != len(sel) or len(tensors["V"]) != len(qs):
+        raise ValueError("tensors must hold the C blocks and V of exactly the q-points qs")
+    return Job(is_complex=problem.is_complex, n_aux=problem.n_aux, n_occ=problem.n_occ, n_virt=problem.n_virt,
+               pair_k=np.asarray(g.pair_k).reshape(-1)[sel],
+               pair_kq=np.asarray(g.pair_kq).reshape(-1)[sel], w_q=np.asarray(g.w_q)[list(qs)], zeta_k=g.zeta_k,
+               omega=problem.omega, zeta_w=problem.zeta_w, eps_occ=tensors["eps_occ"], eps_virt=tensors["eps_virt"],
+               C=tensors["C"], V=tensors["V"], prec=prec, mem=mem)
+
+
 def gpu_rows(ctx, job) -> Callable[[Sequence[int]], np.ndarray]:
     """compute_rows for energy_sharded backed by the library on this rank's GPU."""
 

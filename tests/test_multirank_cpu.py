@@ -76,3 +76,27 @@ def test_two_gloo_ranks_match_single_process():
     assert np.array_equal(t0, t1)
     assert np.allclose(t0, ref["eps"], rtol=1e-13, atol=0)
     assert E0 == pytest.approx(ref["Ec"], rel=1e-13)
+
+
+def test_block_job_equals_sub_job_of_the_whole():
+    """A rank's q-block job built from only its own uploaded blocks (the
+    q-sharded benchmark mode) describes the same job as the whole job
+    restricted to those q-points."""
+    torch = pytest.importorskip("torch")
+    import paper_2505_06021_gb300 as rpa
+
+    p = synth.make_problem("bj", is_complex=True, n_aux=10, n_occ=2, n_virt=3,
+                           grid=synth.regular_kq_grid((3, 2, 1)), n_w=4, seed=62)
+    whole = rpa.job_from_problem(p, rpa.upload_problem(p, "cpu"), prec=rpa.PREC_FP64, mem=rpa.MEM_HOST)
+    for world in (2, 4):
+        for qs in shard.q_blocks(p.n_q, world):
+            qs = list(qs)
+            a = shard.sub_job(whole, qs)
+            b = shard.block_job(p, rpa.upload_problem(p, "cpu", qs=qs), qs, rpa.PREC_FP64, rpa.MEM_HOST)
+            assert np.array_equal(a.pair_k, b.pair_k) and np.array_equal(a.pair_kq, b.pair_kq)
+            assert np.array_equal(a.w_q, b.w_q)
+            assert len(a.C_t) == len(b.C_t) == len(qs) * p.n_k
+            for x, y in zip(a.C_t + a.V_t, b.C_t + b.V_t):
+                assert torch.equal(x, y)
+    with pytest.raises(ValueError):
+        shard.block_job(p, rpa.upload_problem(p, "cpu", qs=[0]), [0, 1], rpa.PREC_FP64, rpa.MEM_HOST)
