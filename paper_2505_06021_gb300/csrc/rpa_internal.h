@@ -47,7 +47,8 @@ cudaError_t launch_chi0_fp64(const BatchGeom& g, const double* const* Cptrs, con
 //   mode 2: input chi of (q, w) = (b / n_w, b % n_w); factorises
 //           M = V^-1 - chi with Wn[q] = -V^-1 (lower triangle) and writes
 //           out[2*b] = ln det M + ldV[q] = ln det(1 - Pi), out[2*b+1] =
-//           Tr(chi V) = Tr Pi, V read from Vc[q].
+//           Tr(chi V) = Tr Pi, V read from Vc[q]; chi's strict upper triangle
+//           is used as scratch (the input is read from the lower triangle).
 // A non-positive pivot sets *status (if still 0) to 1 + status_base + b and
 // the matrix is abandoned.
 cudaError_t launch_cholesky(int cplx, int N, int n_mat, double* mats, long bstride, int mode, double* out,
@@ -232,6 +233,11 @@ struct BinQHost {
   size_t n_meta_i = 0;
   const double* meta_d = nullptr;
   size_t n_meta_d = 0;
+  // the same images already on the device (a job-wide copy made before any
+  // other copy of the job is queued), or null: then each q's preparation
+  // copies its image from the host
+  const int* dmeta_i = nullptr;
+  const double* dmeta_d = nullptr;
 };
 // Fills h (except the meta pointers) and the int image of q.
 void freq_bin_q(const rpa_job* j, const FreqPlan& p, int q, const double* eo, const double* evs, BinQHost& h,
