@@ -90,6 +90,41 @@ __device__ __forceinline__ FFE<C> to_ff(Elem<C> e) {
   return f;
 }
 
+// Float-float element stored in (and loaded from, through L2) the slot of one
+// FP64 element: the two layouts have the same size.
+template <bool C>
+__device__ __forceinline__ void st_ff(double* p, long i, const FFE<C>& f) {
+  if constexpr (C) {
+    *reinterpret_cast<float4*>(p + 2 * i) = make_float4(f.rh, f.rl, f.ih, f.il);
+  } else {
+    *reinterpret_cast<float2*>(p + i) = make_float2(f.rh, f.rl);
+  }
+}
+template <bool C>
+__device__ __forceinline__ FFE<C> ld_ff(const double* p, long i) {
+  FFE<C> f;
+  if constexpr (C) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(p + 2 * i));
+    f.rh = v.x;
+    f.rl = v.y;
+    f.ih = v.z;
+    f.il = v.w;
+  } else {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p + i));
+    f.rh = v.x;
+    f.rl = v.y;
+  }
+  return f;
+}
+template <bool C>
+__device__ __forceinline__ FFE<C> conj_ff(FFE<C> f) {
+  if constexpr (C) {
+    f.ih = -f.ih;
+    f.il = -f.il;
+  }
+  return f;
+}
+
 // (h, l) += (ah + al)(bh + bl): the product's rounding error by one fmaf
 // (Dekker's TwoProd), the cross terms by two more, the sum's error by Knuth's
 // TwoSum; error terms gather in l (renormalised by the caller at the end).

@@ -404,7 +404,8 @@ __device__ void team_sum(double s, double* red, double* part) {
 //         lower triangle becomes M = V^-1 - chi (Wn = -V^-1 of the q, lower
 //         triangle), factorised; ln det(1 - Pi) = ln det M + ln det V
 //         (ldV[q]) and Tr Pi = Tr(chi V) = sum_PQ Re(chi_PQ conj(V_PQ)) from
-//         the copy Vc of V(q).
+//         the copy Vc of V(q).  The strict upper triangle (chi's redundant
+//         half) is overwritten by float-float copies of the panels.
 // One matrix A (N x N) in `mode`; out: 1 double (mode 1) or 2 (ln det, Tr);
 // on a non-positive pivot *status becomes `code` (if still 0).  Mode 2 reads
 // Wq = -V^-1 and Vq = V of the matrix's q and ldv = ln det V.
@@ -556,6 +557,11 @@ __device__ __forceinline__ void chol_one(int N, double* __restrict__ A, int mode
           if constexpr (C) v.im /= dd;
           x[c] = v;
           st_elem<C>(A, (long)i * N + kb + c, v);
+          // mode 2: the float-float copy of L_{i,kb+c} for the trailing
+          // update, converted once here instead of once per tile that reads
+          // it; it goes to the free strict upper triangle (row kb + c, column
+          // i > kb + c), so a tile's operand rows are contiguous there
+          if (mode == 2) st_ff<C>(A, (long)(kb + c) * N + i, to_ff<C>(v));
         }
       }
     }
@@ -576,10 +582,11 @@ __device__ __forceinline__ void chol_one(int N, double* __restrict__ A, int mode
         int TI, TJ;
         tri_index(tt, TI, TJ);
         for (int idx = tid; idx < CB * CB; idx += 256) {
-          const int r = idx / CB, c = idx % CB;
+          const int r = idx % CB, c = idx / CB;
           const int ri = m0 + TI * CB + r, rj = m0 + TJ * CB + r;
-          F1[c][r] = to_ff<C>((ri < N && c < nb) ? ldm<C, CL>(A, (long)ri * N + kb + c) : zero_elem<C>());
-          F2[c][r] = to_ff<C>((rj < N && c < nb) ? conj_e<C>(ldm<C, CL>(A, (long)rj * N + kb + c)) : zero_elem<C>());
+          const long up = (long)(kb + c) * N;
+          F1[c][r] = (ri < N && c < nb) ? ld_ff<C>(A, up + ri) : FFE<C>{};
+          F2[c][r] = (rj < N && c < nb) ? conj_ff<C>(ld_ff<C>(A, up + rj)) : FFE<C>{};
         }
         __syncthreads();
         FFE<C> acc[2][2];
