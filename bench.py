@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--cap-gb", type=float, default=0.0,
                     help="periodic2d/slab: the context's HBM cap (bounds the workspace; profiling small cases)")
     ap.add_argument("--n-q", type=int, default=0, help="profiling only: restrict the job to its first n q-points")
+    ap.add_argument("--tail-case", action="store_true",
+                    help="profiling only: the job's q-points, N_aux and frequencies (the V side and log-det "
+                         "launches at full shape) with N_occ 4, N_virt 24 and, for slab, a 3x3x1 k-grid")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--q-shard", action="store_true",
                     help="periodic2d/slab: one job split over the ranks by q-blocks (strong scaling) instead of "
@@ -90,10 +93,14 @@ def parse():
     return ap.parse_args()
 
 
-def workload(n_q=0, name="periodic2d"):
+def workload(n_q=0, name="periodic2d", tail_case=False):
     from paper_2505_06021_gb300 import synth
 
-    p = synth.config2() if name == "slab" else synth.config1()
+    if tail_case:  # the job's q-points, N_aux and frequencies with a tiny C (profiling the tail)
+        p = (synth.config2(n_occ=4, n_virt=24, k_dims=(3, 3, 1)) if name == "slab" else
+             synth.config1(n_occ=4, n_virt=24))
+    else:
+        p = synth.config2() if name == "slab" else synth.config1()
     if n_q:
         g = p.grid
         g.pair_k, g.pair_kq, g.w_q = g.pair_k[:n_q], g.pair_kq[:n_q], g.w_q[:n_q]
@@ -101,7 +108,7 @@ def workload(n_q=0, name="periodic2d"):
     return p
 
 
-def config_of(p, prec, n_q_override, name="periodic2d"):
+def config_of(p, prec, n_q_override, name="periodic2d", tail_case=False):
     if name == "slab":
         desc = ("slab-dual-c128: slab dual k-grid, complex128, coarse 3x3x1 q-grid without Gamma + 4 near-Gamma "
                 "points, dense 6x6x1 K_reg (12 q x 36 k pairs), N_aux=%d, N_occ=%d, N_virt=%d, %d imaginary "
@@ -110,7 +117,9 @@ def config_of(p, prec, n_q_override, name="periodic2d"):
         desc = ("periodic2d-c128: 2-D periodic, complex128, 4x4x1 k and q grids (16 q x 16 k pairs), "
                 "N_aux=%d, N_occ=%d, N_virt=%d, %d imaginary frequencies" % (p.n_aux, p.n_occ, p.n_virt, p.n_w))
     return {
-        "workload": desc + ("" if not n_q_override else " [first %d q only: profiling case]" % n_q_override),
+        "workload": desc + ("" if not n_q_override else " [first %d q only: profiling case]" % n_q_override) +
+                    (" [tail profiling case: N_occ %d, N_virt %d, %d k per q]" % (p.n_occ, p.n_virt, p.n_k)
+                     if tail_case else ""),
         "n_q": p.n_q, "n_k": p.n_k, "n_aux": p.n_aux, "n_occ": p.n_occ, "n_virt": p.n_virt, "n_w": p.n_w,
         "chi0_prec": prec,
         "l2": "inputs larger than L2 (C alone is %.1f GB per job vs 129 MB L2)" % (p.c_bytes() / 1e9),
@@ -454,7 +463,7 @@ def run_qshard(args):
         prec = "mixed" if rpa_mixed_available() else "fp64"
     pc = rpa.PREC_MIXED if prec == "mixed" else rpa.PREC_FP64
     name = args.workload
-    p = workload(args.n_q, name)
+    p = workload(args.n_q, name, args.tail_case)
     qs = list(shard.q_blocks(p.n_q, world)[rank])
     dev = "cuda:%d" % local
     t_gen = time.perf_counter()
@@ -496,8 +505,9 @@ def run_qshard(args):
     roof["note_qshard"] = "rank 0's chi0 launches (its own q-block)"
     if rank != 0:
         return
-    cfg = dict(config_of(p, prec, args.n_q, name), parallelism="one job q-sharded over %d ranks (strong scaling; "
-               "one all-reduce of the n_q x n_w integrand table per job)" % world)
+    cfg = dict(config_of(p, prec, args.n_q, name, args.tail_case),
+               parallelism="one job q-sharded over %d ranks (strong scaling; one all-reduce of the n_q x n_w "
+                           "integrand table per job)" % world)
     if prec == "mixed":
         cfg.update(chi0_slices=args.slices or 4,
                    chi0_freq=["auto", "per-frequency", "frequency-batched"][args.chi0_freq])
@@ -529,7 +539,7 @@ def run_ours(args):
         prec = "mixed" if rpa_mixed_available() else "fp64"
     pc = rpa.PREC_MIXED if prec == "mixed" else rpa.PREC_FP64
     name = args.workload
-    p = workload(args.n_q, name)
+    p = workload(args.n_q, name, args.tail_case)
     dev = "cuda:%d" % local
     # end-to-end inputs: pinned host copies of the whole job (generated once;
     # the device-resident job is copied from them)
@@ -590,7 +600,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "bf16-slices->f64",
             "data": "synthetic (seeded, shapes of the paper's periodic workloads; no public data)",
-            "config": dict(config_of(p, prec, args.n_q, name),
+            "config": dict(config_of(p, prec, args.n_q, name, args.tail_case),
                            **({"chi0_slices": args.slices or 4, "chi0_freq": ["auto", "per-frequency",
                                                                                "frequency-batched"][args.chi0_freq]}
                               if prec == "mixed" else {})),

@@ -290,7 +290,7 @@ bool freq_plan_build(const rpa_job* j, const double* eo, const double* ev, int m
   if (!delta_range(j, eo, ev, lo, hi)) return false;
   const std::vector<double> evs = sorted_virt(j, ev);
   const double total = (double)j->n_q * j->n_k * j->n_occ * j->n_virt;
-  const double ratios[] = {1.3, 1.5, 1.75, 2.1, 3.0};
+  const double ratios[] = {1.1, 1.15, 1.2, 1.25, 1.3, 1.5, 1.75, 2.1, 3.0};
   double best = std::numeric_limits<double>::infinity();
   for (double rho : ratios) {
     FreqPlan c;
