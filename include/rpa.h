@@ -180,10 +180,12 @@ rpa_status rpa_job_validate(const rpa_job *job, char *msg, size_t msg_len);
  * dense check grid), so chi0 needs rank[b] contractions over bin b instead of
  * n_w: chi0(w) = sum_b sum_r coef[b][r][w] X_{b,r}, X_{b,r} the contraction of
  * bin b's transitions at omega_{skel[b][r]}.  mode: 0 automatic (n_bins = 0
- * when the plan saves no work), 2 always.  Outputs (any may be NULL):
- * edges [16], rank [16], err [16], skel [16][n_w] (-1 past rank[b]), coef
- * [16][n_w][n_w] (row r of bin b), *work_ratio = modelled sum_b rank[b] K_b /
- * (n_w K).  RPA_E_INVAL for an invalid job or mem != RPA_MEM_HOST. */
+ * when the plan saves no work), 2 always.  Outputs (any may be NULL), with
+ * B = RPA_FREQ_MAX_BINS: edges [B], rank [B], err [B], skel [B][n_w] (-1 past
+ * rank[b]), coef [B][n_w][n_w] (row r of bin b), *work_ratio = modelled
+ * sum_b rank[b] K_b / (n_w K).  RPA_E_INVAL for an invalid job or
+ * mem != RPA_MEM_HOST. */
+#define RPA_FREQ_MAX_BINS 32
 rpa_status rpa_freq_plan(const rpa_job *job, int mode, int *n_bins, double *edges, int *rank, int *skel,
                          double *coef, double *err, double *work_ratio);
 

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "lib", "librpa.so")
 RPA_OK, RPA_E_INVAL, RPA_E_NOMEM, RPA_E_CUDA, RPA_E_NOTPD, RPA_E_TIMEOUT, RPA_E_BUSY, RPA_E_NOTREADY = range(8)
 PREC_FP64, PREC_MIXED = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
+FREQ_MAX_BINS = 32  # RPA_FREQ_MAX_BINS: energy bins of the frequency-batched chi0 at most
 
 STATUS_NAMES = {0: "OK", 1: "INVAL", 2: "NOMEM", 3: "CUDA", 4: "NOTPD", 5: "TIMEOUT", 6: "BUSY", 7: "NOTREADY"}
 
@@ -220,11 +221,11 @@ class Job:
         factorisation of the split-precision chi0."""
         nb = ctypes.c_int()
         nw = self.s.n_w
-        edges = np.zeros(16)
-        rank = np.zeros(16, np.int32)
-        skel = np.zeros(16 * nw, np.int32)
-        coef = np.zeros(16 * nw * nw)
-        err = np.zeros(16)
+        edges = np.zeros(FREQ_MAX_BINS)
+        rank = np.zeros(FREQ_MAX_BINS, np.int32)
+        skel = np.zeros(FREQ_MAX_BINS * nw, np.int32)
+        coef = np.zeros(FREQ_MAX_BINS * nw * nw)
+        err = np.zeros(FREQ_MAX_BINS)
         wr = ctypes.c_double()
         ip = ctypes.POINTER(ctypes.c_int)
         st = load_library().rpa_freq_plan(ctypes.byref(self.s), int(mode), ctypes.byref(nb), _dptr(edges),
@@ -234,7 +235,7 @@ class Job:
             raise RpaError(st, "rpa_freq_plan failed")
         n = int(nb.value)
         return {"n_bins": n, "edges": edges[:max(0, n - 1)].copy(), "rank": rank[:n].copy(),
-                "skel": skel.reshape(16, nw)[:n].copy(), "coef": coef.reshape(16, nw, nw)[:n].copy(),
+                "skel": skel.reshape(FREQ_MAX_BINS, nw)[:n].copy(), "coef": coef.reshape(FREQ_MAX_BINS, nw, nw)[:n].copy(),
                 "err": err[:n].copy(), "work_ratio": float(wr.value)}
 
     def footprint(self) -> int:

@@ -656,13 +656,15 @@ rpa_status bin_job_build(rpa_ctx* ctx, Exec& ex, const rpa_job* j, BinJob& bj) {
     peo = eo.data();
     pev = ev.data();
   }
-  if (!freq_plan_build(j, peo, pev, ctx->chi0_freq, &bj.plan)) return RPA_OK;
-  const std::vector<double> evs = freq_sorted_virt(j, pev);
+  std::vector<int> counts;
+  if (!freq_plan_build(j, peo, pev, ctx->chi0_freq, &bj.plan, &counts)) return RPA_OK;
+  const size_t per_q = (size_t)j->n_k * j->n_occ * bj.plan.n_bins;
   std::vector<std::vector<int>> img(j->n_q);
   bj.qh.resize(j->n_q);
+  freq_parallel_q(j->n_q,
+                  [&](int q) { freq_bin_q(j, bj.plan, q, peo, nullptr, bj.qh[q], img[q], counts.data() + per_q * q); });
   size_t n_i = 0;
   for (int q = 0; q < j->n_q; ++q) {
-    freq_bin_q(j, bj.plan, q, peo, evs.data(), bj.qh[q], img[q]);
     n_i += (img[q].size() + 15) & ~(size_t)15;
     bj.Kt_max = std::max(bj.Kt_max, bj.qh[q].Kt);
     bj.np_max = std::max(bj.np_max, bj.qh[q].n_parts);

@@ -36,6 +36,7 @@
 
 #include <algorithm>
 #include <limits>
+#include <thread>
 #include <vector>
 
 #include "rpa_internal.h"
@@ -102,22 +103,23 @@ struct BinFit {
 };
 
 // Interpolative decomposition of the weights on [lo, hi] across the nodes.
-BinFit fit_bin(double lo, double hi, const double* omega, int n_w, double tol, double amp_max) {
+BinFit fit_bin(double lo, double hi, const double* omega, int n_w, double tol, double amp_max,
+               int n_check = N_CHECK) {
   BinFit f;
-  std::vector<double> x(N_FIT), xc(N_CHECK), s(n_w, 0.0);
+  std::vector<double> x(N_FIT), xc(n_check), s(n_w, 0.0);
   for (int i = 0; i < N_FIT; ++i)
     x[i] = 0.5 * (lo + hi) + 0.5 * (hi - lo) * cos(M_PI * (i + 0.5) / N_FIT);
-  for (int i = 0; i < N_CHECK; ++i) xc[i] = lo + (hi - lo) * (double)i / (N_CHECK - 1);
+  for (int i = 0; i < n_check; ++i) xc[i] = lo + (hi - lo) * (double)i / (n_check - 1);
   // column scale: the largest |d| of each node over the bin (check grid and fit points)
-  std::vector<double> Mc((size_t)N_CHECK * n_w);
-  for (int i = 0; i < N_CHECK; ++i)
+  std::vector<double> Mc((size_t)n_check * n_w);
+  for (int i = 0; i < n_check; ++i)
     for (int w = 0; w < n_w; ++w) {
       Mc[(size_t)i * n_w + w] = weight(xc[i], omega[w]);
       s[w] = std::max(s[w], fabs(Mc[(size_t)i * n_w + w]));
     }
   for (int w = 0; w < n_w; ++w)
     for (int i = 0; i < N_FIT; ++i) s[w] = std::max(s[w], fabs(weight(x[i], omega[w])));
-  for (int i = 0; i < N_CHECK; ++i)
+  for (int i = 0; i < n_check; ++i)
     for (int w = 0; w < n_w; ++w) Mc[(size_t)i * n_w + w] /= s[w];
   std::vector<double> A((size_t)N_FIT * n_w);
   for (int i = 0; i < N_FIT; ++i)
@@ -156,7 +158,7 @@ BinFit fit_bin(double lo, double hi, const double* omega, int n_w, double tol, d
     }
     if (amp > amp_max) return false;
     err = 0.0;
-    for (int i = 0; i < N_CHECK; ++i) {
+    for (int i = 0; i < n_check; ++i) {
       const double* m = &Mc[(size_t)i * n_w];
       for (int w = 0; w < n_w; ++w) {
         double v = m[w];
@@ -257,6 +259,21 @@ int count_ge(const double* evs, int n, double e_i, double edge) {
 
 }  // namespace
 
+void freq_parallel_q(int n_q, const std::function<void(int)>& fn) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nt = std::min<int>(n_q, (int)std::min(8u, hw));
+  if (nt <= 1) {
+    for (int q = 0; q < n_q; ++q) fn(q);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      for (int q = t; q < n_q; q += nt) fn(q);
+    });
+  for (auto& x : th) x.join();
+}
+
 int freq_bin_of(const FreqPlan& p, double D) {
   int b = 0;
   while (b < p.n_bins - 1 && D >= p.edges[b]) ++b;
@@ -281,7 +298,8 @@ void freq_counts(const rpa_job* j, const FreqPlan& p, int q, const double* eo, c
   }
 }
 
-bool freq_plan_build(const rpa_job* j, const double* eo, const double* ev, int mode, FreqPlan* out) {
+bool freq_plan_build(const rpa_job* j, const double* eo, const double* ev, int mode, FreqPlan* out,
+                     std::vector<int>* counts) {
   FreqPlan& P = *out;
   P = FreqPlan{};
   if (mode == 1 || j->n_w < 2 || j->n_w > 32) return false;
@@ -290,28 +308,41 @@ bool freq_plan_build(const rpa_job* j, const double* eo, const double* ev, int m
   if (!delta_range(j, eo, ev, lo, hi)) return false;
   const std::vector<double> evs = sorted_virt(j, ev);
   const double total = (double)j->n_q * j->n_k * j->n_occ * j->n_virt;
-  const double ratios[] = {1.1, 1.15, 1.2, 1.25, 1.3, 1.5, 1.75, 2.1, 3.0};
-  double best = std::numeric_limits<double>::infinity();
-  for (double rho : ratios) {
-    FreqPlan c;
-    int nb = std::max(1, (int)ceil(log(hi / lo) / log(rho) - 1e-9));
-    nb = std::min(nb, FREQ_MAX_BINS);
-    c.n_bins = nb;
+  auto bins_for = [&](double rho) {
+    return std::min(FREQ_MAX_BINS, std::max(1, (int)ceil(log(hi / lo) / log(rho) - 1e-9)));
+  };
+  auto bin_ends = [&](int nb, int b, double& blo, double& bhi) {
     const double step = pow(hi / lo, 1.0 / nb);
-    for (int b = 0; b + 1 < nb; ++b) c.edges[b] = lo * pow(step, b + 1);
-    // bin populations over the whole job
-    std::vector<double> kb(nb, 0.0);
-    std::vector<int> cnt((size_t)j->n_k * j->n_occ * nb);
-    for (int q = 0; q < j->n_q; ++q) {
-      freq_counts(j, c, q, eo, evs.data(), cnt.data());
-      for (size_t u = 0; u < cnt.size(); ++u) kb[u % nb] += cnt[u];
+    blo = b == 0 ? lo : lo * pow(step, b);
+    bhi = b == nb - 1 ? hi : lo * pow(step, b + 1);
+  };
+  // The whole plan for bin ratio rho: every bin fitted, the bins' populations
+  // counted over the job, the modelled work.
+  auto plan_full = [&](double rho) {
+    FreqPlan c;
+    const int nb = bins_for(rho);
+    c.n_bins = nb;
+    for (int b = 0; b + 1 < nb; ++b) {
+      double blo, bhi;
+      bin_ends(nb, b, blo, bhi);
+      c.edges[b] = bhi;
     }
+    // bin populations over the whole job (the per-q counts are kept for the
+    // device tables)
+    std::vector<double> kb(nb, 0.0);
+    const size_t per_q = (size_t)j->n_k * j->n_occ * nb;
+    std::vector<int> cnt(per_q * j->n_q);
+    freq_parallel_q(j->n_q, [&](int q) { freq_counts(j, c, q, eo, evs.data(), cnt.data() + per_q * q); });
+    for (size_t u = 0; u < cnt.size(); ++u) kb[u % nb] += cnt[u];
+    if (counts) *counts = std::move(cnt);
     double work = 0.0;
     c.rmax = 0;
     std::vector<BinFit> fits(nb);
     for (int b = 0; b < nb; ++b) {
-      const double blo = b == 0 ? lo : c.edges[b - 1];
-      const double bhi = b == nb - 1 ? hi : c.edges[b];
+      double blo, bhi;
+      bin_ends(nb, b, blo, bhi);
+      if (b > 0) blo = c.edges[b - 1];
+      if (b + 1 < nb) bhi = c.edges[b];
       fits[b] = fit_bin(blo, bhi, j->omega, j->n_w, FREQ_TOL, FREQ_AMP);
       c.rank[b] = fits[b].rank;
       c.err[b] = fits[b].err;
@@ -329,11 +360,30 @@ bool freq_plan_build(const rpa_job* j, const double* eo, const double* ev, int m
         for (int w = 0; w < j->n_w; ++w)
           c.coef[((size_t)b * c.rmax + r) * j->n_w + w] = fits[b].coef[(size_t)r * j->n_w + w];
       }
-    if (c.work_ratio < best) {
-      best = c.work_ratio;
-      P = c;
+    return c;
+  };
+  // Candidate ratios are screened by the mean rank of five sample bins
+  // (fitted against a coarse check grid) and the padding of their bin count,
+  // assuming equal populations; only the most promising is planned in full
+  // (the fits and the population counts of every candidate in full took
+  // ~60 ms on the slab job).
+  const double ratios[] = {1.08, 1.1, 1.12, 1.15, 1.2, 1.25, 1.3, 1.5, 1.75, 2.1, 3.0};
+  std::vector<std::pair<double, double>> est;  // (modelled work, rho)
+  for (double rho : ratios) {
+    const int nb = bins_for(rho);
+    double r = 0.0;
+    int ns = 0;
+    for (int b : {0, nb / 4, nb / 2, (3 * nb) / 4, nb - 1}) {
+      double blo, bhi;
+      bin_ends(nb, b, blo, bhi);
+      r += fit_bin(blo, bhi, j->omega, j->n_w, FREQ_TOL, FREQ_AMP, 101).rank;
+      ++ns;
     }
+    est.push_back({r / ns * (1.0 + 8.0 * j->n_q * nb / total), rho});
   }
+  std::stable_sort(est.begin(), est.end(),
+                   [](const std::pair<double, double>& a, const std::pair<double, double>& b) { return a.first < b.first; });
+  P = plan_full(est[0].second);
   P.dlo = lo;
   P.dhi = hi;
   if ((size_t)P.n_bins * P.rmax * j->n_w * sizeof(double) > 48 * 1024) {  // coefficients of the reduction
@@ -347,14 +397,18 @@ bool freq_plan_build(const rpa_job* j, const double* eo, const double* ev, int m
   return P.n_bins > 0;
 }
 
-std::vector<double> freq_sorted_virt(const rpa_job* j, const double* ev) { return sorted_virt(j, ev); }
 
 void freq_bin_q(const rpa_job* j, const FreqPlan& p, int q, const double* eo, const double* evs, BinQHost& h,
-                std::vector<int>& img) {
+                std::vector<int>& img, const int* counts) {
   const int nb = p.n_bins, tpk = j->is_complex ? 8 : 16;
   const long nrow = (long)j->n_k * j->n_occ;
-  std::vector<int> cnt((size_t)nrow * nb);
-  freq_counts(j, p, q, eo, evs, cnt.data());
+  std::vector<int> own;
+  if (!counts) {
+    own.resize((size_t)nrow * nb);
+    freq_counts(j, p, q, eo, evs, own.data());
+    counts = own.data();
+  }
+  const int* cnt = counts;
   long K[FREQ_MAX_BINS] = {};
   for (long r = 0; r < nrow; ++r)
     for (int b = 0; b < nb; ++b) K[b] += cnt[(size_t)r * nb + b];

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -194,7 +195,7 @@ size_t mixed_seq_workspace_bytes(const BatchGeom& g, int n_slices, size_t slice_
 // bin b the weight of every frequency node is a combination of the weights of
 // rank[b] skeleton nodes, d(D, w) ~= sum_r coef[b][r][w] d(D, w_skel[b][r]),
 // to FREQ_TOL of the bin's largest |d(., w)|.
-constexpr int FREQ_MAX_BINS = 16;
+constexpr int FREQ_MAX_BINS = 32;
 constexpr double FREQ_TOL = 1e-10;
 constexpr double FREQ_AMP = 16.0;
 struct FreqPlan {
@@ -211,8 +212,13 @@ struct FreqPlan {
 };
 // Builds the plan from host copies of the band energies; mode 0 automatic
 // (false when it saves no work), 1 off, 2 always.  Returns whether a plan is
-// to be used.
-bool freq_plan_build(const rpa_job* j, const double* eps_occ_h, const double* eps_virt_h, int mode, FreqPlan* out);
+// to be used.  With counts set it also returns every q's freq_counts for the
+// plan ([q][n_k n_occ][n_bins], the input of freq_bin_q).
+bool freq_plan_build(const rpa_job* j, const double* eps_occ_h, const double* eps_virt_h, int mode, FreqPlan* out,
+                     std::vector<int>* counts = nullptr);
+// fn(q) for q = 0..n_q-1 on up to 8 host threads (fn must not share state
+// between q).
+void freq_parallel_q(int n_q, const std::function<void(int)>& fn);
 // cnt[(jj n_occ + i) n_bins + b]: virtual states of row (k-pair jj, occupied
 // i) of q whose transition falls in bin b.  evs: virtual energies of every
 // k-point sorted ascending.
@@ -239,13 +245,12 @@ struct BinQHost {
   const int* dmeta_i = nullptr;
   const double* dmeta_d = nullptr;
 };
-// Fills h (except the meta pointers) and the int image of q.
+// Fills h (except the meta pointers) and the int image of q (from q's
+// freq_counts when given, else counting here).
 void freq_bin_q(const rpa_job* j, const FreqPlan& p, int q, const double* eo, const double* evs, BinQHost& h,
-                std::vector<int>& img);
+                std::vector<int>& img, const int* counts = nullptr);
 // The double image shared by all q (skeleton frequencies, coefficients).
 void freq_meta_d(const rpa_job* j, const FreqPlan& p, std::vector<double>& img);
-// Virtual energies of every k-point sorted ascending.
-std::vector<double> freq_sorted_virt(const rpa_job* j, const double* ev);
 
 // One q of a frequency-batched launch.
 struct MixedBinQ {

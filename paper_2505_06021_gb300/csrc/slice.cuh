@@ -207,7 +207,7 @@ __device__ __forceinline__ void slice_unit(const SliceArgs& a, long idx) {
 // bin: the digit planes of bin b go to S + aoff[b], blocked as
 //   [slot g - g0][I = P/128][K-block of the bin][plane][4 KB core-matrix block],
 // i.e. each bin is a weighted operand of its own over its K range.
-constexpr int SB_MAX_BINS = 16;
+constexpr int SB_MAX_BINS = 32;
 struct SliceBinArgs {
   int cplx, Npad, Kr, s, n_kb, nb, g0, rmax, Kt;
   const int* cfix;               // [Npad][Kr], positions in bin order
