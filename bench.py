@@ -342,7 +342,8 @@ class near_gpu:
 
 def traffic_for(kernel_key):
     """DRAM bytes per launch of `kernel_key` from the committed ncu summary,
-    valid only while the kernel source is unchanged (hash recorded)."""
+    valid only while the sources it names (the kernel, and the planner that
+    shapes its launches) are unchanged (hash recorded)."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "traffic.txt")
@@ -353,7 +354,9 @@ def traffic_for(kernel_key):
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if f.get("kernel") != kernel_key:
             continue
-        h = hashlib.sha256(open(os.path.join(src, f["source"]), "rb").read()).hexdigest()[:16]
+        # source: one file, or several joined by '+' (hash of their concatenation)
+        blob = b"".join(open(os.path.join(src, name), "rb").read() for name in f["source"].split("+"))
+        h = hashlib.sha256(blob).hexdigest()[:16]
         if h != f.get("sha"):
             return None
         return float(f["bytes_per_launch_full"])
