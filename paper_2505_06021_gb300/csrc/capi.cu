@@ -306,21 +306,27 @@ int choose_qb(const rpa_job* j, int n_slices, size_t cap, const BinJob* bj) {
   }
   while (qb > 1 && plan_layout(j, qb, n_slices, cap, true, 0, bj).total > cap) qb = (qb + 1) / 2;
   // host-resident inputs: at least four q-batches, so that the copies of one
-  // batch overlap the compute of the previous one; with the frequency-batched
+  // batch overlap the compute of the previous one.  With the frequency-batched
   // chi0, fewer q per batch while that keeps all skeletons in one round (the
-  // staging buffers and the chi0 workspace share the cap)
+  // staging buffers and the chi0 workspace share the cap), and one q per batch
+  // when its layout is not pipelined across q anyway: then every q is a launch
+  // sequence of its own, and the only copy nothing overlaps, the first
+  // batch's, is one q's.
   if (j->mem == RPA_MEM_HOST) {
     qb = std::min(qb, std::max(1, (j->n_q + 3) / 4));
     if (bj && bj->on && j->prec == RPA_PREC_MIXED) {
-      auto one_round = [&](int b) {
+      auto layout = [&](int b, int& slots, int& regions) {
         const Layout L = plan_layout(j, b, n_slices, cap, false, j->n_q, nullptr);
         const size_t budget = cap > L.total ? cap - L.total : 0;
         const BatchGeom g{j->is_complex, j->n_aux, j->n_occ, j->n_virt, j->n_occ * j->n_virt, j->n_k, j->n_w, 1};
-        int slots = 0;
-        binned_workspace_bytes(g, bj->plan, bj->Kt_max, bj->np_max, n_slices, budget, &slots);
-        return slots >= bj->plan.rmax;
+        binned_workspace_bytes(g, bj->plan, bj->Kt_max, bj->np_max, n_slices, budget, &slots, &regions);
       };
-      while (qb > 1 && !one_round(qb)) --qb;
+      int slots = 0, regions = 0;
+      for (; qb > 1; --qb) {
+        layout(qb, slots, regions);
+        if (slots >= bj->plan.rmax) break;
+      }
+      if (qb > 1 && regions < 2) qb = 1;
     }
   }
   return qb;
@@ -473,14 +479,23 @@ rpa_status stage_dtab(rpa_ctx* ctx, Exec* pex, const rpa_job* j, const Bufs& b, 
 // sandwich, Cholesky log-det.  V of the batch at Vdev[0..nq).
 // V(q) of nq q-points into slots lo.. of L (and of the inverse form's copy Vc).
 static rpa_status vside_copy(rpa_ctx* ctx, const rpa_job* j, const Bufs& b, int lo, int nq, const void* const* Vdev,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool staging = false) {
   const size_t es = j->is_complex ? 16 : 8;
   const size_t NN = (size_t)j->n_aux * j->n_aux;
+  // with host staging, kernel copies: they run on the compute stream while the
+  // copy engines are busy with the next batch's staging
+  uint64_t nl = 0;
   for (int qi = 0; qi < nq; ++qi) {
-    CK(cudaMemcpyAsync(b.L + (lo + qi) * NN * (es / 8), Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
-    if (b.Vc)
-      CK(cudaMemcpyAsync(b.Vc + (lo + qi) * NN * (es / 8), Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
+    double* dst[2] = {b.L + (lo + qi) * NN * (es / 8), b.Vc ? b.Vc + (lo + qi) * NN * (es / 8) : nullptr};
+    for (double* d : dst) {
+      if (!d) continue;
+      if (staging)
+        CK(launch_copy_d2d(d, Vdev[qi], es * NN, s, &nl));
+      else
+        CK(cudaMemcpyAsync(d, Vdev[qi], es * NN, cudaMemcpyDeviceToDevice, s));
+    }
   }
+  ctx->launches += nl;
   return RPA_OK;
 }
 
@@ -791,7 +806,7 @@ rpa_status energy_enqueue(rpa_ctx* ctx, Exec& ex, const rpa_job* job, size_t ws_
     if (rpa_status st = run_chi(ctx, &ex, job, b, q0, nq, eo, ev, s, b.chi + (size_t)lo * job->n_w * NN * (es / 8),
                                 ctx->n_slices, &bj))
       return st;
-    if (rpa_status st = vside_copy(ctx, job, b, lo, nq, vp.data() + q0, s)) return st;
+    if (rpa_status st = vside_copy(ctx, job, b, lo, nq, vp.data() + q0, s, host)) return st;
     // the tail once its batch of q is complete (chi, V of every q in place)
     if (q0 + nq == t0 + nt) {
       if (rpa_status st = vside_factor(ctx, &ex, job, b, t0, nt, s)) return st;

@@ -691,9 +691,10 @@ int bin_tc_params(const BinRegion& R, const uint16_t* A, const BinLayout& L, con
 }  // namespace
 
 size_t binned_workspace_bytes(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int n_slices,
-                              size_t budget, int* slots) {
+                              size_t budget, int* slots, int* regions) {
   const BinLayout L = bin_layout(g, p, Kt_max, n_parts_max, n_slices, budget, num_sms());
   if (slots) *slots = L.G;
+  if (regions) *regions = L.nreg;
   return L.total;
 }
 

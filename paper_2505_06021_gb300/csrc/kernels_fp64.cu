@@ -20,6 +20,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "fp64_elem.cuh"
@@ -1007,6 +1008,21 @@ cudaError_t launch_vinv(int cplx, int N, int n_q, const double* L, double* X, do
 cudaError_t launch_energy_reduce(int n_q, int n_w, const double* parts, const double* w_q, const double* zeta_w,
                                  double* eps, double* Ec, cudaStream_t s) {
   energy_kernel<<<1, 32, 0, s>>>(n_q, n_w, parts, w_q, zeta_w, eps, Ec);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) copy16_kernel(uint4* __restrict__ dst, const uint4* __restrict__ src, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+cudaError_t launch_copy_d2d(void* dst, const void* src, size_t bytes, cudaStream_t s, uint64_t* n_launch) {
+  if (bytes == 0) return cudaSuccess;
+  if (bytes % 16 || (uintptr_t)dst % 16 || (uintptr_t)src % 16)
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+  const long n = (long)(bytes / 16);
+  const unsigned blocks = (unsigned)std::min<long>((n + 255) / 256, (long)num_sms_fp64() * 8);
+  copy16_kernel<<<blocks, 256, 0, s>>>((uint4*)dst, (const uint4*)src, n);
+  if (n_launch) ++*n_launch;
   return cudaGetLastError();
 }
 

@@ -147,6 +147,12 @@ cudaError_t launch_proj_finish(int cplx, const ProjPtrs& P, int n_mat, int N, in
 cudaError_t launch_sandwich(int cplx, int N, int n_batch, int n_w, const double* chi, const double* L, double* T,
                             double* Y, cudaStream_t s);
 
+// Device-to-device copy by a kernel (a cudaMemcpyAsync when the pointers are
+// not 16-byte aligned or the size is not a multiple of 16): for copies on a
+// compute stream while the copy engines are busy with a job's host staging (a
+// cudaMemcpyAsync there would wait behind those copies).
+cudaError_t launch_copy_d2d(void* dst, const void* src, size_t bytes, cudaStream_t s, uint64_t* n_launch = nullptr);
+
 // E_c and the eps table from parts[q][w][2] = (ln det, Tr Pi):
 // eps[q][w] = ln det + Tr, e_w = sum_q w_q eps[q][w], E = (1/2pi) sum_w zeta_w e_w.
 cudaError_t launch_energy_reduce(int n_q, int n_w, const double* parts, const double* w_q, const double* zeta_w,
@@ -266,9 +272,10 @@ struct MixedBinQ {
   int* status;                 // device status word (plan mismatch)
 };
 // Workspace of the frequency-batched chi0 within `budget` bytes (pipelined
-// with two q regions and two weighted-operand buffers when they fit).
+// with two q regions and two weighted-operand buffers when they fit); slots:
+// skeleton slots per round, regions: 2 when pipelined, else 1.
 size_t binned_workspace_bytes(const BatchGeom& g, const FreqPlan& p, int Kt_max, int n_parts_max, int n_slices,
-                              size_t budget, int* slots = nullptr);
+                              size_t budget, int* slots = nullptr, int* regions = nullptr);
 cudaError_t launch_chi0_binned(const MixedBinQ* qs, int n, const FreqPlan& p, int n_slices, void* work,
                                size_t work_bytes, int* status, uint64_t* n_launch, cudaStream_t s,
                                const LaunchHook* hook);
